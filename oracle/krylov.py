@@ -1,0 +1,137 @@
+"""Outer Stokes solve (Section 2.2): block-triangular preconditioner and FGMRES.
+
+P = [[A, B^T], [0, -S]] (eq. stokes_precond); applying P^-1 to r = [r_u; r_p]:
+    z_p = -S_hat^-1 r_p,   z_u = A_hat^-1 (r_u - B^T z_p),
+with A_hat^-1 one GMG V-cycle and S_hat^-1 a Jacobi-Chebyshev iteration on the
+1/mu-weighted pressure mass matrix M_p (Section 2.2.2). Because S_hat^-1 is an
+inner iteration the outer method is flexible GMRES, restart 50 (Section 2.2.2,
+Section 3.5). Readings: S_hat^-1 is degree 5 (5 updates, zero initial guess)
+on the fixed interval [1/8, 27/8] that bounds the spectrum of diag(M_p)^-1 M_p
+for trilinear hexahedra (A. J. Wathen, IMA J. Numer. Anal. 7 (1987), element
+eigenvalue bound: 1D element mass [[2,1],[1,2]] h/6 scaled by its diagonal has
+eigenvalues 1/2 and 3/2; the tensor product gives [1/8, 27/8]).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .gmg import chebyshev_smooth
+
+
+class StokesPreconditioner:
+    def __init__(self, ops_fine, gmg, schur_degree=5, exact_A=None, exact_S=None):
+        self.ops = ops_fine
+        self.gmg = gmg
+        self.schur_degree = schur_degree
+        self.Mp_dinv = 1.0 / ops_fine.diag_Mp()
+        self.exact_A = exact_A        # optional callables replacing the approximations
+        self.exact_S = exact_S
+
+    def schur_inverse(self, r_p):
+        """S_hat^-1 r_p: Jacobi-Chebyshev on M_p, interval [1/8, 27/8], zero guess."""
+        if self.exact_S is not None:
+            return self.exact_S(r_p)
+        return chebyshev_smooth(self.ops.apply_Mp, self.Mp_dinv, r_p, None,
+                                self.schur_degree, 1.0 / 8.0, 27.0 / 8.0, True)
+
+    def velocity_inverse(self, t):
+        if self.exact_A is not None:
+            return self.exact_A(t)
+        return self.gmg.vcycle(t)
+
+    def apply(self, r):
+        n_u = self.ops.mesh.n_u
+        r_u, r_p = r[:n_u], r[n_u:]
+        z_p = -self.schur_inverse(r_p)
+        t = r_u - self.ops.apply_BT(z_p)
+        z_u = self.velocity_inverse(t)
+        return np.concatenate([z_u, z_p])
+
+
+def fgmres(apply_K, apply_Pinv, b, rtol=1e-8, restart=50, max_it=1000, x0=None):
+    """Right-preconditioned flexible GMRES (Y. Saad, SIAM J. Sci. Comput. 14 (1993);
+    Iterative Methods, Alg. 9.6) with modified Gram-Schmidt and Givens rotations.
+    Stops when the recurrence residual |g_{j+1}| <= rtol * ||b||.
+    Returns (x, iterations, list of relative residual estimates)."""
+    n = b.shape[0]
+    x = np.zeros(n) if x0 is None else x0.copy()
+    bnorm = np.linalg.norm(b)
+    history = []
+    its = 0
+    if bnorm == 0.0:
+        return x, 0, [0.0]
+    while its < max_it:
+        r = b - apply_K(x)
+        beta = np.linalg.norm(r)
+        history.append(beta / bnorm)
+        if beta <= rtol * bnorm:
+            break
+        m = restart
+        V = np.zeros((m + 1, n))
+        Z = np.zeros((m, n))
+        H = np.zeros((m + 1, m))
+        cs = np.zeros(m)
+        sn = np.zeros(m)
+        g = np.zeros(m + 1)
+        g[0] = beta
+        V[0] = r / beta
+        k = 0
+        for j in range(m):
+            Z[j] = apply_Pinv(V[j])
+            w = apply_K(Z[j])
+            for i in range(j + 1):
+                H[i, j] = w @ V[i]
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            if H[j + 1, j] != 0.0:
+                V[j + 1] = w / H[j + 1, j]
+            for i in range(j):
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            denom = np.hypot(H[j, j], H[j + 1, j])
+            cs[j] = H[j, j] / denom
+            sn[j] = H[j + 1, j] / denom
+            H[j, j] = denom
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            its += 1
+            k = j + 1
+            history.append(abs(g[j + 1]) / bnorm)
+            if abs(g[j + 1]) <= rtol * bnorm or its >= max_it:
+                break
+        y = np.linalg.solve(np.triu(H[:k, :k]), g[:k])
+        x = x + Z[:k].T @ y
+        if abs(g[k]) <= rtol * bnorm:
+            break
+    return x, its, history
+
+
+def zero_mean_pressure(ops, up):
+    """Subtract the integral mean of the pressure (the constant pressure is the
+    null space of the all-Dirichlet Stokes operator)."""
+    n_u = ops.mesh.n_u
+    w = ops.pressure_weights()
+    out = up.copy()
+    out[n_u:] -= (w @ up[n_u:]) / w.sum()
+    return out
+
+
+def dense_stokes_solve(ops, F):
+    """Direct solve of [[A_c, B^T], [B, 0]] [u; p] = [F; 0] with the pressure mean
+    fixed to zero by a bordering row (small meshes only)."""
+    A = ops.csr_A().toarray()
+    B = ops.csr_B().toarray()
+    w = ops.pressure_weights()
+    n_u, n_p = A.shape[0], B.shape[0]
+    K = np.zeros((n_u + n_p + 1, n_u + n_p + 1))
+    K[:n_u, :n_u] = A
+    K[:n_u, n_u:n_u + n_p] = B.T
+    K[n_u:n_u + n_p, :n_u] = B
+    K[n_u + n_p, n_u:n_u + n_p] = w
+    K[n_u:n_u + n_p, n_u + n_p] = w
+    rhs = np.zeros(n_u + n_p + 1)
+    rhs[:n_u] = F
+    sol = np.linalg.solve(K, rhs)
+    return sol[:n_u + n_p]

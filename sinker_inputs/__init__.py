@@ -1,0 +1,123 @@
+"""Seeded synthetic inputs for the sinker benchmark (Section 3.2).
+
+This module is shared by the CPU oracle, the tests and the benchmark. It holds
+no arithmetic of the method itself: only a counter-based random stream, the
+sinker parameters drawn from it, and the workload configurations.
+
+The random stream is splitmix64 (G. Steele, D. Lea, C. Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014): output i (0-based) of the
+stream with seed s is mix(s + (i + 1) * 0x9E3779B97F4A7C15 mod 2^64), with
+mix the published 64-bit finaliser. A uniform double in [0, 1) is the top 53
+bits times 2^-53. The CUDA library implements the same definition to draw the
+start vector of its Lanczos eigenvalue estimate.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, count: int, offset: int = 0) -> np.ndarray:
+    """Outputs offset .. offset+count-1 of the splitmix64 stream with `seed`."""
+    with np.errstate(over="ignore"):
+        i = np.arange(offset + 1, offset + count + 1, dtype=np.uint64)
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + i * _GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed: int, count: int, offset: int = 0) -> np.ndarray:
+    """Doubles in [0, 1): top 53 bits of splitmix64 outputs times 2^-53."""
+    z = splitmix64(seed, count, offset)
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def uniform(seed: int, count: int, lo: float = -1.0, hi: float = 1.0, offset: int = 0) -> np.ndarray:
+    return lo + (hi - lo) * uniform01(seed, count, offset)
+
+
+def lanczos_seed(level: int) -> int:
+    """Seed of the Lanczos start vector on multigrid level `level` (0 = coarsest)."""
+    return 1907_000 + level
+
+
+@dataclass
+class SinkerProblem:
+    """Sinker benchmark parameters (Section 3.2).
+
+    mu(x) = X(x) mu_min + (1 - X(x)) mu_max with
+    X(x) = prod_i [1 - exp(-delta max(0, |c_i - x| - omega/2)^2)],
+    f(x) = (0, 0, beta (X(x) - 1)), homogeneous Dirichlet velocity on the unit cube.
+    """
+    n: int                      # cells per axis on the finest level
+    n_levels: int               # multigrid levels; coarsest has n / 2^(n_levels-1) cells per axis
+    centres: np.ndarray         # (n_sinkers, 3)
+    mu_min: float
+    mu_max: float
+    delta: float = 200.0
+    omega: float = 0.1
+    beta: float = 10.0
+    name: str = ""
+    seed: int = 0
+
+    @property
+    def n_sinkers(self) -> int:
+        return int(self.centres.shape[0])
+
+    @property
+    def coarse_n(self) -> int:
+        return self.n >> (self.n_levels - 1)
+
+
+def sinker_centres(seed: int, n_sinkers: int) -> np.ndarray:
+    """Sinker centres i.i.d. uniform in [0.2, 0.8]^3 from the seeded stream."""
+    u = uniform01(seed, 3 * n_sinkers)
+    return (0.2 + 0.6 * u).reshape(n_sinkers, 3)
+
+
+def dr_problem(n: int, n_levels: int, n_sinkers: int, dr: float, seed: int, name: str = "") -> SinkerProblem:
+    """Sinker problem with viscosity ratio DR: mu_min = DR^-1/2, mu_max = DR^1/2."""
+    return SinkerProblem(n=n, n_levels=n_levels, centres=sinker_centres(seed, n_sinkers),
+                         mu_min=dr ** -0.5, mu_max=dr ** 0.5, name=name, seed=seed)
+
+
+def workload(name: str) -> SinkerProblem:
+    """The named synthetic workloads.
+
+    cube8   : 8^3 Q2-Q1 cells, 4 levels, 1 sinker, mu_min = 1, mu_max = 100 (14,739 velocity + 729 pressure DoFs)
+    cube64  : 64^3 cells, 7 levels, 8 sinkers, viscosity ratio 1e4 (~6.4M velocity DoFs)
+    cube128 : 128^3 cells, 8 levels, 16 sinkers, viscosity ratio 1e6 (~51M velocity DoFs)
+    Smaller parity cases: cube16 (16^3, 5 levels, 4 sinkers, DR 1e4), cube32 (32^3, 6 levels, 8 sinkers, DR 1e4).
+    Sinker centres come from splitmix64 with seed 1907 + k (k = 1, 2, 3 for cube8, cube64, cube128).
+    """
+    if name == "cube8":
+        return SinkerProblem(n=8, n_levels=4, centres=sinker_centres(1908, 1), mu_min=1.0, mu_max=100.0,
+                             name=name, seed=1908)
+    if name == "cube64":
+        return dr_problem(64, 7, 8, 1e4, 1909, name)
+    if name == "cube128":
+        return dr_problem(128, 8, 16, 1e6, 1910, name)
+    if name == "cube16":
+        return dr_problem(16, 5, 4, 1e4, 1911, name)
+    if name == "cube32":
+        return dr_problem(32, 6, 8, 1e4, 1912, name)
+    if name == "cube4":
+        return dr_problem(4, 3, 1, 1e2, 1913, name)
+    if name == "cube2":
+        return dr_problem(2, 2, 1, 1e2, 1914, name)
+    raise KeyError(name)
+
+
+def n_velocity(n: int) -> int:
+    return 3 * (2 * n + 1) ** 3
+
+
+def n_pressure(n: int) -> int:
+    return (n + 1) ** 3

@@ -1,0 +1,427 @@
+"""Pins of the CPU oracle against closed forms, invariants and published values.
+
+Each test fixes one part of the oracle by something other than the oracle
+itself, chosen so that a dropped term, wrong sign, transposed operand or wrong
+index fails at least one of them.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as sla
+
+import sinker_inputs as si
+from oracle import fe, gmg, krylov, mesh, operators, sinker
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, v = line.split(":", 1) if ":" in line else line.split(None, 1)
+            out[k.strip()] = v.split()
+    return out
+
+
+# ---------------------------------------------------------------- generator
+def test_splitmix64_published_values():
+    g = _golden("splitmix64.txt")
+    assert [int(x) for x in si.splitmix64(1234567, 5)] == [int(x) for x in g["seed 1234567"]]
+    assert [int(x) for x in si.splitmix64(0, 3)] == [int(x) for x in g["seed 0"]]
+    u = si.uniform01(7, 10000)
+    assert u.min() >= 0.0 and u.max() < 1.0 and abs(u.mean() - 0.5) < 0.01
+
+
+# ---------------------------------------------------------------- 1D bases, quadrature
+def test_gauss3_exactness_and_first_error_term():
+    g, w = fe.gauss3()
+    for k in range(6):
+        assert abs(w @ g ** k - 1.0 / (k + 1)) < 1e-15
+    # Gauss-Legendre error for n = 3 on [0,1]: (3!)^4 / (7 (6!)^3) f^(6) = 720/2800/720 -> 1/2800
+    assert abs((1.0 / 7.0 - w @ g ** 6) - 1.0 / 2800.0) < 1e-15
+
+
+def test_q2_lagrange_properties():
+    x = np.linspace(0, 1, 11)
+    v = fe.q2_1d(x)
+    d = fe.q2_1d_deriv(x)
+    assert np.allclose(fe.q2_1d(fe.Q2_NODES_1D), np.eye(3), atol=1e-15)
+    assert np.allclose(v.sum(1), 1.0)
+    assert np.allclose(d.sum(1), 0.0)
+    # reproduces x^2 and its derivative 2x
+    assert np.allclose(v @ fe.Q2_NODES_1D ** 2, x ** 2)
+    assert np.allclose(d @ fe.Q2_NODES_1D ** 2, 2 * x)
+    # closed forms: l0 = 2x^2 - 3x + 1, l1 = 4x - 4x^2, l2 = 2x^2 - x
+    assert np.allclose(v, np.stack([2 * x ** 2 - 3 * x + 1, 4 * x - 4 * x ** 2, 2 * x ** 2 - x], 1))
+    assert np.allclose(d, np.stack([4 * x - 3, 4 - 8 * x, 4 * x - 1], 1))
+
+
+# ---------------------------------------------------------------- element matrices
+def _nodal(h, field):
+    """Element nodal vector (c*27 + a) of a vector field on [0,h]^3."""
+    pts = np.array([[i / 2, j / 2, k / 2] for k in range(3) for j in range(3) for i in range(3)]) * h
+    vals = np.array([field(p) for p in pts])          # (27, 3)
+    return np.concatenate([vals[:, c] for c in range(3)])
+
+
+def test_element_A_energies_closed_form():
+    h, mu = 0.3, 2.5
+    A = fe.element_A(h, mu)
+    vol = h ** 3
+    # int 2 mu eps:eps over the cell
+    cases = [
+        (lambda p: (p[0], 0, 0), 2 * mu * vol),          # eps_xx = 1
+        (lambda p: (p[1], 0, 0), mu * vol),              # eps_xy = eps_yx = 1/2
+        (lambda p: (p[1], p[0], 0), 4 * mu * vol),       # eps_xy = 1
+        (lambda p: (p[1], -p[0], 0), 0.0),               # rotation
+        (lambda p: (0, 0, p[2]), 2 * mu * vol),
+        (lambda p: (p[2], 0, p[0]), 4 * mu * vol),
+    ]
+    for f, e in cases:
+        u = _nodal(h, f)
+        assert abs(u @ A @ u - e) < 1e-12 * max(1.0, e), (e, u @ A @ u)
+
+
+def test_element_A_symmetric_rank_and_rigid_modes():
+    h = 0.25
+    A = fe.element_A(h, 1.0)
+    assert np.abs(A - A.T).max() < 1e-14
+    ev = np.linalg.eigvalsh(A)
+    assert ev.min() > -1e-12
+    assert int((ev > 1e-10 * ev.max()).sum()) == 75
+    modes = [lambda p: (1, 0, 0), lambda p: (0, 1, 0), lambda p: (0, 0, 1),
+             lambda p: (-p[1], p[0], 0), lambda p: (0, -p[2], p[1]), lambda p: (p[2], 0, -p[0])]
+    for f in modes:
+        assert np.abs(A @ _nodal(h, f)).max() < 1e-13
+
+
+def test_element_B_and_Mp_closed_forms():
+    h = 0.5
+    B = fe.element_B(h)
+    # div u = 1 for u = (x, 0, 0): (B u)_l = -int psi_l = -h^3 / 8
+    assert np.allclose(B @ _nodal(h, lambda p: (p[0], 0, 0)), -h ** 3 / 8)
+    # u = (0, y, z): div = 2
+    assert np.allclose(B @ _nodal(h, lambda p: (0, p[1], p[2])), -2 * h ** 3 / 8)
+    # solenoidal u = (y, -x, 0): zero
+    assert np.abs(B @ _nodal(h, lambda p: (p[1], -p[0], 0))).max() < 1e-15
+    M = fe.element_Mp(h, 1.0 / 3.0)
+    assert abs(M.sum() - h ** 3 / 3.0) < 1e-15
+    px = np.array([(i % 2) * h for i in range(8)])       # p = x at the vertices
+    assert abs(px @ fe.element_Mp(h, 1.0) @ px - h ** 5 / 3.0) < 1e-15
+
+
+# ---------------------------------------------------------------- global operators
+def _int_phi_1d(M):
+    """int of the global 1D Q2 basis function of each node on [0,1] with spacing h/2:
+    boundary vertex h/6, interior vertex h/3, midpoint 2h/3."""
+    n = (M - 1) // 2
+    h = 1.0 / n
+    w = np.where(np.arange(M) % 2 == 1, 2 * h / 3, h / 3)
+    w[0] = w[-1] = h / 6
+    return w
+
+
+def test_global_A_reproduces_quadratic_fields():
+    """For constant mu and quadratic u, -div(2 mu eps(u)) = -mu(lap u + grad div u) = c is
+    constant, so (A u)_i = c_comp * int phi_node for DoFs whose basis vanishes on the boundary."""
+    n, mu = 4, 1.7
+    m = mesh.Mesh(n)
+    ops = operators.Operators(m, np.full(m.n_cells, mu))
+    X = m.node_coords()
+    x, y, z = X[:, 0], X[:, 1], X[:, 2]
+    a, b, d, e, f = 1.0, 2.0, 3.0, 5.0, 7.0
+    u = np.concatenate([a * x ** 2 + b * y ** 2 + e * y * z, x * z, d * z ** 2 + f * x * y])
+    c = -mu * np.array([4 * a + 2 * b, 0.0, 4 * d])
+    w1 = _int_phi_1d(m.M)
+    intphi = np.einsum("k,j,i->kji", w1, w1, w1).ravel()
+    y_ = ops.apply_A_unconstrained(u)
+    inner = ~m.boundary_node
+    for comp in range(3):
+        got = y_[comp * m.n_nodes:(comp + 1) * m.n_nodes][inner]
+        assert np.allclose(got, c[comp] * intphi[inner], rtol=1e-12, atol=1e-12)
+
+
+def test_global_A_rigid_modes_and_constraints():
+    n = 3
+    m = mesh.Mesh(n)
+    mu = 1.0 + si.uniform01(5, m.n_cells)
+    ops = operators.Operators(m, mu)
+    X = m.node_coords()
+    for om in [(1, 0, 0), (0, 1, 0), (0, 0, 1)]:
+        r = np.cross(np.array(om, float)[None, :], X)
+        v = np.concatenate([r[:, 0], r[:, 1], r[:, 2]]) + 0.3
+        assert np.abs(ops.apply_A_unconstrained(v)).max() < 1e-12
+    A = ops.csr_A()
+    assert abs(A - A.T).max() < 1e-14
+    xr = si.uniform(3, m.n_u)
+    assert np.allclose(A @ xr, ops.apply_A(xr), atol=1e-13)
+    y = ops.apply_A(xr)
+    assert np.array_equal(y[m.dirichlet], xr[m.dirichlet])
+
+
+def test_BT_of_linear_pressure_and_adjointness():
+    """(B^T p)_(c,node) = -int d_c phi p = int phi d_c p for interior nodes; for p = x that is
+    int phi on the x component and 0 elsewhere. And (B u, p) = (u, B^T p)."""
+    n = 4
+    m = mesh.Mesh(n)
+    ops = operators.Operators(m, np.ones(m.n_cells))
+    V = m.vertex_coords()
+    p = V[:, 0].copy()
+    g = ops.apply_BT(p)
+    w1 = _int_phi_1d(m.M)
+    intphi = np.einsum("k,j,i->kji", w1, w1, w1).ravel()
+    inner = ~m.boundary_node
+    assert np.allclose(g[:m.n_nodes][inner], intphi[inner], atol=1e-14)
+    assert np.abs(g[m.n_nodes:]).max() < 1e-14
+    u = si.uniform(11, m.n_u) * (~m.dirichlet)
+    q = si.uniform(12, m.n_p)
+    assert abs(ops.apply_B(u) @ q - u @ ops.apply_BT(q)) < 1e-13
+
+
+def test_Mp_integrals_and_wathen_bound():
+    n = 3
+    m = mesh.Mesh(n)
+    mu = 0.5 + si.uniform01(21, m.n_cells) * 10
+    ops = operators.Operators(m, mu)
+    one = np.ones(m.n_p)
+    assert abs(one @ ops.apply_Mp(one) - np.sum(m.h ** 3 / mu)) < 1e-13
+    M = np.column_stack([ops.apply_Mp(e) for e in np.eye(m.n_p)])
+    D = ops.diag_Mp()
+    ev = np.linalg.eigvals(M / D[:, None]).real
+    assert ev.min() >= 1 / 8 - 1e-12 and ev.max() <= 27 / 8 + 1e-12
+    assert abs(ops.pressure_weights().sum() - 1.0) < 1e-14
+
+
+def test_rhs_of_constant_forcing():
+    n = 4
+    m = mesh.Mesh(n)
+    fq = np.zeros((m.n_cells, 27, 3))
+    fq[:, :, 2] = 1.0
+    F = operators.assemble_rhs(m, fq)
+    w1 = _int_phi_1d(m.M)
+    intphi = np.einsum("k,j,i->kji", w1, w1, w1).ravel()
+    inner = ~m.boundary_node
+    assert np.allclose(F[2 * m.n_nodes:][inner], intphi[inner], atol=1e-15)
+    assert np.abs(F[:2 * m.n_nodes]).max() == 0.0
+    assert np.all(F[m.dirichlet] == 0.0)
+
+
+def test_paper_sparsity_example_402_dofs():
+    """Section 2.2.1 figure: 2x2x2 Q2-Q1 has 375 + 27 = 402 DoFs; full coupling has ~3x
+    the velocity entries of the partial coupling (one diagonal block per component)."""
+    g = _golden("stokes_2x2x2_dofs.txt")
+    m = mesh.Mesh(int(g["n_cells_per_axis"][0]))
+    assert m.n_u == int(g["velocity_dofs"][0]) and m.n_p == int(g["pressure_dofs"][0])
+    assert m.n_u + m.n_p == int(g["total_dofs"][0])
+    ops = operators.Operators(m, np.ones(m.n_cells))
+    rows = np.repeat(m.cell_dofs, 81, axis=1).ravel()
+    cols = np.tile(m.cell_dofs, (1, 81)).ravel()
+    pattern = sp.coo_matrix((np.ones(rows.size), (rows, cols)), shape=(m.n_u, m.n_u)).tocsr()
+    full = pattern.nnz
+    comp = lambda i: i // m.n_nodes
+    r, c = pattern.nonzero()
+    partial = int(np.sum(comp(r) == comp(c)))
+    assert full == int(g["full_over_partial_entries"][0]) * partial
+
+
+# ---------------------------------------------------------------- sinker coefficients
+def test_sinker_coefficient_limits_and_averaging():
+    prob = si.SinkerProblem(n=4, n_levels=1, centres=np.array([[0.5, 0.5, 0.5]]), mu_min=0.01, mu_max=100.0)
+    c = np.array([[0.5, 0.5, 0.5], [0.5, 0.5, 0.52], [0.0, 0.0, 0.0]])
+    mu = sinker.viscosity(c, prob)
+    f = sinker.forcing(c, prob)
+    assert mu[0] == 100.0 and mu[1] == 100.0             # inside omega/2: X = 0
+    assert abs(mu[2] - 0.01) < 1e-12                     # far away: X -> 1
+    assert f[0, 2] == -10.0 and abs(f[2, 2]) < 1e-12
+    d = 0.1                                              # distance 0.1: X = 1 - exp(-200 * 0.05^2)
+    X = 1 - np.exp(-200 * 0.05 ** 2)
+    assert abs(sinker.indicator(np.array([[0.6, 0.5, 0.5]]), prob.centres, 200, 0.1)[0] - X) < 1e-15
+    # harmonic mean with quadrature weights: constant -> same; 1/mu linear in weights
+    _, w = fe.quadrature_3d()
+    assert abs(sinker.harmonic_cell_average(np.full(27, 3.0)) - 3.0) < 1e-15
+    vals = np.where(np.arange(27) == 13, 2.0, 1.0)       # centre point has weight (8/18)^3
+    expect = 1.0 / (1 - w[13] + w[13] / 2.0)
+    assert abs(sinker.harmonic_cell_average(vals) - expect) < 1e-15
+    fine = np.arange(64, dtype=float)
+    par = sinker.restrict_cell_viscosity(fine, 4)
+    assert abs(par[0] - np.mean([0, 1, 4, 5, 16, 17, 20, 21])) < 1e-15
+
+
+# ---------------------------------------------------------------- transfers
+def test_prolongation_is_q2_embedding():
+    nc = 2
+    P = gmg.prolongation(nc)
+    cm, fm = mesh.Mesh(nc), mesh.Mesh(2 * nc)
+    coarse = si.uniform(31, cm.n_u)
+    fine = P @ coarse
+    # evaluate the coarse field directly at the fine nodes with the 3D basis of the coarse cell
+    X = fm.node_coords()
+    cell = np.minimum((X / cm.h).astype(int), nc - 1)
+    loc = X / cm.h - cell
+    val, _ = fe.q2_3d_tables(loc)
+    cid = cell[:, 0] + nc * cell[:, 1] + nc * nc * cell[:, 2]
+    for comp in range(3):
+        ref = np.einsum("pa,pa->p", val, coarse[cm.cell_dofs[cid, comp * 27:(comp + 1) * 27]])
+        assert np.allclose(fine[comp * fm.n_nodes:(comp + 1) * fm.n_nodes], ref, atol=1e-14)
+    # 1D weights at 1/4 and 3/4 of a coarse cell
+    P1 = gmg.prolongation_1d(1).toarray()
+    assert np.allclose(P1[1], [3 / 8, 3 / 4, -1 / 8]) and np.allclose(P1[3], [-1 / 8, 3 / 4, 3 / 8])
+
+
+# ---------------------------------------------------------------- Chebyshev and Lanczos
+def _cheb_T(k, x):
+    x = np.asarray(x, dtype=float)
+    return np.where(np.abs(x) <= 1, np.cos(k * np.arccos(np.clip(x, -1, 1))),
+                    np.cosh(k * np.arccosh(np.maximum(np.abs(x), 1))) * np.sign(x) ** k)
+
+
+def test_chebyshev_error_polynomial():
+    """e_k = T_k((theta - lam)/delta) / T_k(theta/delta) e_0 per eigencomponent."""
+    lam = np.linspace(0.05, 2.0, 40)
+    lo, hi = 0.1, 1.8
+    theta, delta = (hi + lo) / 2, (hi - lo) / 2
+    b = si.uniform(41, lam.size)
+    xstar = b / lam
+    x0 = si.uniform(42, lam.size)
+    A = lambda v: lam * v
+    for k in (1, 2, 4, 5):
+        x = gmg.chebyshev_smooth(A, np.ones_like(lam), b, x0, k, lo, hi, False)
+        expect = _cheb_T(k, (theta - lam) / delta) / _cheb_T(k, theta / delta) * (x0 - xstar)
+        assert np.allclose(x - xstar, expect, atol=1e-12)
+        x = gmg.chebyshev_smooth(A, np.ones_like(lam), b, None, k, lo, hi, True)
+        expect = _cheb_T(k, (theta - lam) / delta) / _cheb_T(k, theta / delta) * (-xstar)
+        assert np.allclose(x - xstar, expect, atol=1e-12)
+
+
+def test_lanczos_exact_on_small_spectrum():
+    lam = np.array([0.5, 1.0, 1.5, 2.0, 3.0, 4.5, 7.0, 9.0])
+    x = gmg.lanczos_lambda_max(lambda v: lam * v, np.ones(8), np.ones(8), 77, 12)
+    assert abs(x - 9.0) < 1e-12
+    d = 1.0 / (1.0 + np.arange(8))
+    x = gmg.lanczos_lambda_max(lambda v: lam * v, d, np.ones(8), 78, 12)
+    assert abs(x - np.max(lam * d)) < 1e-12
+
+
+# ---------------------------------------------------------------- solver-level pins
+def _problem(name):
+    p = si.workload(name)
+    m = mesh.Mesh(p.n)
+    mus = sinker.level_viscosities(m, p, p.n_levels)
+    G = gmg.GMG(p.n, p.n_levels, mus)
+    ops = G.levels[-1].ops
+    F = operators.assemble_rhs(m, sinker.forcing(m.quad_points(), p))
+    return p, m, G, ops, F
+
+
+def test_exact_preconditioner_two_iterations():
+    """eq. stokes_precond: with exact A^-1 and S^-1, FGMRES converges in at most 2 iterations."""
+    p, m, G, ops, F = _problem("cube2")
+    A = ops.csr_A().toarray()
+    B = ops.csr_B().toarray()
+    Ainv = np.linalg.inv(A)
+    S = B @ Ainv @ B.T
+    Spinv = np.linalg.pinv(S, rcond=1e-10, hermitian=True)   # S is singular on constants only
+    Pc = krylov.StokesPreconditioner(ops, G, exact_A=lambda t: Ainv @ t, exact_S=lambda r: Spinv @ r)
+    b = np.concatenate([F, np.zeros(m.n_p)])
+    _, its, hist = krylov.fgmres(ops.apply_stokes, Pc.apply, b, rtol=1e-12)
+    assert its <= 2
+
+
+def test_fgmres_gmg_matches_dense_direct_solve():
+    p, m, G, ops, F = _problem("cube4")
+    Pc = krylov.StokesPreconditioner(ops, G)
+    b = np.concatenate([F, np.zeros(m.n_p)])
+    x, its, _ = krylov.fgmres(ops.apply_stokes, Pc.apply, b, rtol=1e-13)
+    xd = krylov.dense_stokes_solve(ops, F)
+    xz = krylov.zero_mean_pressure(ops, x)
+    assert np.abs(xz - xd).max() <= 1e-9 * np.abs(xd).max()
+    assert its < 200
+
+
+def test_vcycle_h_independent_constant_viscosity():
+    rates = []
+    for n, L in [(4, 3), (8, 4), (16, 5)]:
+        mus = [np.ones((n >> (L - 1 - l)) ** 3) for l in range(L)]
+        G = gmg.GMG(n, L, mus)
+        lev = G.levels[-1]
+        b = si.uniform(51, lev.mesh.n_u) * lev.free
+        x = np.zeros_like(b)
+        r0 = np.linalg.norm(b)
+        for _ in range(5):
+            x = x + G.vcycle(b - lev.A(x)) * lev.free
+        rates.append((np.linalg.norm(b - lev.A(x)) / r0) ** (1 / 5))
+    assert max(rates) < 0.15 and max(rates) - min(rates) < 0.05
+
+
+@pytest.mark.slow
+def test_manufactured_solution_convergence_order():
+    """Divergence-free u = curl(0, 0, psi), psi = (x(1-x) y(1-y) z(1-z))^2, mu = 1,
+    p = cos(pi x) cos(pi y) cos(pi z): velocity L2 error O(h^3), pressure O(h^2)."""
+    sym = pytest.importorskip("sympy")
+    X, Y, Z = sym.symbols("x y z")
+    psi = (X * (1 - X) * Y * (1 - Y) * Z * (1 - Z)) ** 2
+    u = [sym.diff(psi, Y), -sym.diff(psi, X), sym.Integer(0)]
+    p = sym.cos(sym.pi * X) * sym.cos(sym.pi * Y) * sym.cos(sym.pi * Z)
+    f = [-(sym.diff(u[c], X, 2) + sym.diff(u[c], Y, 2) + sym.diff(u[c], Z, 2)) + sym.diff(p, v)
+         for c, v in enumerate((X, Y, Z))]
+    uf = [sym.lambdify((X, Y, Z), e, "numpy") for e in u]
+    ff = [sym.lambdify((X, Y, Z), e, "numpy") for e in f]
+    pf = sym.lambdify((X, Y, Z), p, "numpy")
+    errs_u, errs_p = [], []
+    for n in (2, 4, 8):
+        m = mesh.Mesh(n)
+        ops = operators.Operators(m, np.ones(m.n_cells))
+        q = m.quad_points()
+        fq = np.stack([np.broadcast_to(ff[c](q[..., 0], q[..., 1], q[..., 2]), q.shape[:2]) for c in range(3)], -1)
+        F = operators.assemble_rhs(m, fq)
+        A = ops.csr_A()
+        B = ops.csr_B()
+        w = sp.csr_matrix(ops.pressure_weights()[None, :])
+        K = sp.bmat([[A, B.T, None], [B, None, w.T], [None, w, None]]).tocsc()
+        sol = sla.spsolve(K, np.concatenate([F, np.zeros(m.n_p + 1)]))
+        uh, ph = sol[:m.n_u], sol[m.n_u:m.n_u + m.n_p]
+        pts, wq = fe.quadrature_3d()
+        val, _ = fe.q2_3d_tables(pts)
+        e2 = 0.0
+        for c in range(3):
+            uq = uh[m.cell_dofs[:, c * 27:(c + 1) * 27]] @ val.T
+            ex = np.broadcast_to(uf[c](q[..., 0], q[..., 1], q[..., 2]), uq.shape)
+            e2 += np.sum((uq - ex) ** 2 * wq[None, :]) * m.h ** 3
+        errs_u.append(np.sqrt(e2))
+        psiq = fe.q1_3d_values(pts)
+        pq = ph[m.cell_verts] @ psiq.T
+        exq = pf(q[..., 0], q[..., 1], q[..., 2])
+        errs_p.append(np.sqrt(np.sum((pq - exq) ** 2 * wq[None, :]) * m.h ** 3))
+    rate_u = np.log2(errs_u[-2] / errs_u[-1])
+    rate_p = np.log2(errs_p[-2] / errs_p[-1])
+    assert rate_u > 2.6, errs_u
+    assert rate_p > 1.6, errs_p
+
+
+def test_galerkin_identity_and_symmetric_vcycle_constant_viscosity():
+    """Nested Q2 spaces with exact quadrature and constant mu: the rediscretised coarse
+    operator equals P^T A_fine P on free DoFs, and the V(1,1) cycle with equal pre/post
+    Chebyshev smoothers is then a symmetric operator."""
+    nc = 2
+    P = gmg.prolongation(nc)
+    cm, fm = mesh.Mesh(nc), mesh.Mesh(2 * nc)
+    Af = operators.Operators(fm, np.full(fm.n_cells, 3.0)).csr_A()
+    Ac = operators.Operators(cm, np.full(cm.n_cells, 3.0)).csr_A()
+    ff, fc = sp.diags((~fm.dirichlet).astype(float)), sp.diags((~cm.dirichlet).astype(float))
+    Pf = ff @ P @ fc
+    G = (Pf.T @ Af @ Pf).toarray()
+    Acf = (fc @ Ac @ fc).toarray()
+    assert np.abs(G - Acf).max() < 1e-12 * np.abs(Acf).max()
+    n, L = 8, 4
+    mus = [np.full((n >> (L - 1 - l)) ** 3, 2.0) for l in range(L)]
+    Gm = gmg.GMG(n, L, mus)
+    free = Gm.levels[-1].free
+    x = si.uniform(61, free.size) * free
+    y = si.uniform(62, free.size) * free
+    assert abs(Gm.vcycle(x) @ y - x @ Gm.vcycle(y)) < 1e-12 * abs(Gm.vcycle(x) @ y)
