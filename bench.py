@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""Benchmark of the matrix-free GMG Stokes hot path on GB300.
+
+One step = one whole solve of the Stokes system of the 64^3 sinker workload
+(8 sinkers, viscosity ratio 1e4, 7 GMG levels, Chebyshev degree 4) to a
+relative residual of 1e-8: FP64 FGMRES(50) preconditioned by the block-
+triangular P^-1 with the GMG V-cycle in FP32 and the Schur approximation,
+outer operator and coarse solve in FP64. Inputs (viscosity, right-hand side,
+level tables) are resident in HBM; each step starts from a zero guess.
+
+value = whole-job solve throughput: (N_u + N_p) * n_gpus / (seconds per solve)
+in GDoF/s. Extra keys report the pieces of the metric: the solve time with the
+FP32 and the FP64 V-cycle, iterations, the standalone vmult rate (GDoF/s and
+fraction of HBM peak), the roofline of the dominant kernel, the end-to-end
+time through the host-buffer entry point, and the CPU oracle as a baseline.
+
+usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload cube64]
+Multi-GPU (torchrun): each rank solves its own replica (no collective on the
+data path; the path shards into independent problems), time = max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "vmult GDoF/s & %HBM peak; Stokes solve s to 1e-8 rel (FP32 vs FP64 GMG)"
+RTOL = 1e-8
+# Algorithmic flops per cell of the FP64 outer operator [A B^T; B 0] as implemented by sum
+# factorisation (multiply-add = 2 flops): A 2916 MACs, B^T 1188 MACs, B 1188 MACs.
+STOKES_FLOP_PER_CELL = 2 * (2916 + 1188 + 1188)
+# Same for the velocity operator alone.
+A_FLOP_PER_CELL = 2 * 2916
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cube64")
+    ap.add_argument("--no-extras", action="store_true", help="skip the sweep/profile/e2e/cpu legs")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+# ----------------------------------------------------------------- clocks
+CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def clocks_start(index):
+    path = tempfile.mktemp(suffix=".csv")
+    try:
+        p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + CLOCK_Q, "--format=csv,noheader,nounits",
+                              "-lms", "200"], stdout=open(path, "w"), stderr=subprocess.DEVNULL)
+    except (FileNotFoundError, OSError):
+        return None, path
+    return p, path
+
+
+def clocks_stop(p, path):
+    if p is None:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    time.sleep(0.25)
+    p.terminate()
+    p.wait()
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm.append(float(f[1]))
+            smax.append(float(f[2]))
+        except ValueError:
+            continue
+        for name, v in zip(names, f[5:9]):
+            if v.lower() == "active":
+                reasons.add(name)
+    os.unlink(path)
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+            "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("q2_basis.cuh", "ops.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1907_06696_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, workload):
+    """DRAM bytes per launch from a committed ncu summary, if taken on the current kernel source."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    except (OSError, ValueError):
+        return None
+    e = rec.get(kernel, {}).get(workload)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+# ----------------------------------------------------------------- CPU oracle legs
+def oracle_iterations(name):
+    try:
+        return json.load(open(os.path.join(ROOT, "oracle", "iteration_counts.json")))[name]["iterations"]
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import sinker_inputs as si
+    prob = si.workload(args.workload)
+    its = oracle_iterations(args.workload)
+    if its is None:
+        print(json.dumps({"impl": "reference", "unavailable": "no recorded oracle iteration count for %s "
+                          "(run python -m oracle.solve_workload %s)" % (args.workload, args.workload)}))
+        return
+    # each step: one FGMRES iteration of the oracle on the full workload (one shared set-up),
+    # scaled by the oracle's recorded iteration count for the whole solve
+    t_it, ndof = _oracle_steps(prob, args.warmup, args.steps)
+    solve_s = t_it * its
+    value = ndof / solve_s / 1e9
+    line = {"metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": solve_s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "n": prob.n, "levels": prob.n_levels, "sinkers": prob.n_sinkers,
+                       "dr": prob.mu_max / prob.mu_min, "rtol": RTOL},
+            "cpu_baseline": {"value": value, "unit": "GDoF/s", "cores": cpu_threads(), "kind": "oracle",
+                             "sample": "1 FGMRES iteration of the oracle per step on the full %s workload "
+                                       "(numpy/scipy FP64), scaled by the oracle's recorded %d iterations"
+                                       % (args.workload, its)},
+            "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def _oracle_steps(prob, warmup, steps):
+    import numpy as np
+    from oracle import gmg, krylov, mesh, operators, sinker
+    m = mesh.Mesh(prob.n)
+    mus = sinker.level_viscosities(m, prob, prob.n_levels)
+    G = gmg.GMG(prob.n, prob.n_levels, mus)
+    ops = G.levels[-1].ops
+    F = operators.assemble_rhs(m, sinker.forcing(m.quad_points(), prob))
+    b = np.concatenate([F, np.zeros(m.n_p)])
+    Pc = krylov.StokesPreconditioner(ops, G)
+    ts = []
+    for i in range(warmup + steps):
+        t = time.perf_counter()
+        krylov.fgmres(ops.apply_stokes, Pc.apply, b, rtol=1e-30, max_it=1)
+        if i >= warmup:
+            ts.append(time.perf_counter() - t)
+    return statistics.mean(ts), m.n_u + m.n_p
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    from paper_1907_06696_gb300 import build as B
+    if local_rank == 0:
+        B.build()
+    if dist is not None:
+        dist.barrier()
+    from paper_1907_06696_gb300 import capi
+    capi.load()
+    import sinker_inputs as si
+
+    prob = si.workload(args.workload)
+    stream = torch.cuda.current_stream()
+    ctx = capi.stokes_setup_problem(prob, stream=stream)
+    n_u, n_p = ctx.n_u, ctx.n_p
+    N = n_u + n_p
+    up = torch.zeros(N, dtype=torch.float64, device="cuda")
+    FP32, FP64 = capi.STOKES_FP32, capi.STOKES_FP64
+
+    def solve(prec):
+        up.zero_()
+        return capi.stokes_solve(ctx, prec, None, up, rtol=RTOL, max_it=2000, stream=stream)
+
+    for _ in range(args.warmup):
+        info = solve(FP32)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk, clk_path = clocks_start(torch.cuda.current_device())
+    time.sleep(0.3)
+    l0 = capi.stokes_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    its = []
+    for _ in range(args.steps):
+        info = solve(FP32)
+        its.append(info.iterations)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = capi.stokes_launch_count() - l0
+    clocks = clocks_stop(clk, clk_path)
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = world * N / (ms / 1e3) / 1e9
+    true_res32 = info.rel_residual_true
+    if rank != 0:
+        return
+    pk = peaks()
+    hbm = pk.get("hbm_gbs", 6800.0)
+    hbm_src = "of measured" if "hbm_gbs" in pk else "of fallback"
+    line = {"metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 outer + f32 V-cycle", "data": "synthetic",
+            "config": {"workload": args.workload, "n": prob.n, "levels": prob.n_levels, "sinkers": prob.n_sinkers,
+                       "dr": prob.mu_max / prob.mu_min, "n_u": n_u, "n_p": n_p, "rtol": RTOL,
+                       "vcycle": "fp32", "outer": "fp64 FGMRES(50)", "parallelism": "replicas" if world > 1 else "1 GPU",
+                       "l2": "working set %.1f GB > L2 (no flush needed)" % (N * 8 * 103 / 1e9)},
+            "solve": {"fp32_vcycle_s": ms / 1e3, "fp32_vcycle_iterations": its,
+                      "fp32_true_rel_residual": true_res32},
+            "gpu_launches": int(launches), "clocks": clocks}
+    if args.no_extras:
+        print(json.dumps(line))
+        return
+
+    # --- FP64 V-cycle solve (same FGMRES), one timed solve
+    e0.record(stream)
+    info64 = solve(FP64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    line["solve"].update({"fp64_vcycle_s": e0.elapsed_time(e1) / 1e3, "fp64_vcycle_iterations": info64.iterations,
+                          "fp64_true_rel_residual": info64.rel_residual_true})
+    line["solve"]["fp32_speedup_vs_fp64_gmg"] = line["solve"]["fp64_vcycle_s"] / line["solve"]["fp32_vcycle_s"]
+
+    # --- standalone vmult (finest level), FP32 and FP64
+    x32 = torch.rand(n_u, device="cuda", dtype=torch.float32)
+    y32 = torch.empty_like(x32)
+    x64 = x32.double()
+    y64 = torch.empty_like(x64)
+    cells = prob.n ** 3
+    vm = {}
+    for tag, prec, x, y, s in (("fp32", FP32, x32, y32, 4), ("fp64", FP64, x64, y64, 8)):
+        reps = 20 if tag == "fp32" else 5
+        for _ in range(3):
+            capi.stokes_vmult(ctx, -1, capi.BLOCK_A, prec, x, y, stream=stream)
+        capi.stokes_profile(1)
+        capi.stokes_profile_read(reset=True)
+        e0.record(stream)
+        for _ in range(reps):
+            capi.stokes_vmult(ctx, -1, capi.BLOCK_A, prec, x, y, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = capi.stokes_profile_read(reset=True)
+        capi.stokes_profile(0)
+        t_call = e0.elapsed_time(e1) / reps / 1e3
+        kname = "vmult_A_" + tag
+        t_kern = prof[kname][0] / max(prof[kname][1], 1) / 1e3
+        bytes_alg = (2 * n_u + cells) * s
+        vm[tag] = {"gdofs": n_u / t_call / 1e9, "call_ms": t_call * 1e3, "kernel_ms": t_kern * 1e3,
+                   "kernel_gdofs": n_u / t_kern / 1e9, "algorithmic_bytes": bytes_alg,
+                   "achieved_gbs": bytes_alg / t_kern / 1e9, "hbm_frac": bytes_alg / t_kern / 1e9 / hbm,
+                   "gflops": cells * A_FLOP_PER_CELL / t_kern / 1e9}
+    line["vmult"] = vm
+    line["vmult"]["peak_gbs"] = hbm
+    line["vmult"]["peak_note"] = hbm_src
+
+    # --- profiled solve: time share per kernel class inside the step
+    capi.stokes_profile(1)
+    capi.stokes_profile_read(reset=True)
+    solve(FP32)
+    torch.cuda.synchronize()
+    prof = capi.stokes_profile_read(reset=True)
+    capi.stokes_profile(0)
+    tot = sum(v[0] for v in prof.values())
+    line["kernel_share"] = {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / tot, 4)}
+                            for k, v in prof.items() if v[1]}
+    dom = max(prof, key=lambda k: prof[k][0])
+    dms = prof[dom][0] / max(prof[dom][1], 1)
+    if dom == "stokes_fp64":
+        fl = cells * STOKES_FLOP_PER_CELL
+        fp64_peak = 1250.0   # GFLOP/s: GB300 FP64 rate (recipe figure), at the maximum SM clock
+        line["roofline"] = {"kernel": dom, "bound": "alu", "achieved": fl / (dms / 1e3) / 1e9, "peak": fp64_peak,
+                            "unit": "GFLOP/s", "frac": fl / (dms / 1e3) / 1e9 / fp64_peak,
+                            "traffic": recorded_traffic(dom, args.workload),
+                            "peak_note": "FP64 1.25 TFLOP/s nominal (recipe unit figure)",
+                            "per_launch": "%d cells x %d flop" % (cells, STOKES_FLOP_PER_CELL)}
+    else:
+        k = vm["fp32"] if dom == "vmult_A_fp32" else vm["fp64"]
+        line["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": k["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                            "frac": k["hbm_frac"], "traffic": recorded_traffic(dom, args.workload),
+                            "peak_note": hbm_src}
+
+    # --- end to end through the host-buffer entry point (pinned host memory)
+    rhs_h = torch.zeros(N, dtype=torch.float64, pin_memory=True)
+    Fd = torch.empty(n_u, dtype=torch.float64, device="cuda")
+    capi.stokes_get_rhs(ctx, Fd, stream=stream)
+    torch.cuda.synchronize()
+    rhs_h[:n_u].copy_(Fd.cpu())
+    out_h = torch.empty(N, dtype=torch.float64, pin_memory=True)
+    capi.stokes_solve_host(ctx, FP32, rhs_h.numpy(), out_h.numpy(), rtol=RTOL, max_it=2000, stream=stream)
+    e0.record(stream)
+    for _ in range(args.steps):
+        capi.stokes_solve_host(ctx, FP32, rhs_h.numpy(), out_h.numpy(), rtol=RTOL, max_it=2000, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ems = e0.elapsed_time(e1) / args.steps
+    line["e2e"] = {"value": N / (ems / 1e3) / 1e9, "unit": "GDoF/s", "ms_per_step": ems,
+                   "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8}
+    ctx.close()
+    del up, x32, y32, x64, y64
+    torch.cuda.empty_cache()
+
+    # --- CPU oracle baseline: bounded sample, scaled to a solve
+    its_ref = oracle_iterations(args.workload)
+    try:
+        t_it, ndof = _oracle_steps(prob, 0, 2)
+        n_it = its_ref if its_ref else its[-1]
+        line["cpu_baseline"] = {"value": ndof / (t_it * n_it) / 1e9, "unit": "GDoF/s", "cores": cpu_threads(),
+                                "kind": "oracle",
+                                "sample": "2 FGMRES iterations of the numpy/scipy FP64 oracle on the full %s "
+                                          "workload (set-up untimed), %.2f s each, scaled by %d iterations%s"
+                                          % (args.workload, t_it, n_it,
+                                             " (oracle's recorded count)" if its_ref else " (GPU FP32 count)")}
+    except MemoryError as e:
+        line["cpu_baseline"] = {"value": None, "unit": "GDoF/s", "cores": cpu_threads(), "kind": "oracle",
+                                "sample": "failed: %s" % e}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,229 @@
+/*
+ * stokes.h -- C ABI of the GB300 matrix-free GMG Stokes library.
+ *
+ * Method: Clevenger & Heister, "Comparison between algebraic and matrix-free
+ * geometric multigrid for a Stokes problem on adaptive meshes with variable
+ * viscosity" (arXiv 1907.06696).
+ *   - Stokes problem with variable viscosity and homogeneous Dirichlet
+ *     velocity: Section 2, eq. (stokes).
+ *   - Taylor-Hood Q2-Q1 on hexahedra and the blocks A, B, B^T, F:
+ *     Section 2.1, eq. (stokes_linear_system).
+ *   - Block-triangular preconditioner P = [[A, B^T], [0, -S]]:
+ *     Section 2.2, eq. (stokes_precond).
+ *   - A^-1 ~ one matrix-free GMG V-cycle on the fully coupled A with a
+ *     degree-4 Chebyshev smoother, one smoothing step per level: Section 2.2.1.
+ *   - S^-1 ~ Chebyshev iteration on the 1/mu-weighted pressure mass matrix,
+ *     outer FGMRES: Section 2.2.2.
+ *   - Harmonic cell averaging of the viscosity and its Q0 restriction to the
+ *     level hierarchy: Section 2.3.
+ *   - Sinker benchmark coefficients: Section 3.2.
+ *
+ * Mesh and vector layout (every entry point):
+ *   Uniform n^3 cube cells on [0,1]^3, h = 1/n. Level l (0 = coarsest) has
+ *   n_l = n / 2^(L-1-l) cells per axis. Q2 nodes form an M^3 lattice,
+ *   M = 2 n_l + 1, node (i,j,k) -> i + M j + M^2 k. A velocity vector is
+ *   component-blocked: entry c*M^3 + node, length N_u = 3 M^3 (boundary nodes
+ *   included). A pressure vector holds the (n+1)^3 Q1 vertex values,
+ *   vertex (i,j,k) -> i + (n+1) j + (n+1)^2 k. A Stokes vector is [u; p],
+ *   length N_u + N_p, FP64.
+ *   All six walls are no-slip: velocity entries on boundary nodes are
+ *   constrained. Every operator IGNORES the constrained entries of its input
+ *   (treats them as 0) and acts as the IDENTITY on them in its output, i.e.
+ *   the constrained operator is [[A_ff, 0], [0, I]].
+ *
+ * Memory: every pointer named *_dev is a device pointer owned by the caller
+ * (for example a torch tensor's data_ptr()); the library never frees it. The
+ * library owns its tables and workspace (allocated in stokes_setup and, for
+ * the Krylov basis, on the first stokes_solve; freed by stokes_destroy).
+ *
+ * Streams: `stream` is a cudaStream_t (NULL = the legacy default stream).
+ * Calls are asynchronous on that stream unless stated otherwise. One context
+ * must not be used from two streams at the same time (its workspace is shared).
+ *
+ * Errors: every call returns a stokes_status; no C++ exception crosses the
+ * ABI. stokes_last_error() gives a message for the calling thread's last error.
+ */
+#ifndef STOKES_GB300_H
+#define STOKES_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stokes_ctx stokes_ctx;
+
+typedef enum {
+    STOKES_OK = 0,
+    STOKES_EINVAL = 1,          /* bad argument (size, level, precision, null pointer) */
+    STOKES_ENOMEM = 2,          /* device or host allocation failed */
+    STOKES_ECUDA = 3,           /* a CUDA runtime call or kernel launch failed */
+    STOKES_NOT_CONVERGED = 4,   /* stokes_solve hit max_it before rtol */
+    STOKES_BREAKDOWN = 5,       /* NaN/Inf or a zero Krylov norm in stokes_solve */
+    STOKES_TIMEOUT = 6,         /* reserved: a bounded device wait gave up */
+    STOKES_EMESH = 7            /* unsupported mesh description */
+} stokes_status;
+
+typedef enum { STOKES_FP64 = 0, STOKES_FP32 = 1 } stokes_prec;
+
+typedef enum {
+    STOKES_BLOCK_A = 0,         /* u -> A_c u            (N_u -> N_u) */
+    STOKES_BLOCK_B = 1,         /* u -> B u              (N_u -> N_p) */
+    STOKES_BLOCK_BT = 2,        /* p -> B^T p            (N_p -> N_u, zero on constrained rows) */
+    STOKES_BLOCK_MP = 3,        /* p -> M_p p            (N_p -> N_p) */
+    STOKES_BLOCK_STOKES = 4     /* [u;p] -> [A_c u + B^T p; B u]  (N_u+N_p -> N_u+N_p) */
+} stokes_block;
+
+typedef struct {
+    int kind;                   /* 0 = uniform n^3 grid of the unit cube (the only kind) */
+    int n;                      /* cells per axis on the finest level, n = c * 2^(n_levels-1), 1 <= c <= 4 */
+    int n_levels;               /* multigrid levels, >= 1 */
+} stokes_mesh;
+
+typedef struct {
+    int kind;                   /* 0 = sinker formula (Section 3.2); 1 = values at quadrature points */
+    int n_sinkers;              /* kind 0 */
+    const double* centres;      /* kind 0: host, 3*n_sinkers (x,y,z per sinker) */
+    double mu_min, mu_max;      /* kind 0: mu = X mu_min + (1 - X) mu_max */
+    double delta, omega;        /* kind 0: decay (200) and sinker diameter (0.1) */
+    double beta;                /* kind 0: forcing f = (0, 0, beta (X - 1)) (10) */
+    const double* mu_q;         /* kind 1: host, n^3 * 27 values; cell-major (cell index
+                                   ci + n cj + n^2 ck), then Gauss point qx + 3 qy + 9 qz */
+} stokes_mu;
+
+typedef struct {
+    uint32_t noslip_faces;      /* bit f = face f is no-slip; must be 0x3F (all walls, eq. stokes) */
+} stokes_bc;
+
+typedef struct {
+    int cheb_degree;            /* Chebyshev smoother degree per smoothing step (4, Section 2.2.1) */
+    double smoothing_range;     /* eigenvalue interval [lam_hi / range, lam_hi] (15) */
+    double eig_safety;          /* lam_hi = safety * Lanczos estimate of lambda_max(D^-1 A) (1.2) */
+    int lanczos_steps;          /* Lanczos steps for lambda_max (12) */
+    int schur_degree;           /* Chebyshev degree of S_hat^-1 on M_p, interval [1/8, 27/8] (5) */
+    int restart;                /* FGMRES restart length (50, Section 3.5) */
+} stokes_options;
+
+typedef struct {
+    int iterations;             /* FGMRES iterations (preconditioner applications) */
+    double rel_residual;        /* final recurrence estimate |g_k| / ||b|| */
+    double rel_residual_true;   /* ||b - K x|| / ||b|| recomputed in FP64 after the solve */
+    double seconds;             /* wall time of the solve on the host clock */
+    int status;                 /* the stokes_status returned */
+} stokes_solve_info;
+
+/* Fill `opt` with the defaults listed above. */
+void stokes_default_options(stokes_options* opt);
+
+/* Build the level hierarchy (Section 2.2.1) for a uniform mesh: per-level cell
+ * viscosity (harmonic average of mu at the 27 Gauss points of each finest cell,
+ * parent = mean of its 8 children, Section 2.3), inverse diagonals of A_l,
+ * Lanczos estimates of lambda_max(D_l^-1 A_l) (start vector: splitmix64 with
+ * seed 1907000 + l, value u01 - 1/2 per DoF index, constrained entries 0),
+ * the dense FP64 inverse of the coarsest A_0 on its free DoFs, the diagonal of
+ * M_p, and the right-hand side F (kind 0 only; F = 0 for kind 1).
+ * Synchronous on `stream`. On success *out owns all of it. Errors: EINVAL
+ * (null pointer, n or n_levels out of range), EMESH (kind != 0, n not
+ * c*2^(L-1), bc != 0x3F), ENOMEM, ECUDA. */
+stokes_status stokes_setup(const stokes_mesh* mesh, const stokes_mu* mu, const stokes_bc* bc,
+                           const stokes_options* opt /* NULL = defaults */, void* stream,
+                           stokes_ctx** out);
+
+/* Free everything the context owns (synchronises the device first). NULL is a no-op. */
+void stokes_destroy(stokes_ctx* ctx);
+
+const char* stokes_strerror(stokes_status s);
+/* Message for the calling thread's last failed call ("" if none). */
+const char* stokes_last_error(void);
+
+/* Sizes: what = 0 N_u, 1 N_p, 2 cells, 3 cells per axis, 4 number of levels.
+ * level -1 = finest. Returns 0 for a bad argument. */
+size_t stokes_size(const stokes_ctx* ctx, int level, int what);
+
+/* dst = block * src on one level (Section 2.1, eq. stokes_linear_system),
+ * matrix-free, sum-factorised on Q2 cells with the level's cell viscosity.
+ * level -1 = finest. prec FP32 is available for block A only; the B, B^T,
+ * M_p and Stokes blocks are FP64 and finest-level only. src and dst must not
+ * overlap. Errors: EINVAL (bad level/block/precision, null pointer), ECUDA. */
+stokes_status stokes_vmult(stokes_ctx* ctx, int level, int block, int prec,
+                           const void* src_dev, void* dst_dev, void* stream);
+
+/* x = V(rhs): one GMG V-cycle with zero initial guess on the finest level
+ * (Section 2.2.1): per level one pre- and one post-smoothing step of the
+ * degree-k Jacobi-Chebyshev smoother, residual, restriction, recursion,
+ * prolongation; exact FP64 solve on level 0. prec selects the arithmetic of
+ * the whole cycle (FP32: vectors and kernels in FP32, coarse solve in FP64);
+ * rhs and x have that precision and length N_u. x holds rhs on constrained
+ * entries. rhs and x must not overlap. */
+stokes_status gmg_vcycle(stokes_ctx* ctx, int prec, const void* rhs_dev, void* x_dev, void* stream);
+
+/* Solve [[A, B^T], [B, 0]] [u; p] = [rhs_u; rhs_p] with right-preconditioned
+ * FP64 FGMRES(restart) (Section 2.2.2) and P^-1 of eq. stokes_precond:
+ * z_p = -S_hat^-1 r_p, z_u = V(r_u - B^T z_p), the V-cycle in `vcycle_prec`.
+ * rhs_dev = NULL uses the sinker right-hand side [F; 0]. up_dev: in = initial
+ * guess, out = solution with zero-mean pressure. Stops when the recurrence
+ * residual <= rtol ||b||. Host-synchronous (one small device->host read per
+ * iteration). Errors: NOT_CONVERGED (max_it reached; up holds the last
+ * iterate), BREAKDOWN, EINVAL, ENOMEM, ECUDA. */
+stokes_status stokes_solve(stokes_ctx* ctx, int vcycle_prec, const double* rhs_dev, double* up_dev,
+                           double rtol, int max_it, stokes_solve_info* info, void* stream);
+
+/* Same as stokes_solve with HOST buffers: copies rhs_host (or uses the sinker
+ * F when NULL) to library-owned device memory, solves from a zero initial
+ * guess and copies the solution to up_host (length N_u + N_p). */
+stokes_status stokes_solve_host(stokes_ctx* ctx, int vcycle_prec, const double* rhs_host, double* up_host,
+                                double rtol, int max_it, stokes_solve_info* info, void* stream);
+
+/* ---- single steps of the path (each is what the V-cycle / solve runs) ---- */
+
+/* Copy the cell viscosity of `level` (n_l^3 doubles, cell ci + n cj + n^2 ck) (Section 2.3). */
+stokes_status stokes_get_viscosity(stokes_ctx* ctx, int level, double* mu_dev, void* stream);
+/* Copy 1/diag(A_l) (N_u doubles, 0 on constrained entries). */
+stokes_status stokes_get_inv_diagonal(stokes_ctx* ctx, int level, double* dinv_dev, void* stream);
+/* Lanczos estimate of lambda_max(D_l^-1 A_l) (host double; 0 for level 0). */
+stokes_status stokes_get_lambda_max(stokes_ctx* ctx, int level, double* lam_host);
+/* Copy the assembled right-hand side F (N_u doubles, Section 2.1, def. of F). */
+stokes_status stokes_get_rhs(stokes_ctx* ctx, double* F_dev, void* stream);
+/* fine = P coarse (add = 0) or fine += P coarse (add = 1): Q2 embedding from
+ * level fine_level-1 to fine_level, constrained fine entries left 0 / unchanged. */
+stokes_status stokes_prolongate(stokes_ctx* ctx, int fine_level, int prec, const void* coarse_dev,
+                                void* fine_dev, int add, void* stream);
+/* coarse = P^T fine, constrained coarse entries set to 0. */
+stokes_status stokes_restrict(stokes_ctx* ctx, int fine_level, int prec, const void* fine_dev,
+                              void* coarse_dev, void* stream);
+/* One smoothing step of degree k on level >= 1: x <- x + q(D^-1 A) D^-1 (b - A x)
+ * (zero_guess = 1: x is output only). Constrained entries of b must be 0. */
+stokes_status stokes_smooth(stokes_ctx* ctx, int level, int prec, const void* b_dev, void* x_dev,
+                            int zero_guess, void* stream);
+/* x = A_0^-1 b on the coarsest level's free DoFs (FP64 arithmetic), 0 elsewhere. */
+stokes_status stokes_coarse_solve(stokes_ctx* ctx, int prec, const void* b_dev, void* x_dev, void* stream);
+/* z_p = S_hat^-1 r_p: Jacobi-Chebyshev of degree schur_degree on M_p, interval [1/8, 27/8]. */
+stokes_status stokes_schur_inverse(stokes_ctx* ctx, const double* rp_dev, double* zp_dev, void* stream);
+/* z = P^-1 r for a Stokes vector (eq. stokes_precond), V-cycle in vcycle_prec. */
+stokes_status stokes_precondition(stokes_ctx* ctx, int vcycle_prec, const double* r_dev, double* z_dev,
+                                  void* stream);
+
+/* ---- instrumentation (no counterpart in the paper; used by the benchmark) ---- */
+
+/* Kernel classes timed by stokes_profile: 0 velocity cell kernel FP32, 1 velocity
+ * cell kernel FP64, 2 fused A+B^T+B cell kernel, 3 B^T cell kernel, 4 pressure mass
+ * cell kernel, 5 transfers, 6 smoother / residual vector kernels, 7 Krylov vector
+ * kernels, 8 coarse solve, 9 precision casts. */
+#define STOKES_PROF_NCLASS 10
+/* enable = 1: record a CUDA event pair around every kernel launch the library
+ * issues from now on (adds two event records per launch); 0: stop. Process-wide,
+ * for single-threaded use. */
+stokes_status stokes_profile(int enable);
+/* Milliseconds and launches accumulated for class `cls` (synchronises the device);
+ * reset = 1 clears all classes afterwards. */
+stokes_status stokes_profile_read(int cls, double* ms, long long* launches, int reset);
+/* Number of kernel launches the library has issued since it was loaded. */
+long long stokes_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STOKES_GB300_H */

@@ -118,6 +118,43 @@ class Operators:
         return np.bincount(m.cell_verts.ravel(), weights=Y.ravel(), minlength=m.n_p)
 
 
+def apply_A_rows(n, mu_cells, x, dofs):
+    """Selected rows of A_c x on an n^3 mesh, element by element, without the
+    global cell tables (for sampled checks at sizes where those do not fit).
+    dofs: velocity DoF indices (component-blocked numbering)."""
+    M = 2 * n + 1
+    nodes = M ** 3
+    Ahat = fe.element_A(1.0 / n, 1.0)
+    dofs = np.asarray(dofs, dtype=np.int64)
+    out = np.zeros(dofs.size)
+    for t, dof in enumerate(dofs):
+        c, node = divmod(int(dof), nodes)
+        g = (node % M, (node // M) % M, node // (M * M))
+        if min(g) == 0 or max(g) == M - 1:
+            out[t] = x[dof]
+            continue
+        acc = 0.0
+        axes = []
+        for gi in g:     # (cell index, local index) along each axis
+            axes.append([((gi - 1) // 2, 1)] if gi % 2 else
+                        [(ci, li) for ci, li in ((gi // 2 - 1, 2), (gi // 2, 0)) if 0 <= ci < n])
+        for cz, lz in axes[2]:
+            for cy, ly in axes[1]:
+                for cx, lx in axes[0]:
+                    cell = cx + n * cy + n * n * cz
+                    local = np.array([(2 * cx + i) + M * (2 * cy + j) + M * M * (2 * cz + k)
+                                      for k in range(3) for j in range(3) for i in range(3)])
+                    ldofs = np.concatenate([local + comp * nodes for comp in range(3)])
+                    xb = x[ldofs].copy()
+                    lg = np.stack([local % M, (local // M) % M, local // (M * M)], 1)
+                    bnd = np.any((lg == 0) | (lg == M - 1), axis=1)
+                    xb[np.concatenate([bnd] * 3)] = 0.0
+                    row = c * 27 + lx + 3 * ly + 9 * lz
+                    acc += mu_cells[cell] * (Ahat[row] @ xb)
+        out[t] = acc
+    return out
+
+
 def assemble_rhs(mesh: Mesh, f_at_quad):
     """F_(c,node) = int phi . f dx with f sampled at each cell's Gauss points,
     shape (cells, 27, 3); constrained entries zero (Section 2.1, definition of F)."""

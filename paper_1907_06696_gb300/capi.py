@@ -1,0 +1,307 @@
+"""ctypes binding of libstokes_gb300.so (include/stokes.h).
+
+Argument marshalling only: every function forwards to the C entry point of the
+same name. Device vectors are passed as torch CUDA tensors (their data_ptr())
+or raw integer addresses; streams default to torch's current CUDA stream.
+A missing library raises immediately: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libstokes_gb300.so")
+
+STOKES_OK, STOKES_EINVAL, STOKES_ENOMEM, STOKES_ECUDA = 0, 1, 2, 3
+STOKES_NOT_CONVERGED, STOKES_BREAKDOWN, STOKES_TIMEOUT, STOKES_EMESH = 4, 5, 6, 7
+STOKES_FP64, STOKES_FP32 = 0, 1
+BLOCK_A, BLOCK_B, BLOCK_BT, BLOCK_MP, BLOCK_STOKES = 0, 1, 2, 3, 4
+
+
+class StokesError(RuntimeError):
+    def __init__(self, status, where, msg):
+        super().__init__("%s failed: status %d (%s)" % (where, status, msg))
+        self.status = status
+
+
+class stokes_mesh(C.Structure):
+    _fields_ = [("kind", C.c_int), ("n", C.c_int), ("n_levels", C.c_int)]
+
+
+class stokes_mu(C.Structure):
+    _fields_ = [("kind", C.c_int), ("n_sinkers", C.c_int), ("centres", C.POINTER(C.c_double)),
+                ("mu_min", C.c_double), ("mu_max", C.c_double), ("delta", C.c_double),
+                ("omega", C.c_double), ("beta", C.c_double), ("mu_q", C.POINTER(C.c_double))]
+
+
+class stokes_bc(C.Structure):
+    _fields_ = [("noslip_faces", C.c_uint32)]
+
+
+class stokes_options(C.Structure):
+    _fields_ = [("cheb_degree", C.c_int), ("smoothing_range", C.c_double), ("eig_safety", C.c_double),
+                ("lanczos_steps", C.c_int), ("schur_degree", C.c_int), ("restart", C.c_int)]
+
+
+class stokes_solve_info(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("rel_residual", C.c_double), ("rel_residual_true", C.c_double),
+                ("seconds", C.c_double), ("status", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+# name -> (restype, argtypes); mirrors include/stokes.h
+_P = C.c_void_p
+_SIGS = {
+    "stokes_default_options": (None, [C.POINTER(stokes_options)]),
+    "stokes_setup": (C.c_int, [C.POINTER(stokes_mesh), C.POINTER(stokes_mu), C.POINTER(stokes_bc),
+                               C.POINTER(stokes_options), _P, C.POINTER(_P)]),
+    "stokes_destroy": (None, [_P]),
+    "stokes_strerror": (C.c_char_p, [C.c_int]),
+    "stokes_last_error": (C.c_char_p, []),
+    "stokes_size": (C.c_size_t, [_P, C.c_int, C.c_int]),
+    "stokes_vmult": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P]),
+    "gmg_vcycle": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "stokes_solve": (C.c_int, [_P, C.c_int, _P, _P, C.c_double, C.c_int, C.POINTER(stokes_solve_info), _P]),
+    "stokes_solve_host": (C.c_int, [_P, C.c_int, _P, _P, C.c_double, C.c_int, C.POINTER(stokes_solve_info), _P]),
+    "stokes_get_viscosity": (C.c_int, [_P, C.c_int, _P, _P]),
+    "stokes_get_inv_diagonal": (C.c_int, [_P, C.c_int, _P, _P]),
+    "stokes_get_lambda_max": (C.c_int, [_P, C.c_int, C.POINTER(C.c_double)]),
+    "stokes_get_rhs": (C.c_int, [_P, _P, _P]),
+    "stokes_prolongate": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_int, _P]),
+    "stokes_restrict": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
+    "stokes_smooth": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_int, _P]),
+    "stokes_coarse_solve": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "stokes_schur_inverse": (C.c_int, [_P, _P, _P, _P]),
+    "stokes_precondition": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "stokes_profile": (C.c_int, [C.c_int]),
+    "stokes_profile_read": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int]),
+    "stokes_launch_count": (C.c_longlong, []),
+}
+
+PROF_CLASSES = ["vmult_A_fp32", "vmult_A_fp64", "stokes_fp64", "bt_fp64", "mass_p", "transfer",
+                "smoother_vec", "krylov_vec", "coarse", "cast"]
+
+
+def load(path: str = LIB_PATH):
+    """Load the library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libstokes_gb300.so not found at %s; run __graft_entry__.build() first" % path)
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):          # numpy array (host buffers)
+        return x.ctypes.data
+    raise TypeError("expected a tensor, array or integer address, got %r" % type(x))
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(status, where):
+    if status != STOKES_OK:
+        lib = load()
+        raise StokesError(status, where, lib.stokes_last_error().decode())
+
+
+class Context:
+    """Owns one stokes_ctx; destroyed with the object or by close()."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def close(self):
+        if self.handle:
+            load().stokes_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def size(self, level=-1, what=0):
+        return int(load().stokes_size(self.handle, level, what))
+
+    @property
+    def n_u(self):
+        return self.size(-1, 0)
+
+    @property
+    def n_p(self):
+        return self.size(-1, 1)
+
+    @property
+    def n_levels(self):
+        return self.size(-1, 4)
+
+
+def stokes_default_options():
+    o = stokes_options()
+    load().stokes_default_options(C.byref(o))
+    return o
+
+
+def stokes_setup(n, n_levels, centres=None, mu_min=1.0, mu_max=1.0, delta=200.0, omega=0.1, beta=10.0,
+                 mu_q=None, options=None, stream=None) -> Context:
+    """stokes_setup for a uniform n^3 mesh. Sinker viscosity (kind 0) unless mu_q
+    (host float64 array of n^3 * 27 Gauss-point values) is given (kind 1)."""
+    import numpy as np
+    lib = load()
+    mesh = stokes_mesh(0, int(n), int(n_levels))
+    mu = stokes_mu()
+    keep = []
+    if mu_q is not None:
+        q = np.ascontiguousarray(mu_q, dtype=np.float64)
+        keep.append(q)
+        mu.kind = 1
+        mu.mu_q = q.ctypes.data_as(C.POINTER(C.c_double))
+    else:
+        cen = np.ascontiguousarray(np.zeros((0, 3)) if centres is None else centres, dtype=np.float64).reshape(-1, 3)
+        keep.append(cen)
+        mu.kind = 0
+        mu.n_sinkers = cen.shape[0]
+        mu.centres = cen.ctypes.data_as(C.POINTER(C.c_double)) if cen.size else None
+        mu.mu_min, mu.mu_max, mu.delta, mu.omega, mu.beta = mu_min, mu_max, delta, omega, beta
+    bc = stokes_bc(0x3F)
+    h = C.c_void_p()
+    st = lib.stokes_setup(C.byref(mesh), C.byref(mu), C.byref(bc), C.byref(options) if options else None,
+                          _stream(stream), C.byref(h))
+    _check(st, "stokes_setup")
+    return Context(h.value)
+
+
+def stokes_setup_problem(prob, options=None, stream=None) -> Context:
+    """stokes_setup from a sinker_inputs.SinkerProblem."""
+    return stokes_setup(prob.n, prob.n_levels, prob.centres, prob.mu_min, prob.mu_max, prob.delta, prob.omega,
+                        prob.beta, options=options, stream=stream)
+
+
+def stokes_vmult(ctx, level, block, prec, src, dst, stream=None):
+    _check(load().stokes_vmult(ctx.handle, level, block, prec, _ptr(src), _ptr(dst), _stream(stream)), "stokes_vmult")
+
+
+def gmg_vcycle(ctx, prec, rhs, x, stream=None):
+    _check(load().gmg_vcycle(ctx.handle, prec, _ptr(rhs), _ptr(x), _stream(stream)), "gmg_vcycle")
+
+
+def stokes_solve(ctx, vcycle_prec, rhs, up, rtol=1e-8, max_it=1000, stream=None, check=True):
+    info = stokes_solve_info()
+    st = load().stokes_solve(ctx.handle, vcycle_prec, _ptr(rhs), _ptr(up), rtol, max_it, C.byref(info),
+                             _stream(stream))
+    if check:
+        _check(st, "stokes_solve")
+    return info
+
+
+def stokes_solve_host(ctx, vcycle_prec, rhs_host, up_host, rtol=1e-8, max_it=1000, stream=None, check=True):
+    info = stokes_solve_info()
+    st = load().stokes_solve_host(ctx.handle, vcycle_prec, _ptr(rhs_host), _ptr(up_host), rtol, max_it,
+                                  C.byref(info), _stream(stream))
+    if check:
+        _check(st, "stokes_solve_host")
+    return info
+
+
+def stokes_get_viscosity(ctx, level, mu, stream=None):
+    _check(load().stokes_get_viscosity(ctx.handle, level, _ptr(mu), _stream(stream)), "stokes_get_viscosity")
+
+
+def stokes_get_inv_diagonal(ctx, level, dinv, stream=None):
+    _check(load().stokes_get_inv_diagonal(ctx.handle, level, _ptr(dinv), _stream(stream)), "stokes_get_inv_diagonal")
+
+
+def stokes_get_lambda_max(ctx, level):
+    v = C.c_double()
+    _check(load().stokes_get_lambda_max(ctx.handle, level, C.byref(v)), "stokes_get_lambda_max")
+    return v.value
+
+
+def stokes_get_rhs(ctx, F, stream=None):
+    _check(load().stokes_get_rhs(ctx.handle, _ptr(F), _stream(stream)), "stokes_get_rhs")
+
+
+def stokes_prolongate(ctx, fine_level, prec, coarse, fine, add=False, stream=None):
+    _check(load().stokes_prolongate(ctx.handle, fine_level, prec, _ptr(coarse), _ptr(fine), int(add),
+                                    _stream(stream)), "stokes_prolongate")
+
+
+def stokes_restrict(ctx, fine_level, prec, fine, coarse, stream=None):
+    _check(load().stokes_restrict(ctx.handle, fine_level, prec, _ptr(fine), _ptr(coarse), _stream(stream)),
+           "stokes_restrict")
+
+
+def stokes_smooth(ctx, level, prec, b, x, zero_guess, stream=None):
+    _check(load().stokes_smooth(ctx.handle, level, prec, _ptr(b), _ptr(x), int(zero_guess), _stream(stream)),
+           "stokes_smooth")
+
+
+def stokes_coarse_solve(ctx, prec, b, x, stream=None):
+    _check(load().stokes_coarse_solve(ctx.handle, prec, _ptr(b), _ptr(x), _stream(stream)), "stokes_coarse_solve")
+
+
+def stokes_schur_inverse(ctx, rp, zp, stream=None):
+    _check(load().stokes_schur_inverse(ctx.handle, _ptr(rp), _ptr(zp), _stream(stream)), "stokes_schur_inverse")
+
+
+def stokes_precondition(ctx, vcycle_prec, r, z, stream=None):
+    _check(load().stokes_precondition(ctx.handle, vcycle_prec, _ptr(r), _ptr(z), _stream(stream)),
+           "stokes_precondition")
+
+
+def stokes_profile(enable):
+    _check(load().stokes_profile(int(enable)), "stokes_profile")
+
+
+def stokes_profile_read(reset=True):
+    """{class name: (ms, launches)} accumulated since the last reset."""
+    out = {}
+    for i, name in enumerate(PROF_CLASSES):
+        ms, n = C.c_double(), C.c_longlong()
+        _check(load().stokes_profile_read(i, C.byref(ms), C.byref(n), 0), "stokes_profile_read")
+        out[name] = (ms.value, n.value)
+    if reset:
+        _check(load().stokes_profile_read(0, None, None, 1), "stokes_profile_read")
+    return out
+
+
+def stokes_launch_count():
+    return int(load().stokes_launch_count())
+
+
+def header_functions(header=None):
+    """Names of the functions declared in include/stokes.h (used by the export test)."""
+    import re
+    header = header or os.path.join(os.path.dirname(HERE), "include", "stokes.h")
+    src = open(header).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?(?:long\s+long|[A-Za-z_][A-Za-z0-9_]*)\s*\*?\s*([a-z_][a-z0-9_]*)\s*\(",
+                       src, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "while", "return")))

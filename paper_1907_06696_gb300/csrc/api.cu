@@ -1,0 +1,913 @@
+// api.cu -- context, set-up, V-cycle, FGMRES and the C ABI (include/stokes.h).
+//
+// V-cycle (Section 2.2.1): per level l >= 1, one degree-k Jacobi-Chebyshev
+// pre-smoothing step from a zero guess, residual, restriction, recursion,
+// prolongation and one post-smoothing step; level 0 is solved exactly with
+// the dense FP64 inverse of its free block. Chebyshev recurrence: Y. Saad,
+// Iterative Methods for Sparse Linear Systems, 2nd ed., Alg. 12.1, with the
+// Jacobi-preconditioned residual; interval [lam_hi / range, lam_hi],
+// lam_hi = safety * Lanczos estimate of lambda_max(D^-1 A).
+// Outer solve (Section 2.2.2): right-preconditioned FGMRES(restart) in FP64
+// with P^-1 of eq. (stokes_precond); Gram-Schmidt as classical GS applied
+// twice (one fused multi-dot and one fused multi-axpy per pass).
+#include "../../include/stokes.h"
+#include "internal.cuh"
+#include "prof.cuh"
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace stk;
+
+namespace stk {
+
+// Process-wide launch counter and optional event timing (single host thread).
+namespace {
+struct ProfRec {
+    int cls;
+    cudaEvent_t a, b;
+};
+bool g_prof_on = false;
+long long g_launches = 0;
+std::vector<cudaEvent_t> g_pool;
+std::vector<ProfRec> g_recs;
+cudaEvent_t g_open = nullptr;
+double g_ms[PROF_NCLASS] = {};
+long long g_cnt[PROF_NCLASS] = {};
+
+cudaEvent_t take_event() {
+    if (!g_pool.empty()) {
+        cudaEvent_t e = g_pool.back();
+        g_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void drain() {
+    if (g_recs.empty()) return;
+    cudaDeviceSynchronize();
+    for (const ProfRec& r : g_recs) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) g_ms[r.cls] += ms;
+        g_cnt[r.cls] += 1;
+        g_pool.push_back(r.a);
+        g_pool.push_back(r.b);
+    }
+    g_recs.clear();
+}
+}  // namespace
+
+void prof_begin(int, cudaStream_t s) {
+    if (!g_prof_on) return;
+    g_open = take_event();
+    cudaEventRecord(g_open, s);
+}
+void prof_end(int cls, cudaStream_t s) {
+    if (!g_prof_on || !g_open) return;
+    cudaEvent_t e = take_event();
+    cudaEventRecord(e, s);
+    g_recs.push_back({cls, g_open, e});
+    g_open = nullptr;
+    if (g_recs.size() > 200000) drain();
+}
+void prof_count(int k) { g_launches += k; }
+
+}  // namespace stk
+
+namespace {
+
+thread_local std::string g_last_error;
+
+stokes_status fail(stokes_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+
+#define CK(expr)                                                                                         \
+    do {                                                                                                 \
+        cudaError_t _e = (expr);                                                                         \
+        if (_e != cudaSuccess)                                                                           \
+            return fail(_e == cudaErrorMemoryAllocation ? STOKES_ENOMEM : STOKES_ECUDA,                  \
+                        std::string(#expr) + ": " + cudaGetErrorString(_e));                             \
+    } while (0)
+
+#define CKS(expr)                                                                                        \
+    do {                                                                                                 \
+        stokes_status _s = (expr);                                                                       \
+        if (_s != STOKES_OK) return _s;                                                                  \
+    } while (0)
+
+template <typename T>
+struct LevelVecs {
+    T* b = nullptr;   // right-hand side of the level problem
+    T* x = nullptr;   // level solution / correction
+    T* r = nullptr;   // residual
+    T* d = nullptr;   // Chebyshev direction
+    T* t = nullptr;   // operator output
+    T* mu = nullptr;  // cell viscosity
+    T* dinv = nullptr;
+};
+
+struct Level {
+    LevelGeom g;
+    LevelVecs<double> v64;
+    LevelVecs<float> v32;
+    double lam_max = 0.0, lo = 0.0, hi = 0.0;
+};
+
+template <typename T> LevelVecs<T>& vecs(Level& L);
+template <> LevelVecs<double>& vecs<double>(Level& L) { return L.v64; }
+template <> LevelVecs<float>& vecs<float>(Level& L) { return L.v32; }
+
+}  // namespace
+
+struct stokes_ctx {
+    int n = 0, L = 0;
+    stokes_options opt{};
+    std::vector<Level> lev;
+    std::vector<void*> allocs;
+    double* ref_diag = nullptr;
+    double* F = nullptr;          // finest right-hand side (N_u)
+    double* mp_dinv = nullptr;    // 1 / diag(M_p)
+    double* p_weights = nullptr;  // int psi_l
+    double p_wsum = 1.0;
+    // Schur Chebyshev work (N_p each)
+    double *sp_d = nullptr, *sp_t = nullptr;
+    // preconditioner / operator work (N_u)
+    double* tu = nullptr;
+    float *stage_in = nullptr, *stage_out = nullptr;   // FP32 V-cycle input / output
+    // coarse level
+    int nf = 0;
+    int* free_idx = nullptr;
+    double* Ainv = nullptr;
+    // reductions
+    double* partials = nullptr;
+    double* dots = nullptr;       // device results (up to 2*restart+8)
+    double* dots_host = nullptr;  // pinned
+    // Krylov workspace (allocated on first solve)
+    size_t N = 0;
+    double *V = nullptr, *Z = nullptr, *w = nullptr, *bvec = nullptr, *hdev = nullptr;
+    int krylov_restart = 0;
+    // host-buffer solve
+    double *h_rhs_dev = nullptr, *h_up_dev = nullptr;
+};
+
+namespace {
+
+template <typename T>
+stokes_status dalloc(stokes_ctx* c, T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+    if (e != cudaSuccess) return fail(STOKES_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    c->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return STOKES_OK;
+}
+
+// Host reductions: copy k device scalars to host (synchronous on the stream).
+stokes_status fetch(stokes_ctx* c, int k, cudaStream_t s, double* out) {
+    CK(cudaMemcpyAsync(c->dots_host, c->dots, size_t(k) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int i = 0; i < k; ++i) out[i] = c->dots_host[i];
+    return STOKES_OK;
+}
+
+stokes_status dot(stokes_ctx* c, size_t n, const double* a, const double* b, cudaStream_t s, double* out) {
+    CK(launch_multidot(n, 1, a, n, b, c->partials, c->dots, s));
+    return fetch(c, 1, s, out);
+}
+
+// Largest eigenvalue of the symmetric tridiagonal matrix (alpha, beta) by Sturm bisection.
+double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& b) {
+    const int k = int(a.size());
+    double lo = a[0], hi = a[0];
+    for (int i = 0; i < k; ++i) {
+        double r = 0.0;
+        if (i > 0) r += std::fabs(b[i - 1]);
+        if (i < k - 1) r += std::fabs(b[i]);
+        lo = std::fmin(lo, a[i] - r);
+        hi = std::fmax(hi, a[i] + r);
+    }
+    auto count_below = [&](double x) {  // number of eigenvalues < x
+        int cnt = 0;
+        double q = a[0] - x;
+        if (q < 0) ++cnt;
+        for (int i = 1; i < k; ++i) {
+            if (q == 0.0) q = 1e-300;
+            q = a[i] - x - b[i - 1] * b[i - 1] / q;
+            if (q < 0) ++cnt;
+        }
+        return cnt;
+    };
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (count_below(mid) >= k) hi = mid; else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+template <typename T>
+stokes_status vmult_level(stokes_ctx* c, int l, const T* src, T* dst, cudaStream_t s) {
+    Level& L = c->lev[l];
+    CK(launch_vmult_A<T>(L.g, vecs<T>(L).mu, src, dst, s));
+    return STOKES_OK;
+}
+
+// One degree-k Chebyshev smoothing step on level l (x, b caller buffers of the level size).
+template <typename T>
+stokes_status smooth(stokes_ctx* c, int l, const T* b, T* x, bool zero_guess, cudaStream_t s) {
+    Level& L = c->lev[l];
+    LevelVecs<T>& v = vecs<T>(L);
+    const double theta = 0.5 * (L.hi + L.lo), delta = 0.5 * (L.hi - L.lo);
+    const double sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    const size_t n = L.g.n_u;
+    if (zero_guess) {
+        CK(launch_cheb_update<T>(n, b, nullptr, v.dinv, v.d, x, 0.0, 1.0 / theta, false, s));
+    } else {
+        CKS(vmult_level<T>(c, l, x, v.t, s));
+        CK(launch_cheb_update<T>(n, b, v.t, v.dinv, v.d, x, 0.0, 1.0 / theta, true, s));
+    }
+    for (int it = 1; it < c->opt.cheb_degree; ++it) {
+        CKS(vmult_level<T>(c, l, x, v.t, s));
+        const double rho_new = 1.0 / (2.0 * sigma - rho);
+        CK(launch_cheb_update<T>(n, b, v.t, v.dinv, v.d, x, rho_new * rho, 2.0 * rho_new / delta, true, s));
+        rho = rho_new;
+    }
+    return STOKES_OK;
+}
+
+template <typename T>
+stokes_status coarse_solve(stokes_ctx* c, const T* b, T* x, cudaStream_t s) {
+    Level& L0 = c->lev[0];
+    CK(cudaMemsetAsync(x, 0, L0.g.n_u * sizeof(T), s));
+    CK(launch_coarse_solve<T>(c->nf, c->free_idx, c->Ainv, b, x, s));
+    return STOKES_OK;
+}
+
+// x_l = V_l(b_l) with zero initial guess, level buffers.
+template <typename T>
+stokes_status vcycle_level(stokes_ctx* c, int l, cudaStream_t s) {
+    Level& L = c->lev[l];
+    LevelVecs<T>& v = vecs<T>(L);
+    if (l == 0) return coarse_solve<T>(c, v.b, v.x, s);
+    LevelVecs<T>& vc = vecs<T>(c->lev[l - 1]);
+    CKS(smooth<T>(c, l, v.b, v.x, true, s));
+    CKS(vmult_level<T>(c, l, v.x, v.t, s));
+    CK(launch_residual<T>(L.g.n_u, v.b, v.t, v.r, s));
+    CK(launch_restrict<T>(L.g, v.r, vc.b, s));
+    CKS(vcycle_level<T>(c, l - 1, s));
+    CK(launch_prolongate<T>(L.g, vc.x, v.x, true, s));
+    CKS(smooth<T>(c, l, v.b, v.x, false, s));
+    return STOKES_OK;
+}
+
+template <typename T>
+stokes_status vcycle(stokes_ctx* c, const T* rhs, T* x, cudaStream_t s) {
+    Level& F = c->lev[c->L - 1];
+    LevelVecs<T>& v = vecs<T>(F);
+    CK(cudaMemcpyAsync(v.b, rhs, F.g.n_u * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    CK(launch_zero_boundary<T>(F.g, v.b, s));
+    CKS(vcycle_level<T>(c, c->L - 1, s));
+    CK(cudaMemcpyAsync(x, v.x, F.g.n_u * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    CK(launch_copy_boundary<T>(F.g, rhs, x, s));
+    return STOKES_OK;
+}
+
+// z_p = S_hat^-1 r_p: Jacobi-Chebyshev on M_p, interval [1/8, 27/8], zero guess.
+stokes_status schur_inverse(stokes_ctx* c, const double* rp, double* zp, cudaStream_t s) {
+    const LevelGeom& g = c->lev[c->L - 1].g;
+    const double lo = 1.0 / 8.0, hi = 27.0 / 8.0;
+    const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    const double* mu = c->lev[c->L - 1].v64.mu;
+    CK(launch_cheb_update<double>(g.n_p, rp, nullptr, c->mp_dinv, c->sp_d, zp, 0.0, 1.0 / theta, false, s));
+    for (int it = 1; it < c->opt.schur_degree; ++it) {
+        CK(launch_mass_p(g, mu, zp, c->sp_t, s));
+        const double rho_new = 1.0 / (2.0 * sigma - rho);
+        CK(launch_cheb_update<double>(g.n_p, rp, c->sp_t, c->mp_dinv, c->sp_d, zp, rho_new * rho,
+                                      2.0 * rho_new / delta, true, s));
+        rho = rho_new;
+    }
+    return STOKES_OK;
+}
+
+stokes_status apply_stokes(stokes_ctx* c, const double* src, double* dst, cudaStream_t s) {
+    Level& F = c->lev[c->L - 1];
+    CK(launch_stokes_blocks(F.g, F.v64.mu, src, src + F.g.n_u, dst, dst + F.g.n_u, true, true, true, s));
+    return STOKES_OK;
+}
+
+// z = P^-1 r (eq. stokes_precond).
+stokes_status precondition(stokes_ctx* c, int prec, const double* r, double* z, cudaStream_t s) {
+    Level& F = c->lev[c->L - 1];
+    const size_t nu = F.g.n_u, np = F.g.n_p;
+    double* zp = z + nu;
+    CKS(schur_inverse(c, r + nu, zp, s));
+    CK(launch_axpby(np, -1.0, zp, 0.0, zp, s));                               // z_p = -S^-1 r_p
+    CK(launch_stokes_blocks(F.g, F.v64.mu, nullptr, zp, c->tu, nullptr, false, true, false, s));
+    CK(launch_axpby(nu, 1.0, r, -1.0, c->tu, s));                            // t = r_u - B^T z_p
+    if (prec == STOKES_FP64) {
+        CKS(vcycle<double>(c, c->tu, z, s));
+    } else {
+        CK(launch_cast_d2f(nu, c->tu, c->stage_in, s));
+        CKS(vcycle<float>(c, c->stage_in, c->stage_out, s));
+        CK(launch_cast_f2d(nu, c->stage_out, z, s));
+        CK(launch_copy_boundary<double>(F.g, c->tu, z, s));
+    }
+    return STOKES_OK;
+}
+
+stokes_status ensure_krylov(stokes_ctx* c) {
+    const int m = c->opt.restart;
+    if (c->V && c->krylov_restart == m) return STOKES_OK;
+    const LevelGeom& g = c->lev[c->L - 1].g;
+    c->N = g.n_u + g.n_p;
+    CKS(dalloc(c, &c->V, size_t(m + 1) * c->N));
+    CKS(dalloc(c, &c->Z, size_t(m) * c->N));
+    CKS(dalloc(c, &c->w, c->N));
+    CKS(dalloc(c, &c->bvec, c->N));
+    CKS(dalloc(c, &c->hdev, size_t(m + 2)));
+    c->krylov_restart = m;
+    return STOKES_OK;
+}
+
+stokes_status remove_pressure_mean(stokes_ctx* c, double* up, cudaStream_t s) {
+    const LevelGeom& g = c->lev[c->L - 1].g;
+    double wp = 0.0;
+    CKS(dot(c, g.n_p, c->p_weights, up + g.n_u, s, &wp));
+    CK(launch_add_scalar(g.n_p, -wp / c->p_wsum, up + g.n_u, s));
+    return STOKES_OK;
+}
+
+stokes_status fgmres(stokes_ctx* c, int prec, const double* b, double* x, double rtol, int max_it,
+                     stokes_solve_info* info, cudaStream_t s) {
+    CKS(ensure_krylov(c));
+    const size_t N = c->N;
+    const int m = c->opt.restart;
+    double* V = c->V;
+    double* Z = c->Z;
+    double* w = c->w;
+    double bnorm2 = 0.0;
+    CKS(dot(c, N, b, b, s, &bnorm2));
+    const double bnorm = std::sqrt(bnorm2);
+    int its = 0;
+    double est = 1.0;
+    stokes_status st = STOKES_NOT_CONVERGED;
+    std::vector<double> H(size_t(m + 1) * m), cs(m), sn(m), g(m + 1), y(m), h1(m + 2), h2(m + 2);
+    auto Hij = [&](int i, int j) -> double& { return H[size_t(i) * m + j]; };
+    if (bnorm == 0.0) {
+        CK(cudaMemsetAsync(x, 0, N * sizeof(double), s));
+        est = 0.0;
+        st = STOKES_OK;
+    }
+    while (st == STOKES_NOT_CONVERGED && its < max_it) {
+        CKS(apply_stokes(c, x, w, s));
+        CK(launch_axpby(N, 1.0, b, -1.0, w, s));                              // w = b - K x
+        double beta2 = 0.0;
+        CKS(dot(c, N, w, w, s, &beta2));
+        const double beta = std::sqrt(beta2);
+        if (!std::isfinite(beta)) { st = STOKES_BREAKDOWN; break; }
+        est = beta / bnorm;
+        if (beta <= rtol * bnorm) { st = STOKES_OK; break; }
+        CK(launch_axpby(N, 1.0 / beta, w, 0.0, V, s));
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int k = 0;
+        bool done = false;
+        for (int j = 0; j < m && its < max_it; ++j) {
+            double* vj = V + size_t(j) * N;
+            double* zj = Z + size_t(j) * N;
+            CKS(precondition(c, prec, vj, zj, s));
+            CKS(apply_stokes(c, zj, w, s));
+            // classical Gram-Schmidt, twice
+            CK(launch_multidot(N, j + 1, V, N, w, c->partials, c->hdev, s));
+            CK(launch_multiaxpy(N, j + 1, V, N, c->hdev, w, -1.0, s));
+            CK(cudaMemcpyAsync(c->dots_host, c->hdev, size_t(j + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            for (int i = 0; i <= j; ++i) h1[i] = c->dots_host[i];
+            CK(launch_multidot(N, j + 1, V, N, w, c->partials, c->hdev, s));
+            CK(launch_multiaxpy(N, j + 1, V, N, c->hdev, w, -1.0, s));
+            CK(cudaMemcpyAsync(c->dots_host, c->hdev, size_t(j + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            for (int i = 0; i <= j; ++i) h2[i] = c->dots_host[i];
+            double hn2 = 0.0;
+            CKS(dot(c, N, w, w, s, &hn2));
+            const double hn = std::sqrt(hn2);
+            if (!std::isfinite(hn)) { st = STOKES_BREAKDOWN; done = true; break; }
+            for (int i = 0; i <= j; ++i) Hij(i, j) = h1[i] + h2[i];
+            Hij(j + 1, j) = hn;
+            if (hn > 0.0) CK(launch_axpby(N, 1.0 / hn, w, 0.0, V + size_t(j + 1) * N, s));
+            for (int i = 0; i < j; ++i) {
+                const double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
+                Hij(i + 1, j) = -sn[i] * Hij(i, j) + cs[i] * Hij(i + 1, j);
+                Hij(i, j) = t;
+            }
+            const double den = std::hypot(Hij(j, j), Hij(j + 1, j));
+            cs[j] = Hij(j, j) / den;
+            sn[j] = Hij(j + 1, j) / den;
+            Hij(j, j) = den;
+            Hij(j + 1, j) = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            ++its;
+            k = j + 1;
+            est = std::fabs(g[j + 1]) / bnorm;
+            if (std::fabs(g[j + 1]) <= rtol * bnorm || hn == 0.0) { done = true; break; }
+        }
+        if (st == STOKES_BREAKDOWN) break;
+        for (int i = k - 1; i >= 0; --i) {
+            double t = g[i];
+            for (int l = i + 1; l < k; ++l) t -= Hij(i, l) * y[l];
+            y[i] = t / Hij(i, i);
+        }
+        CK(cudaMemcpyAsync(c->hdev, y.data(), size_t(k) * sizeof(double), cudaMemcpyHostToDevice, s));
+        CK(launch_multiaxpy(N, k, Z, N, c->hdev, x, 1.0, s));
+        CK(cudaStreamSynchronize(s));
+        if (done) st = (est <= rtol) ? STOKES_OK : st;
+    }
+    CKS(remove_pressure_mean(c, x, s));
+    // true residual
+    CKS(apply_stokes(c, x, w, s));
+    CK(launch_axpby(N, 1.0, b, -1.0, w, s));
+    double r2 = 0.0;
+    CKS(dot(c, N, w, w, s, &r2));
+    if (info) {
+        info->iterations = its;
+        info->rel_residual = est;
+        info->rel_residual_true = bnorm > 0 ? std::sqrt(r2) / bnorm : 0.0;
+        info->status = st;
+    }
+    if (st != STOKES_OK) return fail(st, st == STOKES_BREAKDOWN ? "FGMRES breakdown (non-finite norm)"
+                                                                 : "FGMRES reached max_it");
+    return STOKES_OK;
+}
+
+stokes_status check_level(const stokes_ctx* c, int& level) {
+    if (!c) return fail(STOKES_EINVAL, "null context");
+    if (level == -1) level = c->L - 1;
+    if (level < 0 || level >= c->L) return fail(STOKES_EINVAL, "level out of range");
+    return STOKES_OK;
+}
+
+stokes_status setup_impl(const stokes_mesh* mesh, const stokes_mu* mu, const stokes_bc* bc,
+                         const stokes_options* opt, cudaStream_t s, stokes_ctx* c) {
+    if (opt) c->opt = *opt; else stokes_default_options(&c->opt);
+    const stokes_options& o = c->opt;
+    if (o.cheb_degree < 1 || o.smoothing_range <= 1.0 || o.eig_safety <= 0.0 || o.lanczos_steps < 1 ||
+        o.schur_degree < 1 || o.restart < 1 || o.restart > 500)
+        return fail(STOKES_EINVAL, "bad options");
+    c->n = mesh->n;
+    c->L = mesh->n_levels;
+    const int L = c->L;
+    c->lev.resize(L);
+    for (int l = 0; l < L; ++l) c->lev[l].g = make_geom(mesh->n >> (L - 1 - l));
+    const LevelGeom& gf = c->lev[L - 1].g;
+    // ---- per-level storage
+    for (int l = 0; l < L; ++l) {
+        Level& Lv = c->lev[l];
+        const size_t nu = Lv.g.n_u, nc = Lv.g.cells;
+        for (auto* p : {&Lv.v64.b, &Lv.v64.x, &Lv.v64.r, &Lv.v64.d, &Lv.v64.t, &Lv.v64.dinv}) CKS(dalloc(c, p, nu));
+        for (auto* p : {&Lv.v32.b, &Lv.v32.x, &Lv.v32.r, &Lv.v32.d, &Lv.v32.t, &Lv.v32.dinv}) CKS(dalloc(c, p, nu));
+        CKS(dalloc(c, &Lv.v64.mu, nc));
+        CKS(dalloc(c, &Lv.v32.mu, nc));
+    }
+    CKS(dalloc(c, &c->ref_diag, 81));
+    CKS(dalloc(c, &c->F, gf.n_u));
+    CKS(dalloc(c, &c->mp_dinv, gf.n_p));
+    CKS(dalloc(c, &c->p_weights, gf.n_p));
+    CKS(dalloc(c, &c->sp_d, gf.n_p));
+    CKS(dalloc(c, &c->sp_t, gf.n_p));
+    CKS(dalloc(c, &c->tu, gf.n_u));
+    CKS(dalloc(c, &c->stage_in, gf.n_u));
+    CKS(dalloc(c, &c->stage_out, gf.n_u));
+    CKS(dalloc(c, &c->partials, size_t(multidot_blocks()) * (o.restart + 8)));
+    CKS(dalloc(c, &c->dots, size_t(o.restart + 8)));
+    CK(cudaMallocHost(&c->dots_host, size_t(o.restart + 8) * sizeof(double)));
+    // ---- viscosity (Section 2.3) and right-hand side (Section 3.2)
+    double* centres = nullptr;
+    if (mu->kind == 0) {
+        const int ns = mu->n_sinkers;
+        if (ns < 0 || (ns > 0 && !mu->centres)) return fail(STOKES_EINVAL, "bad sinker list");
+        CKS(dalloc(c, &centres, size_t(3) * (ns > 0 ? ns : 1)));
+        if (ns > 0) CK(cudaMemcpyAsync(centres, mu->centres, sizeof(double) * 3 * ns, cudaMemcpyHostToDevice, s));
+        CK(launch_mu_sinker(gf, centres, ns, mu->mu_min, mu->mu_max, mu->delta, mu->omega, c->lev[L - 1].v64.mu, s));
+        CK(launch_rhs_sinker(gf, centres, ns, mu->delta, mu->omega, mu->beta, c->F, s));
+    } else if (mu->kind == 1) {
+        if (!mu->mu_q) return fail(STOKES_EINVAL, "mu_q is null");
+        double* q = nullptr;
+        CKS(dalloc(c, &q, gf.cells * 27));
+        CK(cudaMemcpyAsync(q, mu->mu_q, sizeof(double) * 27 * gf.cells, cudaMemcpyHostToDevice, s));
+        CK(launch_mu_from_q(gf, q, c->lev[L - 1].v64.mu, s));
+        CK(cudaMemsetAsync(c->F, 0, gf.n_u * sizeof(double), s));
+    } else {
+        return fail(STOKES_EINVAL, "unknown viscosity kind");
+    }
+    for (int l = L - 2; l >= 0; --l)
+        CK(launch_mu_restrict(c->lev[l].g, c->lev[l + 1].v64.mu, c->lev[l].v64.mu, s));
+    CK(launch_ref_diag(c->ref_diag, s));
+    for (int l = 0; l < L; ++l) {
+        Level& Lv = c->lev[l];
+        CK(launch_cast_d2f(Lv.g.cells, Lv.v64.mu, Lv.v32.mu, s));
+        CK(launch_inv_diag(Lv.g, Lv.v64.mu, c->ref_diag, Lv.v64.dinv, s));
+        CK(launch_cast_d2f(Lv.g.n_u, Lv.v64.dinv, Lv.v32.dinv, s));
+    }
+    // ---- pressure mass diagonal and weights (Section 2.2.2)
+    CK(launch_mass_p_diag(gf, c->lev[L - 1].v64.mu, c->sp_t, c->p_weights, s));
+    CK(launch_recip(gf.n_p, c->sp_t, c->mp_dinv, s));
+    {
+        double* ones = c->sp_d;
+        CK(launch_fill(gf.n_p, 1.0, ones, s));
+        CKS(dot(c, gf.n_p, c->p_weights, ones, s, &c->p_wsum));
+    }
+    // ---- Lanczos estimates of lambda_max(D^-1 A) per level >= 1
+    for (int l = 1; l < L; ++l) {
+        Level& Lv = c->lev[l];
+        const size_t n = Lv.g.n_u;
+        double *sq = Lv.v64.r, *v = Lv.v64.x, *vp = Lv.v64.d, *w = Lv.v64.t, *tmp = Lv.v64.b;
+        CK(launch_sqrt_vec(n, Lv.v64.dinv, sq, s));
+        CK(launch_splitmix_vector(n, uint64_t(1907000 + l), nullptr, v, s));
+        CK(launch_zero_boundary<double>(Lv.g, v, s));
+        double vv = 0.0;
+        CKS(dot(c, n, v, v, s, &vv));
+        CK(launch_axpby(n, 1.0 / std::sqrt(vv), v, 0.0, v, s));
+        CK(cudaMemsetAsync(vp, 0, n * sizeof(double), s));
+        double beta_prev = 0.0;
+        std::vector<double> al, be;
+        for (int it = 0; it < o.lanczos_steps; ++it) {
+            CK(launch_mul(n, sq, v, tmp, s));
+            CK(launch_vmult_A<double>(Lv.g, Lv.v64.mu, tmp, w, s));
+            CK(launch_mul(n, sq, w, w, s));
+            double alpha = 0.0;
+            CKS(dot(c, n, w, v, s, &alpha));
+            CK(launch_axpby(n, -alpha, v, 1.0, w, s));
+            CK(launch_axpby(n, -beta_prev, vp, 1.0, w, s));
+            double b2 = 0.0;
+            CKS(dot(c, n, w, w, s, &b2));
+            const double beta = std::sqrt(b2);
+            al.push_back(alpha);
+            if (beta <= 1e-12 * std::fabs(alpha)) break;
+            be.push_back(beta);
+            std::swap(vp, v);                                   // v_prev <- v
+            CK(launch_axpby(n, 1.0 / beta, w, 0.0, v, s));      // v <- w / beta
+            beta_prev = beta;
+        }
+        Lv.lam_max = tridiag_max_eig(al, be);
+        Lv.hi = o.eig_safety * Lv.lam_max;
+        Lv.lo = Lv.hi / o.smoothing_range;
+    }
+    // ---- dense inverse of the coarsest free block (FP64)
+    {
+        Level& L0 = c->lev[0];
+        const int M = L0.g.M;
+        std::vector<int> idx;
+        for (int comp = 0; comp < 3; ++comp)
+            for (int k = 1; k < M - 1; ++k)
+                for (int j = 1; j < M - 1; ++j)
+                    for (int i = 1; i < M - 1; ++i) idx.push_back(int(comp * L0.g.nodes + i + size_t(M) * (j + size_t(M) * k)));
+        const int nf = int(idx.size());
+        c->nf = nf;
+        if (nf > 0) {
+            CKS(dalloc(c, &c->free_idx, size_t(nf)));
+            CK(cudaMemcpyAsync(c->free_idx, idx.data(), sizeof(int) * nf, cudaMemcpyHostToDevice, s));
+            std::vector<double> A(size_t(nf) * nf), col(L0.g.n_u);
+            double *e = L0.v64.b, *Ae = L0.v64.t;
+            for (int j = 0; j < nf; ++j) {
+                CK(cudaMemsetAsync(e, 0, L0.g.n_u * sizeof(double), s));
+                const double one = 1.0;
+                CK(cudaMemcpyAsync(e + idx[j], &one, sizeof(double), cudaMemcpyHostToDevice, s));
+                CK(launch_vmult_A<double>(L0.g, L0.v64.mu, e, Ae, s));
+                CK(cudaMemcpyAsync(col.data(), Ae, L0.g.n_u * sizeof(double), cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                for (int i = 0; i < nf; ++i) A[size_t(i) * nf + j] = col[idx[i]];
+            }
+            // Cholesky A = R^T R (upper R in place), then the inverse column by column.
+            std::vector<double> R = A;
+            for (int i = 0; i < nf; ++i) {
+                for (int k = 0; k < i; ++k) {
+                    const double rki = R[size_t(k) * nf + i];
+                    for (int jj = i; jj < nf; ++jj) R[size_t(i) * nf + jj] -= rki * R[size_t(k) * nf + jj];
+                }
+                const double d = R[size_t(i) * nf + i];
+                if (!(d > 0.0)) return fail(STOKES_EINVAL, "coarse matrix is not positive definite");
+                const double sd = std::sqrt(d);
+                for (int jj = i; jj < nf; ++jj) R[size_t(i) * nf + jj] /= sd;
+            }
+            std::vector<double> Ainv(size_t(nf) * nf), zz(nf);
+            for (int j = 0; j < nf; ++j) {
+                for (int i = 0; i < nf; ++i) {   // R^T z = e_j
+                    double t = (i == j) ? 1.0 : 0.0;
+                    for (int k = 0; k < i; ++k) t -= R[size_t(k) * nf + i] * zz[k];
+                    zz[i] = t / R[size_t(i) * nf + i];
+                }
+                for (int i = nf - 1; i >= 0; --i) {   // R x = z
+                    double t = zz[i];
+                    for (int k = i + 1; k < nf; ++k) t -= R[size_t(i) * nf + k] * Ainv[size_t(k) * nf + j];
+                    Ainv[size_t(i) * nf + j] = t / R[size_t(i) * nf + i];
+                }
+            }
+            CKS(dalloc(c, &c->Ainv, size_t(nf) * nf));
+            CK(cudaMemcpyAsync(c->Ainv, Ainv.data(), sizeof(double) * nf * nf, cudaMemcpyHostToDevice, s));
+        }
+    }
+    CK(cudaStreamSynchronize(s));
+    return STOKES_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void stokes_default_options(stokes_options* opt) {
+    if (!opt) return;
+    opt->cheb_degree = 4;
+    opt->smoothing_range = 15.0;
+    opt->eig_safety = 1.2;
+    opt->lanczos_steps = 12;
+    opt->schur_degree = 5;
+    opt->restart = 50;
+}
+
+const char* stokes_strerror(stokes_status s) {
+    switch (s) {
+        case STOKES_OK: return "ok";
+        case STOKES_EINVAL: return "invalid argument";
+        case STOKES_ENOMEM: return "out of memory";
+        case STOKES_ECUDA: return "CUDA error";
+        case STOKES_NOT_CONVERGED: return "not converged";
+        case STOKES_BREAKDOWN: return "breakdown";
+        case STOKES_TIMEOUT: return "timeout";
+        case STOKES_EMESH: return "unsupported mesh";
+    }
+    return "unknown status";
+}
+
+const char* stokes_last_error(void) { return g_last_error.c_str(); }
+
+stokes_status stokes_profile(int enable) {
+    if (!enable) drain();
+    g_prof_on = enable != 0;
+    return STOKES_OK;
+}
+
+stokes_status stokes_profile_read(int cls, double* ms, long long* launches, int reset) {
+    if (cls < 0 || cls >= PROF_NCLASS) return fail(STOKES_EINVAL, "bad profile class");
+    drain();
+    if (ms) *ms = g_ms[cls];
+    if (launches) *launches = g_cnt[cls];
+    if (reset) {
+        for (int i = 0; i < PROF_NCLASS; ++i) { g_ms[i] = 0.0; g_cnt[i] = 0; }
+    }
+    return STOKES_OK;
+}
+
+long long stokes_launch_count(void) { return g_launches; }
+
+stokes_status stokes_setup(const stokes_mesh* mesh, const stokes_mu* mu, const stokes_bc* bc,
+                           const stokes_options* opt, void* stream, stokes_ctx** out) {
+    g_last_error.clear();
+    if (!mesh || !mu || !bc || !out) return fail(STOKES_EINVAL, "null argument");
+    *out = nullptr;
+    if (mesh->kind != 0) return fail(STOKES_EMESH, "only the uniform mesh kind 0 is supported");
+    if (bc->noslip_faces != 0x3Fu) return fail(STOKES_EMESH, "all six walls must be no-slip (0x3F)");
+    if (mesh->n_levels < 1 || mesh->n_levels > 12 || mesh->n < 1 || mesh->n > 1024)
+        return fail(STOKES_EINVAL, "n or n_levels out of range");
+    const int cdiv = 1 << (mesh->n_levels - 1);
+    if (mesh->n % cdiv != 0) return fail(STOKES_EMESH, "n must be c * 2^(n_levels-1)");
+    const int coarse = mesh->n / cdiv;
+    if (coarse > 4) return fail(STOKES_EMESH, "coarsest level must have at most 4 cells per axis");
+    stokes_ctx* c = new (std::nothrow) stokes_ctx();
+    if (!c) return fail(STOKES_ENOMEM, "host allocation failed");
+    stokes_status st = setup_impl(mesh, mu, bc, opt, static_cast<cudaStream_t>(stream), c);
+    if (st != STOKES_OK) {
+        const std::string msg = g_last_error;
+        stokes_destroy(c);
+        g_last_error = msg;
+        return st;
+    }
+    *out = c;
+    return STOKES_OK;
+}
+
+void stokes_destroy(stokes_ctx* c) {
+    if (!c) return;
+    cudaDeviceSynchronize();
+    for (void* p : c->allocs) cudaFree(p);
+    if (c->dots_host) cudaFreeHost(c->dots_host);
+    delete c;
+}
+
+size_t stokes_size(const stokes_ctx* c, int level, int what) {
+    if (!c) return 0;
+    if (level == -1) level = c->L - 1;
+    if (level < 0 || level >= c->L) return 0;
+    const LevelGeom& g = c->lev[level].g;
+    switch (what) {
+        case 0: return g.n_u;
+        case 1: return g.n_p;
+        case 2: return g.cells;
+        case 3: return size_t(g.n);
+        case 4: return size_t(c->L);
+    }
+    return 0;
+}
+
+stokes_status stokes_vmult(stokes_ctx* c, int level, int block, int prec, const void* src, void* dst,
+                           void* stream) {
+    CKS(check_level(c, level));
+    if (!src || !dst) return fail(STOKES_EINVAL, "null vector");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Level& Lv = c->lev[level];
+    if (block == STOKES_BLOCK_A) {
+        if (prec == STOKES_FP32) {
+            CK(launch_vmult_A<float>(Lv.g, Lv.v32.mu, static_cast<const float*>(src), static_cast<float*>(dst), s));
+        } else if (prec == STOKES_FP64) {
+            CK(launch_vmult_A<double>(Lv.g, Lv.v64.mu, static_cast<const double*>(src), static_cast<double*>(dst), s));
+        } else {
+            return fail(STOKES_EINVAL, "bad precision");
+        }
+        return STOKES_OK;
+    }
+    if (prec != STOKES_FP64) return fail(STOKES_EINVAL, "B, B^T, M_p and Stokes blocks are FP64 only");
+    if (level != c->L - 1) return fail(STOKES_EINVAL, "B, B^T, M_p and Stokes blocks are finest-level only");
+    const double* sd = static_cast<const double*>(src);
+    double* dd = static_cast<double*>(dst);
+    switch (block) {
+        case STOKES_BLOCK_B:
+            CK(launch_stokes_blocks(Lv.g, Lv.v64.mu, sd, nullptr, nullptr, dd, false, false, true, s));
+            return STOKES_OK;
+        case STOKES_BLOCK_BT:
+            CK(launch_stokes_blocks(Lv.g, Lv.v64.mu, nullptr, sd, dd, nullptr, false, true, false, s));
+            return STOKES_OK;
+        case STOKES_BLOCK_MP:
+            CK(launch_mass_p(Lv.g, Lv.v64.mu, sd, dd, s));
+            return STOKES_OK;
+        case STOKES_BLOCK_STOKES:
+            return apply_stokes(c, sd, dd, s);
+    }
+    return fail(STOKES_EINVAL, "bad block");
+}
+
+stokes_status gmg_vcycle(stokes_ctx* c, int prec, const void* rhs, void* x, void* stream) {
+    if (!c || !rhs || !x) return fail(STOKES_EINVAL, "null argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (prec == STOKES_FP32) return vcycle<float>(c, static_cast<const float*>(rhs), static_cast<float*>(x), s);
+    if (prec == STOKES_FP64) return vcycle<double>(c, static_cast<const double*>(rhs), static_cast<double*>(x), s);
+    return fail(STOKES_EINVAL, "bad precision");
+}
+
+stokes_status stokes_solve(stokes_ctx* c, int vcycle_prec, const double* rhs, double* up, double rtol, int max_it,
+                           stokes_solve_info* info, void* stream) {
+    if (!c || !up) return fail(STOKES_EINVAL, "null argument");
+    if (vcycle_prec != STOKES_FP32 && vcycle_prec != STOKES_FP64) return fail(STOKES_EINVAL, "bad precision");
+    if (!(rtol > 0.0) || max_it < 1) return fail(STOKES_EINVAL, "bad rtol or max_it");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const auto t0 = std::chrono::steady_clock::now();
+    CKS(ensure_krylov(c));
+    const LevelGeom& g = c->lev[c->L - 1].g;
+    const double* b = rhs;
+    if (!b) {
+        CK(cudaMemcpyAsync(c->bvec, c->F, g.n_u * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemsetAsync(c->bvec + g.n_u, 0, g.n_p * sizeof(double), s));
+        b = c->bvec;
+    }
+    stokes_status st = fgmres(c, vcycle_prec, b, up, rtol, max_it, info, s);
+    const auto t1 = std::chrono::steady_clock::now();
+    if (info) {
+        info->seconds = std::chrono::duration<double>(t1 - t0).count();
+        info->status = st;
+    }
+    return st;
+}
+
+stokes_status stokes_solve_host(stokes_ctx* c, int vcycle_prec, const double* rhs_host, double* up_host,
+                                double rtol, int max_it, stokes_solve_info* info, void* stream) {
+    if (!c || !up_host) return fail(STOKES_EINVAL, "null argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const LevelGeom& g = c->lev[c->L - 1].g;
+    const size_t N = g.n_u + g.n_p;
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!c->h_up_dev) {
+        CKS(dalloc(c, &c->h_up_dev, N));
+        CKS(dalloc(c, &c->h_rhs_dev, N));
+    }
+    const double* rhs_dev = nullptr;
+    if (rhs_host) {
+        CK(cudaMemcpyAsync(c->h_rhs_dev, rhs_host, N * sizeof(double), cudaMemcpyHostToDevice, s));
+        rhs_dev = c->h_rhs_dev;
+    }
+    CK(cudaMemsetAsync(c->h_up_dev, 0, N * sizeof(double), s));
+    stokes_status st = stokes_solve(c, vcycle_prec, rhs_dev, c->h_up_dev, rtol, max_it, info, stream);
+    if (st != STOKES_OK && st != STOKES_NOT_CONVERGED) return st;
+    CK(cudaMemcpyAsync(up_host, c->h_up_dev, N * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (info) info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return st;
+}
+
+stokes_status stokes_get_viscosity(stokes_ctx* c, int level, double* mu_dev, void* stream) {
+    CKS(check_level(c, level));
+    if (!mu_dev) return fail(STOKES_EINVAL, "null pointer");
+    Level& Lv = c->lev[level];
+    CK(cudaMemcpyAsync(mu_dev, Lv.v64.mu, Lv.g.cells * sizeof(double), cudaMemcpyDeviceToDevice,
+                       static_cast<cudaStream_t>(stream)));
+    return STOKES_OK;
+}
+
+stokes_status stokes_get_inv_diagonal(stokes_ctx* c, int level, double* dinv_dev, void* stream) {
+    CKS(check_level(c, level));
+    if (!dinv_dev) return fail(STOKES_EINVAL, "null pointer");
+    Level& Lv = c->lev[level];
+    CK(cudaMemcpyAsync(dinv_dev, Lv.v64.dinv, Lv.g.n_u * sizeof(double), cudaMemcpyDeviceToDevice,
+                       static_cast<cudaStream_t>(stream)));
+    return STOKES_OK;
+}
+
+stokes_status stokes_get_lambda_max(stokes_ctx* c, int level, double* lam_host) {
+    CKS(check_level(c, level));
+    if (!lam_host) return fail(STOKES_EINVAL, "null pointer");
+    *lam_host = c->lev[level].lam_max;
+    return STOKES_OK;
+}
+
+stokes_status stokes_get_rhs(stokes_ctx* c, double* F_dev, void* stream) {
+    if (!c || !F_dev) return fail(STOKES_EINVAL, "null argument");
+    const LevelGeom& g = c->lev[c->L - 1].g;
+    CK(cudaMemcpyAsync(F_dev, c->F, g.n_u * sizeof(double), cudaMemcpyDeviceToDevice,
+                       static_cast<cudaStream_t>(stream)));
+    return STOKES_OK;
+}
+
+stokes_status stokes_prolongate(stokes_ctx* c, int fine_level, int prec, const void* coarse, void* fine, int add,
+                                void* stream) {
+    CKS(check_level(c, fine_level));
+    if (fine_level < 1) return fail(STOKES_EINVAL, "fine_level must be >= 1");
+    if (!coarse || !fine) return fail(STOKES_EINVAL, "null vector");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const LevelGeom& g = c->lev[fine_level].g;
+    if (prec == STOKES_FP32)
+        CK(launch_prolongate<float>(g, static_cast<const float*>(coarse), static_cast<float*>(fine), add != 0, s));
+    else if (prec == STOKES_FP64)
+        CK(launch_prolongate<double>(g, static_cast<const double*>(coarse), static_cast<double*>(fine), add != 0, s));
+    else
+        return fail(STOKES_EINVAL, "bad precision");
+    return STOKES_OK;
+}
+
+stokes_status stokes_restrict(stokes_ctx* c, int fine_level, int prec, const void* fine, void* coarse,
+                              void* stream) {
+    CKS(check_level(c, fine_level));
+    if (fine_level < 1) return fail(STOKES_EINVAL, "fine_level must be >= 1");
+    if (!coarse || !fine) return fail(STOKES_EINVAL, "null vector");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const LevelGeom& g = c->lev[fine_level].g;
+    if (prec == STOKES_FP32)
+        CK(launch_restrict<float>(g, static_cast<const float*>(fine), static_cast<float*>(coarse), s));
+    else if (prec == STOKES_FP64)
+        CK(launch_restrict<double>(g, static_cast<const double*>(fine), static_cast<double*>(coarse), s));
+    else
+        return fail(STOKES_EINVAL, "bad precision");
+    return STOKES_OK;
+}
+
+stokes_status stokes_smooth(stokes_ctx* c, int level, int prec, const void* b, void* x, int zero_guess,
+                            void* stream) {
+    CKS(check_level(c, level));
+    if (level < 1) return fail(STOKES_EINVAL, "smoothing needs level >= 1");
+    if (!b || !x) return fail(STOKES_EINVAL, "null vector");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (prec == STOKES_FP32)
+        return smooth<float>(c, level, static_cast<const float*>(b), static_cast<float*>(x), zero_guess != 0, s);
+    if (prec == STOKES_FP64)
+        return smooth<double>(c, level, static_cast<const double*>(b), static_cast<double*>(x), zero_guess != 0, s);
+    return fail(STOKES_EINVAL, "bad precision");
+}
+
+stokes_status stokes_coarse_solve(stokes_ctx* c, int prec, const void* b, void* x, void* stream) {
+    if (!c || !b || !x) return fail(STOKES_EINVAL, "null argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (prec == STOKES_FP32) return coarse_solve<float>(c, static_cast<const float*>(b), static_cast<float*>(x), s);
+    if (prec == STOKES_FP64) return coarse_solve<double>(c, static_cast<const double*>(b), static_cast<double*>(x), s);
+    return fail(STOKES_EINVAL, "bad precision");
+}
+
+stokes_status stokes_schur_inverse(stokes_ctx* c, const double* rp, double* zp, void* stream) {
+    if (!c || !rp || !zp) return fail(STOKES_EINVAL, "null argument");
+    return schur_inverse(c, rp, zp, static_cast<cudaStream_t>(stream));
+}
+
+stokes_status stokes_precondition(stokes_ctx* c, int vcycle_prec, const double* r, double* z, void* stream) {
+    if (!c || !r || !z) return fail(STOKES_EINVAL, "null argument");
+    if (vcycle_prec != STOKES_FP32 && vcycle_prec != STOKES_FP64) return fail(STOKES_EINVAL, "bad precision");
+    return precondition(c, vcycle_prec, r, z, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,106 @@
+// internal.cuh -- launchers shared by the translation units of the library.
+// Not part of the public ABI (include/stokes.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+namespace stk {
+
+// Geometry of one uniform level: n cells per axis, Q2 lattice M = 2n+1.
+struct LevelGeom {
+    int n;
+    int M;
+    size_t nodes;    // M^3
+    size_t n_u;      // 3 M^3
+    size_t cells;    // n^3
+    size_t n_p;      // (n+1)^3
+    double h;
+};
+
+inline LevelGeom make_geom(int n) {
+    LevelGeom g;
+    g.n = n;
+    g.M = 2 * n + 1;
+    g.nodes = size_t(g.M) * g.M * g.M;
+    g.n_u = 3 * g.nodes;
+    g.cells = size_t(n) * n * n;
+    g.n_p = size_t(n + 1) * (n + 1) * (n + 1);
+    g.h = 1.0 / n;
+    return g;
+}
+
+// ---- operators (ops.cu) ----
+// dst = A_c src on one level (constrained rows: identity).
+template <typename T>
+cudaError_t launch_vmult_A(const LevelGeom& g, const T* mu, const T* src, T* dst, cudaStream_t s);
+// Finest-level FP64 blocks. Flags select the parts of [[A, B^T], [B, 0]]:
+// the u-part of dst gets A u (DO_A) + B^T p (DO_BT), the p-part gets B u (DO_B).
+// src_u / src_p may be null when unused; dst parts are overwritten.
+cudaError_t launch_stokes_blocks(const LevelGeom& g, const double* mu, const double* src_u, const double* src_p,
+                                 double* dst_u, double* dst_p, bool do_a, bool do_bt, bool do_b,
+                                 cudaStream_t s);
+// dst = M_p src (weighted pressure mass, FP64).
+cudaError_t launch_mass_p(const LevelGeom& g, const double* mu, const double* src, double* dst, cudaStream_t s);
+// diag(M_p) and int psi_l (pressure weights), FP64.
+cudaError_t launch_mass_p_diag(const LevelGeom& g, const double* mu, double* diag, double* weights,
+                               cudaStream_t s);
+// Diagonal of the reference cell operator (81 values, mu = h = 1).
+cudaError_t launch_ref_diag(double* ref_diag81, cudaStream_t s);
+// dinv = 1 / diag(A_c) on free DoFs, 0 on constrained ones.
+cudaError_t launch_inv_diag(const LevelGeom& g, const double* mu, const double* ref_diag81, double* dinv,
+                            cudaStream_t s);
+// Cell viscosity on the finest level from the sinker formula (harmonic average).
+cudaError_t launch_mu_sinker(const LevelGeom& g, const double* centres, int n_sinkers, double mu_min,
+                             double mu_max, double delta, double omega, double* mu, cudaStream_t s);
+// Cell viscosity from values at the quadrature points (harmonic average).
+cudaError_t launch_mu_from_q(const LevelGeom& g, const double* mu_q, double* mu, cudaStream_t s);
+// Parent viscosity = mean of 8 children.
+cudaError_t launch_mu_restrict(const LevelGeom& coarse, const double* mu_fine, double* mu_coarse, cudaStream_t s);
+// F = int phi . f, f = (0,0,beta(X-1)) at the Gauss points (accumulates into zeroed F).
+cudaError_t launch_rhs_sinker(const LevelGeom& g, const double* centres, int n_sinkers, double delta,
+                              double omega, double beta, double* F, cudaStream_t s);
+
+// ---- vectors and transfers (vec.cu) ----
+template <typename T>
+cudaError_t launch_prolongate(const LevelGeom& fine, const T* coarse, T* finev, bool add, cudaStream_t s);
+template <typename T>
+cudaError_t launch_restrict(const LevelGeom& fine, const T* finev, T* coarse, cudaStream_t s);
+// Chebyshev update: r = Dinv (b - Ax) (Ax may be null = 0); d = c1 d + c2 r; x = (x_valid ? x : 0) + d.
+template <typename T>
+cudaError_t launch_cheb_update(size_t n, const T* b, const T* Ax, const T* dinv, T* d, T* x, double c1, double c2,
+                               bool x_valid, cudaStream_t s);
+// r = b - Ax
+template <typename T>
+cudaError_t launch_residual(size_t n, const T* b, const T* Ax, T* r, cudaStream_t s);
+// Zero the velocity entries on boundary nodes of a level vector.
+template <typename T>
+cudaError_t launch_zero_boundary(const LevelGeom& g, T* x, cudaStream_t s);
+// out = in on boundary nodes (identity rows).
+template <typename T>
+cudaError_t launch_copy_boundary(const LevelGeom& g, const T* in, T* out, cudaStream_t s);
+// Casts with the boundary entries zeroed (to_boundary_zero) or kept.
+cudaError_t launch_cast_d2f(size_t n, const double* in, float* out, cudaStream_t s);
+cudaError_t launch_cast_f2d(size_t n, const float* in, double* out, cudaStream_t s);
+// Coarse solve: x[free[i]] = sum_j Ainv[i][j] b[free[j]], FP64 arithmetic; x elsewhere untouched.
+template <typename T>
+cudaError_t launch_coarse_solve(int nf, const int* free_idx, const double* Ainv, const T* b, T* x, cudaStream_t s);
+
+// FP64 vector ops.
+cudaError_t launch_axpby(size_t n, double a, const double* x, double b, double* y, cudaStream_t s);   // y = a x + b y
+cudaError_t launch_mul(size_t n, const double* a, const double* x, double* y, cudaStream_t s);         // y = a .* x
+cudaError_t launch_sqrt_vec(size_t n, const double* a, double* y, cudaStream_t s);                     // y = sqrt(a)
+cudaError_t launch_fill(size_t n, double v, double* y, cudaStream_t s);
+cudaError_t launch_recip(size_t n, const double* a, double* y, cudaStream_t s);                       // y = 1 / a
+cudaError_t launch_add_scalar(size_t n, double v, double* y, cudaStream_t s);                          // y += v
+cudaError_t launch_splitmix_vector(size_t n, uint64_t seed, const double* mask, double* y, cudaStream_t s);
+// Multi-dot: out[i] = sum_e V[i*ld + e] * w[e], i < k, deterministic two-pass reduction through `partials`.
+cudaError_t launch_multidot(size_t n, int k, const double* V, size_t ld, const double* w, double* partials,
+                            double* out, cudaStream_t s);
+int multidot_blocks();
+// w -= sum_i h[i] V[i*ld + :], i < k (h on device); with sign = +1 adds instead.
+cudaError_t launch_multiaxpy(size_t n, int k, const double* V, size_t ld, const double* h, double* w, double sign,
+                             cudaStream_t s);
+
+}  // namespace stk

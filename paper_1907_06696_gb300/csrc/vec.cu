@@ -1,0 +1,350 @@
+// vec.cu -- level transfers, Chebyshev updates, coarse solve and the FP64
+// vector kernels of the Krylov solver.
+//
+// Transfers (Section 2.2.1; level data of Section 2.3): prolongation is the
+// Q2 embedding of a coarse field into the fine space. Along one axis, fine
+// node i_f of a fine level with 2 nc cells takes the coarse value at i_f/2
+// when i_f is even; when odd it sits at 1/4 or 3/4 of coarse cell m = i_f/4
+// and takes l_0, l_1, l_2 of the coarse cell at that point:
+// (3/8, 3/4, -1/8) at 1/4 and (-1/8, 3/4, 3/8) at 3/4. The 3D weights are the
+// products over the axes. Restriction is the exact transpose, evaluated as a
+// gather per coarse node (no atomics).
+#include "internal.cuh"
+#include "prof.cuh"
+
+#define LAUNCH(cls, s, ...)              \
+    do {                                \
+        prof_begin((cls), (s));         \
+        __VA_ARGS__;                    \
+        prof_end((cls), (s));           \
+        prof_count(1);                  \
+    } while (0)
+
+namespace stk {
+
+namespace {
+
+inline unsigned blocks_for(size_t n, int t) { return unsigned((n + t - 1) / t); }
+
+__device__ __forceinline__ bool on_bnd(int gi, int M) { return gi == 0 || gi == M - 1; }
+
+// Coarse nodes and weights feeding fine node index f (one axis).
+__device__ __forceinline__ int pro_axis(int f, int* idx, float* wt) {
+    if ((f & 1) == 0) { idx[0] = f >> 1; wt[0] = 1.0f; return 1; }
+    const int m = f >> 2;
+    idx[0] = 2 * m; idx[1] = 2 * m + 1; idx[2] = 2 * m + 2;
+    if ((f & 3) == 1) { wt[0] = 0.375f; wt[1] = 0.75f; wt[2] = -0.125f; }
+    else { wt[0] = -0.125f; wt[1] = 0.75f; wt[2] = 0.375f; }
+    return 3;
+}
+
+// Fine nodes and weights of coarse node index c (one axis), nc coarse cells.
+__device__ __forceinline__ int res_axis(int c, int nc, int* idx, float* wt) {
+    int k = 0;
+    if (c & 1) {
+        const int m = c >> 1;
+        idx[k] = 4 * m + 2; wt[k++] = 1.0f;
+        idx[k] = 4 * m + 1; wt[k++] = 0.75f;
+        idx[k] = 4 * m + 3; wt[k++] = 0.75f;
+        return k;
+    }
+    const int m = c >> 1;
+    idx[k] = 4 * m; wt[k++] = 1.0f;
+    if (m < nc) { idx[k] = 4 * m + 1; wt[k++] = 0.375f; idx[k] = 4 * m + 3; wt[k++] = -0.125f; }
+    if (m >= 1) { idx[k] = 4 * m - 1; wt[k++] = 0.375f; idx[k] = 4 * m - 3; wt[k++] = -0.125f; }
+    return k;
+}
+
+template <typename T>
+__global__ void k_prolongate(int nf, const T* __restrict__ coarse, T* __restrict__ fine, bool add) {
+    const size_t node = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int Mf = 2 * nf + 1, Mc = nf + 1;
+    const size_t nodes_f = size_t(Mf) * Mf * Mf, nodes_c = size_t(Mc) * Mc * Mc;
+    if (node >= nodes_f) return;
+    const int i = int(node % Mf), j = int((node / Mf) % Mf), k = int(node / (size_t(Mf) * Mf));
+    if (on_bnd(i, Mf) || on_bnd(j, Mf) || on_bnd(k, Mf)) {
+        if (!add)
+            for (int c = 0; c < 3; ++c) fine[c * nodes_f + node] = T(0);
+        return;
+    }
+    int ix[3], iy[3], iz[3];
+    float wx[3], wy[3], wz[3];
+    const int nx = pro_axis(i, ix, wx), ny = pro_axis(j, iy, wy), nz = pro_axis(k, iz, wz);
+    T acc[3] = {T(0), T(0), T(0)};
+    for (int c3 = 0; c3 < nz; ++c3)
+        for (int c2 = 0; c2 < ny; ++c2) {
+            const T wyz = T(wy[c2]) * T(wz[c3]);
+            const size_t base = size_t(Mc) * (iy[c2] + size_t(Mc) * iz[c3]);
+            for (int c1 = 0; c1 < nx; ++c1) {
+                const T wgt = wyz * T(wx[c1]);
+                const size_t cn = base + ix[c1];
+                for (int c = 0; c < 3; ++c) acc[c] += wgt * coarse[c * nodes_c + cn];
+            }
+        }
+    for (int c = 0; c < 3; ++c) {
+        if (add) fine[c * nodes_f + node] += acc[c];
+        else fine[c * nodes_f + node] = acc[c];
+    }
+}
+
+template <typename T>
+__global__ void k_restrict(int nf, const T* __restrict__ fine, T* __restrict__ coarse) {
+    const size_t node = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int Mf = 2 * nf + 1, Mc = nf + 1, nc = nf / 2;
+    const size_t nodes_f = size_t(Mf) * Mf * Mf, nodes_c = size_t(Mc) * Mc * Mc;
+    if (node >= nodes_c) return;
+    const int i = int(node % Mc), j = int((node / Mc) % Mc), k = int(node / (size_t(Mc) * Mc));
+    if (on_bnd(i, Mc) || on_bnd(j, Mc) || on_bnd(k, Mc)) {
+        for (int c = 0; c < 3; ++c) coarse[c * nodes_c + node] = T(0);
+        return;
+    }
+    int ix[5], iy[5], iz[5];
+    float wx[5], wy[5], wz[5];
+    const int nx = res_axis(i, nc, ix, wx), ny = res_axis(j, nc, iy, wy), nz = res_axis(k, nc, iz, wz);
+    T acc[3] = {T(0), T(0), T(0)};
+    for (int c3 = 0; c3 < nz; ++c3)
+        for (int c2 = 0; c2 < ny; ++c2) {
+            const T wyz = T(wy[c2]) * T(wz[c3]);
+            const size_t base = size_t(Mf) * (iy[c2] + size_t(Mf) * iz[c3]);
+            for (int c1 = 0; c1 < nx; ++c1) {
+                const T wgt = wyz * T(wx[c1]);
+                const size_t fn = base + ix[c1];
+                for (int c = 0; c < 3; ++c) acc[c] += wgt * fine[c * nodes_f + fn];
+            }
+        }
+    for (int c = 0; c < 3; ++c) coarse[c * nodes_c + node] = acc[c];
+}
+
+template <typename T>
+__global__ void k_cheb_update(size_t n, const T* __restrict__ b, const T* __restrict__ Ax,
+                              const T* __restrict__ dinv, T* __restrict__ d, T* __restrict__ x, T c1, T c2,
+                              bool x_valid) {
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
+        const T r = dinv[i] * (Ax ? b[i] - Ax[i] : b[i]);
+        const T dn = (c1 != T(0) ? c1 * d[i] : T(0)) + c2 * r;
+        d[i] = dn;
+        x[i] = (x_valid ? x[i] : T(0)) + dn;
+    }
+}
+
+template <typename T>
+__global__ void k_residual(size_t n, const T* __restrict__ b, const T* __restrict__ Ax, T* __restrict__ r) {
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+        r[i] = b[i] - Ax[i];
+}
+
+__global__ void k_cast_d2f(size_t n, const double* __restrict__ in, float* __restrict__ out) {
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+        out[i] = float(in[i]);
+}
+__global__ void k_cast_f2d(size_t n, const float* __restrict__ in, double* __restrict__ out) {
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+        out[i] = double(in[i]);
+}
+
+template <typename T>
+__global__ void k_coarse_solve(int nf, const int* __restrict__ idx, const double* __restrict__ Ainv,
+                               const T* __restrict__ b, T* __restrict__ x) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nf) return;
+    double s = 0.0;
+    for (int j = 0; j < nf; ++j) s += Ainv[size_t(r) * nf + j] * double(b[idx[j]]);
+    x[idx[r]] = T(s);
+}
+
+__global__ void k_axpby(size_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+        y[i] = a * x[i] + (b == 0.0 ? 0.0 : b * y[i]);
+}
+__global__ void k_mul(size_t n, const double* __restrict__ a, const double* __restrict__ x, double* __restrict__ y) {
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+        y[i] = a[i] * x[i];
+}
+__global__ void k_sqrt(size_t n, const double* __restrict__ a, double* __restrict__ y) {
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+        y[i] = sqrt(a[i]);
+}
+__global__ void k_recip(size_t n, const double* __restrict__ a, double* __restrict__ y) {
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+        y[i] = 1.0 / a[i];
+}
+__global__ void k_add_scalar(size_t n, double v, double* __restrict__ y) {
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+        y[i] += v;
+}
+__global__ void k_fill(size_t n, double v, double* __restrict__ y) {
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+        y[i] = v;
+}
+
+// splitmix64 (Steele, Lea, Flood 2014): output i of seed s is mix(s + (i+1) * golden);
+// uniform double = top 53 bits * 2^-53; the vector entry is (u - 1/2) * mask.
+__global__ void k_splitmix(size_t n, unsigned long long seed, const double* __restrict__ mask,
+                           double* __restrict__ y) {
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
+        unsigned long long z = seed + (unsigned long long)(i + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z = z ^ (z >> 31);
+        const double u = double(z >> 11) * (1.0 / 9007199254740992.0);
+        y[i] = (u - 0.5) * (mask ? mask[i] : 1.0);
+    }
+}
+
+constexpr int kDotThreads = 256;
+constexpr int kDotBlocks = 608;   // 4 per SM on 152 SMs
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double warp_part[kDotThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) warp_part[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < kDotThreads / 32; ++i) s += warp_part[i];
+    __syncthreads();
+    return s;
+}
+
+// grid (kDotBlocks, k): partials[i * kDotBlocks + bx] = sum over the block's slice of V_i . w
+__global__ void __launch_bounds__(kDotThreads) k_multidot_partial(size_t n, const double* __restrict__ V, size_t ld,
+                                                                 const double* __restrict__ w,
+                                                                 double* __restrict__ partials) {
+    const int i = blockIdx.y;
+    const double* v = V + size_t(i) * ld;
+    double acc = 0.0;
+    for (size_t e = size_t(blockIdx.x) * kDotThreads + threadIdx.x; e < n; e += size_t(kDotBlocks) * kDotThreads)
+        acc += v[e] * w[e];
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) partials[size_t(i) * kDotBlocks + blockIdx.x] = s;
+}
+
+__global__ void k_multidot_final(int k, const double* __restrict__ partials, double* __restrict__ out) {
+    const int i = blockIdx.x;
+    if (i >= k) return;
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < kDotBlocks; b += kDotThreads) acc += partials[size_t(i) * kDotBlocks + b];
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) out[i] = s;
+}
+
+__global__ void k_multiaxpy(size_t n, int k, const double* __restrict__ V, size_t ld, const double* __restrict__ h,
+                            double* __restrict__ w, double sign) {
+    for (size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += size_t(gridDim.x) * blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < k; ++i) s += h[i] * V[size_t(i) * ld + e];
+        w[e] += sign * s;
+    }
+}
+
+inline unsigned grid_stride_blocks(size_t n) {
+    const size_t b = (n + 255) / 256;
+    return unsigned(b < 4864 ? (b == 0 ? 1 : b) : 4864);
+}
+
+}  // namespace
+
+int multidot_blocks() { return kDotBlocks; }
+
+template <typename T>
+cudaError_t launch_prolongate(const LevelGeom& fine, const T* coarse, T* finev, bool add, cudaStream_t s) {
+    LAUNCH(PROF_TRANSFER, s, k_prolongate<T><<<blocks_for(fine.nodes, 256), 256, 0, s>>>(fine.n, coarse, finev, add));
+    return cudaGetLastError();
+}
+template cudaError_t launch_prolongate<float>(const LevelGeom&, const float*, float*, bool, cudaStream_t);
+template cudaError_t launch_prolongate<double>(const LevelGeom&, const double*, double*, bool, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_restrict(const LevelGeom& fine, const T* finev, T* coarse, cudaStream_t s) {
+    const size_t Mc = size_t(fine.n) + 1;
+    LAUNCH(PROF_TRANSFER, s, k_restrict<T><<<blocks_for(Mc * Mc * Mc, 256), 256, 0, s>>>(fine.n, finev, coarse));
+    return cudaGetLastError();
+}
+template cudaError_t launch_restrict<float>(const LevelGeom&, const float*, float*, cudaStream_t);
+template cudaError_t launch_restrict<double>(const LevelGeom&, const double*, double*, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_cheb_update(size_t n, const T* b, const T* Ax, const T* dinv, T* d, T* x, double c1, double c2,
+                               bool x_valid, cudaStream_t s) {
+    LAUNCH(PROF_SMOOTH_VEC, s, k_cheb_update<T><<<grid_stride_blocks(n), 256, 0, s>>>(n, b, Ax, dinv, d, x, T(c1), T(c2), x_valid));
+    return cudaGetLastError();
+}
+template cudaError_t launch_cheb_update<float>(size_t, const float*, const float*, const float*, float*, float*,
+                                               double, double, bool, cudaStream_t);
+template cudaError_t launch_cheb_update<double>(size_t, const double*, const double*, const double*, double*,
+                                                double*, double, double, bool, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_residual(size_t n, const T* b, const T* Ax, T* r, cudaStream_t s) {
+    LAUNCH(PROF_SMOOTH_VEC, s, k_residual<T><<<grid_stride_blocks(n), 256, 0, s>>>(n, b, Ax, r));
+    return cudaGetLastError();
+}
+template cudaError_t launch_residual<float>(size_t, const float*, const float*, float*, cudaStream_t);
+template cudaError_t launch_residual<double>(size_t, const double*, const double*, double*, cudaStream_t);
+
+cudaError_t launch_cast_d2f(size_t n, const double* in, float* out, cudaStream_t s) {
+    LAUNCH(PROF_CAST, s, k_cast_d2f<<<grid_stride_blocks(n), 256, 0, s>>>(n, in, out));
+    return cudaGetLastError();
+}
+cudaError_t launch_cast_f2d(size_t n, const float* in, double* out, cudaStream_t s) {
+    LAUNCH(PROF_CAST, s, k_cast_f2d<<<grid_stride_blocks(n), 256, 0, s>>>(n, in, out));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_coarse_solve(int nf, const int* free_idx, const double* Ainv, const T* b, T* x, cudaStream_t s) {
+    if (nf <= 0) return cudaSuccess;
+    LAUNCH(PROF_COARSE, s, k_coarse_solve<T><<<blocks_for(size_t(nf), 128), 128, 0, s>>>(nf, free_idx, Ainv, b, x));
+    return cudaGetLastError();
+}
+template cudaError_t launch_coarse_solve<float>(int, const int*, const double*, const float*, float*, cudaStream_t);
+template cudaError_t launch_coarse_solve<double>(int, const int*, const double*, const double*, double*,
+                                                 cudaStream_t);
+
+cudaError_t launch_axpby(size_t n, double a, const double* x, double b, double* y, cudaStream_t s) {
+    LAUNCH(PROF_KRYLOV, s, k_axpby<<<grid_stride_blocks(n), 256, 0, s>>>(n, a, x, b, y));
+    return cudaGetLastError();
+}
+cudaError_t launch_mul(size_t n, const double* a, const double* x, double* y, cudaStream_t s) {
+    LAUNCH(PROF_KRYLOV, s, k_mul<<<grid_stride_blocks(n), 256, 0, s>>>(n, a, x, y));
+    return cudaGetLastError();
+}
+cudaError_t launch_sqrt_vec(size_t n, const double* a, double* y, cudaStream_t s) {
+    LAUNCH(PROF_KRYLOV, s, k_sqrt<<<grid_stride_blocks(n), 256, 0, s>>>(n, a, y));
+    return cudaGetLastError();
+}
+cudaError_t launch_recip(size_t n, const double* a, double* y, cudaStream_t s) {
+    LAUNCH(PROF_KRYLOV, s, k_recip<<<grid_stride_blocks(n), 256, 0, s>>>(n, a, y));
+    return cudaGetLastError();
+}
+cudaError_t launch_add_scalar(size_t n, double v, double* y, cudaStream_t s) {
+    LAUNCH(PROF_KRYLOV, s, k_add_scalar<<<grid_stride_blocks(n), 256, 0, s>>>(n, v, y));
+    return cudaGetLastError();
+}
+cudaError_t launch_fill(size_t n, double v, double* y, cudaStream_t s) {
+    LAUNCH(PROF_KRYLOV, s, k_fill<<<grid_stride_blocks(n), 256, 0, s>>>(n, v, y));
+    return cudaGetLastError();
+}
+cudaError_t launch_splitmix_vector(size_t n, uint64_t seed, const double* mask, double* y, cudaStream_t s) {
+    LAUNCH(PROF_KRYLOV, s, k_splitmix<<<grid_stride_blocks(n), 256, 0, s>>>(n, (unsigned long long)seed, mask, y));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_multidot(size_t n, int k, const double* V, size_t ld, const double* w, double* partials,
+                            double* out, cudaStream_t s) {
+    if (k <= 0) return cudaSuccess;
+    dim3 grid(kDotBlocks, unsigned(k));
+    LAUNCH(PROF_KRYLOV, s, k_multidot_partial<<<grid, kDotThreads, 0, s>>>(n, V, ld, w, partials));
+    LAUNCH(PROF_KRYLOV, s, k_multidot_final<<<unsigned(k), kDotThreads, 0, s>>>(k, partials, out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_multiaxpy(size_t n, int k, const double* V, size_t ld, const double* h, double* w, double sign,
+                             cudaStream_t s) {
+    if (k <= 0) return cudaSuccess;
+    LAUNCH(PROF_KRYLOV, s, k_multiaxpy<<<grid_stride_blocks(n), 256, 0, s>>>(n, k, V, ld, h, w, sign));
+    return cudaGetLastError();
+}
+
+}  // namespace stk

@@ -1,0 +1,381 @@
+"""GPU parity: every step of the path, called through the C ABI, against the
+CPU FP64 oracle on the same seeded inputs.
+
+Tolerances (derived from the arithmetic):
+* FP64 kernels: the oracle and the GPU evaluate the same sums in a different
+  order (sum factorisation vs element matrices, atomics vs bincount). Each
+  output is a sum of <= 8 cells x 81 terms of similar magnitude, so the
+  rounding difference is a few hundred ulp at most: relative 2-norm error
+  <= 1e-12 (the benchmark spec's bound) and max-norm error <= 1e-12 ||ref||_inf.
+* FP32 operator / transfer kernels: inputs rounded to FP32 (2^-24 relative)
+  and ~100 FP32 operations per output: relative error <= 2e-6.
+* FP32 smoothing and V-cycle: the same per-kernel error, propagated through
+  up to ~10 operator applications per level and the level recursion, with
+  Chebyshev coefficients of magnitude <= 1/delta: relative error <= 2e-5.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+import sinker_inputs as si
+from oracle import gmg, krylov, mesh, operators, sinker
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+F64_TOL = 1e-12
+F32_TOL = 2e-6
+F32_CYCLE_TOL = 2e-5
+
+
+@pytest.fixture(scope="module")
+def capi():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1907_06696_gb300 import build as B
+    from paper_1907_06696_gb300 import capi as api
+    B.build()
+    api.load()
+    return api
+
+
+# sizes: several 128-cell tiles and a ragged tail (12^3 = 1728 cells = 13.5 tiles)
+PROBLEMS = {
+    "cube8": lambda: si.workload("cube8"),
+    "n12": lambda: si.dr_problem(12, 3, 2, 1e3, 2001, "n12"),
+    "cube16": lambda: si.workload("cube16"),
+    "n24": lambda: si.dr_problem(24, 4, 4, 1e4, 2002, "n24"),
+}
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_problem(name):
+    p = PROBLEMS[name]()
+    m = mesh.Mesh(p.n)
+    mus = sinker.level_viscosities(m, p, p.n_levels)
+    G = gmg.GMG(p.n, p.n_levels, mus)
+    ops = G.levels[-1].ops
+    F = operators.assemble_rhs(m, sinker.forcing(m.quad_points(), p))
+    return p, m, mus, G, ops, F
+
+
+_ctx_cache = {}
+
+
+def gpu_ctx(capi, name):
+    if name not in _ctx_cache:
+        p = oracle_problem(name)[0]
+        _ctx_cache[name] = capi.stokes_setup_problem(p)
+    return _ctx_cache[name]
+
+
+def dev(x, dtype=torch.float64):
+    return torch.tensor(np.asarray(x), dtype=dtype, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.double().cpu().numpy()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def assert_close(got, ref, tol):
+    assert rel(got, ref) <= tol, rel(got, ref)
+    assert np.abs(got - ref).max() <= tol * max(np.abs(ref).max(), 1e-300) * 10
+
+
+# ----------------------------------------------------------------- set-up data
+@pytest.mark.parametrize("name", ["cube8", "n12", "cube16"])
+def test_viscosity_levels_and_rhs(capi, name):
+    p, m, mus, G, ops, F = oracle_problem(name)
+    ctx = gpu_ctx(capi, name)
+    for l in range(p.n_levels):
+        out = torch.empty(len(mus[l]), dtype=torch.float64, device="cuda")
+        capi.stokes_get_viscosity(ctx, l, out)
+        assert_close(host(out), mus[l], 1e-13)
+    Fd = torch.empty(m.n_u, dtype=torch.float64, device="cuda")
+    capi.stokes_get_rhs(ctx, Fd)
+    assert_close(host(Fd), F, 1e-12)
+
+
+@pytest.mark.parametrize("name", ["cube8", "n12"])
+def test_inverse_diagonal_and_lambda(capi, name):
+    p, m, mus, G, ops, F = oracle_problem(name)
+    ctx = gpu_ctx(capi, name)
+    for l, lev in enumerate(G.levels):
+        out = torch.empty(lev.mesh.n_u, dtype=torch.float64, device="cuda")
+        capi.stokes_get_inv_diagonal(ctx, l, out)
+        assert_close(host(out), lev.Dinv, 1e-13)
+        if l >= 1:
+            lam = capi.stokes_get_lambda_max(ctx, l)
+            assert abs(lam - lev.lam_max) <= 1e-10 * lev.lam_max, (l, lam, lev.lam_max)
+
+
+# ----------------------------------------------------------------- operators
+@pytest.mark.parametrize("name", ["cube8", "n12", "cube16", "n24"])
+def test_vmult_A_all_levels(capi, name):
+    p, m, mus, G, ops, F = oracle_problem(name)
+    ctx = gpu_ctx(capi, name)
+    for l, lev in enumerate(G.levels):
+        x = si.uniform(300 + l, lev.mesh.n_u)          # includes constrained entries
+        ref = lev.ops.apply_A(x)
+        for prec, dt, tol in ((capi.STOKES_FP64, torch.float64, F64_TOL), (capi.STOKES_FP32, torch.float32, F32_TOL)):
+            src = dev(x, dt)
+            dst = torch.full_like(src, float("nan"))
+            capi.stokes_vmult(ctx, l, capi.BLOCK_A, prec, src, dst)
+            got = host(dst)
+            assert_close(got, ref, tol)
+            assert np.array_equal(got[lev.mesh.dirichlet], np.asarray(src.cpu().double())[lev.mesh.dirichlet])
+
+
+@pytest.mark.parametrize("name", ["cube8", "n12"])
+def test_pressure_blocks_and_stokes_operator(capi, name):
+    p, m, mus, G, ops, F = oracle_problem(name)
+    ctx = gpu_ctx(capi, name)
+    u = si.uniform(401, m.n_u)
+    q = si.uniform(402, m.n_p)
+    out_p = torch.empty(m.n_p, dtype=torch.float64, device="cuda")
+    capi.stokes_vmult(ctx, -1, capi.BLOCK_B, capi.STOKES_FP64, dev(u), out_p)
+    assert_close(host(out_p), ops.apply_B(u), F64_TOL)
+    out_u = torch.empty(m.n_u, dtype=torch.float64, device="cuda")
+    capi.stokes_vmult(ctx, -1, capi.BLOCK_BT, capi.STOKES_FP64, dev(q), out_u)
+    assert_close(host(out_u), ops.apply_BT(q), F64_TOL)
+    capi.stokes_vmult(ctx, -1, capi.BLOCK_MP, capi.STOKES_FP64, dev(q), out_p)
+    assert_close(host(out_p), ops.apply_Mp(q), F64_TOL)
+    up = np.concatenate([u, q])
+    out = torch.empty(m.n_u + m.n_p, dtype=torch.float64, device="cuda")
+    capi.stokes_vmult(ctx, -1, capi.BLOCK_STOKES, capi.STOKES_FP64, dev(up), out)
+    assert_close(host(out), ops.apply_stokes(up), F64_TOL)
+
+
+# ----------------------------------------------------------------- multigrid pieces
+@pytest.mark.parametrize("name", ["cube8", "n12"])
+def test_transfers(capi, name):
+    p, m, mus, G, ops, F = oracle_problem(name)
+    ctx = gpu_ctx(capi, name)
+    for l in range(1, p.n_levels):
+        fine, coarse = G.levels[l], G.levels[l - 1]
+        xc = si.uniform(500 + l, coarse.mesh.n_u)
+        xf = si.uniform(600 + l, fine.mesh.n_u) * fine.free
+        ref_p = (G.P[l] @ xc) * fine.free
+        ref_r = (G.P[l].T @ xf) * coarse.free
+        for prec, dt, tol in ((capi.STOKES_FP64, torch.float64, 1e-14), (capi.STOKES_FP32, torch.float32, F32_TOL)):
+            out = torch.empty(fine.mesh.n_u, dtype=dt, device="cuda")
+            capi.stokes_prolongate(ctx, l, prec, dev(xc, dt), out, add=False)
+            assert_close(host(out), ref_p, tol)
+            base = dev(xf, dt)
+            capi.stokes_prolongate(ctx, l, prec, dev(xc, dt), base, add=True)
+            assert_close(host(base), xf + ref_p, tol)
+            outc = torch.empty(coarse.mesh.n_u, dtype=dt, device="cuda")
+            capi.stokes_restrict(ctx, l, prec, dev(xf, dt), outc)
+            assert_close(host(outc), ref_r, tol)
+
+
+@pytest.mark.parametrize("name", ["cube8", "n12"])
+def test_chebyshev_smoother(capi, name):
+    p, m, mus, G, ops, F = oracle_problem(name)
+    ctx = gpu_ctx(capi, name)
+    for l in range(1, p.n_levels):
+        lev = G.levels[l]
+        b = si.uniform(700 + l, lev.mesh.n_u) * lev.free
+        x0 = si.uniform(800 + l, lev.mesh.n_u) * lev.free
+        for zero in (True, False):
+            ref = G.smooth(l, b, None if zero else x0, zero)
+            for prec, dt, tol in ((capi.STOKES_FP64, torch.float64, 1e-11),
+                                  (capi.STOKES_FP32, torch.float32, F32_CYCLE_TOL)):
+                x = dev(x0, dt)
+                capi.stokes_smooth(ctx, l, prec, dev(b, dt), x, zero)
+                assert_close(host(x), ref, tol)
+
+
+@pytest.mark.parametrize("name", ["cube8", "n12"])
+def test_coarse_solve(capi, name):
+    p, m, mus, G, ops, F = oracle_problem(name)
+    ctx = gpu_ctx(capi, name)
+    c = G.levels[0]
+    b = si.uniform(900, c.mesh.n_u) * c.free
+    ref = G.coarse_solve(b)
+    for prec, dt, tol in ((capi.STOKES_FP64, torch.float64, 1e-12), (capi.STOKES_FP32, torch.float32, F32_TOL)):
+        x = torch.full((c.mesh.n_u,), float("nan"), dtype=dt, device="cuda")
+        capi.stokes_coarse_solve(ctx, prec, dev(b, dt), x)
+        assert_close(host(x), ref, tol)
+
+
+@pytest.mark.parametrize("name", ["cube8", "n12", "cube16", "n24"])
+def test_vcycle(capi, name):
+    p, m, mus, G, ops, F = oracle_problem(name)
+    ctx = gpu_ctx(capi, name)
+    rhs = si.uniform(1000, m.n_u)
+    ref = G.vcycle(rhs)
+    for prec, dt, tol in ((capi.STOKES_FP64, torch.float64, 1e-10), (capi.STOKES_FP32, torch.float32, F32_CYCLE_TOL)):
+        x = torch.full((m.n_u,), float("nan"), dtype=dt, device="cuda")
+        capi.gmg_vcycle(ctx, prec, dev(rhs, dt), x)
+        assert_close(host(x), ref, tol)
+
+
+# ----------------------------------------------------------------- outer solve pieces
+@pytest.mark.parametrize("name", ["cube8", "n12"])
+def test_schur_and_block_preconditioner(capi, name):
+    p, m, mus, G, ops, F = oracle_problem(name)
+    ctx = gpu_ctx(capi, name)
+    Pc = krylov.StokesPreconditioner(ops, G)
+    rp = si.uniform(1100, m.n_p)
+    zp = torch.empty(m.n_p, dtype=torch.float64, device="cuda")
+    capi.stokes_schur_inverse(ctx, dev(rp), zp)
+    assert_close(host(zp), Pc.schur_inverse(rp), 1e-12)
+    r = si.uniform(1101, m.n_u + m.n_p)
+    ref = Pc.apply(r)
+    z = torch.empty(m.n_u + m.n_p, dtype=torch.float64, device="cuda")
+    capi.stokes_precondition(ctx, capi.STOKES_FP64, dev(r), z)
+    assert_close(host(z), ref, 1e-10)
+    capi.stokes_precondition(ctx, capi.STOKES_FP32, dev(r), z)
+    assert_close(host(z), ref, F32_CYCLE_TOL)
+
+
+@pytest.mark.parametrize("name", ["cube8", "n12"])
+def test_solve_fp64_and_fp32_vcycle(capi, name):
+    p, m, mus, G, ops, F = oracle_problem(name)
+    ctx = gpu_ctx(capi, name)
+    b = np.concatenate([F, np.zeros(m.n_p)])
+    Pc = krylov.StokesPreconditioner(ops, G)
+    xo, its_o, _ = krylov.fgmres(ops.apply_stokes, Pc.apply, b, rtol=1e-8)
+    xo = krylov.zero_mean_pressure(ops, xo)
+    its = {}
+    for prec in (capi.STOKES_FP64, capi.STOKES_FP32):
+        up = torch.zeros(m.n_u + m.n_p, dtype=torch.float64, device="cuda")
+        info = capi.stokes_solve(ctx, prec, None, up, rtol=1e-8, max_it=500)
+        x = host(up)
+        # property: the true FP64 residual, recomputed by the oracle's operator
+        true = np.linalg.norm(b - ops.apply_stokes(x)) / np.linalg.norm(b)
+        assert true <= 1.5e-8, (prec, true)
+        assert abs(info.rel_residual_true - true) <= 1e-3 * true + 1e-14
+        assert np.abs(x - xo).max() <= 1e-5 * np.abs(xo).max()
+        its[prec] = info.iterations
+    assert abs(its[capi.STOKES_FP64] - its_o) <= 2, (its, its_o)
+    assert its[capi.STOKES_FP32] <= 1.2 * its[capi.STOKES_FP64] + 1
+
+
+def test_solve_matches_dense_direct(capi):
+    p = si.workload("cube4")
+    m = mesh.Mesh(p.n)
+    mus = sinker.level_viscosities(m, p, p.n_levels)
+    ops = operators.Operators(m, mus[-1])
+    F = operators.assemble_rhs(m, sinker.forcing(m.quad_points(), p))
+    xd = krylov.dense_stokes_solve(ops, F)
+    ctx = capi.stokes_setup_problem(p)
+    for prec in (capi.STOKES_FP64, capi.STOKES_FP32):
+        up = torch.zeros(m.n_u + m.n_p, dtype=torch.float64, device="cuda")
+        capi.stokes_solve(ctx, prec, None, up, rtol=1e-12, max_it=500)
+        assert np.abs(host(up) - xd).max() <= 1e-9 * np.abs(xd).max()
+    # host-buffer entry point
+    out = np.zeros(m.n_u + m.n_p)
+    info = capi.stokes_solve_host(ctx, capi.STOKES_FP32, None, out, rtol=1e-12, max_it=500)
+    assert np.abs(out - xd).max() <= 1e-9 * np.abs(xd).max() and info.iterations > 0
+    ctx.close()
+
+
+# ----------------------------------------------------------------- edge cases
+def test_single_level_and_two_level_meshes(capi):
+    for n, L in ((1, 1), (2, 2), (3, 1), (4, 1)):
+        p = si.dr_problem(n, L, 1, 1e2, 3000 + n)
+        m = mesh.Mesh(n)
+        mus = sinker.level_viscosities(m, p, L)
+        G = gmg.GMG(n, L, mus)
+        ctx = capi.stokes_setup_problem(p)
+        rhs = si.uniform(3100 + n, m.n_u)
+        x = torch.empty(m.n_u, dtype=torch.float64, device="cuda")
+        capi.gmg_vcycle(ctx, capi.STOKES_FP64, dev(rhs), x)
+        assert_close(host(x), G.vcycle(rhs), 1e-10)
+        ctx.close()
+
+
+def test_quadrature_point_viscosity_input(capi):
+    n, L = 8, 4
+    m = mesh.Mesh(n)
+    mu_q = 1.0 + 9.0 * si.uniform01(3200, m.n_cells * 27).reshape(m.n_cells, 27)
+    ctx = capi.stokes_setup(n, L, mu_q=mu_q)
+    out = torch.empty(m.n_cells, dtype=torch.float64, device="cuda")
+    capi.stokes_get_viscosity(ctx, -1, out)
+    assert_close(host(out), sinker.harmonic_cell_average(mu_q), 1e-14)
+    ctx.close()
+
+
+def test_invalid_arguments_on_device(capi):
+    ctx = gpu_ctx(capi, "cube8")
+    x = torch.zeros(10, dtype=torch.float64, device="cuda")
+    with pytest.raises(capi.StokesError):
+        capi.stokes_vmult(ctx, 7, capi.BLOCK_A, capi.STOKES_FP64, x, x)
+    with pytest.raises(capi.StokesError):
+        capi.stokes_vmult(ctx, 0, capi.BLOCK_B, capi.STOKES_FP64, x, x)      # B only on the finest level
+    with pytest.raises(capi.StokesError):
+        capi.stokes_vmult(ctx, -1, capi.BLOCK_BT, capi.STOKES_FP32, x, x)    # FP64 only
+    with pytest.raises(capi.StokesError):
+        capi.stokes_smooth(ctx, 0, capi.STOKES_FP64, x, x, True)
+
+
+# ----------------------------------------------------------------- full size, sampled
+@pytest.mark.parametrize("name", ["cube64", "cube128"])
+def test_full_size_vmult_sampled_rows(capi, name):
+    """The benchmark workloads at full size: rows sampled uniformly plus rows next
+    to the boundary and at tile corners, recomputed one by one by the oracle."""
+    p = si.workload(name)
+    n = p.n
+    M = 2 * n + 1
+    n_u = 3 * M ** 3
+    ctx = gpu_ctx_full(capi, p)
+    mu = torch.empty(n ** 3, dtype=torch.float64, device="cuda")
+    capi.stokes_get_viscosity(ctx, -1, mu)
+    mu_h = host(mu)
+    # the viscosity itself, sampled, against the oracle formula
+    cells = np.unique(np.concatenate([np.arange(0, n ** 3, 9973), [0, n ** 3 - 1]]))
+    ijk = np.stack([cells % n, (cells // n) % n, cells // (n * n)], 1)
+    from oracle import fe
+    pts, _ = fe.quadrature_3d()
+    q = (ijk[:, None, :] + pts[None]) / n
+    ref_mu = sinker.harmonic_cell_average(sinker.viscosity(q, p))
+    assert_close(mu_h[cells], ref_mu, 1e-13)
+    rng = np.random.default_rng(7)
+    rows = np.unique(np.concatenate([rng.integers(0, n_u, 400),
+                                     [M * M + M + 1, 2 * M ** 3 - M * M - M - 2, M ** 3 // 2, n_u - 1, 0]]))
+    x = si.uniform(4000, n_u)
+    ref = operators.apply_A_rows(n, mu_h, x, rows)
+    for prec, dt, tol in ((capi.STOKES_FP64, torch.float64, F64_TOL), (capi.STOKES_FP32, torch.float32, F32_TOL)):
+        src = dev(x, dt)
+        dst = torch.empty_like(src)
+        capi.stokes_vmult(ctx, -1, capi.BLOCK_A, prec, src, dst)
+        got = host(dst)[rows]
+        assert np.abs(got - ref).max() <= tol * 10 * np.abs(ref).max(), (prec, np.abs(got - ref).max())
+        del src, dst
+
+
+_full_cache = {}
+
+
+def gpu_ctx_full(capi, p):
+    if p.name not in _full_cache:
+        _full_cache.clear()
+        _full_cache[p.name] = capi.stokes_setup_problem(p)
+    return _full_cache[p.name]
+
+
+def test_full_size_solve_residual_cube64(capi):
+    """64^3, 8 sinkers, DR 1e4: FP32 V-cycle inside FP64 FGMRES reaches a true FP64
+    residual <= 1e-8 (recomputed by the oracle's element-by-element operator)."""
+    p = si.workload("cube64")
+    ctx = gpu_ctx_full(capi, p)
+    n_u, n_p = ctx.n_u, ctx.n_p
+    up = torch.zeros(n_u + n_p, dtype=torch.float64, device="cuda")
+    info = capi.stokes_solve(ctx, capi.STOKES_FP32, None, up, rtol=1e-8, max_it=1000)
+    m = mesh.Mesh(p.n)
+    mu = torch.empty(m.n_cells, dtype=torch.float64, device="cuda")
+    capi.stokes_get_viscosity(ctx, -1, mu)
+    ops = operators.Operators(m, host(mu))
+    F = operators.assemble_rhs(m, sinker.forcing(m.quad_points(), p))
+    b = np.concatenate([F, np.zeros(m.n_p)])
+    true = np.linalg.norm(b - ops.apply_stokes(host(up))) / np.linalg.norm(b)
+    assert true <= 1.5e-8, true
+    assert info.iterations < 1000
