@@ -205,6 +205,26 @@ stokes_status stokes_schur_inverse(stokes_ctx* ctx, const double* rp_dev, double
 stokes_status stokes_precondition(stokes_ctx* ctx, int vcycle_prec, const double* r_dev, double* z_dev,
                                   void* stream);
 
+/* ---- allocation-free entry point (no counterpart in the paper) ---- */
+
+/* Largest pressure space stokes_schur_inverse_noalloc accepts: the (n+1)^3 Q1
+ * vertices of a 32^3 mesh. */
+#define STOKES_NOALLOC_MAX_NP 35937
+/* z_p = S_hat^-1 r_p exactly as stokes_schur_inverse computes it (Jacobi-
+ * Chebyshev of the given degree on the 1/mu-weighted pressure mass matrix,
+ * interval [1/8, 27/8]), for callers that cannot allocate device memory and so
+ * cannot create a context: it takes the uniform mesh size n and the caller's
+ * cell viscosity mu_dev (n^3 doubles, cell ci + n cj + n^2 ck), needs no
+ * stokes_ctx, and calls no cudaMalloc/cudaFree. Its three work vectors live in
+ * one fixed device array of 3 * STOKES_NOALLOC_MAX_NP doubles (~0.86 MB) that
+ * every GPU loading the library holds until exit. The first call on a device
+ * looks up that array's address (make it before any stream capture). All
+ * calls share the array: calls that overlap on the GPU race; serialise them.
+ * rp_dev and zp_dev hold (n+1)^3 doubles and must not overlap. Errors: EINVAL
+ * (null pointer, n < 1, degree < 1, (n+1)^3 > STOKES_NOALLOC_MAX_NP), ECUDA. */
+stokes_status stokes_schur_inverse_noalloc(int n, const double* mu_dev, const double* rp_dev, double* zp_dev,
+                                           int degree, void* stream);
+
 /* ---- instrumentation (no counterpart in the paper; used by the benchmark) ---- */
 
 /* Kernel classes timed by stokes_profile: 0 velocity cell kernel FP32, 1 velocity

@@ -78,6 +78,7 @@ _SIGS = {
     "stokes_coarse_solve": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "stokes_schur_inverse": (C.c_int, [_P, _P, _P, _P]),
     "stokes_precondition": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "stokes_schur_inverse_noalloc": (C.c_int, [C.c_int, _P, _P, _P, C.c_int, _P]),
     "stokes_profile": (C.c_int, [C.c_int]),
     "stokes_profile_read": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int]),
     "stokes_launch_count": (C.c_longlong, []),
@@ -274,6 +275,12 @@ def stokes_schur_inverse(ctx, rp, zp, stream=None):
 def stokes_precondition(ctx, vcycle_prec, r, z, stream=None):
     _check(load().stokes_precondition(ctx.handle, vcycle_prec, _ptr(r), _ptr(z), _stream(stream)),
            "stokes_precondition")
+
+
+def stokes_schur_inverse_noalloc(n, mu, rp, zp, degree=5, stream=None):
+    """Context-free, allocation-free S_hat^-1 (scratch in a fixed device array)."""
+    _check(load().stokes_schur_inverse_noalloc(int(n), _ptr(mu), _ptr(rp), _ptr(zp), int(degree), _stream(stream)),
+           "stokes_schur_inverse_noalloc")
 
 
 def stokes_profile(enable):
