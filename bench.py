@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cube64")
     ap.add_argument("--no-extras", action="store_true", help="skip the sweep/profile/e2e/cpu legs")
+    ap.add_argument("--kernels", action="store_true",
+                    help="profiling case: set up the workload, run 3 FP32 vmults, 2 FP64 Stokes applies, "
+                         "1 FP32 V-cycle, print one line and exit (for ncu)")
     return ap.parse_args()
 
 
@@ -376,9 +379,34 @@ def run_ours(args):
     print(json.dumps(line))
 
 
+def run_kernels(args):
+    import torch
+    from paper_1907_06696_gb300 import build as B
+    B.build()
+    from paper_1907_06696_gb300 import capi
+    capi.load()
+    import sinker_inputs as si
+    prob = si.workload(args.workload)
+    ctx = capi.stokes_setup_problem(prob)
+    n_u, n_p = ctx.n_u, ctx.n_p
+    x = torch.rand(n_u, device="cuda", dtype=torch.float32)
+    y = torch.empty_like(x)
+    for _ in range(3):
+        capi.stokes_vmult(ctx, -1, capi.BLOCK_A, capi.STOKES_FP32, x, y)
+    up = torch.rand(n_u + n_p, device="cuda", dtype=torch.float64)
+    out = torch.empty_like(up)
+    for _ in range(2):
+        capi.stokes_vmult(ctx, -1, capi.BLOCK_STOKES, capi.STOKES_FP64, up, out)
+    capi.gmg_vcycle(ctx, capi.STOKES_FP32, x, y)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernels": args.workload, "n_u": n_u, "n_p": n_p}))
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.kernels:
+        run_kernels(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -8,8 +8,9 @@
 // Jacobi-preconditioned residual; interval [lam_hi / range, lam_hi],
 // lam_hi = safety * Lanczos estimate of lambda_max(D^-1 A).
 // Outer solve (Section 2.2.2): right-preconditioned FGMRES(restart) in FP64
-// with P^-1 of eq. (stokes_precond); Gram-Schmidt as classical GS applied
-// twice (one fused multi-dot and one fused multi-axpy per pass).
+// with P^-1 of eq. (stokes_precond); classical Gram-Schmidt (one fused
+// multi-dot and one fused multi-axpy), repeated once when the projection
+// removed more than half of the squared norm.
 #include "../../include/stokes.h"
 #include "internal.cuh"
 #include "prof.cuh"
@@ -155,6 +156,7 @@ struct stokes_ctx {
     size_t N = 0;
     double *V = nullptr, *Z = nullptr, *w = nullptr, *bvec = nullptr, *hdev = nullptr;
     int krylov_restart = 0;
+    long long reorth_count = 0;   // second Gram-Schmidt passes taken
     // host-buffer solve
     double *h_rhs_dev = nullptr, *h_up_dev = nullptr;
 };
@@ -335,7 +337,7 @@ stokes_status ensure_krylov(stokes_ctx* c) {
     CKS(dalloc(c, &c->Z, size_t(m) * c->N));
     CKS(dalloc(c, &c->w, c->N));
     CKS(dalloc(c, &c->bvec, c->N));
-    CKS(dalloc(c, &c->hdev, size_t(m + 2)));
+    CKS(dalloc(c, &c->hdev, size_t(m + 4)));
     c->krylov_restart = m;
     return STOKES_OK;
 }
@@ -388,19 +390,26 @@ stokes_status fgmres(stokes_ctx* c, int prec, const double* b, double* x, double
             double* zj = Z + size_t(j) * N;
             CKS(precondition(c, prec, vj, zj, s));
             CKS(apply_stokes(c, zj, w, s));
-            // classical Gram-Schmidt, twice
-            CK(launch_multidot(N, j + 1, V, N, w, c->partials, c->hdev, s));
+            // classical Gram-Schmidt; a second pass only when the norm fell below 1/sqrt(2) of
+            // its value before the projection (Kahan-Parlett "twice is enough" criterion)
+            CK(launch_multidot(N, j + 1, V, N, w, c->partials, c->hdev, s, true));      // h, then |w|^2
             CK(launch_multiaxpy(N, j + 1, V, N, c->hdev, w, -1.0, s));
-            CK(cudaMemcpyAsync(c->dots_host, c->hdev, size_t(j + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+            CK(launch_multidot(N, 1, w, N, w, c->partials, c->hdev + j + 2, s));       // |w - V h|^2
+            CK(cudaMemcpyAsync(c->dots_host, c->hdev, size_t(j + 3) * sizeof(double), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
-            for (int i = 0; i <= j; ++i) h1[i] = c->dots_host[i];
-            CK(launch_multidot(N, j + 1, V, N, w, c->partials, c->hdev, s));
-            CK(launch_multiaxpy(N, j + 1, V, N, c->hdev, w, -1.0, s));
-            CK(cudaMemcpyAsync(c->dots_host, c->hdev, size_t(j + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            for (int i = 0; i <= j; ++i) h2[i] = c->dots_host[i];
-            double hn2 = 0.0;
-            CKS(dot(c, N, w, w, s, &hn2));
+            for (int i = 0; i <= j; ++i) { h1[i] = c->dots_host[i]; h2[i] = 0.0; }
+            const double before2 = c->dots_host[j + 1];
+            double hn2 = c->dots_host[j + 2];
+            if (!(hn2 > 0.5 * before2)) {
+                CK(launch_multidot(N, j + 1, V, N, w, c->partials, c->hdev, s));
+                CK(launch_multiaxpy(N, j + 1, V, N, c->hdev, w, -1.0, s));
+                CK(launch_multidot(N, 1, w, N, w, c->partials, c->hdev + j + 1, s));
+                CK(cudaMemcpyAsync(c->dots_host, c->hdev, size_t(j + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                for (int i = 0; i <= j; ++i) h2[i] = c->dots_host[i];
+                hn2 = c->dots_host[j + 1];
+                ++c->reorth_count;
+            }
             const double hn = std::sqrt(hn2);
             if (!std::isfinite(hn)) { st = STOKES_BREAKDOWN; done = true; break; }
             for (int i = 0; i <= j; ++i) Hij(i, j) = h1[i] + h2[i];
@@ -491,7 +500,7 @@ stokes_status setup_impl(const stokes_mesh* mesh, const stokes_mu* mu, const sto
     CKS(dalloc(c, &c->stage_out, gf.n_u));
     CKS(dalloc(c, &c->partials, size_t(multidot_blocks()) * (o.restart + 8)));
     CKS(dalloc(c, &c->dots, size_t(o.restart + 8)));
-    CK(cudaMallocHost(&c->dots_host, size_t(o.restart + 8) * sizeof(double)));
+    CK(cudaMallocHost(&c->dots_host, size_t(o.restart + 8) * sizeof(double)));   // >= restart + 4
     // ---- viscosity (Section 2.3) and right-hand side (Section 3.2)
     double* centres = nullptr;
     if (mu->kind == 0) {

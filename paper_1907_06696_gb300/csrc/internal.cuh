@@ -95,9 +95,10 @@ cudaError_t launch_fill(size_t n, double v, double* y, cudaStream_t s);
 cudaError_t launch_recip(size_t n, const double* a, double* y, cudaStream_t s);                       // y = 1 / a
 cudaError_t launch_add_scalar(size_t n, double v, double* y, cudaStream_t s);                          // y += v
 cudaError_t launch_splitmix_vector(size_t n, uint64_t seed, const double* mask, double* y, cudaStream_t s);
-// Multi-dot: out[i] = sum_e V[i*ld + e] * w[e], i < k, deterministic two-pass reduction through `partials`.
+// Multi-dot: out[i] = sum_e V[i*ld + e] * w[e], i < k, and out[k] = w . w when self; deterministic
+// two-pass reduction through `partials` (multidot_blocks() * (k + 1) doubles).
 cudaError_t launch_multidot(size_t n, int k, const double* V, size_t ld, const double* w, double* partials,
-                            double* out, cudaStream_t s);
+                            double* out, cudaStream_t s, bool self = false);
 int multidot_blocks();
 // w -= sum_i h[i] V[i*ld + :], i < k (h on device); with sign = +1 adds instead.
 cudaError_t launch_multiaxpy(size_t n, int k, const double* V, size_t ld, const double* h, double* w, double sign,

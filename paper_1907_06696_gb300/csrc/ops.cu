@@ -113,20 +113,13 @@ __global__ void __launch_bounds__(kCellThreads) k_stokes_blocks(int n, double h,
     double u[3][27], w[3][27];
     if (DO_A || DO_B) gather_u(src_u, nodes, M, ci, cj, ck, u);
     if (DO_B) {
-        // div u at the Gauss points, then (B u)_l = -h^2 sum_q w_q div_ref(q) psi_l(q)
-        double uq[3][27];
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int a = 0; a < 27; ++a) uq[c][a] = u[c][a];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) { q2::interp<0>(uq[c]); q2::interp<1>(uq[c]); q2::interp<2>(uq[c]); }
-        double dv[27];
-        q2::deriv<0, false>(uq[0], dv);
-        q2::deriv<1, true>(uq[1], dv);
-        q2::deriv<2, true>(uq[2], dv);
+        // (B u)_v = -int div(u_h) psi_v = -h^2 sum_c (moments along each axis) . u_c
         double bp[8];
-        q2::gauss_to_q1_w(dv, bp);
+#pragma unroll
+        for (int v = 0; v < 8; ++v) bp[v] = 0.0;
+        q2::b_component<0>(u[0], bp);
+        q2::b_component<1>(u[1], bp);
+        q2::b_component<2>(u[2], bp);
         const double s = -h * h;
 #pragma unroll
         for (int v = 0; v < 8; ++v) {
@@ -135,9 +128,9 @@ __global__ void __launch_bounds__(kCellThreads) k_stokes_blocks(int n, double h,
         }
     }
     if (DO_A || DO_BT) {
-        const double sA = mu[cell] * h;
         if (DO_A) {
             q2::cell_A(u, w);
+            const double sA = mu[cell] * h;
 #pragma unroll
             for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -149,34 +142,18 @@ __global__ void __launch_bounds__(kCellThreads) k_stokes_blocks(int n, double h,
                 for (int a = 0; a < 27; ++a) w[c][a] = 0.0;
         }
         if (DO_BT) {
-            // (B^T p)_(a,c) = -h^2 sum_q w_q p(q) d_c phi_a(q) (reference derivative)
-            double p8[8], pq[27];
+            // (B^T p)_(c,m) = -int d_c(phi_m) p_h = -h^2 sum_v (moments along each axis) p_v
+            double p8[8];
+            const double s = -h * h;
 #pragma unroll
             for (int v = 0; v < 8; ++v) {
                 const size_t vert =
                     size_t(ci + (v & 1)) + size_t(P) * (cj + ((v >> 1) & 1) + size_t(P) * (ck + (v >> 2)));
-                p8[v] = src_p[vert];
+                p8[v] = s * src_p[vert];
             }
-            q2::q1_to_gauss(p8, pq);
-            const double s = -h * h;
-#pragma unroll
-            for (int a = 0; a < 27; ++a) pq[a] *= s;
-            // The A part of w is still in the Gauss-point basis only before interpT; add B^T in the
-            // nodal basis instead: w_c += V^T (DC_c^T (W3 .* pq)).
-            double t[3][27];
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-#pragma unroll
-                for (int a = 0; a < 27; ++a) t[c][a] = 0.0;
-            q2::derivT_w<0, 1>(pq, t[0]);
-            q2::derivT_w<1, 1>(pq, t[1]);
-            q2::derivT_w<2, 1>(pq, t[2]);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                q2::interpT<0>(t[c]); q2::interpT<1>(t[c]); q2::interpT<2>(t[c]);
-#pragma unroll
-                for (int a = 0; a < 27; ++a) w[c][a] += t[c][a];
-            }
+            q2::bt_component<0>(p8, w[0]);
+            q2::bt_component<1>(p8, w[1]);
+            q2::bt_component<2>(p8, w[2]);
         }
         scatter_u(dst_u, nodes, M, ci, cj, ck, w, 1.0);
     }

@@ -69,7 +69,7 @@ __host__ __device__ constexpr int lin(int a, int o1, int o2) {
 // ---------------------------------------------------------------- 1D sweeps
 // x <- V x along AX, in place (nodes -> Gauss points).
 template <int AX, typename T>
-__device__ __forceinline__ void interp(T* x) {
+__host__ __device__ __forceinline__ void interp(T* x) {
 #pragma unroll
     for (int o2 = 0; o2 < 3; ++o2)
 #pragma unroll
@@ -83,7 +83,7 @@ __device__ __forceinline__ void interp(T* x) {
 
 // x <- V^T x along AX, in place (Gauss-point sums -> nodes).
 template <int AX, typename T>
-__device__ __forceinline__ void interpT(T* x) {
+__host__ __device__ __forceinline__ void interpT(T* x) {
 #pragma unroll
     for (int o2 = 0; o2 < 3; ++o2)
 #pragma unroll
@@ -97,7 +97,7 @@ __device__ __forceinline__ void interpT(T* x) {
 
 // g (+)= DC x along AX (collocation derivative at the Gauss points).
 template <int AX, bool ADD, typename T>
-__device__ __forceinline__ void deriv(const T* x, T* g) {
+__host__ __device__ __forceinline__ void deriv(const T* x, T* g) {
 #pragma unroll
     for (int o2 = 0; o2 < 3; ++o2)
 #pragma unroll
@@ -113,7 +113,7 @@ __device__ __forceinline__ void deriv(const T* x, T* g) {
 
 // w += S * DC^T (W3 .* g) along AX, W3 the 3D quadrature weight of each Gauss point.
 template <int AX, int S, typename T>
-__device__ __forceinline__ void derivT_w(const T* g, T* w) {
+__host__ __device__ __forceinline__ void derivT_w(const T* g, T* w) {
 #pragma unroll
     for (int o2 = 0; o2 < 3; ++o2)
 #pragma unroll
@@ -133,7 +133,7 @@ __device__ __forceinline__ void derivT_w(const T* g, T* w) {
 // in: u[c][a] nodal values (overwritten by their Gauss-point values);
 // out: w[c][a] = sum_q w_q sum_d sigma_cd d_d phi_a.
 template <typename T>
-__device__ __forceinline__ void cell_A(T (&u)[3][27], T (&w)[3][27]) {
+__host__ __device__ __forceinline__ void cell_A(T (&u)[3][27], T (&w)[3][27]) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         interp<0>(u[c]); interp<1>(u[c]); interp<2>(u[c]);
@@ -157,39 +157,74 @@ __device__ __forceinline__ void cell_A(T (&u)[3][27], T (&w)[3][27]) {
     }
 }
 
-// Q1 vertex values (8) -> Gauss-point values (27).
-template <typename T>
-__device__ __forceinline__ void q1_to_gauss(const T (&p)[8], T (&pq)[27]) {
+// 1D moments of the Q2 basis against the Q1 basis on [0,1], exact by the same
+// quadrature: VP(m,v) = int l_m psi_v, DP(m,v) = int l_m' psi_v.
+__host__ __device__ constexpr double VP(int m, int v) {
+    return gw(0) * lag(m, gp(0)) * Pq(0, v) + gw(1) * lag(m, gp(1)) * Pq(1, v) + gw(2) * lag(m, gp(2)) * Pq(2, v);
+}
+__host__ __device__ constexpr double DP(int m, int v) {
+    return gw(0) * dlag(m, gp(0)) * Pq(0, v) + gw(1) * dlag(m, gp(1)) * Pq(1, v) + gw(2) * dlag(m, gp(2)) * Pq(2, v);
+}
+// 1D factor of int d_c(phi_m) psi_v along axis AX for velocity component C.
+template <int C, int AX>
+__host__ __device__ constexpr double XP(int m, int v) { return C == AX ? DP(m, v) : VP(m, v); }
+
+// out_c(i,j,k) (+)= sum_v [int d_c(phi_ijk) psi_v] p_v on the reference cell: the
+// tensor product of three 3x2 moment matrices, applied axis by axis (B^T without h).
+template <int C, typename T>
+__host__ __device__ __forceinline__ void bt_component(const T (&p)[8], T* out) {
+    T s1[3][2][2], s2[3][3][2];
 #pragma unroll
-    for (int qz = 0; qz < 3; ++qz)
+    for (int d = 0; d < 2; ++d)
 #pragma unroll
-        for (int qy = 0; qy < 3; ++qy)
+        for (int b = 0; b < 2; ++b)
 #pragma unroll
-            for (int qx = 0; qx < 3; ++qx) {
-                T s = T(0);
+            for (int i = 0; i < 3; ++i)
+                s1[i][b][d] = T(XP<C, 0>(i, 0)) * p[0 + 2 * b + 4 * d] + T(XP<C, 0>(i, 1)) * p[1 + 2 * b + 4 * d];
 #pragma unroll
-                for (int v = 0; v < 8; ++v)
-                    s += T(Pq(qx, v & 1) * Pq(qy, (v >> 1) & 1) * Pq(qz, v >> 2)) * p[v];
-                pq[qx + 3 * qy + 9 * qz] = s;
-            }
+    for (int d = 0; d < 2; ++d)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                s2[i][j][d] = T(XP<C, 1>(j, 0)) * s1[i][0][d] + T(XP<C, 1>(j, 1)) * s1[i][1][d];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                out[i + 3 * j + 9 * k] += T(XP<C, 2>(k, 0)) * s2[i][j][0] + T(XP<C, 2>(k, 1)) * s2[i][j][1];
 }
 
-// out_v = sum_q W3(q) psi_v(q) x_q (Gauss-point values -> weighted Q1 moments).
-template <typename T>
-__device__ __forceinline__ void gauss_to_q1_w(const T (&x)[27], T (&out)[8]) {
+// out_v += sum_(c,m) [int d_c(phi_m) psi_v] u_c(m): the transpose (B without h).
+template <int C, typename T>
+__host__ __device__ __forceinline__ void b_component(const T* u, T (&out)[8]) {
+    T t1[3][3][2], t2[3][2][2];
 #pragma unroll
-    for (int v = 0; v < 8; ++v) {
-        T s = T(0);
+    for (int d = 0; d < 2; ++d)
 #pragma unroll
-        for (int qz = 0; qz < 3; ++qz)
+        for (int j = 0; j < 3; ++j)
 #pragma unroll
-            for (int qy = 0; qy < 3; ++qy)
+            for (int i = 0; i < 3; ++i)
+                t1[i][j][d] = T(XP<C, 2>(0, d)) * u[i + 3 * j] + T(XP<C, 2>(1, d)) * u[i + 3 * j + 9] +
+                              T(XP<C, 2>(2, d)) * u[i + 3 * j + 18];
 #pragma unroll
-                for (int qx = 0; qx < 3; ++qx)
-                    s += T(gw(qx) * gw(qy) * gw(qz) * Pq(qx, v & 1) * Pq(qy, (v >> 1) & 1) * Pq(qz, v >> 2)) *
-                         x[qx + 3 * qy + 9 * qz];
-        out[v] = s;
-    }
+    for (int d = 0; d < 2; ++d)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                t2[i][b][d] = T(XP<C, 1>(0, b)) * t1[i][0][d] + T(XP<C, 1>(1, b)) * t1[i][1][d] +
+                              T(XP<C, 1>(2, b)) * t1[i][2][d];
+#pragma unroll
+    for (int d = 0; d < 2; ++d)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+                out[a + 2 * b + 4 * d] += T(XP<C, 0>(0, a)) * t2[0][b][d] + T(XP<C, 0>(1, a)) * t2[1][b][d] +
+                                          T(XP<C, 0>(2, a)) * t2[2][b][d];
 }
 
 }  // namespace q2

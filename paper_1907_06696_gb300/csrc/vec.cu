@@ -207,17 +207,33 @@ __device__ __forceinline__ double block_sum(double v) {
     return s;
 }
 
-// grid (kDotBlocks, k): partials[i * kDotBlocks + bx] = sum over the block's slice of V_i . w
-__global__ void __launch_bounds__(kDotThreads) k_multidot_partial(size_t n, const double* __restrict__ V, size_t ld,
+constexpr int kDotBatch = 8;
+
+// grid (kDotBlocks, ceil((k + self) / kDotBatch)): partials[i * kDotBlocks + bx] = the block's slice
+// of V_i . w for the kDotBatch vectors of its batch (vector k is w itself when self = 1), so w is
+// read once per batch and every V_i once.
+__global__ void __launch_bounds__(kDotThreads) k_multidot_partial(size_t n, int k, int self,
+                                                                 const double* __restrict__ V, size_t ld,
                                                                  const double* __restrict__ w,
                                                                  double* __restrict__ partials) {
-    const int i = blockIdx.y;
-    const double* v = V + size_t(i) * ld;
-    double acc = 0.0;
-    for (size_t e = size_t(blockIdx.x) * kDotThreads + threadIdx.x; e < n; e += size_t(kDotBlocks) * kDotThreads)
-        acc += v[e] * w[e];
-    const double s = block_sum(acc);
-    if (threadIdx.x == 0) partials[size_t(i) * kDotBlocks + blockIdx.x] = s;
+    const int i0 = blockIdx.y * kDotBatch;
+    const int kt = k + self;
+    double acc[kDotBatch];
+#pragma unroll
+    for (int b = 0; b < kDotBatch; ++b) acc[b] = 0.0;
+    for (size_t e = size_t(blockIdx.x) * kDotThreads + threadIdx.x; e < n; e += size_t(kDotBlocks) * kDotThreads) {
+        const double we = w[e];
+#pragma unroll
+        for (int b = 0; b < kDotBatch; ++b) {
+            const int i = i0 + b;
+            if (i < kt) acc[b] += (i < k ? V[size_t(i) * ld + e] : we) * we;
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < kDotBatch; ++b) {
+        const double s = block_sum(acc[b]);
+        if (threadIdx.x == 0 && i0 + b < kt) partials[size_t(i0 + b) * kDotBlocks + blockIdx.x] = s;
+    }
 }
 
 __global__ void k_multidot_final(int k, const double* __restrict__ partials, double* __restrict__ out) {
@@ -332,11 +348,12 @@ cudaError_t launch_splitmix_vector(size_t n, uint64_t seed, const double* mask, 
 }
 
 cudaError_t launch_multidot(size_t n, int k, const double* V, size_t ld, const double* w, double* partials,
-                            double* out, cudaStream_t s) {
-    if (k <= 0) return cudaSuccess;
-    dim3 grid(kDotBlocks, unsigned(k));
-    LAUNCH(PROF_KRYLOV, s, k_multidot_partial<<<grid, kDotThreads, 0, s>>>(n, V, ld, w, partials));
-    LAUNCH(PROF_KRYLOV, s, k_multidot_final<<<unsigned(k), kDotThreads, 0, s>>>(k, partials, out));
+                            double* out, cudaStream_t s, bool self) {
+    const int kt = k + (self ? 1 : 0);
+    if (kt <= 0) return cudaSuccess;
+    dim3 grid(kDotBlocks, unsigned((kt + kDotBatch - 1) / kDotBatch));
+    LAUNCH(PROF_KRYLOV, s, k_multidot_partial<<<grid, kDotThreads, 0, s>>>(n, k, self ? 1 : 0, V, ld, w, partials));
+    LAUNCH(PROF_KRYLOV, s, k_multidot_final<<<unsigned(kt), kDotThreads, 0, s>>>(kt, partials, out));
     return cudaGetLastError();
 }
 

@@ -95,6 +95,7 @@ def workload(name: str) -> SinkerProblem:
     cube64  : 64^3 cells, 7 levels, 8 sinkers, viscosity ratio 1e4 (~6.4M velocity DoFs)
     cube128 : 128^3 cells, 8 levels, 16 sinkers, viscosity ratio 1e6 (~51M velocity DoFs)
     Smaller parity cases: cube16 (16^3, 5 levels, 4 sinkers, DR 1e4), cube32 (32^3, 6 levels, 8 sinkers, DR 1e4).
+    Profiling case: cube96 (96^3, 6 levels, 8 sinkers, DR 1e4; FP32 vectors of 86 MB exceed L2).
     Sinker centres come from splitmix64 with seed 1907 + k (k = 1, 2, 3 for cube8, cube64, cube128).
     """
     if name == "cube8":
@@ -104,6 +105,8 @@ def workload(name: str) -> SinkerProblem:
         return dr_problem(64, 7, 8, 1e4, 1909, name)
     if name == "cube128":
         return dr_problem(128, 8, 16, 1e6, 1910, name)
+    if name == "cube96":
+        return dr_problem(96, 6, 8, 1e4, 1915, name)
     if name == "cube16":
         return dr_problem(16, 5, 4, 1e4, 1911, name)
     if name == "cube32":
