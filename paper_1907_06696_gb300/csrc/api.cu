@@ -8,10 +8,11 @@
 // Jacobi-preconditioned residual; interval [lam_hi / range, lam_hi],
 // lam_hi = safety * Lanczos estimate of lambda_max(D^-1 A).
 // Outer solve (Section 2.2.2): right-preconditioned FGMRES(restart) in FP64
-// with P^-1 of eq. (stokes_precond); classical Gram-Schmidt (one fused
-// multi-dot and one fused multi-axpy), repeated once when the projection
-// removed more than half of the squared norm.
+// with P^-1 of eq. (stokes_precond); classical Gram-Schmidt applied twice,
+// each pass one fused multi-dot and one fused multi-axpy, one host
+// synchronisation per iteration.
 #include "../../include/stokes.h"
+#include "brick.cuh"
 #include "internal.cuh"
 #include "prof.cuh"
 
@@ -114,18 +115,25 @@ struct LevelVecs {
     T* t = nullptr;   // operator output
     T* mu = nullptr;  // cell viscosity
     T* dinv = nullptr;
+    T* acc = nullptr; // operator accumulator of the cell-parallel kernel (kept at zero between uses)
 };
 
 struct Level {
     LevelGeom g;
     LevelVecs<double> v64;
     LevelVecs<float> v32;
+    PlaneLayout planes{};        // brick-plane slots of the tiled operator
+    double* slots64 = nullptr;
+    float* slots32 = nullptr;
     double lam_max = 0.0, lo = 0.0, hi = 0.0;
 };
 
 template <typename T> LevelVecs<T>& vecs(Level& L);
 template <> LevelVecs<double>& vecs<double>(Level& L) { return L.v64; }
 template <> LevelVecs<float>& vecs<float>(Level& L) { return L.v32; }
+template <typename T> T* slots(Level& L);
+template <> double* slots<double>(Level& L) { return L.slots64; }
+template <> float* slots<float>(Level& L) { return L.slots32; }
 
 }  // namespace
 
@@ -156,7 +164,6 @@ struct stokes_ctx {
     size_t N = 0;
     double *V = nullptr, *Z = nullptr, *w = nullptr, *bvec = nullptr, *hdev = nullptr;
     int krylov_restart = 0;
-    long long reorth_count = 0;   // second Gram-Schmidt passes taken
     // host-buffer solve
     double *h_rhs_dev = nullptr, *h_up_dev = nullptr;
 };
@@ -219,7 +226,18 @@ double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& 
 template <typename T>
 stokes_status vmult_level(stokes_ctx* c, int l, const T* src, T* dst, cudaStream_t s) {
     Level& L = c->lev[l];
-    CK(launch_vmult_A<T>(L.g, vecs<T>(L).mu, src, dst, s));
+    CK(launch_level_op<T>(c->opt.vmult_kernel, L.g, L.planes, EPI_PLAIN, vecs<T>(L).mu, src, dst, nullptr, nullptr,
+                          nullptr, 0.0, 0.0, slots<T>(L), vecs<T>(L).acc, s));
+    return STOKES_OK;
+}
+
+// Chebyshev step fused into the operator: d = c1 d + c2 D^-1 (b - A x); x += d (x in place).
+template <typename T>
+stokes_status cheb_step(stokes_ctx* c, int l, const T* b, T* x, double c1, double c2, cudaStream_t s) {
+    Level& L = c->lev[l];
+    LevelVecs<T>& v = vecs<T>(L);
+    CK(launch_level_op<T>(c->opt.vmult_kernel, L.g, L.planes, EPI_CHEB, v.mu, x, nullptr, b, v.dinv, v.d, c1, c2,
+                          slots<T>(L), v.acc, s));
     return STOKES_OK;
 }
 
@@ -235,13 +253,11 @@ stokes_status smooth(stokes_ctx* c, int l, const T* b, T* x, bool zero_guess, cu
     if (zero_guess) {
         CK(launch_cheb_update<T>(n, b, nullptr, v.dinv, v.d, x, 0.0, 1.0 / theta, false, s));
     } else {
-        CKS(vmult_level<T>(c, l, x, v.t, s));
-        CK(launch_cheb_update<T>(n, b, v.t, v.dinv, v.d, x, 0.0, 1.0 / theta, true, s));
+        CKS(cheb_step<T>(c, l, b, x, 0.0, 1.0 / theta, s));
     }
     for (int it = 1; it < c->opt.cheb_degree; ++it) {
-        CKS(vmult_level<T>(c, l, x, v.t, s));
         const double rho_new = 1.0 / (2.0 * sigma - rho);
-        CK(launch_cheb_update<T>(n, b, v.t, v.dinv, v.d, x, rho_new * rho, 2.0 * rho_new / delta, true, s));
+        CKS(cheb_step<T>(c, l, b, x, rho_new * rho, 2.0 * rho_new / delta, s));
         rho = rho_new;
     }
     return STOKES_OK;
@@ -263,8 +279,8 @@ stokes_status vcycle_level(stokes_ctx* c, int l, cudaStream_t s) {
     if (l == 0) return coarse_solve<T>(c, v.b, v.x, s);
     LevelVecs<T>& vc = vecs<T>(c->lev[l - 1]);
     CKS(smooth<T>(c, l, v.b, v.x, true, s));
-    CKS(vmult_level<T>(c, l, v.x, v.t, s));
-    CK(launch_residual<T>(L.g.n_u, v.b, v.t, v.r, s));
+    CK(launch_level_op<T>(c->opt.vmult_kernel, L.g, L.planes, EPI_RESID, v.mu, v.x, v.r, v.b, nullptr, nullptr, 0.0,
+                          0.0, slots<T>(L), v.acc, s));
     CK(launch_restrict<T>(L.g, v.r, vc.b, s));
     CKS(vcycle_level<T>(c, l - 1, s));
     CK(launch_prolongate<T>(L.g, vc.x, v.x, true, s));
@@ -304,7 +320,7 @@ stokes_status schur_inverse(stokes_ctx* c, const double* rp, double* zp, cudaStr
 
 stokes_status apply_stokes(stokes_ctx* c, const double* src, double* dst, cudaStream_t s) {
     Level& F = c->lev[c->L - 1];
-    CK(launch_stokes_blocks(F.g, F.v64.mu, src, src + F.g.n_u, dst, dst + F.g.n_u, true, true, true, s));
+    CK(launch_stokes_blocks(F.g, F.v64.mu, src, src + F.g.n_u, dst, dst + F.g.n_u, true, true, true, c->opt.outer_arith == 1, s));
     return STOKES_OK;
 }
 
@@ -315,7 +331,7 @@ stokes_status precondition(stokes_ctx* c, int prec, const double* r, double* z, 
     double* zp = z + nu;
     CKS(schur_inverse(c, r + nu, zp, s));
     CK(launch_axpby(np, -1.0, zp, 0.0, zp, s));                               // z_p = -S^-1 r_p
-    CK(launch_stokes_blocks(F.g, F.v64.mu, nullptr, zp, c->tu, nullptr, false, true, false, s));
+    CK(launch_stokes_blocks(F.g, F.v64.mu, nullptr, zp, c->tu, nullptr, false, true, false, c->opt.outer_arith == 1, s));
     CK(launch_axpby(nu, 1.0, r, -1.0, c->tu, s));                            // t = r_u - B^T z_p
     if (prec == STOKES_FP64) {
         CKS(vcycle<double>(c, c->tu, z, s));
@@ -337,7 +353,7 @@ stokes_status ensure_krylov(stokes_ctx* c) {
     CKS(dalloc(c, &c->Z, size_t(m) * c->N));
     CKS(dalloc(c, &c->w, c->N));
     CKS(dalloc(c, &c->bvec, c->N));
-    CKS(dalloc(c, &c->hdev, size_t(m + 4)));
+    CKS(dalloc(c, &c->hdev, size_t(2 * (m + 2))));
     c->krylov_restart = m;
     return STOKES_OK;
 }
@@ -390,26 +406,25 @@ stokes_status fgmres(stokes_ctx* c, int prec, const double* b, double* x, double
             double* zj = Z + size_t(j) * N;
             CKS(precondition(c, prec, vj, zj, s));
             CKS(apply_stokes(c, zj, w, s));
-            // classical Gram-Schmidt; a second pass only when the norm fell below 1/sqrt(2) of
-            // its value before the projection (Kahan-Parlett "twice is enough" criterion)
-            CK(launch_multidot(N, j + 1, V, N, w, c->partials, c->hdev, s, true));      // h, then |w|^2
-            CK(launch_multiaxpy(N, j + 1, V, N, c->hdev, w, -1.0, s));
-            CK(launch_multidot(N, 1, w, N, w, c->partials, c->hdev + j + 2, s));       // |w - V h|^2
-            CK(cudaMemcpyAsync(c->dots_host, c->hdev, size_t(j + 3) * sizeof(double), cudaMemcpyDeviceToHost, s));
+            // classical Gram-Schmidt applied twice ("twice is enough"); the second multi-dot also
+            // returns |w1|^2 of the once-projected vector, so |w2|^2 = |w1|^2 - |h2|^2 (no cancellation:
+            // h2 is small after the first pass) and one host synchronisation serves the iteration.
+            double* h1d = c->hdev;              // j + 2 entries: h1, |w|^2
+            double* h2d = c->hdev + (m + 2);    // j + 2 entries: h2, |w1|^2
+            CK(launch_multidot(N, j + 1, V, N, w, c->partials, h1d, s, true));
+            CK(launch_multiaxpy(N, j + 1, V, N, h1d, w, -1.0, s));
+            CK(launch_multidot(N, j + 1, V, N, w, c->partials, h2d, s, true));
+            CK(launch_multiaxpy(N, j + 1, V, N, h2d, w, -1.0, s));
+            CK(cudaMemcpyAsync(c->dots_host, h1d, size_t(j + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(c->dots_host + (m + 2), h2d, size_t(j + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
-            for (int i = 0; i <= j; ++i) { h1[i] = c->dots_host[i]; h2[i] = 0.0; }
-            const double before2 = c->dots_host[j + 1];
-            double hn2 = c->dots_host[j + 2];
-            if (!(hn2 > 0.5 * before2)) {
-                CK(launch_multidot(N, j + 1, V, N, w, c->partials, c->hdev, s));
-                CK(launch_multiaxpy(N, j + 1, V, N, c->hdev, w, -1.0, s));
-                CK(launch_multidot(N, 1, w, N, w, c->partials, c->hdev + j + 1, s));
-                CK(cudaMemcpyAsync(c->dots_host, c->hdev, size_t(j + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
-                CK(cudaStreamSynchronize(s));
-                for (int i = 0; i <= j; ++i) h2[i] = c->dots_host[i];
-                hn2 = c->dots_host[j + 1];
-                ++c->reorth_count;
+            double h2sq = 0.0;
+            for (int i = 0; i <= j; ++i) {
+                h1[i] = c->dots_host[i];
+                h2[i] = c->dots_host[m + 2 + i];
+                h2sq += h2[i] * h2[i];
             }
+            const double hn2 = std::fmax(c->dots_host[m + 2 + j + 1] - h2sq, 0.0);
             const double hn = std::sqrt(hn2);
             if (!std::isfinite(hn)) { st = STOKES_BREAKDOWN; done = true; break; }
             for (int i = 0; i <= j; ++i) Hij(i, j) = h1[i] + h2[i];
@@ -472,7 +487,8 @@ stokes_status setup_impl(const stokes_mesh* mesh, const stokes_mu* mu, const sto
     if (opt) c->opt = *opt; else stokes_default_options(&c->opt);
     const stokes_options& o = c->opt;
     if (o.cheb_degree < 1 || o.smoothing_range <= 1.0 || o.eig_safety <= 0.0 || o.lanczos_steps < 1 ||
-        o.schur_degree < 1 || o.restart < 1 || o.restart > 500)
+        o.schur_degree < 1 || o.restart < 1 || o.restart > 500 || (o.outer_arith != 0 && o.outer_arith != 1) ||
+        (o.vmult_kernel != 0 && o.vmult_kernel != 1))
         return fail(STOKES_EINVAL, "bad options");
     c->n = mesh->n;
     c->L = mesh->n_levels;
@@ -484,10 +500,19 @@ stokes_status setup_impl(const stokes_mesh* mesh, const stokes_mu* mu, const sto
     for (int l = 0; l < L; ++l) {
         Level& Lv = c->lev[l];
         const size_t nu = Lv.g.n_u, nc = Lv.g.cells;
-        for (auto* p : {&Lv.v64.b, &Lv.v64.x, &Lv.v64.r, &Lv.v64.d, &Lv.v64.t, &Lv.v64.dinv}) CKS(dalloc(c, p, nu));
-        for (auto* p : {&Lv.v32.b, &Lv.v32.x, &Lv.v32.r, &Lv.v32.d, &Lv.v32.t, &Lv.v32.dinv}) CKS(dalloc(c, p, nu));
+        for (auto* p : {&Lv.v64.b, &Lv.v64.x, &Lv.v64.r, &Lv.v64.d, &Lv.v64.t, &Lv.v64.dinv, &Lv.v64.acc})
+            CKS(dalloc(c, p, nu));
+        for (auto* p : {&Lv.v32.b, &Lv.v32.x, &Lv.v32.r, &Lv.v32.d, &Lv.v32.t, &Lv.v32.dinv, &Lv.v32.acc})
+            CKS(dalloc(c, p, nu));
+        CK(cudaMemsetAsync(Lv.v64.acc, 0, nu * sizeof(double), s));
+        CK(cudaMemsetAsync(Lv.v32.acc, 0, nu * sizeof(float), s));
+        CK(cudaMemsetAsync(Lv.v64.d, 0, nu * sizeof(double), s));
+        CK(cudaMemsetAsync(Lv.v32.d, 0, nu * sizeof(float), s));
         CKS(dalloc(c, &Lv.v64.mu, nc));
         CKS(dalloc(c, &Lv.v32.mu, nc));
+        Lv.planes = brick_layout(Lv.g.n);
+        CKS(dalloc(c, &Lv.slots64, Lv.planes.total));
+        CKS(dalloc(c, &Lv.slots32, Lv.planes.total));
     }
     CKS(dalloc(c, &c->ref_diag, 81));
     CKS(dalloc(c, &c->F, gf.n_u));
@@ -500,7 +525,7 @@ stokes_status setup_impl(const stokes_mesh* mesh, const stokes_mu* mu, const sto
     CKS(dalloc(c, &c->stage_out, gf.n_u));
     CKS(dalloc(c, &c->partials, size_t(multidot_blocks()) * (o.restart + 8)));
     CKS(dalloc(c, &c->dots, size_t(o.restart + 8)));
-    CK(cudaMallocHost(&c->dots_host, size_t(o.restart + 8) * sizeof(double)));   // >= restart + 4
+    CK(cudaMallocHost(&c->dots_host, size_t(2 * (o.restart + 8)) * sizeof(double)));
     // ---- viscosity (Section 2.3) and right-hand side (Section 3.2)
     double* centres = nullptr;
     if (mu->kind == 0) {
@@ -553,7 +578,7 @@ stokes_status setup_impl(const stokes_mesh* mesh, const stokes_mu* mu, const sto
         std::vector<double> al, be;
         for (int it = 0; it < o.lanczos_steps; ++it) {
             CK(launch_mul(n, sq, v, tmp, s));
-            CK(launch_vmult_A<double>(Lv.g, Lv.v64.mu, tmp, w, s));
+            CKS(vmult_level<double>(c, l, tmp, w, s));
             CK(launch_mul(n, sq, w, w, s));
             double alpha = 0.0;
             CKS(dot(c, n, w, v, s, &alpha));
@@ -593,7 +618,7 @@ stokes_status setup_impl(const stokes_mesh* mesh, const stokes_mu* mu, const sto
                 CK(cudaMemsetAsync(e, 0, L0.g.n_u * sizeof(double), s));
                 const double one = 1.0;
                 CK(cudaMemcpyAsync(e + idx[j], &one, sizeof(double), cudaMemcpyHostToDevice, s));
-                CK(launch_vmult_A<double>(L0.g, L0.v64.mu, e, Ae, s));
+                CKS(vmult_level<double>(c, 0, e, Ae, s));
                 CK(cudaMemcpyAsync(col.data(), Ae, L0.g.n_u * sizeof(double), cudaMemcpyDeviceToHost, s));
                 CK(cudaStreamSynchronize(s));
                 for (int i = 0; i < nf; ++i) A[size_t(i) * nf + j] = col[idx[i]];
@@ -643,6 +668,8 @@ void stokes_default_options(stokes_options* opt) {
     opt->lanczos_steps = 12;
     opt->schur_degree = 5;
     opt->restart = 50;
+    opt->outer_arith = 0;
+    opt->vmult_kernel = 0;
 }
 
 const char* stokes_strerror(stokes_status s) {
@@ -737,9 +764,9 @@ stokes_status stokes_vmult(stokes_ctx* c, int level, int block, int prec, const 
     Level& Lv = c->lev[level];
     if (block == STOKES_BLOCK_A) {
         if (prec == STOKES_FP32) {
-            CK(launch_vmult_A<float>(Lv.g, Lv.v32.mu, static_cast<const float*>(src), static_cast<float*>(dst), s));
+            CKS(vmult_level<float>(c, level, static_cast<const float*>(src), static_cast<float*>(dst), s));
         } else if (prec == STOKES_FP64) {
-            CK(launch_vmult_A<double>(Lv.g, Lv.v64.mu, static_cast<const double*>(src), static_cast<double*>(dst), s));
+            CKS(vmult_level<double>(c, level, static_cast<const double*>(src), static_cast<double*>(dst), s));
         } else {
             return fail(STOKES_EINVAL, "bad precision");
         }
@@ -751,10 +778,10 @@ stokes_status stokes_vmult(stokes_ctx* c, int level, int block, int prec, const 
     double* dd = static_cast<double*>(dst);
     switch (block) {
         case STOKES_BLOCK_B:
-            CK(launch_stokes_blocks(Lv.g, Lv.v64.mu, sd, nullptr, nullptr, dd, false, false, true, s));
+            CK(launch_stokes_blocks(Lv.g, Lv.v64.mu, sd, nullptr, nullptr, dd, false, false, true, c->opt.outer_arith == 1, s));
             return STOKES_OK;
         case STOKES_BLOCK_BT:
-            CK(launch_stokes_blocks(Lv.g, Lv.v64.mu, nullptr, sd, dd, nullptr, false, true, false, s));
+            CK(launch_stokes_blocks(Lv.g, Lv.v64.mu, nullptr, sd, dd, nullptr, false, true, false, c->opt.outer_arith == 1, s));
             return STOKES_OK;
         case STOKES_BLOCK_MP:
             CK(launch_mass_p(Lv.g, Lv.v64.mu, sd, dd, s));

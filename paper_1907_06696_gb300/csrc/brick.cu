@@ -1,0 +1,229 @@
+// brick.cu -- launchers of the brick-tiled velocity operator (brick.cuh).
+#include "brick.cuh"
+#include "prof.cuh"
+
+#include <cstdint>
+
+#define LAUNCH(cls, s, ...)              \
+    do {                                \
+        prof_begin((cls), (s));         \
+        __VA_ARGS__;                    \
+        prof_end((cls), (s));           \
+        prof_count(1);                  \
+    } while (0)
+
+namespace stk {
+
+namespace {
+
+template <typename T, int EPI, int BX, int BY, int BZ>
+__global__ void __launch_bounds__(BX * BY * BZ, sizeof(T) == 4 ? 3 : 1) k_brick(BrickArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    const int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
+    {
+        T w[3][27];
+        const bool valid = brick_compute<T, BX, BY, BZ>(a, bx, by, bz, threadIdx.x, w);
+        if (valid) brick_export<T, BX, BY, BZ>(threadIdx.x, w, sm);
+        __syncthreads();
+        if (valid) brick_own<T, BX, BY, BZ>(a, bx, by, bz, threadIdx.x, w, sm);
+    }
+    __syncthreads();
+    brick_epilogue<T, EPI, BX, BY, BZ>(a, bx, by, bz, threadIdx.x, blockDim.x, sm);
+}
+
+// ---- cell-parallel variant: one thread per cell, atomic adds into a zeroed accumulator;
+// the consumer kernels below run the epilogue and clear the accumulator again.
+template <typename T>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1) k_cell_atomic(BrickArgs<T> a, T* acc) {
+    const size_t cell = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (cell >= size_t(a.n) * a.n * a.n) return;
+    const int ci = int(cell % a.n), cj = int((cell / a.n) % a.n), ck = int(cell / (size_t(a.n) * a.n));
+    T w[3][27];
+    // brick_compute with a 1x1x1 brick at (ci, cj, ck)
+    if (!brick_compute<T, 1, 1, 1>(a, ci, cj, ck, 0, w)) return;
+    const int M = a.M;
+    T* out = acc + (size_t(2 * ci) + size_t(M) * (size_t(2 * cj) + size_t(M) * size_t(2 * ck)));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const bool bk = (2 * ck + k == 0) || (2 * ck + k == M - 1);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const bool bj = bk || (2 * cj + j == 0) || (2 * cj + j == M - 1);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                if (bj || (2 * ci + i == 0) || (2 * ci + i == M - 1)) continue;
+                const int off = i + M * (j + M * k);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) atomicAdd(out + c * a.nodes + off, w[c][i + 3 * j + 9 * k]);
+            }
+        }
+    }
+}
+
+// Consume the accumulated product and clear it. Constrained entries need no special
+// case: acc, b, dinv and d are 0 there. 128-bit accesses on the aligned bulk, scalar tail.
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = double2; };
+
+__device__ __forceinline__ float4 vzero(float4) { return make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ double2 vzero(double2) { return make_double2(0.0, 0.0); }
+
+// d = c1 d + c2 dinv (b - acc); x += d; acc = 0
+template <typename T>
+__global__ void __launch_bounds__(256) k_consume_cheb(size_t n, T* __restrict__ acc, const T* __restrict__ b,
+                                                     const T* __restrict__ dinv, T* __restrict__ d, T* __restrict__ x,
+                                                     T c1, T c2, bool vec) {
+    using V = typename Vec4<T>::type;
+    constexpr int W = sizeof(V) / sizeof(T);
+    const size_t nv = vec ? n / W : 0;
+    const size_t stride = size_t(gridDim.x) * blockDim.x;
+    for (size_t v = size_t(blockIdx.x) * blockDim.x + threadIdx.x; v < nv; v += stride) {
+        V A = reinterpret_cast<V*>(acc)[v];
+        const V B = reinterpret_cast<const V*>(b)[v], Di = reinterpret_cast<const V*>(dinv)[v];
+        V Dd = reinterpret_cast<V*>(d)[v], X = reinterpret_cast<V*>(x)[v];
+        T* a_ = reinterpret_cast<T*>(&A);
+        const T* b_ = reinterpret_cast<const T*>(&B);
+        const T* di_ = reinterpret_cast<const T*>(&Di);
+        T* d_ = reinterpret_cast<T*>(&Dd);
+        T* x_ = reinterpret_cast<T*>(&X);
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            const T dn = (c1 != T(0) ? c1 * d_[q] : T(0)) + c2 * (di_[q] * (b_[q] - a_[q]));
+            d_[q] = dn;
+            x_[q] += dn;
+        }
+        reinterpret_cast<V*>(acc)[v] = vzero(A);
+        reinterpret_cast<V*>(d)[v] = Dd;
+        reinterpret_cast<V*>(x)[v] = X;
+    }
+    for (size_t i = nv * W + size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const T dn = (c1 != T(0) ? c1 * d[i] : T(0)) + c2 * (dinv[i] * (b[i] - acc[i]));
+        acc[i] = T(0);
+        d[i] = dn;
+        x[i] += dn;
+    }
+}
+
+// r = b - acc; acc = 0
+template <typename T>
+__global__ void __launch_bounds__(256) k_consume_resid(size_t n, T* __restrict__ acc, const T* __restrict__ b,
+                                                      T* __restrict__ r, bool vec) {
+    using V = typename Vec4<T>::type;
+    constexpr int W = sizeof(V) / sizeof(T);
+    const size_t nv = vec ? n / W : 0;
+    const size_t stride = size_t(gridDim.x) * blockDim.x;
+    for (size_t v = size_t(blockIdx.x) * blockDim.x + threadIdx.x; v < nv; v += stride) {
+        V A = reinterpret_cast<V*>(acc)[v];
+        const V B = reinterpret_cast<const V*>(b)[v];
+        V R;
+        const T* a_ = reinterpret_cast<const T*>(&A);
+        const T* b_ = reinterpret_cast<const T*>(&B);
+        T* r_ = reinterpret_cast<T*>(&R);
+#pragma unroll
+        for (int q = 0; q < W; ++q) r_[q] = b_[q] - a_[q];
+        reinterpret_cast<V*>(acc)[v] = vzero(A);
+        reinterpret_cast<V*>(r)[v] = R;
+    }
+    for (size_t i = nv * W + size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+        r[i] = b[i] - acc[i];
+        acc[i] = T(0);
+    }
+}
+
+template <typename T, int EPI>
+__global__ void k_planes(BrickArgs<T> a, size_t total) {
+    const size_t t = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t < total) plane_node<T, EPI, kBrickX, kBrickY, kBrickZ>(a, t);
+}
+
+template <typename T, int EPI>
+cudaError_t launch_epi(const BrickArgs<T>& a, cudaStream_t s) {
+    using S = BrickShape<kBrickX, kBrickY, kBrickZ>;
+    constexpr size_t smem = S::template smem_bytes<T>();
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_brick<T, EPI, kBrickX, kBrickY, kBrickZ>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const dim3 grid(unsigned((a.n + kBrickX - 1) / kBrickX), unsigned((a.n + kBrickY - 1) / kBrickY),
+                    unsigned((a.n + kBrickZ - 1) / kBrickZ));
+    const int cls = sizeof(T) == 4 ? PROF_VMULT_F32 : PROF_VMULT_F64;
+    LAUNCH(cls, s, (k_brick<T, EPI, kBrickX, kBrickY, kBrickZ><<<grid, S::NC, smem, s>>>(a)));
+    const size_t total = plane_threads(a.L);
+    if (total > 0) LAUNCH(PROF_SMOOTH_VEC, s, (k_planes<T, EPI><<<unsigned((total + 255) / 256), 256, 0, s>>>(a, total)));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cell_epi(const BrickArgs<T>& a, int epi, T* acc, size_t n_u, cudaStream_t s) {
+    const size_t cells = size_t(a.n) * a.n * a.n;
+    const int cls = sizeof(T) == 4 ? PROF_VMULT_F32 : PROF_VMULT_F64;
+    if (epi == EPI_PLAIN) {
+        // dst = A src: accumulate straight into the zeroed dst, identity rows afterwards
+        cudaError_t e = cudaMemsetAsync(a.dst, 0, n_u * sizeof(T), s);
+        if (e != cudaSuccess) return e;
+        LAUNCH(cls, s, (k_cell_atomic<T><<<unsigned((cells + 127) / 128), 128, 0, s>>>(a, a.dst)));
+        LevelGeom g = make_geom(a.n);
+        return launch_copy_boundary<T>(g, a.src, a.dst, s);
+    }
+    LAUNCH(cls, s, (k_cell_atomic<T><<<unsigned((cells + 127) / 128), 128, 0, s>>>(a, acc)));
+    const size_t per = sizeof(T) == 4 ? 4 : 2;
+    const size_t b = (n_u / per + 255) / 256;
+    const unsigned blocks = unsigned(b < 1 ? 1 : (b < 4864 ? b : 4864));
+    // 128-bit accesses only when every operand is 16-byte aligned (callers may pass offset views)
+    auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+    if (epi == EPI_RESID) {
+        const bool vec = al(acc) && al(a.b) && al(a.dst);
+        LAUNCH(PROF_SMOOTH_VEC, s, (k_consume_resid<T><<<blocks, 256, 0, s>>>(n_u, acc, a.b, a.dst, vec)));
+    } else {
+        const bool vec = al(acc) && al(a.b) && al(a.dinv) && al(a.d) && al(a.src);
+        LAUNCH(PROF_SMOOTH_VEC, s, (k_consume_cheb<T><<<blocks, 256, 0, s>>>(n_u, acc, a.b, a.dinv, a.d,
+                                                                            const_cast<T*>(a.src), a.c1, a.c2, vec)));
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+PlaneLayout brick_layout(int n) { return make_plane_layout(n, kBrickX, kBrickY, kBrickZ); }
+
+template <typename T>
+cudaError_t launch_level_op(int kernel, const LevelGeom& g, const PlaneLayout& L, int epi, const T* mu, const T* src,
+                            T* dst, const T* b, const T* dinv, T* d, double c1, double c2, T* slots, T* acc,
+                            cudaStream_t s) {
+    BrickArgs<T> a;
+    a.n = g.n;
+    a.M = g.M;
+    a.nodes = g.nodes;
+    a.h = T(g.h);
+    a.mu = mu;
+    a.src = src;
+    a.dst = dst;
+    a.b = b;
+    a.dinv = dinv;
+    a.d = d;
+    a.c1 = T(c1);
+    a.c2 = T(c2);
+    a.slots = slots;
+    a.L = L;
+    if (kernel == 0) return launch_cell_epi<T>(a, epi, acc, g.n_u, s);
+    switch (epi) {
+        case EPI_PLAIN: return launch_epi<T, EPI_PLAIN>(a, s);
+        case EPI_RESID: return launch_epi<T, EPI_RESID>(a, s);
+        case EPI_CHEB: return launch_epi<T, EPI_CHEB>(a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template cudaError_t launch_level_op<float>(int, const LevelGeom&, const PlaneLayout&, int, const float*,
+                                            const float*, float*, const float*, const float*, float*, double, double,
+                                            float*, float*, cudaStream_t);
+template cudaError_t launch_level_op<double>(int, const LevelGeom&, const PlaneLayout&, int, const double*,
+                                             const double*, double*, const double*, const double*, double*, double,
+                                             double, double*, double*, cudaStream_t);
+
+}  // namespace stk

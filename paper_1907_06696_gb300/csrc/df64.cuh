@@ -1,0 +1,100 @@
+// df64.cuh -- double-float arithmetic: a value is the unevaluated sum hi + lo
+// of two floats (|lo| <= ulp(hi)/2), about 48 significant bits.
+//
+// Used for the FP64-accuracy outer Stokes operator: GB300 executes FP32 FMAs
+// at 72x its FP64 rate, and a double-float multiply-add costs ~18 FP32
+// instructions, so the operator runs several times faster than in native
+// FP64 while its rounding error (~2^-44 relative per operation) stays far
+// below the 1e-12 parity bound against the FP64 oracle.
+//
+// Error-free transformations (published methods):
+//   two_sum (Knuth, TAOCP vol. 2, 4.2.2): s = a + b exactly as s + e;
+//   fast_two_sum (Dekker 1971): the same when |a| >= |b|;
+//   two_prod with FMA: p = a * b exactly as p + fma(a, b, -p).
+// add() is the "sloppy" double-float sum (one two_sum on the high parts,
+// the low parts added in float), mul() the FMA-based double-float product
+// (T. J. Dekker, "A floating-point technique for extending the available
+// precision", Numer. Math. 18 (1971); Y. Hida, X. S. Li, D. H. Bailey,
+// "Algorithms for quad-double precision floating point arithmetic", 2001).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace q2 {
+
+struct df64 {
+    float hi, lo;
+    __host__ __device__ constexpr df64() : hi(0.0f), lo(0.0f) {}
+    __host__ __device__ constexpr df64(float h, float l) : hi(h), lo(l) {}
+    // rounds a double to the nearest double-float (exact for the constants used here to ~2^-48)
+    __host__ __device__ constexpr df64(double v) : hi(float(v)), lo(float(v - double(float(v)))) {}
+    __host__ __device__ constexpr df64(int v) : hi(float(v)), lo(0.0f) {}
+    __host__ __device__ double to_double() const { return double(hi) + double(lo); }
+};
+
+// Rounded float operations that the compiler must not contract into FMAs
+// (a contracted product would break the error-free transformations).
+// Host builds of this header must use -ffp-contract=off.
+__host__ __device__ __forceinline__ float fma_f(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
+    return __fmaf_rn(a, b, c);
+#else
+    return __builtin_fmaf(a, b, c);
+#endif
+}
+__host__ __device__ __forceinline__ float add_f(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fadd_rn(a, b);
+#else
+    return a + b;
+#endif
+}
+__host__ __device__ __forceinline__ float sub_f(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fsub_rn(a, b);
+#else
+    return a - b;
+#endif
+}
+__host__ __device__ __forceinline__ float mul_f(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fmul_rn(a, b);
+#else
+    return a * b;
+#endif
+}
+
+__host__ __device__ __forceinline__ df64 fast_two_sum(float a, float b) {
+    const float s = add_f(a, b);
+    return df64(s, sub_f(b, sub_f(s, a)));
+}
+
+__host__ __device__ __forceinline__ df64 operator+(const df64& x, const df64& y) {
+    const float s = add_f(x.hi, y.hi);
+    const float bb = sub_f(s, x.hi);
+    float e = add_f(sub_f(x.hi, sub_f(s, bb)), sub_f(y.hi, bb));
+    e = add_f(e, add_f(x.lo, y.lo));
+    return fast_two_sum(s, e);
+}
+
+__host__ __device__ __forceinline__ df64 operator-(const df64& x) { return df64(-x.hi, -x.lo); }
+__host__ __device__ __forceinline__ df64 operator-(const df64& x, const df64& y) { return x + (-y); }
+
+__host__ __device__ __forceinline__ df64 operator*(const df64& x, const df64& y) {
+    const float p = mul_f(x.hi, y.hi);
+    float e = fma_f(x.hi, y.hi, -p);
+    e = fma_f(x.hi, y.lo, e);
+    e = fma_f(x.lo, y.hi, e);
+    return fast_two_sum(p, e);
+}
+
+__host__ __device__ __forceinline__ df64& operator+=(df64& x, const df64& y) { return x = x + y; }
+__host__ __device__ __forceinline__ df64& operator*=(df64& x, const df64& y) { return x = x * y; }
+
+// Exact split of a double into a double-float (rounding of the low part only).
+__host__ __device__ __forceinline__ df64 from_double(double v) {
+    const float h = float(v);
+    return df64(h, float(v - double(h)));
+}
+
+}  // namespace q2

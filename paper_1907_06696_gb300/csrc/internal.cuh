@@ -32,15 +32,16 @@ inline LevelGeom make_geom(int n) {
 }
 
 // ---- operators (ops.cu) ----
-// dst = A_c src on one level (constrained rows: identity).
-template <typename T>
-cudaError_t launch_vmult_A(const LevelGeom& g, const T* mu, const T* src, T* dst, cudaStream_t s);
 // Finest-level FP64 blocks. Flags select the parts of [[A, B^T], [B, 0]]:
 // the u-part of dst gets A u (DO_A) + B^T p (DO_BT), the p-part gets B u (DO_B).
 // src_u / src_p may be null when unused; dst parts are overwritten.
+// df64 selects double-float arithmetic on the FP32 pipes (q2::df64) instead of native FP64.
 cudaError_t launch_stokes_blocks(const LevelGeom& g, const double* mu, const double* src_u, const double* src_p,
-                                 double* dst_u, double* dst_p, bool do_a, bool do_bt, bool do_b,
+                                 double* dst_u, double* dst_p, bool do_a, bool do_bt, bool do_b, bool df64,
                                  cudaStream_t s);
+// The same blocks in double-float arithmetic, one velocity component per thread (outer.cu).
+cudaError_t launch_outer_df64(const LevelGeom& g, const double* mu, const double* src_u, const double* src_p,
+                              double* dst_u, double* dst_p, bool do_a, bool do_bt, bool do_b, cudaStream_t s);
 // dst = M_p src (weighted pressure mass, FP64).
 cudaError_t launch_mass_p(const LevelGeom& g, const double* mu, const double* src, double* dst, cudaStream_t s);
 // diag(M_p) and int psi_l (pressure weights), FP64.

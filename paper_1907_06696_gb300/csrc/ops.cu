@@ -1,16 +1,17 @@
 // ops.cu -- matrix-free Q2-Q1 operators and the set-up kernels.
 //
-// A (Section 2.1): dst = A_c src, sum-factorised per cube cell (q2::cell_A),
-//   one thread per cell; contributions are accumulated into the zeroed dst
-//   with atomic adds; constrained (boundary-node) rows then get src.
-// B, B^T (Section 2.1) and the full Stokes operator: the same cell kernel plus
-//   the Q1 pressure interpolation / divergence moments, FP64.
+// The FP64 outer operator [A, B^T; B, 0] (Section 2.1): one thread per cube
+//   cell, sum-factorised A (q2::cell_A) and the 1D-moment tensor products of
+//   B and B^T; contributions are accumulated into the zeroed outputs with
+//   atomic adds and constrained (boundary-node) rows then get src. (The level
+//   operators of the V-cycle use the brick-tiled kernel of brick.cuh.)
 // M_p (Section 2.2.2): Q1 mass matrix weighted by 1/mu per cell.
 // Set-up: viscosity at the Gauss points and its harmonic cell average
 //   (Section 2.3), Q0 restriction (parent = mean of children, Section 2.3),
 //   the sinker right-hand side (Section 3.2), diagonals.
 #include "internal.cuh"
 #include "q2_basis.cuh"
+#include "df64.cuh"
 #include "prof.cuh"
 
 #define LAUNCH(cls, s, ...)              \
@@ -46,6 +47,48 @@ __device__ __forceinline__ void gather_u(const T* __restrict__ src, size_t nodes
             }
 }
 
+__device__ __forceinline__ double to_io(double v) { return v; }
+__device__ __forceinline__ double to_io(const q2::df64& v) { return double(v.hi) + double(v.lo); }
+template <typename CT> __device__ __forceinline__ CT from_io(double v);
+template <> __device__ __forceinline__ double from_io<double>(double v) { return v; }
+template <> __device__ __forceinline__ q2::df64 from_io<q2::df64>(double v) { return q2::from_double(v); }
+
+// dst += w (converted to FP64) on the free nodes of one cell.
+template <typename CT>
+__device__ __forceinline__ void scatter_io(double* __restrict__ dst, size_t nodes, int M, int ci, int cj, int ck,
+                                           const CT (&w)[3][27]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const int gi = 2 * ci + i, gj = 2 * cj + j, gk = 2 * ck + k;
+                if (on_bnd(gi, M) || on_bnd(gj, M) || on_bnd(gk, M)) continue;
+                const size_t node = size_t(gi) + size_t(M) * (gj + size_t(M) * gk);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) atomicAdd(dst + c * nodes + node, to_io(w[c][i + 3 * j + 9 * k]));
+            }
+}
+
+// u = src on the free nodes of one cell, 0 on constrained ones, converted to the compute type.
+template <typename CT>
+__device__ __forceinline__ void gather_io(const double* __restrict__ src, size_t nodes, int M, int ci, int cj, int ck,
+                                          CT (&u)[3][27]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const int gi = 2 * ci + i, gj = 2 * cj + j, gk = 2 * ck + k;
+                const bool b = on_bnd(gi, M) || on_bnd(gj, M) || on_bnd(gk, M);
+                const size_t node = size_t(gi) + size_t(M) * (gj + size_t(M) * gk);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) u[c][i + 3 * j + 9 * k] = b ? CT(0) : from_io<CT>(src[c * nodes + node]);
+            }
+}
+
 template <typename T>
 __device__ __forceinline__ void scatter_u(T* __restrict__ dst, size_t nodes, int M, int ci, int cj, int ck,
                                           const T (&w)[3][27], T scale) {
@@ -62,21 +105,6 @@ __device__ __forceinline__ void scatter_u(T* __restrict__ dst, size_t nodes, int
 #pragma unroll
                 for (int c = 0; c < 3; ++c) atomicAdd(dst + c * nodes + node, scale * w[c][i + 3 * j + 9 * k]);
             }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kCellThreads) k_vmult_A_atomic(int n, T h, const T* __restrict__ mu,
-                                                                 const T* __restrict__ src, T* __restrict__ dst) {
-    const size_t cell = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const size_t cells = size_t(n) * n * n;
-    if (cell >= cells) return;
-    const int ci = int(cell % n), cj = int((cell / n) % n), ck = int(cell / (size_t(n) * n));
-    const int M = 2 * n + 1;
-    const size_t nodes = size_t(M) * M * M;
-    T u[3][27], w[3][27];
-    gather_u(src, nodes, M, ci, cj, ck, u);
-    q2::cell_A(u, w);
-    scatter_u(dst, nodes, M, ci, cj, ck, w, mu[cell] * h);
 }
 
 // Boundary nodes of an M^3 lattice: 6 faces of M*M nodes (edges repeated; writes are identical).
@@ -96,8 +124,10 @@ __global__ void k_copy_boundary(int M, const T* __restrict__ in, T* __restrict__
     for (int c = 0; c < 3; ++c) out[c * nodes + node] = in ? in[c * nodes + node] : T(0);
 }
 
-// ---------------------------------------------------------------- Stokes blocks (FP64)
-template <bool DO_A, bool DO_BT, bool DO_B>
+// ---------------------------------------------------------------- Stokes blocks (FP64 in/out)
+// Native FP64, one thread per cell (CT = double). The double-float variant is the
+// component-split kernel of outer.cuh.
+template <typename CT, bool DO_A, bool DO_BT, bool DO_B>
 __global__ void __launch_bounds__(kCellThreads) k_stokes_blocks(int n, double h, const double* __restrict__ mu,
                                                                 const double* __restrict__ src_u,
                                                                 const double* __restrict__ src_p,
@@ -110,13 +140,13 @@ __global__ void __launch_bounds__(kCellThreads) k_stokes_blocks(int n, double h,
     const int M = 2 * n + 1;
     const size_t nodes = size_t(M) * M * M;
     const int P = n + 1;
-    double u[3][27], w[3][27];
-    if (DO_A || DO_B) gather_u(src_u, nodes, M, ci, cj, ck, u);
+    CT u[3][27], w[3][27];
+    if (DO_A || DO_B) gather_io<CT>(src_u, nodes, M, ci, cj, ck, u);
     if (DO_B) {
         // (B u)_v = -int div(u_h) psi_v = -h^2 sum_c (moments along each axis) . u_c
-        double bp[8];
+        CT bp[8];
 #pragma unroll
-        for (int v = 0; v < 8; ++v) bp[v] = 0.0;
+        for (int v = 0; v < 8; ++v) bp[v] = CT(0);
         q2::b_component<0>(u[0], bp);
         q2::b_component<1>(u[1], bp);
         q2::b_component<2>(u[2], bp);
@@ -124,13 +154,13 @@ __global__ void __launch_bounds__(kCellThreads) k_stokes_blocks(int n, double h,
 #pragma unroll
         for (int v = 0; v < 8; ++v) {
             const size_t vert = size_t(ci + (v & 1)) + size_t(P) * (cj + ((v >> 1) & 1) + size_t(P) * (ck + (v >> 2)));
-            atomicAdd(dst_p + vert, s * bp[v]);
+            atomicAdd(dst_p + vert, s * to_io(bp[v]));
         }
     }
     if (DO_A || DO_BT) {
         if (DO_A) {
             q2::cell_A(u, w);
-            const double sA = mu[cell] * h;
+            const CT sA = from_io<CT>(mu[cell] * h);
 #pragma unroll
             for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -139,23 +169,23 @@ __global__ void __launch_bounds__(kCellThreads) k_stokes_blocks(int n, double h,
 #pragma unroll
             for (int c = 0; c < 3; ++c)
 #pragma unroll
-                for (int a = 0; a < 27; ++a) w[c][a] = 0.0;
+                for (int a = 0; a < 27; ++a) w[c][a] = CT(0);
         }
         if (DO_BT) {
             // (B^T p)_(c,m) = -int d_c(phi_m) p_h = -h^2 sum_v (moments along each axis) p_v
-            double p8[8];
+            CT p8[8];
             const double s = -h * h;
 #pragma unroll
             for (int v = 0; v < 8; ++v) {
                 const size_t vert =
                     size_t(ci + (v & 1)) + size_t(P) * (cj + ((v >> 1) & 1) + size_t(P) * (ck + (v >> 2)));
-                p8[v] = s * src_p[vert];
+                p8[v] = from_io<CT>(s * src_p[vert]);
             }
             q2::bt_component<0>(p8, w[0]);
             q2::bt_component<1>(p8, w[1]);
             q2::bt_component<2>(p8, w[2]);
         }
-        scatter_u(dst_u, nodes, M, ci, cj, ck, w, 1.0);
+        scatter_io<CT>(dst_u, nodes, M, ci, cj, ck, w);
     }
 }
 
@@ -348,18 +378,6 @@ inline unsigned blocks_for(size_t n, int t) { return unsigned((n + t - 1) / t); 
 }  // namespace
 
 template <typename T>
-cudaError_t launch_vmult_A(const LevelGeom& g, const T* mu, const T* src, T* dst, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(dst, 0, g.n_u * sizeof(T), s);
-    if (e != cudaSuccess) return e;
-    LAUNCH((sizeof(T) == 4 ? PROF_VMULT_F32 : PROF_VMULT_F64), s, k_vmult_A_atomic<T><<<blocks_for(g.cells, kCellThreads), kCellThreads, 0, s>>>(g.n, T(g.h), mu, src, dst));
-    const size_t nb = 6 * size_t(g.M) * g.M;
-    LAUNCH(PROF_SMOOTH_VEC, s, k_copy_boundary<T><<<blocks_for(nb, 256), 256, 0, s>>>(g.M, src, dst));
-    return cudaGetLastError();
-}
-template cudaError_t launch_vmult_A<float>(const LevelGeom&, const float*, const float*, float*, cudaStream_t);
-template cudaError_t launch_vmult_A<double>(const LevelGeom&, const double*, const double*, double*, cudaStream_t);
-
-template <typename T>
 cudaError_t launch_copy_boundary(const LevelGeom& g, const T* in, T* out, cudaStream_t s) {
     const size_t nb = 6 * size_t(g.M) * g.M;
     LAUNCH(PROF_SMOOTH_VEC, s, k_copy_boundary<T><<<blocks_for(nb, 256), 256, 0, s>>>(g.M, in, out));
@@ -375,8 +393,26 @@ cudaError_t launch_zero_boundary(const LevelGeom& g, T* x, cudaStream_t s) {
 template cudaError_t launch_zero_boundary<float>(const LevelGeom&, float*, cudaStream_t);
 template cudaError_t launch_zero_boundary<double>(const LevelGeom&, double*, cudaStream_t);
 
+template <typename CT>
+cudaError_t stokes_blocks_ct(const LevelGeom& g, const double* mu, const double* src_u, const double* src_p,
+                             double* dst_u, double* dst_p, bool do_a, bool do_bt, bool do_b, cudaStream_t s) {
+    const unsigned nb = blocks_for(g.cells, kCellThreads);
+    const double h = g.h;
+    if (do_a && do_bt && do_b)
+        LAUNCH(PROF_STOKES_F64, s, (k_stokes_blocks<CT, true, true, true><<<nb, kCellThreads, 0, s>>>(g.n, h, mu, src_u, src_p, dst_u, dst_p)));
+    else if (do_a && !do_bt && !do_b)
+        LAUNCH(PROF_STOKES_F64, s, (k_stokes_blocks<CT, true, false, false><<<nb, kCellThreads, 0, s>>>(g.n, h, mu, src_u, src_p, dst_u, dst_p)));
+    else if (!do_a && do_bt && !do_b)
+        LAUNCH(PROF_BT_F64, s, (k_stokes_blocks<CT, false, true, false><<<nb, kCellThreads, 0, s>>>(g.n, h, mu, src_u, src_p, dst_u, dst_p)));
+    else if (!do_a && !do_bt && do_b)
+        LAUNCH(PROF_STOKES_F64, s, (k_stokes_blocks<CT, false, false, true><<<nb, kCellThreads, 0, s>>>(g.n, h, mu, src_u, src_p, dst_u, dst_p)));
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_stokes_blocks(const LevelGeom& g, const double* mu, const double* src_u, const double* src_p,
-                                 double* dst_u, double* dst_p, bool do_a, bool do_bt, bool do_b,
+                                 double* dst_u, double* dst_p, bool do_a, bool do_bt, bool do_b, bool df64,
                                  cudaStream_t s) {
     cudaError_t e;
     if (do_a || do_bt) {
@@ -387,21 +423,12 @@ cudaError_t launch_stokes_blocks(const LevelGeom& g, const double* mu, const dou
         e = cudaMemsetAsync(dst_p, 0, g.n_p * sizeof(double), s);
         if (e != cudaSuccess) return e;
     }
-    const unsigned nb = blocks_for(g.cells, kCellThreads);
-    const double h = g.h;
-    if (do_a && do_bt && do_b)
-        LAUNCH(PROF_STOKES_F64, s, k_stokes_blocks<true, true, true><<<nb, kCellThreads, 0, s>>>(g.n, h, mu, src_u, src_p, dst_u, dst_p));
-    else if (do_a && !do_bt && !do_b)
-        LAUNCH(PROF_STOKES_F64, s, k_stokes_blocks<true, false, false><<<nb, kCellThreads, 0, s>>>(g.n, h, mu, src_u, src_p, dst_u, dst_p));
-    else if (!do_a && do_bt && !do_b)
-        LAUNCH(PROF_BT_F64, s, k_stokes_blocks<false, true, false><<<nb, kCellThreads, 0, s>>>(g.n, h, mu, src_u, src_p, dst_u, dst_p));
-    else if (!do_a && !do_bt && do_b)
-        LAUNCH(PROF_STOKES_F64, s, k_stokes_blocks<false, false, true><<<nb, kCellThreads, 0, s>>>(g.n, h, mu, src_u, src_p, dst_u, dst_p));
-    else
-        return cudaErrorInvalidValue;
+    e = df64 ? launch_outer_df64(g, mu, src_u, src_p, dst_u, dst_p, do_a, do_bt, do_b, s)
+             : stokes_blocks_ct<double>(g, mu, src_u, src_p, dst_u, dst_p, do_a, do_bt, do_b, s);
+    if (e != cudaSuccess) return e;
     if (do_a) {
         const size_t nbd = 6 * size_t(g.M) * g.M;
-        LAUNCH(PROF_SMOOTH_VEC, s, k_copy_boundary<double><<<blocks_for(nbd, 256), 256, 0, s>>>(g.M, src_u, dst_u));
+        LAUNCH(PROF_SMOOTH_VEC, s, (k_copy_boundary<double><<<blocks_for(nbd, 256), 256, 0, s>>>(g.M, src_u, dst_u)));
     }
     return cudaGetLastError();
 }

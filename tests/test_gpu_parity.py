@@ -63,11 +63,16 @@ def oracle_problem(name):
 _ctx_cache = {}
 
 
-def gpu_ctx(capi, name):
-    if name not in _ctx_cache:
+def gpu_ctx(capi, name, kernel=0):
+    """Context of a named problem; kernel selects the V-cycle level operator
+    (0 = cell-parallel with atomic adds, 1 = brick-tiled deterministic)."""
+    key = (name, kernel)
+    if key not in _ctx_cache:
         p = oracle_problem(name)[0]
-        _ctx_cache[name] = capi.stokes_setup_problem(p)
-    return _ctx_cache[name]
+        opt = capi.stokes_default_options()
+        opt.vmult_kernel = kernel
+        _ctx_cache[key] = capi.stokes_setup_problem(p, options=opt)
+    return _ctx_cache[key]
 
 
 def dev(x, dtype=torch.float64):
@@ -116,10 +121,11 @@ def test_inverse_diagonal_and_lambda(capi, name):
 
 
 # ----------------------------------------------------------------- operators
+@pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("name", ["cube8", "n12", "cube16", "n24"])
-def test_vmult_A_all_levels(capi, name):
+def test_vmult_A_all_levels(capi, name, kernel):
     p, m, mus, G, ops, F = oracle_problem(name)
-    ctx = gpu_ctx(capi, name)
+    ctx = gpu_ctx(capi, name, kernel)
     for l, lev in enumerate(G.levels):
         x = si.uniform(300 + l, lev.mesh.n_u)          # includes constrained entries
         ref = lev.ops.apply_A(x)
@@ -132,10 +138,14 @@ def test_vmult_A_all_levels(capi, name):
             assert np.array_equal(got[lev.mesh.dirichlet], np.asarray(src.cpu().double())[lev.mesh.dirichlet])
 
 
+@pytest.mark.parametrize("arith", [0, 1])
 @pytest.mark.parametrize("name", ["cube8", "n12"])
-def test_pressure_blocks_and_stokes_operator(capi, name):
+def test_pressure_blocks_and_stokes_operator(capi, name, arith):
+    """Both arithmetics of the outer blocks: native FP64 and double-float."""
     p, m, mus, G, ops, F = oracle_problem(name)
-    ctx = gpu_ctx(capi, name)
+    opt = capi.stokes_default_options()
+    opt.outer_arith = arith
+    ctx = capi.stokes_setup_problem(p, options=opt)
     u = si.uniform(401, m.n_u)
     q = si.uniform(402, m.n_p)
     out_p = torch.empty(m.n_p, dtype=torch.float64, device="cuda")
@@ -150,6 +160,7 @@ def test_pressure_blocks_and_stokes_operator(capi, name):
     out = torch.empty(m.n_u + m.n_p, dtype=torch.float64, device="cuda")
     capi.stokes_vmult(ctx, -1, capi.BLOCK_STOKES, capi.STOKES_FP64, dev(up), out)
     assert_close(host(out), ops.apply_stokes(up), F64_TOL)
+    ctx.close()
 
 
 # ----------------------------------------------------------------- multigrid pieces
@@ -175,10 +186,11 @@ def test_transfers(capi, name):
             assert_close(host(outc), ref_r, tol)
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("name", ["cube8", "n12"])
-def test_chebyshev_smoother(capi, name):
+def test_chebyshev_smoother(capi, name, kernel):
     p, m, mus, G, ops, F = oracle_problem(name)
-    ctx = gpu_ctx(capi, name)
+    ctx = gpu_ctx(capi, name, kernel)
     for l in range(1, p.n_levels):
         lev = G.levels[l]
         b = si.uniform(700 + l, lev.mesh.n_u) * lev.free
@@ -205,10 +217,11 @@ def test_coarse_solve(capi, name):
         assert_close(host(x), ref, tol)
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("name", ["cube8", "n12", "cube16", "n24"])
-def test_vcycle(capi, name):
+def test_vcycle(capi, name, kernel):
     p, m, mus, G, ops, F = oracle_problem(name)
-    ctx = gpu_ctx(capi, name)
+    ctx = gpu_ctx(capi, name, kernel)
     rhs = si.uniform(1000, m.n_u)
     ref = G.vcycle(rhs)
     for prec, dt, tol in ((capi.STOKES_FP64, torch.float64, 1e-10), (capi.STOKES_FP32, torch.float32, F32_CYCLE_TOL)):
@@ -259,14 +272,17 @@ def test_solve_fp64_and_fp32_vcycle(capi, name):
     assert its[capi.STOKES_FP32] <= 1.2 * its[capi.STOKES_FP64] + 1
 
 
-def test_solve_matches_dense_direct(capi):
+@pytest.mark.parametrize("arith", [0, 1])
+def test_solve_matches_dense_direct(capi, arith):
     p = si.workload("cube4")
     m = mesh.Mesh(p.n)
     mus = sinker.level_viscosities(m, p, p.n_levels)
     ops = operators.Operators(m, mus[-1])
     F = operators.assemble_rhs(m, sinker.forcing(m.quad_points(), p))
     xd = krylov.dense_stokes_solve(ops, F)
-    ctx = capi.stokes_setup_problem(p)
+    opt = capi.stokes_default_options()
+    opt.outer_arith = arith
+    ctx = capi.stokes_setup_problem(p, options=opt)
     for prec in (capi.STOKES_FP64, capi.STOKES_FP32):
         up = torch.zeros(m.n_u + m.n_p, dtype=torch.float64, device="cuda")
         capi.stokes_solve(ctx, prec, None, up, rtol=1e-12, max_it=500)
