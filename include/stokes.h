@@ -247,6 +247,9 @@ stokes_status stokes_profile(int enable);
 stokes_status stokes_profile_read(int cls, double* ms, long long* launches, int reset);
 /* Number of kernel launches the library has issued since it was loaded. */
 long long stokes_launch_count(void);
+/* FP32 and FP64 FMA throughput of the current device in TFLOP/s (eight independent FMA
+ * chains per thread, 8 CTAs of 256 threads per SM, ~10 ms each; synchronous). */
+stokes_status stokes_probe_fma(double* fp32_tflops, double* fp64_tflops);
 
 #ifdef __cplusplus
 }

@@ -83,6 +83,7 @@ _SIGS = {
     "stokes_profile": (C.c_int, [C.c_int]),
     "stokes_profile_read": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int]),
     "stokes_launch_count": (C.c_longlong, []),
+    "stokes_probe_fma": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double)]),
 }
 
 PROF_CLASSES = ["vmult_A_fp32", "vmult_A_fp64", "stokes_fp64", "bt_fp64", "mass_p", "transfer",
@@ -302,6 +303,13 @@ def stokes_profile_read(reset=True):
 
 def stokes_launch_count():
     return int(load().stokes_launch_count())
+
+
+def stokes_probe_fma():
+    """(FP32, FP64) FMA throughput of the current device in TFLOP/s."""
+    a, b = C.c_double(), C.c_double()
+    _check(load().stokes_probe_fma(C.byref(a), C.byref(b)), "stokes_probe_fma")
+    return a.value, b.value
 
 
 def header_functions(header=None):
