@@ -110,6 +110,10 @@ typedef struct {
     int vmult_kernel;           /* level operator of the V-cycle: 0 = one thread per cell with atomic adds
                                    and a separate epilogue pass (default, fastest); 1 = brick-tiled,
                                    atomic-free and deterministic, epilogue fused */
+    int graphs;                 /* 1 = capture the V-cycle's level recursion once per precision as a CUDA
+                                   graph and replay it on a library stream ordered with the caller's
+                                   stream by events (default); 0 = launch kernel by kernel. The first
+                                   V-cycle of each precision performs the capture. */
 } stokes_options;
 
 typedef struct {

@@ -80,6 +80,8 @@ void prof_end(int cls, cudaStream_t s) {
     if (g_recs.size() > 200000) drain();
 }
 void prof_count(int k) { g_launches += k; }
+bool prof_enabled() { return g_prof_on; }
+long long launch_total() { return g_launches; }
 
 }  // namespace stk
 
@@ -166,6 +168,11 @@ struct stokes_ctx {
     int krylov_restart = 0;
     // host-buffer solve
     double *h_rhs_dev = nullptr, *h_up_dev = nullptr;
+    // V-cycle replayed as a captured CUDA graph on a library stream (per precision)
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t gev_in = nullptr, gev_out = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // [FP64, FP32]
+    long long glaunches[2] = {0, 0};                 // kernel launches inside each graph
 };
 
 namespace {
@@ -288,13 +295,50 @@ stokes_status vcycle_level(stokes_ctx* c, int l, cudaStream_t s) {
     return STOKES_OK;
 }
 
+// The level recursion of one V-cycle. It touches only the context's level buffers, so it is
+// captured once per precision as a CUDA graph and replayed on the library stream (ordered
+// after and before the caller's stream by events). Profiling runs it launch by launch.
+template <typename T>
+stokes_status run_levels(stokes_ctx* c, cudaStream_t s) {
+    if (!c->opt.graphs || prof_enabled()) return vcycle_level<T>(c, c->L - 1, s);
+    const int p = sizeof(T) == 4 ? 1 : 0;
+    if (!c->gstream) {
+        CK(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&c->gev_in, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c->gev_out, cudaEventDisableTiming));
+    }
+    CK(cudaEventRecord(c->gev_in, s));
+    CK(cudaStreamWaitEvent(c->gstream, c->gev_in, 0));
+    if (!c->gexec[p]) {
+        cudaGraph_t graph = nullptr;
+        const long long before = launch_total();
+        CK(cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
+        stokes_status st = vcycle_level<T>(c, c->L - 1, c->gstream);
+        cudaError_t e = cudaStreamEndCapture(c->gstream, &graph);
+        if (st != STOKES_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        CK(e);
+        e = cudaGraphInstantiate(&c->gexec[p], graph, 0);
+        cudaGraphDestroy(graph);
+        CK(e);
+        c->glaunches[p] = launch_total() - before;
+    }
+    CK(cudaGraphLaunch(c->gexec[p], c->gstream));
+    prof_count(int(c->glaunches[p]));
+    CK(cudaEventRecord(c->gev_out, c->gstream));
+    CK(cudaStreamWaitEvent(s, c->gev_out, 0));
+    return STOKES_OK;
+}
+
 template <typename T>
 stokes_status vcycle(stokes_ctx* c, const T* rhs, T* x, cudaStream_t s) {
     Level& F = c->lev[c->L - 1];
     LevelVecs<T>& v = vecs<T>(F);
     CK(cudaMemcpyAsync(v.b, rhs, F.g.n_u * sizeof(T), cudaMemcpyDeviceToDevice, s));
     CK(launch_zero_boundary<T>(F.g, v.b, s));
-    CKS(vcycle_level<T>(c, c->L - 1, s));
+    CKS(run_levels<T>(c, s));
     CK(cudaMemcpyAsync(x, v.x, F.g.n_u * sizeof(T), cudaMemcpyDeviceToDevice, s));
     CK(launch_copy_boundary<T>(F.g, rhs, x, s));
     return STOKES_OK;
@@ -488,8 +532,9 @@ stokes_status setup_impl(const stokes_mesh* mesh, const stokes_mu* mu, const sto
     const stokes_options& o = c->opt;
     if (o.cheb_degree < 1 || o.smoothing_range <= 1.0 || o.eig_safety <= 0.0 || o.lanczos_steps < 1 ||
         o.schur_degree < 1 || o.restart < 1 || o.restart > 500 || (o.outer_arith != 0 && o.outer_arith != 1) ||
-        (o.vmult_kernel != 0 && o.vmult_kernel != 1))
+        (o.vmult_kernel != 0 && o.vmult_kernel != 1) || (o.graphs != 0 && o.graphs != 1))
         return fail(STOKES_EINVAL, "bad options");
+    CK(brick_configure());
     c->n = mesh->n;
     c->L = mesh->n_levels;
     const int L = c->L;
@@ -670,6 +715,7 @@ void stokes_default_options(stokes_options* opt) {
     opt->restart = 50;
     opt->outer_arith = 0;
     opt->vmult_kernel = 0;
+    opt->graphs = 1;
 }
 
 const char* stokes_strerror(stokes_status s) {
@@ -736,6 +782,11 @@ stokes_status stokes_setup(const stokes_mesh* mesh, const stokes_mu* mu, const s
 void stokes_destroy(stokes_ctx* c) {
     if (!c) return;
     cudaDeviceSynchronize();
+    for (cudaGraphExec_t& ge : c->gexec)
+        if (ge) cudaGraphExecDestroy(ge);
+    if (c->gev_in) cudaEventDestroy(c->gev_in);
+    if (c->gev_out) cudaEventDestroy(c->gev_out);
+    if (c->gstream) cudaStreamDestroy(c->gstream);
     for (void* p : c->allocs) cudaFree(p);
     if (c->dots_host) cudaFreeHost(c->dots_host);
     delete c;

@@ -139,16 +139,16 @@ __global__ void k_planes(BrickArgs<T> a, size_t total) {
 }
 
 template <typename T, int EPI>
+cudaError_t configure_epi() {
+    using S = BrickShape<kBrickX, kBrickY, kBrickZ>;
+    return cudaFuncSetAttribute(k_brick<T, EPI, kBrickX, kBrickY, kBrickZ>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::template smem_bytes<T>()));
+}
+
+template <typename T, int EPI>
 cudaError_t launch_epi(const BrickArgs<T>& a, cudaStream_t s) {
     using S = BrickShape<kBrickX, kBrickY, kBrickZ>;
     constexpr size_t smem = S::template smem_bytes<T>();
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_brick<T, EPI, kBrickX, kBrickY, kBrickZ>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
     const dim3 grid(unsigned((a.n + kBrickX - 1) / kBrickX), unsigned((a.n + kBrickY - 1) / kBrickY),
                     unsigned((a.n + kBrickZ - 1) / kBrickZ));
     const int cls = sizeof(T) == 4 ? PROF_VMULT_F32 : PROF_VMULT_F64;
@@ -190,6 +190,16 @@ cudaError_t launch_cell_epi(const BrickArgs<T>& a, int epi, T* acc, size_t n_u, 
 }  // namespace
 
 PlaneLayout brick_layout(int n) { return make_plane_layout(n, kBrickX, kBrickY, kBrickZ); }
+
+cudaError_t brick_configure() {
+    cudaError_t e;
+    if ((e = configure_epi<float, EPI_PLAIN>()) != cudaSuccess) return e;
+    if ((e = configure_epi<float, EPI_RESID>()) != cudaSuccess) return e;
+    if ((e = configure_epi<float, EPI_CHEB>()) != cudaSuccess) return e;
+    if ((e = configure_epi<double, EPI_PLAIN>()) != cudaSuccess) return e;
+    if ((e = configure_epi<double, EPI_RESID>()) != cudaSuccess) return e;
+    return configure_epi<double, EPI_CHEB>();
+}
 
 template <typename T>
 cudaError_t launch_level_op(int kernel, const LevelGeom& g, const PlaneLayout& L, int epi, const T* mu, const T* src,

@@ -343,6 +343,8 @@ inline size_t plane_threads(const PlaneLayout& L) {
 
 // Layout of the plane slots for an n^3 level with the library's brick shape.
 PlaneLayout brick_layout(int n);
+// Shared-memory opt-in of every brick kernel instantiation (call once before any launch or capture).
+cudaError_t brick_configure();
 // A x with an epilogue (EPI_PLAIN: dst = A x; EPI_RESID: dst = b - A x;
 // EPI_CHEB: d = c1 d + c2 dinv (b - A x), src += d in place).
 // kernel 0: one thread per cell with atomic adds into acc (n_u entries, zero on entry and on

@@ -25,5 +25,7 @@ enum ProfClass {
 void prof_begin(int cls, cudaStream_t s);
 void prof_end(int cls, cudaStream_t s);
 void prof_count(int launches);
+bool prof_enabled();
+long long launch_total();
 
 }  // namespace stk

@@ -295,6 +295,35 @@ def test_solve_matches_dense_direct(capi, arith):
 
 
 # ----------------------------------------------------------------- edge cases
+@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_graph_replay_matches_kernel_launches(capi, prec, kernel):
+    """The captured V-cycle graph runs the same kernels in the same order, over two replays with
+    different right-hand sides: bitwise equal output with the deterministic brick operator; with
+    the atomic operator (summation order varies from run to run) equal to rounding."""
+    p = oracle_problem("n12")[0]
+    outs = []
+    for graphs in (0, 1):
+        opt = capi.stokes_default_options()
+        opt.graphs = graphs
+        opt.vmult_kernel = kernel
+        ctx = capi.stokes_setup_problem(p, options=opt)
+        dt = torch.float64 if prec == 0 else torch.float32
+        res = []
+        for seed in (5000, 5001):
+            rhs = dev(si.uniform(seed, ctx.n_u), dt)
+            x = torch.empty_like(rhs)
+            capi.gmg_vcycle(ctx, prec, rhs, x)
+            res.append(host(x))
+        outs.append(res)
+        ctx.close()
+    for a, b in zip(outs[0], outs[1]):
+        if kernel == 1:
+            assert np.array_equal(a, b)
+        else:
+            assert rel(a, b) <= (1e-13 if prec == 0 else 1e-6)
+
+
 def test_single_level_and_two_level_meshes(capi):
     for n, L in ((1, 1), (2, 2), (3, 1), (4, 1)):
         p = si.dr_problem(n, L, 1, 1e2, 3000 + n)
