@@ -410,9 +410,70 @@ def run_kernels(args):
     print(json.dumps({"kernels": args.workload, "n_u": n_u, "n_p": n_p}))
 
 
+def run_batch(args):
+    """Batched workload: many independent sinker problems of uneven sizes solved together with the
+    FP32 V-cycle (stokes_batch_solve), against the same problems solved one after the other with the
+    FP64 V-cycle."""
+    import torch
+    from paper_1907_06696_gb300 import build as B
+    B.build()
+    from paper_1907_06696_gb300 import capi
+    capi.load()
+    import sinker_inputs as si
+    count = int(args.workload[len("batch"):] or 64)
+    probs = si.batch_workload(count)
+    ctxs = [capi.stokes_setup_problem(p) for p in probs]
+    ups = [torch.zeros(c.n_u + c.n_p, dtype=torch.float64, device="cuda") for c in ctxs]
+    ndof = sum(c.n_u + c.n_p for c in ctxs)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def batch():
+        for u in ups:
+            u.zero_()
+        return capi.stokes_batch_solve(ctxs, capi.STOKES_FP32, ups, rtol=RTOL, max_it=3000)
+
+    for _ in range(max(args.warmup, 1)):
+        batch()
+    torch.cuda.synchronize()
+    clk, clk_path = clocks_start(torch.cuda.current_device())
+    l0 = capi.stokes_launch_count()
+    e0.record()
+    for _ in range(args.steps):
+        infos = batch()
+    e1.record()
+    torch.cuda.synchronize()
+    launches = capi.stokes_launch_count() - l0
+    clocks = clocks_stop(clk, clk_path)
+    ms = e0.elapsed_time(e1) / args.steps
+    # reference: the same problems solved one after the other with the FP64 V-cycle
+    e0.record()
+    seq_its = []
+    for c, u in zip(ctxs, ups):
+        u.zero_()
+        seq_its.append(capi.stokes_solve(c, capi.STOKES_FP64, None, u, rtol=RTOL, max_it=3000).iterations)
+    e1.record()
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    line = {"metric": METRIC, "value": ndof / (ms / 1e3) / 1e9, "unit": "GDoF/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 outer + f32 V-cycle", "data": "synthetic",
+            "config": {"workload": args.workload, "problems": count,
+                       "sizes": sorted(set(p.n for p in probs)), "total_dofs": ndof, "rtol": RTOL},
+            "batch": {"fp32_batch_s": ms / 1e3, "iterations": [i.iterations for i in infos],
+                      "max_true_rel_residual": max(i.rel_residual_true for i in infos),
+                      "fp64_sequential_s": seq_ms / 1e3, "fp64_sequential_iterations": seq_its,
+                      "speedup": seq_ms / ms},
+            "gpu_launches": int(launches), "clocks": clocks}
+    for c in ctxs:
+        c.close()
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
-    if args.kernels:
+    if args.workload.startswith("batch") and args.impl != "reference":
+        run_batch(args)
+    elif args.kernels:
         run_kernels(args)
     elif args.impl == "reference":
         run_reference(args)

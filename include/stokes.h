@@ -180,6 +180,20 @@ stokes_status gmg_vcycle(stokes_ctx* ctx, int prec, const void* rhs_dev, void* x
 stokes_status stokes_solve(stokes_ctx* ctx, int vcycle_prec, const double* rhs_dev, double* up_dev,
                            double rtol, int max_it, stokes_solve_info* info, void* stream);
 
+/* Solve n_problems independent Stokes systems together (each context from its own stokes_setup,
+ * any sizes): the same FGMRES as stokes_solve, with the iterations of all unconverged problems
+ * advancing in lock step. Each problem's kernels run on its own stream (streams[i]; streams = NULL:
+ * library-created streams), so small problems share the GPU, and each problem's V-cycle is replayed
+ * as its captured graph. rhs_devs = NULL or rhs_devs[i] = NULL: the sinker right-hand side [F; 0].
+ * up_devs[i]: in = initial guess, out = solution (zero-mean pressure). infos[i] (optional) per
+ * problem; seconds = wall time of the whole batch. Host-synchronous. A context may appear only once.
+ * Errors: EINVAL, ENOMEM, ECUDA; NOT_CONVERGED or BREAKDOWN if any problem ended so (the others
+ * are still solved). No counterpart in the paper: batching is the GPU's way to fill the device with
+ * many small problems. */
+stokes_status stokes_batch_solve(int n_problems, stokes_ctx* const* ctxs, int vcycle_prec,
+                                 const double* const* rhs_devs, double* const* up_devs, double rtol, int max_it,
+                                 stokes_solve_info* infos, void* const* streams);
+
 /* Same as stokes_solve with HOST buffers: copies rhs_host (or uses the sinker
  * F when NULL) to library-owned device memory, solves from a zero initial
  * guess and copies the solution to up_host (length N_u + N_p). */

@@ -69,6 +69,8 @@ _SIGS = {
     "gmg_vcycle": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "stokes_solve": (C.c_int, [_P, C.c_int, _P, _P, C.c_double, C.c_int, C.POINTER(stokes_solve_info), _P]),
     "stokes_solve_host": (C.c_int, [_P, C.c_int, _P, _P, C.c_double, C.c_int, C.POINTER(stokes_solve_info), _P]),
+    "stokes_batch_solve": (C.c_int, [C.c_int, C.POINTER(_P), C.c_int, C.POINTER(_P), C.POINTER(_P), C.c_double,
+                                     C.c_int, C.POINTER(stokes_solve_info), C.POINTER(_P)]),
     "stokes_get_viscosity": (C.c_int, [_P, C.c_int, _P, _P]),
     "stokes_get_inv_diagonal": (C.c_int, [_P, C.c_int, _P, _P]),
     "stokes_get_lambda_max": (C.c_int, [_P, C.c_int, C.POINTER(C.c_double)]),
@@ -222,6 +224,21 @@ def stokes_solve(ctx, vcycle_prec, rhs, up, rtol=1e-8, max_it=1000, stream=None,
     if check:
         _check(st, "stokes_solve")
     return info
+
+
+def stokes_batch_solve(ctxs, vcycle_prec, ups, rtol=1e-8, max_it=1000, rhs=None, streams=None, check=True):
+    """Solve the problems of several contexts together; ups: device solution vectors (in: guess)."""
+    n = len(ctxs)
+    infos = (stokes_solve_info * n)()
+    P = C.c_void_p
+    cptr = (P * n)(*[x.handle for x in ctxs])
+    uptr = (P * n)(*[_ptr(u) for u in ups])
+    rptr = (P * n)(*[_ptr(r) for r in rhs]) if rhs is not None else None
+    sptr = (P * n)(*[_stream(s) for s in streams]) if streams is not None else None
+    st = load().stokes_batch_solve(n, cptr, vcycle_prec, rptr, uptr, rtol, max_it, infos, sptr)
+    if check:
+        _check(st, "stokes_batch_solve")
+    return list(infos)
 
 
 def stokes_solve_host(ctx, vcycle_prec, rhs_host, up_host, rtol=1e-8, max_it=1000, stream=None, check=True):

@@ -410,110 +410,221 @@ stokes_status remove_pressure_mean(stokes_ctx* c, double* up, cudaStream_t s) {
     return STOKES_OK;
 }
 
-stokes_status fgmres(stokes_ctx* c, int prec, const double* b, double* x, double rtol, int max_it,
-                     stokes_solve_info* info, cudaStream_t s) {
-    CKS(ensure_krylov(c));
-    const size_t N = c->N;
-    const int m = c->opt.restart;
-    double* V = c->V;
-    double* Z = c->Z;
-    double* w = c->w;
-    double bnorm2 = 0.0;
-    CKS(dot(c, N, b, b, s, &bnorm2));
-    const double bnorm = std::sqrt(bnorm2);
-    int its = 0;
-    double est = 1.0;
+// Right-preconditioned FGMRES(restart) as a resumable state machine: enqueue() issues one
+// phase's kernels on the run's stream and a small device->host copy; complete() runs the host
+// part once that stream has finished. One problem (stokes_solve) or many in lock step
+// (stokes_batch_solve) use the same code.
+struct FgmresRun {
+    enum Phase { P_BNORM, P_RESTART, P_ITER, P_FINAL, P_DONE };
+    stokes_ctx* c = nullptr;
+    int prec = 0;
+    const double* b = nullptr;
+    double* x = nullptr;
+    double rtol = 1e-8;
+    int max_it = 1;
+    cudaStream_t s = nullptr;
+    stokes_solve_info* info = nullptr;
+    Phase phase = P_BNORM;
     stokes_status st = STOKES_NOT_CONVERGED;
-    std::vector<double> H(size_t(m + 1) * m), cs(m), sn(m), g(m + 1), y(m), h1(m + 2), h2(m + 2);
-    auto Hij = [&](int i, int j) -> double& { return H[size_t(i) * m + j]; };
-    if (bnorm == 0.0) {
-        CK(cudaMemsetAsync(x, 0, N * sizeof(double), s));
-        est = 0.0;
-        st = STOKES_OK;
-    }
-    while (st == STOKES_NOT_CONVERGED && its < max_it) {
-        CKS(apply_stokes(c, x, w, s));
-        CK(launch_axpby(N, 1.0, b, -1.0, w, s));                              // w = b - K x
-        double beta2 = 0.0;
-        CKS(dot(c, N, w, w, s, &beta2));
-        const double beta = std::sqrt(beta2);
-        if (!std::isfinite(beta)) { st = STOKES_BREAKDOWN; break; }
-        est = beta / bnorm;
-        if (beta <= rtol * bnorm) { st = STOKES_OK; break; }
-        CK(launch_axpby(N, 1.0 / beta, w, 0.0, V, s));
-        std::fill(g.begin(), g.end(), 0.0);
-        g[0] = beta;
-        int k = 0;
-        bool done = false;
-        for (int j = 0; j < m && its < max_it; ++j) {
+    int its = 0, j = 0, m = 0;
+    double bnorm = 0.0, est = 1.0, hn_prev = 0.0;
+    bool next_v = false;   // V_{j} = w / hn_prev still to be formed before iteration j
+    std::vector<double> H, cs, sn, g, y;
+    double& Hij(int i, int jj) { return H[size_t(i) * m + jj]; }
+};
+
+stokes_status fgmres_enqueue(FgmresRun& r) {
+    stokes_ctx* c = r.c;
+    const size_t N = c->N;
+    const int m = r.m;
+    cudaStream_t s = r.s;
+    switch (r.phase) {
+        case FgmresRun::P_BNORM:
+            CK(launch_multidot(N, 1, r.b, N, r.b, c->partials, c->dots, s));
+            CK(cudaMemcpyAsync(c->dots_host, c->dots, sizeof(double), cudaMemcpyDeviceToHost, s));
+            return STOKES_OK;
+        case FgmresRun::P_RESTART:
+            CKS(apply_stokes(c, r.x, c->w, s));
+            CK(launch_axpby(N, 1.0, r.b, -1.0, c->w, s));                              // w = b - K x
+            CK(launch_multidot(N, 1, c->w, N, c->w, c->partials, c->dots, s));
+            CK(cudaMemcpyAsync(c->dots_host, c->dots, sizeof(double), cudaMemcpyDeviceToHost, s));
+            return STOKES_OK;
+        case FgmresRun::P_ITER: {
+            const int j = r.j;
+            double* V = c->V;
             double* vj = V + size_t(j) * N;
-            double* zj = Z + size_t(j) * N;
-            CKS(precondition(c, prec, vj, zj, s));
-            CKS(apply_stokes(c, zj, w, s));
+            double* zj = c->Z + size_t(j) * N;
+            if (r.next_v) CK(launch_axpby(N, 1.0 / r.hn_prev, c->w, 0.0, vj, s));   // V_j = w / |w|
+            CKS(precondition(c, r.prec, vj, zj, s));
+            CKS(apply_stokes(c, zj, c->w, s));
             // classical Gram-Schmidt applied twice ("twice is enough"); the second multi-dot also
-            // returns |w1|^2 of the once-projected vector, so |w2|^2 = |w1|^2 - |h2|^2 (no cancellation:
-            // h2 is small after the first pass) and one host synchronisation serves the iteration.
-            double* h1d = c->hdev;              // j + 2 entries: h1, |w|^2
-            double* h2d = c->hdev + (m + 2);    // j + 2 entries: h2, |w1|^2
-            CK(launch_multidot(N, j + 1, V, N, w, c->partials, h1d, s, true));
-            CK(launch_multiaxpy(N, j + 1, V, N, h1d, w, -1.0, s));
-            CK(launch_multidot(N, j + 1, V, N, w, c->partials, h2d, s, true));
-            CK(launch_multiaxpy(N, j + 1, V, N, h2d, w, -1.0, s));
-            CK(cudaMemcpyAsync(c->dots_host, h1d, size_t(j + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
-            CK(cudaMemcpyAsync(c->dots_host + (m + 2), h2d, size_t(j + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
+            // returns |w1|^2 of the once-projected vector, so |w2|^2 = |w1|^2 - |h2|^2 (no
+            // cancellation: h2 is small after the first pass)
+            double* h1d = c->hdev;
+            double* h2d = c->hdev + (m + 2);
+            CK(launch_multidot(N, j + 1, V, N, c->w, c->partials, h1d, s, true));
+            CK(launch_multiaxpy(N, j + 1, V, N, h1d, c->w, -1.0, s));
+            CK(launch_multidot(N, j + 1, V, N, c->w, c->partials, h2d, s, true));
+            CK(launch_multiaxpy(N, j + 1, V, N, h2d, c->w, -1.0, s));
+            CK(cudaMemcpyAsync(c->dots_host, c->hdev, size_t(2 * (m + 2)) * sizeof(double), cudaMemcpyDeviceToHost, s));
+            return STOKES_OK;
+        }
+        case FgmresRun::P_FINAL:
+            CKS(remove_pressure_mean(c, r.x, s));   // synchronous (one dot)
+            CKS(apply_stokes(c, r.x, c->w, s));
+            CK(launch_axpby(N, 1.0, r.b, -1.0, c->w, s));
+            CK(launch_multidot(N, 1, c->w, N, c->w, c->partials, c->dots, s));
+            CK(cudaMemcpyAsync(c->dots_host, c->dots, sizeof(double), cudaMemcpyDeviceToHost, s));
+            return STOKES_OK;
+        case FgmresRun::P_DONE:
+            return STOKES_OK;
+    }
+    return STOKES_OK;
+}
+
+// x += Z y for the finished cycle (y from the upper-triangular solve on the host).
+stokes_status fgmres_update_x(FgmresRun& r, int k) {
+    stokes_ctx* c = r.c;
+    for (int i = k - 1; i >= 0; --i) {
+        double t = r.g[i];
+        for (int l = i + 1; l < k; ++l) t -= r.Hij(i, l) * r.y[l];
+        r.y[i] = t / r.Hij(i, i);
+    }
+    CK(cudaMemcpyAsync(c->hdev, r.y.data(), size_t(k) * sizeof(double), cudaMemcpyHostToDevice, r.s));
+    CK(launch_multiaxpy(c->N, k, c->Z, c->N, c->hdev, r.x, 1.0, r.s));
+    CK(cudaStreamSynchronize(r.s));   // r.y is pageable host memory
+    return STOKES_OK;
+}
+
+// Host part of the phase just finished (the run's stream is idle); chooses the next phase.
+stokes_status fgmres_complete(FgmresRun& r) {
+    stokes_ctx* c = r.c;
+    const int m = r.m;
+    const double* hd = c->dots_host;
+    switch (r.phase) {
+        case FgmresRun::P_BNORM:
+            r.bnorm = std::sqrt(hd[0]);
+            if (r.bnorm == 0.0) {
+                CK(cudaMemsetAsync(r.x, 0, c->N * sizeof(double), r.s));
+                r.est = 0.0;
+                r.st = STOKES_OK;
+                r.phase = FgmresRun::P_FINAL;
+            } else {
+                r.phase = FgmresRun::P_RESTART;
+            }
+            return STOKES_OK;
+        case FgmresRun::P_RESTART: {
+            const double beta = std::sqrt(hd[0]);
+            if (!std::isfinite(beta)) { r.st = STOKES_BREAKDOWN; r.phase = FgmresRun::P_FINAL; return STOKES_OK; }
+            r.est = beta / r.bnorm;
+            if (beta <= r.rtol * r.bnorm) { r.st = STOKES_OK; r.phase = FgmresRun::P_FINAL; return STOKES_OK; }
+            if (r.its >= r.max_it) { r.phase = FgmresRun::P_FINAL; return STOKES_OK; }
+            std::fill(r.g.begin(), r.g.end(), 0.0);
+            r.g[0] = beta;
+            r.j = 0;
+            r.hn_prev = beta;      // V_0 = (b - K x) / beta
+            r.next_v = true;
+            r.phase = FgmresRun::P_ITER;
+            return STOKES_OK;
+        }
+        case FgmresRun::P_ITER: {
+            const int j = r.j;
             double h2sq = 0.0;
             for (int i = 0; i <= j; ++i) {
-                h1[i] = c->dots_host[i];
-                h2[i] = c->dots_host[m + 2 + i];
-                h2sq += h2[i] * h2[i];
+                const double h2 = hd[m + 2 + i];
+                r.Hij(i, j) = hd[i] + h2;
+                h2sq += h2 * h2;
             }
-            const double hn2 = std::fmax(c->dots_host[m + 2 + j + 1] - h2sq, 0.0);
-            const double hn = std::sqrt(hn2);
-            if (!std::isfinite(hn)) { st = STOKES_BREAKDOWN; done = true; break; }
-            for (int i = 0; i <= j; ++i) Hij(i, j) = h1[i] + h2[i];
-            Hij(j + 1, j) = hn;
-            if (hn > 0.0) CK(launch_axpby(N, 1.0 / hn, w, 0.0, V + size_t(j + 1) * N, s));
+            const double hn = std::sqrt(std::fmax(hd[m + 2 + j + 1] - h2sq, 0.0));
+            if (!std::isfinite(hn)) { r.st = STOKES_BREAKDOWN; r.phase = FgmresRun::P_FINAL; return STOKES_OK; }
+            r.Hij(j + 1, j) = hn;
             for (int i = 0; i < j; ++i) {
-                const double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
-                Hij(i + 1, j) = -sn[i] * Hij(i, j) + cs[i] * Hij(i + 1, j);
-                Hij(i, j) = t;
+                const double t = r.cs[i] * r.Hij(i, j) + r.sn[i] * r.Hij(i + 1, j);
+                r.Hij(i + 1, j) = -r.sn[i] * r.Hij(i, j) + r.cs[i] * r.Hij(i + 1, j);
+                r.Hij(i, j) = t;
             }
-            const double den = std::hypot(Hij(j, j), Hij(j + 1, j));
-            cs[j] = Hij(j, j) / den;
-            sn[j] = Hij(j + 1, j) / den;
-            Hij(j, j) = den;
-            Hij(j + 1, j) = 0.0;
-            g[j + 1] = -sn[j] * g[j];
-            g[j] = cs[j] * g[j];
-            ++its;
-            k = j + 1;
-            est = std::fabs(g[j + 1]) / bnorm;
-            if (std::fabs(g[j + 1]) <= rtol * bnorm || hn == 0.0) { done = true; break; }
+            const double den = std::hypot(r.Hij(j, j), r.Hij(j + 1, j));
+            r.cs[j] = r.Hij(j, j) / den;
+            r.sn[j] = r.Hij(j + 1, j) / den;
+            r.Hij(j, j) = den;
+            r.Hij(j + 1, j) = 0.0;
+            r.g[j + 1] = -r.sn[j] * r.g[j];
+            r.g[j] = r.cs[j] * r.g[j];
+            ++r.its;
+            r.est = std::fabs(r.g[j + 1]) / r.bnorm;
+            const bool conv = std::fabs(r.g[j + 1]) <= r.rtol * r.bnorm || hn == 0.0;
+            if (conv || j + 1 == m || r.its >= r.max_it) {
+                CKS(fgmres_update_x(r, j + 1));
+                if (conv) { r.st = STOKES_OK; r.phase = FgmresRun::P_FINAL; }
+                else if (r.its >= r.max_it) r.phase = FgmresRun::P_FINAL;
+                else r.phase = FgmresRun::P_RESTART;
+            } else {
+                r.hn_prev = hn;
+                r.next_v = true;
+                r.j = j + 1;
+            }
+            return STOKES_OK;
         }
-        if (st == STOKES_BREAKDOWN) break;
-        for (int i = k - 1; i >= 0; --i) {
-            double t = g[i];
-            for (int l = i + 1; l < k; ++l) t -= Hij(i, l) * y[l];
-            y[i] = t / Hij(i, i);
+        case FgmresRun::P_FINAL:
+            if (r.info) {
+                r.info->iterations = r.its;
+                r.info->rel_residual = r.est;
+                r.info->rel_residual_true = r.bnorm > 0 ? std::sqrt(hd[0]) / r.bnorm : 0.0;
+                r.info->status = r.st;
+            }
+            r.phase = FgmresRun::P_DONE;
+            return STOKES_OK;
+        case FgmresRun::P_DONE:
+            return STOKES_OK;
+    }
+    return STOKES_OK;
+}
+
+stokes_status fgmres_init(FgmresRun& r, stokes_ctx* c, int prec, const double* b, double* x, double rtol,
+                          int max_it, stokes_solve_info* info, cudaStream_t s) {
+    CKS(ensure_krylov(c));
+    r.c = c;
+    r.prec = prec;
+    r.b = b;
+    r.x = x;
+    r.rtol = rtol;
+    r.max_it = max_it;
+    r.s = s;
+    r.info = info;
+    r.m = c->opt.restart;
+    r.H.assign(size_t(r.m + 1) * r.m, 0.0);
+    r.cs.assign(r.m, 0.0);
+    r.sn.assign(r.m, 0.0);
+    r.g.assign(r.m + 1, 0.0);
+    r.y.assign(r.m, 0.0);
+    r.phase = FgmresRun::P_BNORM;
+    return STOKES_OK;
+}
+
+// Advance all runs in lock step until every one is done (one host synchronisation per run per round).
+stokes_status fgmres_drive(std::vector<FgmresRun>& runs) {
+    bool active = true;
+    while (active) {
+        active = false;
+        for (FgmresRun& r : runs)
+            if (r.phase != FgmresRun::P_DONE) CKS(fgmres_enqueue(r));
+        for (FgmresRun& r : runs) {
+            if (r.phase == FgmresRun::P_DONE) continue;
+            CK(cudaStreamSynchronize(r.s));
+            CKS(fgmres_complete(r));
+            if (r.phase != FgmresRun::P_DONE) active = true;
         }
-        CK(cudaMemcpyAsync(c->hdev, y.data(), size_t(k) * sizeof(double), cudaMemcpyHostToDevice, s));
-        CK(launch_multiaxpy(N, k, Z, N, c->hdev, x, 1.0, s));
-        CK(cudaStreamSynchronize(s));
-        if (done) st = (est <= rtol) ? STOKES_OK : st;
     }
-    CKS(remove_pressure_mean(c, x, s));
-    // true residual
-    CKS(apply_stokes(c, x, w, s));
-    CK(launch_axpby(N, 1.0, b, -1.0, w, s));
-    double r2 = 0.0;
-    CKS(dot(c, N, w, w, s, &r2));
-    if (info) {
-        info->iterations = its;
-        info->rel_residual = est;
-        info->rel_residual_true = bnorm > 0 ? std::sqrt(r2) / bnorm : 0.0;
-        info->status = st;
-    }
+    return STOKES_OK;
+}
+
+stokes_status fgmres(stokes_ctx* c, int prec, const double* b, double* x, double rtol, int max_it,
+                     stokes_solve_info* info, cudaStream_t s) {
+    std::vector<FgmresRun> runs(1);
+    stokes_solve_info local{};
+    CKS(fgmres_init(runs[0], c, prec, b, x, rtol, max_it, info ? info : &local, s));
+    CKS(fgmres_drive(runs));
+    const stokes_status st = runs[0].st;
     if (st != STOKES_OK) return fail(st, st == STOKES_BREAKDOWN ? "FGMRES breakdown (non-finite norm)"
                                                                  : "FGMRES reached max_it");
     return STOKES_OK;
@@ -873,6 +984,56 @@ stokes_status stokes_solve(stokes_ctx* c, int vcycle_prec, const double* rhs, do
         info->status = st;
     }
     return st;
+}
+
+stokes_status stokes_batch_solve(int n_problems, stokes_ctx* const* ctxs, int vcycle_prec,
+                                 const double* const* rhs_devs, double* const* up_devs, double rtol, int max_it,
+                                 stokes_solve_info* infos, void* const* streams) {
+    if (n_problems < 1 || !ctxs || !up_devs) return fail(STOKES_EINVAL, "null argument or no problems");
+    if (vcycle_prec != STOKES_FP32 && vcycle_prec != STOKES_FP64) return fail(STOKES_EINVAL, "bad precision");
+    if (!(rtol > 0.0) || max_it < 1) return fail(STOKES_EINVAL, "bad rtol or max_it");
+    for (int i = 0; i < n_problems; ++i) {
+        if (!ctxs[i] || !up_devs[i]) return fail(STOKES_EINVAL, "null context or solution vector");
+        for (int k = 0; k < i; ++k)
+            if (ctxs[k] == ctxs[i]) return fail(STOKES_EINVAL, "a context appears twice in the batch");
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    std::vector<cudaStream_t> own;
+    std::vector<FgmresRun> runs(n_problems);
+    std::vector<stokes_solve_info> local(n_problems);
+    stokes_status st = STOKES_OK;
+    for (int i = 0; i < n_problems && st == STOKES_OK; ++i) {
+        stokes_ctx* c = ctxs[i];
+        cudaStream_t s = streams ? static_cast<cudaStream_t>(streams[i]) : nullptr;
+        if (!streams) {
+            if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) { st = fail(STOKES_ECUDA, "stream"); break; }
+            own.push_back(s);
+        }
+        st = ensure_krylov(c);
+        if (st != STOKES_OK) break;
+        const LevelGeom& g = c->lev[c->L - 1].g;
+        const double* b = rhs_devs ? rhs_devs[i] : nullptr;
+        if (!b) {
+            if (cudaMemcpyAsync(c->bvec, c->F, g.n_u * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+                cudaMemsetAsync(c->bvec + g.n_u, 0, g.n_p * sizeof(double), s) != cudaSuccess) {
+                st = fail(STOKES_ECUDA, "rhs copy");
+                break;
+            }
+            b = c->bvec;
+        }
+        st = fgmres_init(runs[i], c, vcycle_prec, b, up_devs[i], rtol, max_it, infos ? &infos[i] : &local[i], s);
+    }
+    if (st == STOKES_OK) st = fgmres_drive(runs);
+    for (cudaStream_t s : own) cudaStreamDestroy(s);
+    if (st != STOKES_OK) return st;
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    stokes_status worst = STOKES_OK;
+    for (int i = 0; i < n_problems; ++i) {
+        if (infos) infos[i].seconds = secs;
+        if (runs[i].st != STOKES_OK && worst == STOKES_OK) worst = runs[i].st;
+    }
+    if (worst != STOKES_OK) return fail(worst, "at least one problem did not converge");
+    return STOKES_OK;
 }
 
 stokes_status stokes_solve_host(stokes_ctx* c, int vcycle_prec, const double* rhs_host, double* up_host,

@@ -118,6 +118,23 @@ def workload(name: str) -> SinkerProblem:
     raise KeyError(name)
 
 
+BATCH_SIZES = ((16, 5), (24, 4), (32, 6), (48, 5))   # (cells per axis, levels): coarsest 1 or 3 cells
+
+
+def batch_workload(count: int = 64, seed: int = 1907 + 5):
+    """Batched sinker problems: size drawn uniformly from BATCH_SIZES (16^3..48^3 with a
+    coarsest mesh of at most 3^3 cells), 1-8 sinkers, viscosity ratio log-uniform in [1e2, 1e6];
+    all draws from splitmix64 with `seed` (problem i uses seed * 1000 + i for its centres)."""
+    u = uniform01(seed, 3 * count)
+    probs = []
+    for i in range(count):
+        n, L = BATCH_SIZES[min(int(u[3 * i] * len(BATCH_SIZES)), len(BATCH_SIZES) - 1)]
+        k = 1 + min(int(u[3 * i + 1] * 8), 7)
+        dr = 10.0 ** (2.0 + 4.0 * u[3 * i + 2])
+        probs.append(dr_problem(n, L, k, dr, seed * 1000 + i, "batch%d" % i))
+    return probs
+
+
 def n_velocity(n: int) -> int:
     return 3 * (2 * n + 1) ** 3
 

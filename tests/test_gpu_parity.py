@@ -324,6 +324,30 @@ def test_graph_replay_matches_kernel_launches(capi, prec, kernel):
             assert rel(a, b) <= (1e-13 if prec == 0 else 1e-6)
 
 
+def test_batch_solve_matches_individual_solves(capi):
+    """stokes_batch_solve over problems of different sizes and level counts runs the same FGMRES as
+    stokes_solve: same iteration counts, same solutions (to the rounding of the atomic adds), and
+    each true FP64 residual (recomputed by the oracle) <= 1.5e-8."""
+    probs = [si.dr_problem(8, 4, 1, 1e2, 6001), si.dr_problem(12, 3, 3, 1e4, 6002),
+             si.dr_problem(16, 5, 2, 1e3, 6003), si.dr_problem(8, 2, 4, 1e5, 6004)]
+    ctxs = [capi.stokes_setup_problem(p) for p in probs]
+    ups = [torch.zeros(c.n_u + c.n_p, dtype=torch.float64, device="cuda") for c in ctxs]
+    infos = capi.stokes_batch_solve(ctxs, capi.STOKES_FP32, ups, rtol=1e-8, max_it=500)
+    for p, ctx, up, info in zip(probs, ctxs, ups, infos):
+        ref = torch.zeros_like(up)
+        ri = capi.stokes_solve(ctx, capi.STOKES_FP32, None, ref, rtol=1e-8, max_it=500)
+        assert info.iterations == ri.iterations and info.status == 0
+        x, xr = host(up), host(ref)
+        assert np.abs(x - xr).max() <= 1e-6 * np.abs(xr).max()
+        m = mesh.Mesh(p.n)
+        ops = operators.Operators(m, sinker.level_viscosities(m, p, p.n_levels)[-1])
+        F = operators.assemble_rhs(m, sinker.forcing(m.quad_points(), p))
+        b = np.concatenate([F, np.zeros(m.n_p)])
+        assert np.linalg.norm(b - ops.apply_stokes(x)) / np.linalg.norm(b) <= 1.5e-8
+    for c in ctxs:
+        c.close()
+
+
 def test_single_level_and_two_level_meshes(capi):
     for n, L in ((1, 1), (2, 2), (3, 1), (4, 1)):
         p = si.dr_problem(n, L, 1, 1e2, 3000 + n)
