@@ -229,6 +229,16 @@ stokes_status stokes_schur_inverse(stokes_ctx* ctx, const double* rp_dev, double
 stokes_status stokes_precondition(stokes_ctx* ctx, int vcycle_prec, const double* r_dev, double* z_dev,
                                   void* stream);
 
+/* Autotuner (no counterpart in the paper). what = 1: threads per block of the cell-parallel level
+ * operator (64, 128 or 256; the fastest FP32 product on the finest level); what = 2: the Chebyshev
+ * degree (3..6) with the shortest wall time of an FGMRES solve to relative residual 1e-3 with the
+ * FP32 V-cycle and the context's own right-hand side; what = 3: both. The choice is kept in the
+ * context for later V-cycles and solves (captured graphs are dropped and recaptured). Outputs may
+ * be NULL. Synchronous; allocates work vectors (and the Krylov basis) on first use.
+ * Note: the paper's smoother degree is 4; a tuned degree trades smoothing work per V-cycle against
+ * the outer iteration count. */
+stokes_status stokes_autotune(stokes_ctx* ctx, int what, void* stream, int* block_out, int* degree_out);
+
 /* ---- allocation-free entry point (no counterpart in the paper) ---- */
 
 /* Largest pressure space stokes_schur_inverse_noalloc accepts: the (n+1)^3 Q1

@@ -82,6 +82,7 @@ _SIGS = {
     "stokes_schur_inverse": (C.c_int, [_P, _P, _P, _P]),
     "stokes_precondition": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "stokes_schur_inverse_noalloc": (C.c_int, [C.c_int, _P, _P, _P, C.c_int, _P]),
+    "stokes_autotune": (C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "stokes_profile": (C.c_int, [C.c_int]),
     "stokes_profile_read": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int]),
     "stokes_launch_count": (C.c_longlong, []),
@@ -300,6 +301,14 @@ def stokes_schur_inverse_noalloc(n, mu, rp, zp, degree=5, stream=None):
     """Context-free, allocation-free S_hat^-1 (scratch in a fixed device array)."""
     _check(load().stokes_schur_inverse_noalloc(int(n), _ptr(mu), _ptr(rp), _ptr(zp), int(degree), _stream(stream)),
            "stokes_schur_inverse_noalloc")
+
+
+def stokes_autotune(ctx, what=3, stream=None):
+    """Tune the level-operator block size (what & 1) and the Chebyshev degree (what & 2);
+    returns (block, degree) now used by the context."""
+    b, d = C.c_int(), C.c_int()
+    _check(load().stokes_autotune(ctx.handle, int(what), _stream(stream), C.byref(b), C.byref(d)), "stokes_autotune")
+    return b.value, d.value
 
 
 def stokes_profile(enable):

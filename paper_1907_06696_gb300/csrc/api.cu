@@ -173,6 +173,9 @@ struct stokes_ctx {
     cudaEvent_t gev_in = nullptr, gev_out = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // [FP64, FP32]
     long long glaunches[2] = {0, 0};                 // kernel launches inside each graph
+    int cell_block = 128;                            // threads per block of the cell kernel (autotuned)
+    float *tune_x = nullptr, *tune_r = nullptr, *tune_b = nullptr;   // autotuner work (FP32, finest level)
+    double* tune_up = nullptr;                                        // autotuner solution vector
 };
 
 namespace {
@@ -230,10 +233,13 @@ double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& 
     return 0.5 * (lo + hi);
 }
 
+// Level-operator selector for launch_level_op: 1 = brick kernel, else the cell kernel's block size.
+int level_kernel(const stokes_ctx* c) { return c->opt.vmult_kernel == 1 ? 1 : c->cell_block; }
+
 template <typename T>
 stokes_status vmult_level(stokes_ctx* c, int l, const T* src, T* dst, cudaStream_t s) {
     Level& L = c->lev[l];
-    CK(launch_level_op<T>(c->opt.vmult_kernel, L.g, L.planes, EPI_PLAIN, vecs<T>(L).mu, src, dst, nullptr, nullptr,
+    CK(launch_level_op<T>(level_kernel(c), L.g, L.planes, EPI_PLAIN, vecs<T>(L).mu, src, dst, nullptr, nullptr,
                           nullptr, 0.0, 0.0, slots<T>(L), vecs<T>(L).acc, s));
     return STOKES_OK;
 }
@@ -243,7 +249,7 @@ template <typename T>
 stokes_status cheb_step(stokes_ctx* c, int l, const T* b, T* x, double c1, double c2, cudaStream_t s) {
     Level& L = c->lev[l];
     LevelVecs<T>& v = vecs<T>(L);
-    CK(launch_level_op<T>(c->opt.vmult_kernel, L.g, L.planes, EPI_CHEB, v.mu, x, nullptr, b, v.dinv, v.d, c1, c2,
+    CK(launch_level_op<T>(level_kernel(c), L.g, L.planes, EPI_CHEB, v.mu, x, nullptr, b, v.dinv, v.d, c1, c2,
                           slots<T>(L), v.acc, s));
     return STOKES_OK;
 }
@@ -286,7 +292,7 @@ stokes_status vcycle_level(stokes_ctx* c, int l, cudaStream_t s) {
     if (l == 0) return coarse_solve<T>(c, v.b, v.x, s);
     LevelVecs<T>& vc = vecs<T>(c->lev[l - 1]);
     CKS(smooth<T>(c, l, v.b, v.x, true, s));
-    CK(launch_level_op<T>(c->opt.vmult_kernel, L.g, L.planes, EPI_RESID, v.mu, v.x, v.r, v.b, nullptr, nullptr, 0.0,
+    CK(launch_level_op<T>(level_kernel(c), L.g, L.planes, EPI_RESID, v.mu, v.x, v.r, v.b, nullptr, nullptr, 0.0,
                           0.0, slots<T>(L), v.acc, s));
     CK(launch_restrict<T>(L.g, v.r, vc.b, s));
     CKS(vcycle_level<T>(c, l - 1, s));
@@ -984,6 +990,90 @@ stokes_status stokes_solve(stokes_ctx* c, int vcycle_prec, const double* rhs, do
         info->status = st;
     }
     return st;
+}
+
+// Drop the captured V-cycle graphs (after a change of the smoother); they are recaptured on next use.
+static stokes_status drop_graphs(stokes_ctx* c) {
+    CK(cudaDeviceSynchronize());
+    for (cudaGraphExec_t& ge : c->gexec)
+        if (ge) {
+            cudaGraphExecDestroy(ge);
+            ge = nullptr;
+        }
+    return STOKES_OK;
+}
+
+stokes_status stokes_autotune(stokes_ctx* c, int what, void* stream, int* block_out, int* degree_out) {
+    if (!c) return fail(STOKES_EINVAL, "null context");
+    if (what < 0 || what > 3) return fail(STOKES_EINVAL, "what must be a combination of 1 and 2");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Level& F = c->lev[c->L - 1];
+    const size_t n = F.g.n_u;
+    if (!c->tune_x) {
+        CKS(dalloc(c, &c->tune_x, n));
+        CKS(dalloc(c, &c->tune_r, n));
+        CKS(dalloc(c, &c->tune_b, n));
+    }
+    // seeded right-hand side with zero constrained entries
+    CK(launch_splitmix_vector(n, 4242, nullptr, c->tu, s));
+    CK(launch_cast_d2f(n, c->tu, c->tune_b, s));
+    CK(launch_zero_boundary<float>(F.g, c->tune_b, s));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    stokes_status st = STOKES_OK;
+    if ((what & 1) && c->opt.vmult_kernel != 1) {
+        // threads per block of the cell kernel: the fastest FP32 level operator on the finest level
+        float best = 1e30f;
+        int best_bs = c->cell_block;
+        for (int bs : {64, 128, 256}) {
+            c->cell_block = bs;
+            for (int it = 0; it < 2; ++it) st = vmult_level<float>(c, c->L - 1, c->tune_b, c->tune_r, s);
+            cudaEventRecord(e0, s);
+            for (int it = 0; it < 10 && st == STOKES_OK; ++it) st = vmult_level<float>(c, c->L - 1, c->tune_b, c->tune_r, s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (st != STOKES_OK) break;
+            if (ms < best) { best = ms; best_bs = bs; }
+        }
+        c->cell_block = best_bs;
+        if (st == STOKES_OK) st = drop_graphs(c);
+    }
+    if (st == STOKES_OK && (what & 2)) {
+        // Chebyshev degree: wall time of a short FGMRES solve (FP32 V-cycle, relative residual 1e-3,
+        // zero guess, the context's own right-hand side [F; 0]) for each candidate degree
+        const int keep = c->opt.cheb_degree;
+        if ((st = ensure_krylov(c)) == STOKES_OK && !c->tune_up) st = dalloc(c, &c->tune_up, c->N);
+        double best_t = 1e300;
+        int best_deg = keep;
+        const LevelGeom& g = F.g;
+        for (int deg = 3; deg <= 6 && st == STOKES_OK; ++deg) {
+            c->opt.cheb_degree = deg;
+            if ((st = drop_graphs(c)) != STOKES_OK) break;
+            for (int rep = 0; rep < 2 && st == STOKES_OK; ++rep) {     // first run captures the graph
+                cudaMemcpyAsync(c->bvec, c->F, g.n_u * sizeof(double), cudaMemcpyDeviceToDevice, s);
+                cudaMemsetAsync(c->bvec + g.n_u, 0, g.n_p * sizeof(double), s);
+                cudaMemsetAsync(c->tune_up, 0, c->N * sizeof(double), s);
+                const auto t0 = std::chrono::steady_clock::now();
+                stokes_solve_info info{};
+                stokes_status sst = fgmres(c, STOKES_FP32, c->bvec, c->tune_up, 1e-3, 2000, &info, s);
+                const double t = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+                if (sst != STOKES_OK && sst != STOKES_NOT_CONVERGED) st = sst;
+                if (rep == 1 && sst == STOKES_OK && t < best_t) { best_t = t; best_deg = deg; }
+            }
+        }
+        g_last_error.clear();
+        c->opt.cheb_degree = best_deg;
+        if (st == STOKES_OK) st = drop_graphs(c);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != STOKES_OK) return st;
+    if (block_out) *block_out = c->opt.vmult_kernel == 1 ? 0 : c->cell_block;
+    if (degree_out) *degree_out = c->opt.cheb_degree;
+    return STOKES_OK;
 }
 
 stokes_status stokes_batch_solve(int n_problems, stokes_ctx* const* ctxs, int vcycle_prec,

@@ -34,8 +34,9 @@ __global__ void __launch_bounds__(BX * BY * BZ, sizeof(T) == 4 ? 3 : 1) k_brick(
 
 // ---- cell-parallel variant: one thread per cell, atomic adds into a zeroed accumulator;
 // the consumer kernels below run the epilogue and clear the accumulator again.
-template <typename T>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1) k_cell_atomic(BrickArgs<T> a, T* acc) {
+// Threads per block BS: 64, 128 or 256 (the register budget per thread is the same, 170 for FP32).
+template <typename T, int BS>
+__global__ void __launch_bounds__(BS, sizeof(T) == 4 ? 384 / BS : 1) k_cell_atomic(BrickArgs<T> a, T* acc) {
     const size_t cell = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (cell >= size_t(a.n) * a.n * a.n) return;
     const int ci = int(cell % a.n), cj = int((cell / a.n) % a.n), ck = int(cell / (size_t(a.n) * a.n));
@@ -159,18 +160,31 @@ cudaError_t launch_epi(const BrickArgs<T>& a, cudaStream_t s) {
 }
 
 template <typename T>
-cudaError_t launch_cell_epi(const BrickArgs<T>& a, int epi, T* acc, size_t n_u, cudaStream_t s) {
+cudaError_t launch_cell(const BrickArgs<T>& a, T* acc, int bs, cudaStream_t s) {
     const size_t cells = size_t(a.n) * a.n * a.n;
     const int cls = sizeof(T) == 4 ? PROF_VMULT_F32 : PROF_VMULT_F64;
+    if (bs == 64)
+        LAUNCH(cls, s, (k_cell_atomic<T, 64><<<unsigned((cells + 63) / 64), 64, 0, s>>>(a, acc)));
+    else if (bs == 256)
+        LAUNCH(cls, s, (k_cell_atomic<T, 256><<<unsigned((cells + 255) / 256), 256, 0, s>>>(a, acc)));
+    else
+        LAUNCH(cls, s, (k_cell_atomic<T, 128><<<unsigned((cells + 127) / 128), 128, 0, s>>>(a, acc)));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cell_epi(const BrickArgs<T>& a, int epi, T* acc, size_t n_u, int bs, cudaStream_t s) {
     if (epi == EPI_PLAIN) {
         // dst = A src: accumulate straight into the zeroed dst, identity rows afterwards
         cudaError_t e = cudaMemsetAsync(a.dst, 0, n_u * sizeof(T), s);
         if (e != cudaSuccess) return e;
-        LAUNCH(cls, s, (k_cell_atomic<T><<<unsigned((cells + 127) / 128), 128, 0, s>>>(a, a.dst)));
+        e = launch_cell<T>(a, a.dst, bs, s);
+        if (e != cudaSuccess) return e;
         LevelGeom g = make_geom(a.n);
         return launch_copy_boundary<T>(g, a.src, a.dst, s);
     }
-    LAUNCH(cls, s, (k_cell_atomic<T><<<unsigned((cells + 127) / 128), 128, 0, s>>>(a, acc)));
+    cudaError_t e = launch_cell<T>(a, acc, bs, s);
+    if (e != cudaSuccess) return e;
     const size_t per = sizeof(T) == 4 ? 4 : 2;
     const size_t b = (n_u / per + 255) / 256;
     const unsigned blocks = unsigned(b < 1 ? 1 : (b < 4864 ? b : 4864));
@@ -220,7 +234,8 @@ cudaError_t launch_level_op(int kernel, const LevelGeom& g, const PlaneLayout& L
     a.c2 = T(c2);
     a.slots = slots;
     a.L = L;
-    if (kernel == 0) return launch_cell_epi<T>(a, epi, acc, g.n_u, s);
+    if (kernel == 0 || kernel == 64 || kernel == 128 || kernel == 256)
+        return launch_cell_epi<T>(a, epi, acc, g.n_u, kernel == 0 ? 128 : kernel, s);
     switch (epi) {
         case EPI_PLAIN: return launch_epi<T, EPI_PLAIN>(a, s);
         case EPI_RESID: return launch_epi<T, EPI_RESID>(a, s);

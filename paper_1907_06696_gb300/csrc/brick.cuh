@@ -347,8 +347,9 @@ PlaneLayout brick_layout(int n);
 cudaError_t brick_configure();
 // A x with an epilogue (EPI_PLAIN: dst = A x; EPI_RESID: dst = b - A x;
 // EPI_CHEB: d = c1 d + c2 dinv (b - A x), src += d in place).
-// kernel 0: one thread per cell with atomic adds into acc (n_u entries, zero on entry and on
-//           return) and a consumer kernel for the epilogue;
+// kernel 0, 64, 128, 256: one thread per cell (blocks of 128, 64, 128, 256 threads) with atomic
+//           adds into acc (n_u entries, zero on entry and on return) and a consumer kernel for the
+//           epilogue;
 // kernel 1: the brick-tiled kernel with the epilogue fused (slots: brick_layout(n).total entries).
 template <typename T>
 cudaError_t launch_level_op(int kernel, const LevelGeom& g, const PlaneLayout& L, int epi, const T* mu, const T* src,

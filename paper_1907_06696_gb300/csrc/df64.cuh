@@ -91,6 +91,41 @@ __host__ __device__ __forceinline__ df64 operator*(const df64& x, const df64& y)
 __host__ __device__ __forceinline__ df64& operator+=(df64& x, const df64& y) { return x = x + y; }
 __host__ __device__ __forceinline__ df64& operator*=(df64& x, const df64& y) { return x = x * y; }
 
+// c0 x0 + c1 x1 + c2 x2 (+ acc) with one final renormalisation: the exact products'
+// high parts are summed with two_sum, every rounding error and low part is collected
+// in one float and added at the end (the accurate dot-product scheme of Ogita, Rump
+// and Oishi, SIAM J. Sci. Comput. 26 (2005), applied to double-float operands).
+__host__ __device__ __forceinline__ void two_sum_acc(float& s, float b, float& err) {
+    const float t = add_f(s, b);
+    const float bb = sub_f(t, s);
+    err = add_f(err, add_f(sub_f(s, sub_f(t, bb)), sub_f(b, bb)));
+    s = t;
+}
+__host__ __device__ __forceinline__ float prod_err(const df64& c, const df64& x, float p) {
+    float e = fma_f(c.hi, x.hi, -p);
+    e = fma_f(c.hi, x.lo, e);
+    return fma_f(c.lo, x.hi, e);
+}
+__host__ __device__ __forceinline__ df64 dot3(const df64& c0, const df64& x0, const df64& c1, const df64& x1,
+                                             const df64& c2, const df64& x2) {
+    const float p0 = mul_f(c0.hi, x0.hi), p1 = mul_f(c1.hi, x1.hi), p2 = mul_f(c2.hi, x2.hi);
+    float err = add_f(add_f(prod_err(c0, x0, p0), prod_err(c1, x1, p1)), prod_err(c2, x2, p2));
+    float s = p0;
+    two_sum_acc(s, p1, err);
+    two_sum_acc(s, p2, err);
+    return fast_two_sum(s, err);
+}
+__host__ __device__ __forceinline__ df64 dot3_acc(const df64& acc, const df64& c0, const df64& x0, const df64& c1,
+                                                 const df64& x1, const df64& c2, const df64& x2) {
+    const float p0 = mul_f(c0.hi, x0.hi), p1 = mul_f(c1.hi, x1.hi), p2 = mul_f(c2.hi, x2.hi);
+    float err = add_f(add_f(add_f(prod_err(c0, x0, p0), prod_err(c1, x1, p1)), prod_err(c2, x2, p2)), acc.lo);
+    float s = acc.hi;
+    two_sum_acc(s, p0, err);
+    two_sum_acc(s, p1, err);
+    two_sum_acc(s, p2, err);
+    return fast_two_sum(s, err);
+}
+
 // Exact split of a double into a double-float (rounding of the low part only).
 __host__ __device__ __forceinline__ df64 from_double(double v) {
     const float h = float(v);

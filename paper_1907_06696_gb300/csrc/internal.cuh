@@ -91,6 +91,7 @@ cudaError_t launch_coarse_solve(int nf, const int* free_idx, const double* Ainv,
 // FP64 vector ops.
 cudaError_t launch_axpby(size_t n, double a, const double* x, double b, double* y, cudaStream_t s);   // y = a x + b y
 cudaError_t launch_mul(size_t n, const double* a, const double* x, double* y, cudaStream_t s);         // y = a .* x
+cudaError_t launch_axpby_f(size_t n, float a, const float* x, float b, float* y, cudaStream_t s);      // FP32
 cudaError_t launch_sqrt_vec(size_t n, const double* a, double* y, cudaStream_t s);                     // y = sqrt(a)
 cudaError_t launch_fill(size_t n, double v, double* y, cudaStream_t s);
 cudaError_t launch_recip(size_t n, const double* a, double* y, cudaStream_t s);                       // y = 1 / a

@@ -16,7 +16,7 @@ namespace stk {
 namespace {
 
 template <bool DO_A, bool DO_BT, bool DO_B>
-__global__ void __launch_bounds__(kOuterThreads) k_outer_df64(OuterArgs a) {
+__global__ void __launch_bounds__(kOuterThreads, 2) k_outer_df64(OuterArgs a) {
     __shared__ OuterShared sh;
     const int c = threadIdx.x / kOuterCells, g = threadIdx.x % kOuterCells;
     q2::df64 U[27], W[27];

@@ -21,6 +21,8 @@
 
 #include <cuda_runtime.h>
 
+#include "df64.cuh"
+
 namespace q2 {
 
 // ---------------------------------------------------------------- constants
@@ -124,6 +126,65 @@ __host__ __device__ __forceinline__ void derivT_w(const T* g, T* w) {
                 const double wl = gw(o1) * gw(o2) * double(S);
                 w[lin<AX>(m, o1, o2)] += T(DC(0, m) * gw(0) * wl) * a0 + T(DC(1, m) * gw(1) * wl) * a1 +
                                          T(DC(2, m) * gw(2) * wl) * a2;
+            }
+        }
+}
+
+// ---------------------------------------------------------------- double-float sweeps
+// The same four sweeps for double-float values, each output formed by dot3 / dot3_acc
+// (one renormalisation per output instead of one per operation).
+template <int AX>
+__host__ __device__ __forceinline__ void interp(df64* x) {
+#pragma unroll
+    for (int o2 = 0; o2 < 3; ++o2)
+#pragma unroll
+        for (int o1 = 0; o1 < 3; ++o1) {
+            const df64 a0 = x[lin<AX>(0, o1, o2)], a1 = x[lin<AX>(1, o1, o2)], a2 = x[lin<AX>(2, o1, o2)];
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                x[lin<AX>(q, o1, o2)] = dot3(df64(Vq(q, 0)), a0, df64(Vq(q, 1)), a1, df64(Vq(q, 2)), a2);
+        }
+}
+template <int AX>
+__host__ __device__ __forceinline__ void interpT(df64* x) {
+#pragma unroll
+    for (int o2 = 0; o2 < 3; ++o2)
+#pragma unroll
+        for (int o1 = 0; o1 < 3; ++o1) {
+            const df64 a0 = x[lin<AX>(0, o1, o2)], a1 = x[lin<AX>(1, o1, o2)], a2 = x[lin<AX>(2, o1, o2)];
+#pragma unroll
+            for (int m = 0; m < 3; ++m)
+                x[lin<AX>(m, o1, o2)] = dot3(df64(Vq(0, m)), a0, df64(Vq(1, m)), a1, df64(Vq(2, m)), a2);
+        }
+}
+template <int AX, bool ADD>
+__host__ __device__ __forceinline__ void deriv(const df64* x, df64* g) {
+#pragma unroll
+    for (int o2 = 0; o2 < 3; ++o2)
+#pragma unroll
+        for (int o1 = 0; o1 < 3; ++o1) {
+            const df64 a0 = x[lin<AX>(0, o1, o2)], a1 = x[lin<AX>(1, o1, o2)], a2 = x[lin<AX>(2, o1, o2)];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                df64& out = g[lin<AX>(q, o1, o2)];
+                out = ADD ? dot3_acc(out, df64(DC(q, 0)), a0, df64(DC(q, 1)), a1, df64(DC(q, 2)), a2)
+                          : dot3(df64(DC(q, 0)), a0, df64(DC(q, 1)), a1, df64(DC(q, 2)), a2);
+            }
+        }
+}
+template <int AX, int S>
+__host__ __device__ __forceinline__ void derivT_w(const df64* g, df64* w) {
+#pragma unroll
+    for (int o2 = 0; o2 < 3; ++o2)
+#pragma unroll
+        for (int o1 = 0; o1 < 3; ++o1) {
+            const df64 a0 = g[lin<AX>(0, o1, o2)], a1 = g[lin<AX>(1, o1, o2)], a2 = g[lin<AX>(2, o1, o2)];
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const double wl = gw(o1) * gw(o2) * double(S);
+                df64& out = w[lin<AX>(m, o1, o2)];
+                out = dot3_acc(out, df64(DC(0, m) * gw(0) * wl), a0, df64(DC(1, m) * gw(1) * wl), a1,
+                               df64(DC(2, m) * gw(2) * wl), a2);
             }
         }
 }

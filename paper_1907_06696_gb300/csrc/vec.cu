@@ -156,6 +156,10 @@ __global__ void k_axpby(size_t n, double a, const double* __restrict__ x, double
     for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
         y[i] = a * x[i] + (b == 0.0 ? 0.0 : b * y[i]);
 }
+__global__ void k_axpby_f(size_t n, float a, const float* __restrict__ x, float b, float* __restrict__ y) {
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+        y[i] = a * x[i] + (b == 0.0f ? 0.0f : b * y[i]);
+}
 __global__ void k_mul(size_t n, const double* __restrict__ a, const double* __restrict__ x, double* __restrict__ y) {
     for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
         y[i] = a[i] * x[i];
@@ -320,6 +324,10 @@ template cudaError_t launch_coarse_solve<double>(int, const int*, const double*,
 
 cudaError_t launch_axpby(size_t n, double a, const double* x, double b, double* y, cudaStream_t s) {
     LAUNCH(PROF_KRYLOV, s, k_axpby<<<grid_stride_blocks(n), 256, 0, s>>>(n, a, x, b, y));
+    return cudaGetLastError();
+}
+cudaError_t launch_axpby_f(size_t n, float a, const float* x, float b, float* y, cudaStream_t s) {
+    LAUNCH(PROF_KRYLOV, s, k_axpby_f<<<grid_stride_blocks(n), 256, 0, s>>>(n, a, x, b, y));
     return cudaGetLastError();
 }
 cudaError_t launch_mul(size_t n, const double* a, const double* x, double* y, cudaStream_t s) {

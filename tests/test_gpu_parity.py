@@ -348,6 +348,19 @@ def test_batch_solve_matches_individual_solves(capi):
         c.close()
 
 
+def test_autotune_keeps_the_solve_correct(capi):
+    p, m, mus, G, ops, F = oracle_problem("cube16")
+    ctx = capi.stokes_setup_problem(p)
+    block, degree = capi.stokes_autotune(ctx, 3)
+    assert block in (64, 128, 256) and 3 <= degree <= 6
+    up = torch.zeros(m.n_u + m.n_p, dtype=torch.float64, device="cuda")
+    info = capi.stokes_solve(ctx, capi.STOKES_FP32, None, up, rtol=1e-8, max_it=1000)
+    b = np.concatenate([F, np.zeros(m.n_p)])
+    assert np.linalg.norm(b - ops.apply_stokes(host(up))) / np.linalg.norm(b) <= 1.5e-8
+    assert info.iterations > 0
+    ctx.close()
+
+
 def test_single_level_and_two_level_meshes(capi):
     for n, L in ((1, 1), (2, 2), (3, 1), (4, 1)):
         p = si.dr_problem(n, L, 1, 1e2, 3000 + n)
