@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cube64")
     ap.add_argument("--no-extras", action="store_true", help="skip the sweep/profile/e2e/cpu legs")
+    ap.add_argument("--solve-report", action="store_true",
+                    help="one FP32-V-cycle and one FP64-V-cycle solve of the workload: iterations, times, "
+                         "true FP64 residuals and the difference of the two solutions (any size)")
     ap.add_argument("--kernels", action="store_true",
                     help="profiling case: set up the workload, run 3 FP32 vmults, 2 FP64 Stokes applies, "
                          "1 FP32 V-cycle, print one line and exit (for ncu)")
@@ -489,8 +492,49 @@ def run_batch(args):
     print(json.dumps(line))
 
 
+def run_report(args):
+    import torch
+    from paper_1907_06696_gb300 import build as B
+    B.build()
+    from paper_1907_06696_gb300 import capi
+    capi.load()
+    import sinker_inputs as si
+    prob = si.workload(args.workload)
+    t0 = time.perf_counter()
+    ctx = capi.stokes_setup_problem(prob)
+    setup_s = time.perf_counter() - t0
+    N = ctx.n_u + ctx.n_p
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    sols = {}
+    for tag, prec in (("fp32_vcycle", capi.STOKES_FP32), ("fp64_vcycle", capi.STOKES_FP64)):
+        up = torch.zeros(N, dtype=torch.float64, device="cuda")
+        for _ in range(args.warmup):
+            up.zero_()
+            capi.stokes_solve(ctx, prec, None, up, rtol=RTOL, max_it=5000)
+        up.zero_()
+        e0.record()
+        info = capi.stokes_solve(ctx, prec, None, up, rtol=RTOL, max_it=5000, check=False)
+        e1.record()
+        torch.cuda.synchronize()
+        out[tag] = {"s": e0.elapsed_time(e1) / 1e3, "iterations": info.iterations, "status": info.status,
+                    "true_rel_residual": info.rel_residual_true}
+        sols[tag] = up
+    u32, u64 = sols["fp32_vcycle"][:ctx.n_u], sols["fp64_vcycle"][:ctx.n_u]
+    p32, p64 = sols["fp32_vcycle"][ctx.n_u:], sols["fp64_vcycle"][ctx.n_u:]
+    out["rel_diff_u"] = float((u32 - u64).norm() / u64.norm())
+    out["rel_diff_p"] = float((p32 - p64).norm() / p64.norm())
+    out["speedup"] = out["fp64_vcycle"]["s"] / out["fp32_vcycle"]["s"]
+    print(json.dumps({"report": args.workload, "n_u": ctx.n_u, "n_p": ctx.n_p, "setup_s": setup_s,
+                      "sinkers": prob.n_sinkers, "dr": prob.mu_max / prob.mu_min, "rtol": RTOL, **out}))
+    ctx.close()
+
+
 def main():
     args = parse()
+    if args.solve_report:
+        run_report(args)
+        return
     if args.workload.startswith("batch") and args.impl != "reference":
         run_batch(args)
     elif args.kernels:
