@@ -830,7 +830,7 @@ void stokes_default_options(stokes_options* opt) {
     opt->lanczos_steps = 12;
     opt->schur_degree = 5;
     opt->restart = 50;
-    opt->outer_arith = 0;
+    opt->outer_arith = 1;
     opt->vmult_kernel = 0;
     opt->graphs = 1;
 }

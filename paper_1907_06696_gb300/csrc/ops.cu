@@ -423,8 +423,9 @@ cudaError_t launch_stokes_blocks(const LevelGeom& g, const double* mu, const dou
         e = cudaMemsetAsync(dst_p, 0, g.n_p * sizeof(double), s);
         if (e != cudaSuccess) return e;
     }
-    e = df64 ? launch_outer_df64(g, mu, src_u, src_p, dst_u, dst_p, do_a, do_bt, do_b, s)
-             : stokes_blocks_ct<double>(g, mu, src_u, src_p, dst_u, dst_p, do_a, do_bt, do_b, s);
+    // double-float pays off where the A part is present; B^T or B alone are cheaper in native FP64
+    e = (df64 && do_a) ? launch_outer_df64(g, mu, src_u, src_p, dst_u, dst_p, do_a, do_bt, do_b, s)
+                       : stokes_blocks_ct<double>(g, mu, src_u, src_p, dst_u, dst_p, do_a, do_bt, do_b, s);
     if (e != cudaSuccess) return e;
     if (do_a) {
         const size_t nbd = 6 * size_t(g.M) * g.M;

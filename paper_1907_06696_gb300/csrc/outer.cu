@@ -16,17 +16,17 @@ namespace stk {
 namespace {
 
 template <bool DO_A, bool DO_BT, bool DO_B>
-__global__ void __launch_bounds__(kOuterThreads, 2) k_outer_df64(OuterArgs a) {
-    __shared__ OuterShared sh;
+__global__ void __launch_bounds__(kOuterThreads, 3) k_outer_df64(OuterArgs a) {
+    extern __shared__ __align__(16) unsigned char outer_smem[];
+    OuterShared& sh = *reinterpret_cast<OuterShared*>(outer_smem);
     const int c = threadIdx.x / kOuterCells, g = threadIdx.x % kOuterCells;
-    q2::df64 U[27], W[27];
-    if (c == 0) outer_phase1<0, DO_A, DO_B>(a, blockIdx.x, g, sh, U, W);
-    else if (c == 1) outer_phase1<1, DO_A, DO_B>(a, blockIdx.x, g, sh, U, W);
-    else outer_phase1<2, DO_A, DO_B>(a, blockIdx.x, g, sh, U, W);
+    {
+        q2::df64 U[27];
+        outer_phase1<DO_A, DO_B>(a, c, blockIdx.x, g, sh, U);
+    }
     __syncthreads();
-    if (c == 0) outer_phase2<0, DO_A, DO_BT>(a, blockIdx.x, g, sh, W);
-    else if (c == 1) outer_phase2<1, DO_A, DO_BT>(a, blockIdx.x, g, sh, W);
-    else outer_phase2<2, DO_A, DO_BT>(a, blockIdx.x, g, sh, W);
+    q2::df64 W[27];
+    outer_phase2<DO_A, DO_BT>(a, c, blockIdx.x, g, sh, W);
 }
 
 }  // namespace
@@ -34,15 +34,26 @@ __global__ void __launch_bounds__(kOuterThreads, 2) k_outer_df64(OuterArgs a) {
 cudaError_t launch_outer_df64(const LevelGeom& g, const double* mu, const double* src_u, const double* src_p,
                               double* dst_u, double* dst_p, bool do_a, bool do_bt, bool do_b, cudaStream_t s) {
     OuterArgs a{g.n, g.M, g.nodes, g.h, mu, src_u, src_p, dst_u, dst_p};
+    static bool configured = false;
+    constexpr int smem = int(sizeof(OuterShared));
+    if (!configured) {   // first call happens in set-up or a solve, never inside a stream capture
+        cudaError_t e;
+        if ((e = cudaFuncSetAttribute(k_outer_df64<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_outer_df64<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_outer_df64<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_outer_df64<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+            return e;
+        configured = true;
+    }
     const unsigned nb = unsigned((g.cells + kOuterCells - 1) / kOuterCells);
     if (do_a && do_bt && do_b)
-        LAUNCH(PROF_STOKES_F64, s, (k_outer_df64<true, true, true><<<nb, kOuterThreads, 0, s>>>(a)));
+        LAUNCH(PROF_STOKES_F64, s, (k_outer_df64<true, true, true><<<nb, kOuterThreads, smem, s>>>(a)));
     else if (do_a && !do_bt && !do_b)
-        LAUNCH(PROF_STOKES_F64, s, (k_outer_df64<true, false, false><<<nb, kOuterThreads, 0, s>>>(a)));
+        LAUNCH(PROF_STOKES_F64, s, (k_outer_df64<true, false, false><<<nb, kOuterThreads, smem, s>>>(a)));
     else if (!do_a && do_bt && !do_b)
-        LAUNCH(PROF_BT_F64, s, (k_outer_df64<false, true, false><<<nb, kOuterThreads, 0, s>>>(a)));
+        LAUNCH(PROF_BT_F64, s, (k_outer_df64<false, true, false><<<nb, kOuterThreads, smem, s>>>(a)));
     else if (!do_a && !do_bt && do_b)
-        LAUNCH(PROF_STOKES_F64, s, (k_outer_df64<false, false, true><<<nb, kOuterThreads, 0, s>>>(a)));
+        LAUNCH(PROF_STOKES_F64, s, (k_outer_df64<false, false, true><<<nb, kOuterThreads, smem, s>>>(a)));
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();

@@ -7,10 +7,10 @@
 // of component c and DC_d the collocation derivative along axis d:
 //   W_c  = 2 DC_c^T (w .* DC_c U_c)                          (diagonal term)
 //        + sum_{d != c} DC_d^T (w .* (DC_d U_c + DC_c U_d))   (symmetric pairs)
-// The products DC_d U_c (d != c) are exchanged through shared memory so
-// that each thread only keeps its own component: three 27-vectors of
-// double-floats. Then out_c = mu h V^T W_c - h^2 (moments of B^T) p, and B's
-// moments of u_c are added into the pressure output per component.
+// The products DC_d U_c (d != c) and DC_c U_c are exchanged through shared
+// memory so that each thread only keeps its own component. Then
+// out_c = mu h V^T W_c - h^2 (moments of B^T) p, and B's moments of u_c are
+// added into the pressure output per component.
 // The phases are plain functions of the thread index so that a host program
 // can run them and compare with the FP64 kernel.
 #pragma once
@@ -34,9 +34,11 @@ struct OuterArgs {
     double* dst_p;
 };
 
-// Shared exchange buffer: X[pair(c,d)][q][g], pair over the 6 ordered pairs c != d.
+// Shared exchange buffer: X[pair(c,d)][q][g] over the 6 ordered pairs c != d, and the
+// diagonal term Dg[c][q][g] = DC_c U_c (so that phase 1 holds only U and one temporary).
 struct OuterShared {
     q2::df64 X[6][27][kOuterCells];
+    q2::df64 Dg[3][27][kOuterCells];
 };
 
 __host__ __device__ __forceinline__ constexpr int outer_pair(int c, int d) { return 2 * c + (d > c ? d - 1 : d); }
@@ -52,82 +54,138 @@ __host__ __device__ __forceinline__ void outer_atomic_add(double* p, double v) {
 #endif
 }
 
-// Phase 1 of thread (C, g): gather, B moments, interpolation, diagonal term, and the two
-// cross products DC_d U_C for d != C into shared memory. U and W stay in registers
-// (passed back to phase 2 by reference).
-template <int C, bool DO_A, bool DO_B>
-__host__ __device__ __forceinline__ void outer_phase1(const OuterArgs& a, int blk, int g, OuterShared& sh,
-                                                      q2::df64 (&U)[27], q2::df64 (&W)[27]) {
+// Every thread runs the same code: in its local frame the axes are rotated cyclically so that
+// its own velocity component C lies along local axis 0 (local axes = global axes C, C+1, C+2
+// mod 3). The operator is invariant under this relabelling (same 1D matrices and weights on every
+// axis), so only the addressing differs between the three warps: gathers, scatters and the
+// shared-memory exchange map local indices to global ones at run time. This keeps one copy of
+// the unrolled double-float code (three copies overflow the instruction cache).
+struct OuterFrame {
+    int C;            // velocity component of this thread
+    int D1, D2;       // global axes of local axes 1 and 2
+    size_t sn[3];     // global node strides of local axes 0, 1, 2
+    int sq[3];        // global Gauss-point strides (1, 3, 9 rotated)
+    int sv[3];        // global Q1-vertex bits (1, 2, 4 rotated)
+    int cl[3];        // cell coordinates along the local axes
+    int ci, cj, ck;   // global cell coordinates
+};
+
+__host__ __device__ __forceinline__ OuterFrame outer_frame(const OuterArgs& a, int C, size_t cell) {
+    OuterFrame f;
+    f.C = C;
+    f.D1 = (C + 1) % 3;
+    f.D2 = (C + 2) % 3;
+    f.ci = int(cell % a.n);
+    f.cj = int((cell / a.n) % a.n);
+    f.ck = int(cell / (size_t(a.n) * a.n));
+    const size_t ns[3] = {1, size_t(a.M), size_t(a.M) * a.M};
+    const int qs[3] = {1, 3, 9}, vs[3] = {1, 2, 4};
+    const int cc[3] = {f.ci, f.cj, f.ck};
+    const int ax[3] = {C, f.D1, f.D2};
+    for (int d = 0; d < 3; ++d) {
+        f.sn[d] = ns[ax[d]];
+        f.sq[d] = qs[ax[d]];
+        f.sv[d] = vs[ax[d]];
+        f.cl[d] = cc[ax[d]];
+    }
+    return f;
+}
+
+// Global Gauss-point index of local index q (= qa + 3 qb + 9 qc).
+__host__ __device__ __forceinline__ int outer_gq(const OuterFrame& f, int q) {
+    return (q % 3) * f.sq[0] + ((q / 3) % 3) * f.sq[1] + (q / 9) * f.sq[2];
+}
+
+// Phase 1: gather own component, B moments, interpolation, and the diagonal derivative
+// DC_0 U and the two cross products DC_1 U, DC_2 U (local axes) into shared memory.
+template <bool DO_A, bool DO_B>
+__host__ __device__ __forceinline__ void outer_phase1(const OuterArgs& a, int C, int blk, int g, OuterShared& sh,
+                                                      q2::df64 (&U)[27]) {
     using q2::df64;
     const size_t cells = size_t(a.n) * a.n * a.n;
     const size_t cell = size_t(blk) * kOuterCells + g;
     const bool valid = cell < cells;
 #pragma unroll
-    for (int m = 0; m < 27; ++m) { U[m] = df64(0); W[m] = df64(0); }
+    for (int m = 0; m < 27; ++m) U[m] = df64(0);
     if (!(DO_A || DO_B)) return;
     if (valid) {
-        const int ci = int(cell % a.n), cj = int((cell / a.n) % a.n), ck = int(cell / (size_t(a.n) * a.n));
+        const OuterFrame f = outer_frame(a, C, cell);
+        const double* src = a.src_u + size_t(C) * a.nodes +
+                            (size_t(2 * f.ci) + size_t(a.M) * (size_t(2 * f.cj) + size_t(a.M) * size_t(2 * f.ck)));
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
+        for (int c = 0; c < 3; ++c)
 #pragma unroll
-            for (int j = 0; j < 3; ++j)
+            for (int b = 0; b < 3; ++b)
 #pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    const int gi = 2 * ci + i, gj = 2 * cj + j, gk = 2 * ck + k;
-                    if (!(outer_bnd(gi, a.M) || outer_bnd(gj, a.M) || outer_bnd(gk, a.M)))
-                        U[i + 3 * j + 9 * k] =
-                            q2::from_double(a.src_u[C * a.nodes + size_t(gi) + size_t(a.M) * (gj + size_t(a.M) * gk)]);
+                for (int aa = 0; aa < 3; ++aa) {
+                    const int g0 = 2 * f.cl[0] + aa, g1 = 2 * f.cl[1] + b, g2 = 2 * f.cl[2] + c;
+                    if (!(outer_bnd(g0, a.M) || outer_bnd(g1, a.M) || outer_bnd(g2, a.M)))
+                        U[aa + 3 * b + 9 * c] = q2::from_double(src[aa * f.sn[0] + b * f.sn[1] + c * f.sn[2]]);
                 }
         if (DO_B) {
             df64 bp[8];
 #pragma unroll
             for (int v = 0; v < 8; ++v) bp[v] = df64(0);
-            q2::b_component<C>(U, bp);
+            q2::b_component<0>(U, bp);
             const int P = a.n + 1;
             const double s = -a.h * a.h;
 #pragma unroll
             for (int v = 0; v < 8; ++v) {
-                const size_t vert =
-                    size_t(ci + (v & 1)) + size_t(P) * (cj + ((v >> 1) & 1) + size_t(P) * (ck + (v >> 2)));
-                outer_atomic_add<C>(a.dst_p + vert, s * bp[v].to_double());
+                const int gv = (v & 1) * f.sv[0] + ((v >> 1) & 1) * f.sv[1] + (v >> 2) * f.sv[2];
+                const size_t vert = size_t(f.ci + (gv & 1)) +
+                                    size_t(P) * (f.cj + ((gv >> 1) & 1) + size_t(P) * (f.ck + (gv >> 2)));
+                outer_atomic_add<0>(a.dst_p + vert, s * bp[v].to_double());
             }
         }
     }
     if (!DO_A) return;
+    const int D1 = (C + 1) % 3, D2 = (C + 2) % 3;
+    const OuterFrame f = outer_frame(a, C, valid ? cell : 0);
     q2::interp<0>(U);
     q2::interp<1>(U);
     q2::interp<2>(U);
     df64 T[27];
-    q2::deriv<C, false>(U, T);
-    q2::derivT_w<C, 2>(T, W);
-    constexpr int D0 = C == 0 ? 1 : 0, D1 = C == 2 ? 1 : 2;
-    q2::deriv<D0, false>(U, T);
+    q2::deriv<0, false>(U, T);
 #pragma unroll
-    for (int q = 0; q < 27; ++q) sh.X[outer_pair(C, D0)][q][g] = T[q];
-    q2::deriv<D1, false>(U, T);
+    for (int q = 0; q < 27; ++q) sh.Dg[C][outer_gq(f, q)][g] = T[q];
+    q2::deriv<1, false>(U, T);
 #pragma unroll
-    for (int q = 0; q < 27; ++q) sh.X[outer_pair(C, D1)][q][g] = T[q];
+    for (int q = 0; q < 27; ++q) sh.X[outer_pair(C, D1)][outer_gq(f, q)][g] = T[q];
+    q2::deriv<2, false>(U, T);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) sh.X[outer_pair(C, D2)][outer_gq(f, q)][g] = T[q];
 }
 
-// Phase 2 (after a barrier): finish the symmetric pairs, transposed interpolation,
+// Phase 2 (after a barrier): diagonal and symmetric pairs, transposed interpolation,
 // B^T moments, scatter into the velocity output.
-template <int C, bool DO_A, bool DO_BT>
-__host__ __device__ __forceinline__ void outer_phase2(const OuterArgs& a, int blk, int g, const OuterShared& sh,
+template <bool DO_A, bool DO_BT>
+__host__ __device__ __forceinline__ void outer_phase2(const OuterArgs& a, int C, int blk, int g, const OuterShared& sh,
                                                       q2::df64 (&W)[27]) {
     using q2::df64;
     const size_t cells = size_t(a.n) * a.n * a.n;
     const size_t cell = size_t(blk) * kOuterCells + g;
     if (cell >= cells || !(DO_A || DO_BT)) return;
-    const int ci = int(cell % a.n), cj = int((cell / a.n) % a.n), ck = int(cell / (size_t(a.n) * a.n));
+    const OuterFrame f = outer_frame(a, C, cell);
+#pragma unroll
+    for (int m = 0; m < 27; ++m) W[m] = df64(0);
     if (DO_A) {
-        constexpr int D0 = C == 0 ? 1 : 0, D1 = C == 2 ? 1 : 2;
+        const int D1 = f.D1, D2 = f.D2;
         df64 T[27];
 #pragma unroll
-        for (int q = 0; q < 27; ++q) T[q] = sh.X[outer_pair(C, D0)][q][g] + sh.X[outer_pair(D0, C)][q][g];
-        q2::derivT_w<D0, 1>(T, W);
+        for (int q = 0; q < 27; ++q) T[q] = sh.Dg[C][outer_gq(f, q)][g];
+        q2::derivT_w<0, 2>(T, W);
 #pragma unroll
-        for (int q = 0; q < 27; ++q) T[q] = sh.X[outer_pair(C, D1)][q][g] + sh.X[outer_pair(D1, C)][q][g];
-        q2::derivT_w<D1, 1>(T, W);
+        for (int q = 0; q < 27; ++q) {
+            const int gq = outer_gq(f, q);
+            T[q] = sh.X[outer_pair(C, D1)][gq][g] + sh.X[outer_pair(D1, C)][gq][g];
+        }
+        q2::derivT_w<1, 1>(T, W);
+#pragma unroll
+        for (int q = 0; q < 27; ++q) {
+            const int gq = outer_gq(f, q);
+            T[q] = sh.X[outer_pair(C, D2)][gq][g] + sh.X[outer_pair(D2, C)][gq][g];
+        }
+        q2::derivT_w<2, 1>(T, W);
         q2::interpT<0>(W);
         q2::interpT<1>(W);
         q2::interpT<2>(W);
@@ -141,21 +199,24 @@ __host__ __device__ __forceinline__ void outer_phase2(const OuterArgs& a, int bl
         df64 p8[8];
 #pragma unroll
         for (int v = 0; v < 8; ++v) {
-            const size_t vert = size_t(ci + (v & 1)) + size_t(P) * (cj + ((v >> 1) & 1) + size_t(P) * (ck + (v >> 2)));
+            const int gv = (v & 1) * f.sv[0] + ((v >> 1) & 1) * f.sv[1] + (v >> 2) * f.sv[2];
+            const size_t vert = size_t(f.ci + (gv & 1)) +
+                                size_t(P) * (f.cj + ((gv >> 1) & 1) + size_t(P) * (f.ck + (gv >> 2)));
             p8[v] = q2::from_double(s * a.src_p[vert]);
         }
-        q2::bt_component<C>(p8, W);
+        q2::bt_component<0>(p8, W);
     }
+    double* dst = a.dst_u + size_t(C) * a.nodes +
+                  (size_t(2 * f.ci) + size_t(a.M) * (size_t(2 * f.cj) + size_t(a.M) * size_t(2 * f.ck)));
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
+    for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int j = 0; j < 3; ++j)
+        for (int b = 0; b < 3; ++b)
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const int gi = 2 * ci + i, gj = 2 * cj + j, gk = 2 * ck + k;
-                if (outer_bnd(gi, a.M) || outer_bnd(gj, a.M) || outer_bnd(gk, a.M)) continue;
-                outer_atomic_add<C>(a.dst_u + C * a.nodes + size_t(gi) + size_t(a.M) * (gj + size_t(a.M) * gk),
-                                    W[i + 3 * j + 9 * k].to_double());
+            for (int aa = 0; aa < 3; ++aa) {
+                const int g0 = 2 * f.cl[0] + aa, g1 = 2 * f.cl[1] + b, g2 = 2 * f.cl[2] + c;
+                if (outer_bnd(g0, a.M) || outer_bnd(g1, a.M) || outer_bnd(g2, a.M)) continue;
+                outer_atomic_add<0>(dst + aa * f.sn[0] + b * f.sn[1] + c * f.sn[2], W[aa + 3 * b + 9 * c].to_double());
             }
 }
 
