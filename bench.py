@@ -117,9 +117,19 @@ def peaks():
         return {}
 
 
-def kernel_source_hash():
+# Sources that define each profiled kernel class (a recorded ncu traffic figure is used only
+# while these files are unchanged).
+KERNEL_SOURCES = {
+    "stokes_df64": ("q2_basis.cuh", "df64.cuh", "outer.cuh", "outer.cu"),
+    "stokes_fp64": ("q2_basis.cuh", "ops.cu"),
+    "vmult_A_fp32": ("q2_basis.cuh", "brick.cuh", "brick.cu"),
+    "krylov_vec": ("krylov.cu", "vec.cu"),
+}
+
+
+def kernel_source_hash(kernel):
     h = hashlib.sha256()
-    for f in ("q2_basis.cuh", "df64.cuh", "outer.cuh", "outer.cu", "brick.cuh", "brick.cu", "ops.cu"):
+    for f in KERNEL_SOURCES[kernel]:
         h.update(open(os.path.join(ROOT, "paper_1907_06696_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -131,9 +141,26 @@ def recorded_traffic(kernel, workload):
     except (OSError, ValueError):
         return None
     e = rec.get(kernel, {}).get(workload)
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or kernel not in KERNEL_SOURCES or e.get("source_hash") != kernel_source_hash(kernel):
         return None
     return e.get("bytes_per_launch")
+
+
+def krylov_alg_bytes(N, its, m):
+    """Algorithmic HBM bytes of the FGMRES vector kernels over a solve of `its` iterations with
+    restart m: per cycle the residual (w = b - K x: 3 vectors, |w|: 1) and V_0 = w / beta (2);
+    per iteration with k = j + 1 basis vectors the three Gram-Schmidt passes, (k + 1) + (k + 2)
+    vectors and (k + 2) more when V_k is formed (k < m); x += Z y, k + 2; and the final residual."""
+    vecs, left = N, its   # |b|
+    while left > 0:
+        kc = min(m, left)
+        vecs += 6 * N
+        for k in range(1, kc + 1):
+            vecs += (2 * k + 3) * N + ((k + 2) * N if k < m else 0)
+        vecs += (kc + 2) * N
+        left -= kc
+    vecs += 4 * N
+    return 8 * vecs
 
 
 # ----------------------------------------------------------------- CPU oracle legs
@@ -369,6 +396,15 @@ def run_ours(args):
                                 "frac": ach / (f64_peak * 1e3), "traffic": recorded_traffic("stokes_fp64", args.workload),
                                 "peak_note": "of measured (DFMA probe, this run)",
                                 "per_launch": "%d cells x %d flop" % (cells, STOKES_FLOP_PER_CELL)}
+    elif dom == "krylov_vec":
+        # whole class over the profiled solve: algorithmic bytes of its passes / its summed time
+        kb = krylov_alg_bytes(N, its[-1], capi.stokes_default_options().restart)
+        ach = kb / (prof[dom][0] / 1e3) / 1e9
+        line["roofline"] = {"kernel": "krylov_vec (Gram-Schmidt passes k_gs_tile + FGMRES vector kernels)",
+                            "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                            "traffic": recorded_traffic(dom, args.workload), "peak_note": hbm_src,
+                            "per_launch": "class total over one solve: %.1f GB algorithmic in %d launches"
+                                          % (kb / 1e9, prof[dom][1])}
     else:
         k = vm["fp32"] if dom == "vmult_A_fp32" else vm["fp64"]
         line["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": k["achieved_gbs"], "peak": hbm, "unit": "GB/s",

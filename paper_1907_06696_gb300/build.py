@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libstokes_gb300.so")
-SOURCES = ["ops.cu", "vec.cu", "brick.cu", "outer.cu", "api.cu", "noalloc.cu", "probe.cu"]
+SOURCES = ["ops.cu", "vec.cu", "krylov.cu", "brick.cu", "outer.cu", "api.cu", "noalloc.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-I" + os.path.join(ROOT, "include")]

@@ -164,6 +164,7 @@ struct stokes_ctx {
     double* dots_host = nullptr;  // pinned
     // Krylov workspace (allocated on first solve)
     size_t N = 0;
+    size_t ldv = 0;   // row stride of V (N rounded up to even)
     double *V = nullptr, *Z = nullptr, *w = nullptr, *bvec = nullptr, *hdev = nullptr;
     int krylov_restart = 0;
     // host-buffer solve
@@ -399,11 +400,12 @@ stokes_status ensure_krylov(stokes_ctx* c) {
     if (c->V && c->krylov_restart == m) return STOKES_OK;
     const LevelGeom& g = c->lev[c->L - 1].g;
     c->N = g.n_u + g.n_p;
-    CKS(dalloc(c, &c->V, size_t(m + 1) * c->N));
+    c->ldv = c->N + (c->N & 1);   // even row stride: 16-byte aligned entry pairs (krylov.cu)
+    CKS(dalloc(c, &c->V, size_t(m + 1) * c->ldv));
     CKS(dalloc(c, &c->Z, size_t(m) * c->N));
     CKS(dalloc(c, &c->w, c->N));
     CKS(dalloc(c, &c->bvec, c->N));
-    CKS(dalloc(c, &c->hdev, size_t(2 * (m + 2))));
+    CKS(dalloc(c, &c->hdev, size_t(2 * (m + 4))));
     c->krylov_restart = m;
     return STOKES_OK;
 }
@@ -458,21 +460,30 @@ stokes_status fgmres_enqueue(FgmresRun& r) {
         case FgmresRun::P_ITER: {
             const int j = r.j;
             double* V = c->V;
-            double* vj = V + size_t(j) * N;
+            const size_t ldv = c->ldv;
+            double* vj = V + size_t(j) * ldv;
             double* zj = c->Z + size_t(j) * N;
-            if (r.next_v) CK(launch_axpby(N, 1.0 / r.hn_prev, c->w, 0.0, vj, s));   // V_j = w / |w|
-            CKS(precondition(c, r.prec, vj, zj, s));
+            const bool df = c->opt.outer_arith == 1 && m <= gs_max_k();   // V as double-float pairs (krylov.cu)
+            if (df) {
+                if (r.next_v) CK(launch_df_store_scaled(N, c->w, 1.0 / r.hn_prev, vj, s));   // V_j = w / |w|
+                CK(launch_df_to_double(N, vj, c->w, s));
+                CKS(precondition(c, r.prec, c->w, zj, s));
+            } else {
+                if (r.next_v) CK(launch_axpby(N, 1.0 / r.hn_prev, c->w, 0.0, vj, s));
+                CKS(precondition(c, r.prec, vj, zj, s));
+            }
             CKS(apply_stokes(c, zj, c->w, s));
-            // classical Gram-Schmidt applied twice ("twice is enough"); the second multi-dot also
-            // returns |w1|^2 of the once-projected vector, so |w2|^2 = |w1|^2 - |h2|^2 (no
-            // cancellation: h2 is small after the first pass)
+            // classical Gram-Schmidt applied twice ("twice is enough") in three passes over V:
+            // h1 = V^T w; w1 = w - V h1 with h2 = V^T w1 and |w1|^2 in the same sweep;
+            // V_{j+1} = (w1 - V h2) / hn with hn = sqrt(|w1|^2 - |h2|^2) computed on the device
+            // (no cancellation: h2 is small after the first pass). The last vector of a cycle is
+            // not needed (the restart recomputes the residual).
             double* h1d = c->hdev;
-            double* h2d = c->hdev + (m + 2);
-            CK(launch_multidot(N, j + 1, V, N, c->w, c->partials, h1d, s, true));
-            CK(launch_multiaxpy(N, j + 1, V, N, h1d, c->w, -1.0, s));
-            CK(launch_multidot(N, j + 1, V, N, c->w, c->partials, h2d, s, true));
-            CK(launch_multiaxpy(N, j + 1, V, N, h2d, c->w, -1.0, s));
-            CK(cudaMemcpyAsync(c->dots_host, c->hdev, size_t(2 * (m + 2)) * sizeof(double), cudaMemcpyDeviceToHost, s));
+            double* h2d = c->hdev + (m + 4);
+            CK(launch_gs_dot(N, j + 1, V, ldv, c->w, c->partials, h1d, df, s));
+            CK(launch_gs_project_dot(N, j + 1, V, ldv, h1d, c->w, c->partials, h2d, df, s));
+            if (j + 1 < m) CK(launch_gs_project_scale(N, j + 1, V, ldv, h2d, c->w, h2d + j + 3, vj + ldv, df, s));
+            CK(cudaMemcpyAsync(c->dots_host, c->hdev, size_t(2 * (m + 4)) * sizeof(double), cudaMemcpyDeviceToHost, s));
             return STOKES_OK;
         }
         case FgmresRun::P_FINAL:
@@ -535,13 +546,8 @@ stokes_status fgmres_complete(FgmresRun& r) {
         }
         case FgmresRun::P_ITER: {
             const int j = r.j;
-            double h2sq = 0.0;
-            for (int i = 0; i <= j; ++i) {
-                const double h2 = hd[m + 2 + i];
-                r.Hij(i, j) = hd[i] + h2;
-                h2sq += h2 * h2;
-            }
-            const double hn = std::sqrt(std::fmax(hd[m + 2 + j + 1] - h2sq, 0.0));
+            for (int i = 0; i <= j; ++i) r.Hij(i, j) = hd[i] + hd[m + 4 + i];
+            const double hn = hd[m + 4 + j + 2];   // the norm V_{j+1} was scaled with
             if (!std::isfinite(hn)) { r.st = STOKES_BREAKDOWN; r.phase = FgmresRun::P_FINAL; return STOKES_OK; }
             r.Hij(j + 1, j) = hn;
             for (int i = 0; i < j; ++i) {
@@ -565,8 +571,7 @@ stokes_status fgmres_complete(FgmresRun& r) {
                 else if (r.its >= r.max_it) r.phase = FgmresRun::P_FINAL;
                 else r.phase = FgmresRun::P_RESTART;
             } else {
-                r.hn_prev = hn;
-                r.next_v = true;
+                r.next_v = false;   // V_{j+1} was formed on the device
                 r.j = j + 1;
             }
             return STOKES_OK;
@@ -652,6 +657,7 @@ stokes_status setup_impl(const stokes_mesh* mesh, const stokes_mu* mu, const sto
         (o.vmult_kernel != 0 && o.vmult_kernel != 1) || (o.graphs != 0 && o.graphs != 1))
         return fail(STOKES_EINVAL, "bad options");
     CK(brick_configure());
+    CK(gs_configure());
     c->n = mesh->n;
     c->L = mesh->n_levels;
     const int L = c->L;
@@ -685,7 +691,7 @@ stokes_status setup_impl(const stokes_mesh* mesh, const stokes_mu* mu, const sto
     CKS(dalloc(c, &c->tu, gf.n_u));
     CKS(dalloc(c, &c->stage_in, gf.n_u));
     CKS(dalloc(c, &c->stage_out, gf.n_u));
-    CKS(dalloc(c, &c->partials, size_t(multidot_blocks()) * (o.restart + 8)));
+    CKS(dalloc(c, &c->partials, size_t(std::max(multidot_blocks(), gs_partials_blocks())) * (o.restart + 8)));
     CKS(dalloc(c, &c->dots, size_t(o.restart + 8)));
     CK(cudaMallocHost(&c->dots_host, size_t(2 * (o.restart + 8)) * sizeof(double)));
     // ---- viscosity (Section 2.3) and right-hand side (Section 3.2)

@@ -132,4 +132,58 @@ __host__ __device__ __forceinline__ df64 from_double(double v) {
     return df64(h, float(v - double(h)));
 }
 
+// Split of a double into a double-float with integer and FP32 instructions only (no FP64
+// instruction, whose throughput is the bottleneck of FP64 vector kernels on this GPU).
+// For 2^-97 <= |v| < 2^128: hi = v's sign, exponent and the leading 24 significand bits
+// (truncated); lo = the next 23 bits rounded to nearest, as (1 + R 2^-23) - 1 scaled by a power
+// of two (both steps exact). |v - (hi + lo)| <= 2^-47 |v|. Zero and FP64 subnormals give 0;
+// other magnitudes take the conversion path (from_double).
+__host__ __device__ __forceinline__ unsigned long long dbl_bits(double v) {
+#ifdef __CUDA_ARCH__
+    return static_cast<unsigned long long>(__double_as_longlong(v));
+#else
+    unsigned long long b;
+    __builtin_memcpy(&b, &v, sizeof b);
+    return b;
+#endif
+}
+__host__ __device__ __forceinline__ float flt_from_bits(unsigned u) {
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float f;
+    __builtin_memcpy(&f, &u, sizeof f);
+    return f;
+#endif
+}
+__host__ __device__ __forceinline__ df64 split_double(double v) {
+    const unsigned long long b = dbl_bits(v);
+    const unsigned H = unsigned(b >> 32), L = unsigned(b);
+    const unsigned e = (H >> 20) & 0x7FFu;
+    const unsigned sign = H & 0x80000000u;
+    if (e - 926u <= 224u) {
+        const float hi = flt_from_bits(sign | ((e - 896u) << 23) | ((H & 0xFFFFFu) << 3) | (L >> 29));
+        const unsigned R = ((L & 0x1FFFFFFFu) + 32u) >> 6;   // <= 2^23
+        const float t = sub_f(flt_from_bits(0x3F800000u + R), 1.0f);
+        const float lo = mul_f(t, flt_from_bits((e - 919u) << 23));
+        return df64(hi, sign ? -lo : lo);
+    }
+    if (e == 0u) return df64(0.0f, 0.0f);
+    return from_double(v);
+}
+
+// acc += a * b: the exact product (two_prod by FMA plus the cross terms) is added to acc.hi
+// by two_sum, and the rounding errors are collected in acc.lo without renormalising; call
+// renorm() every few terms so that |acc.lo| stays near ulp(acc.hi) (Ogita-Rump-Oishi Dot2
+// with periodic renormalisation).
+__host__ __device__ __forceinline__ void mac(df64& acc, const df64& a, const df64& b) {
+    const float p = mul_f(a.hi, b.hi);
+    const float ep = prod_err(a, b, p);
+    const float s = add_f(acc.hi, p);
+    const float bb = sub_f(s, acc.hi);
+    const float e = add_f(sub_f(acc.hi, sub_f(s, bb)), sub_f(p, bb));
+    acc = df64(s, add_f(acc.lo, add_f(ep, e)));
+}
+__host__ __device__ __forceinline__ void renorm(df64& acc) { acc = fast_two_sum(acc.hi, acc.lo); }
+
 }  // namespace q2

@@ -106,4 +106,24 @@ int multidot_blocks();
 cudaError_t launch_multiaxpy(size_t n, int k, const double* V, size_t ld, const double* h, double* w, double sign,
                              cudaStream_t s);
 
+// Fused Gram-Schmidt passes (krylov.cu), all results on the device; `partials` holds
+// gs_partials_blocks() * (k + 1) doubles at least. df = double-float arithmetic with V stored
+// as double-float pairs (k <= 64); otherwise native FP64 kernels with V in FP64.
+//   launch_gs_dot:           out[i] = V_i . w, i < k
+//   launch_gs_project_dot:   w -= V h; out[i] = V_i . w (i < k), out[k] = w . w,
+//                            out[k+1] = hn = sqrt(max(out[k] - sum_i out[i]^2, 0)), out[k+2] = 1 / hn
+//   launch_gs_project_scale: y = (w - V h) * scale[0]
+cudaError_t gs_configure();
+int gs_partials_blocks();
+int gs_max_k();   // restart lengths above this use the native FP64 passes
+cudaError_t launch_gs_dot(size_t n, int k, const double* V, size_t ld, const double* w, double* partials,
+                          double* out, bool df, cudaStream_t s);
+cudaError_t launch_gs_project_dot(size_t n, int k, const double* V, size_t ld, const double* h, double* w,
+                                  double* partials, double* out, bool df, cudaStream_t s);
+cudaError_t launch_gs_project_scale(size_t n, int k, const double* V, size_t ld, const double* h, const double* w,
+                                    const double* scale, double* y, bool df, cudaStream_t s);
+// y = w * scale stored as double-float pairs; x = double-float pairs v as FP64.
+cudaError_t launch_df_store_scaled(size_t n, const double* w, double scale, double* y, cudaStream_t s);
+cudaError_t launch_df_to_double(size_t n, const double* v, double* x, cudaStream_t s);
+
 }  // namespace stk
