@@ -120,7 +120,7 @@ __host__ __device__ __forceinline__ void outer_phase1(const OuterArgs& a, int C,
                 for (int aa = 0; aa < 3; ++aa) {
                     const int g0 = 2 * f.cl[0] + aa, g1 = 2 * f.cl[1] + b, g2 = 2 * f.cl[2] + c;
                     if (!(outer_bnd(g0, a.M) || outer_bnd(g1, a.M) || outer_bnd(g2, a.M)))
-                        U[aa + 3 * b + 9 * c] = q2::from_double(src[aa * f.sn[0] + b * f.sn[1] + c * f.sn[2]]);
+                        U[aa + 3 * b + 9 * c] = q2::split_double(src[aa * f.sn[0] + b * f.sn[1] + c * f.sn[2]]);
                 }
         if (DO_B) {
             df64 bp[8];
@@ -202,7 +202,7 @@ __host__ __device__ __forceinline__ void outer_phase2(const OuterArgs& a, int C,
             const int gv = (v & 1) * f.sv[0] + ((v >> 1) & 1) * f.sv[1] + (v >> 2) * f.sv[2];
             const size_t vert = size_t(f.ci + (gv & 1)) +
                                 size_t(P) * (f.cj + ((gv >> 1) & 1) + size_t(P) * (f.ck + (gv >> 2)));
-            p8[v] = q2::from_double(s * a.src_p[vert]);
+            p8[v] = q2::split_double(s * a.src_p[vert]);
         }
         q2::bt_component<0>(p8, W);
     }
