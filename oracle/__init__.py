@@ -20,6 +20,11 @@ with no blocking, fusion or reordering beyond what the definitions state:
                smoothing, Lanczos eigenvalue estimate, V-cycle (Section 2.2.1).
 * krylov.py    Schur approximation (Section 2.2.2), block-triangular
                preconditioner (eq. stokes_precond), FGMRES(50) and dense solves.
+* octree.py    adaptive octree: refinement in shells around the sinkers, 2:1
+               balance, hanging-node constraints, level structure of local
+               smoothing (refinement-edge nodes, copy levels).
+* adaptive.py  active operators with constraints (C^T E C), right-hand side,
+               level operators and transfers, local-smoothing V-cycle.
 
 Parity pins live in tests/test_oracle_*.py. Functions with no independent pin
 say "parity unpinned" in their docstring.

@@ -118,6 +118,66 @@ def workload(name: str) -> SinkerProblem:
     raise KeyError(name)
 
 
+@dataclass
+class OctreeProblem:
+    """Adaptive sinker problem: an octree refined in shells around the sinkers.
+
+    The base mesh is the uniform 2^base_level grid of the unit cube. A leaf is split while
+    its level is below its sinker's maximum level and its distance interval to the sinker
+    centre meets the shell shell_radius - shell_half_width < |x - c| < shell_radius +
+    shell_half_width; then the tree is 2:1 balanced (faces, edges and vertices). The
+    coefficients are those of SinkerProblem (Section 3.2). The multigrid hierarchy runs from
+    the finest leaf level down to coarsest_level (uniform, <= base_level).
+    """
+    base_level: int
+    coarsest_level: int
+    centres: np.ndarray
+    max_levels: np.ndarray      # one per sinker
+    mu_min: float
+    mu_max: float
+    shell_radius: float = 0.05
+    shell_half_width: float = 0.02
+    delta: float = 200.0
+    omega: float = 0.1
+    beta: float = 10.0
+    name: str = ""
+    seed: int = 0
+
+    @property
+    def n_sinkers(self) -> int:
+        return int(self.centres.shape[0])
+
+
+def octree_problem(base_level, coarsest_level, n_sinkers, level_choices, dr, seed, name=""):
+    """Centres from splitmix64(seed) as for the uniform problems; each sinker's maximum
+    level drawn uniformly from level_choices with the stream of seed + 1."""
+    u = uniform01(seed + 1, n_sinkers)
+    lv = np.array([level_choices[min(int(x * len(level_choices)), len(level_choices) - 1)] for x in u])
+    return OctreeProblem(base_level=base_level, coarsest_level=coarsest_level,
+                         centres=sinker_centres(seed, n_sinkers), max_levels=lv,
+                         mu_min=dr ** -0.5, mu_max=dr ** 0.5, name=name, seed=seed)
+
+
+def octree_workload(name: str) -> OctreeProblem:
+    """The named adaptive workloads.
+
+    octree   : base 8^3, 12 sinkers refined to levels 7-9 (drawn per sinker), viscosity ratio 1e6,
+               multigrid down to 4^3 (~20M velocity DoFs); seed 1911
+    oct_m    : base 8^3, 4 sinkers, levels 5-6, ratio 1e4 (parity case)
+    oct_s    : base 4^3, 2 sinkers, levels 4-5, ratio 1e4 (parity case)
+    oct_xs   : base 2^3, 1 sinker, level 4, ratio 1e2 (dense-solve case)
+    """
+    if name == "octree":
+        return octree_problem(3, 2, 12, (7, 8, 9), 1e6, 1911, name)
+    if name == "oct_m":
+        return octree_problem(3, 2, 4, (5, 6), 1e4, 1921, name)
+    if name == "oct_s":
+        return octree_problem(2, 2, 2, (4, 5), 1e4, 1922, name)
+    if name == "oct_xs":
+        return octree_problem(1, 1, 1, (4,), 1e2, 1923, name)
+    raise KeyError(name)
+
+
 BATCH_SIZES = ((16, 5), (24, 4), (32, 6), (48, 5))   # (cells per axis, levels): coarsest 1 or 3 cells
 
 
