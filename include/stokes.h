@@ -144,6 +144,69 @@ stokes_status stokes_setup(const stokes_mesh* mesh, const stokes_mu* mu, const s
                            const stokes_options* opt /* NULL = defaults */, void* stream,
                            stokes_ctx** out);
 
+/* ---- Adaptive octree meshes (Abstract; local smoothing by citation in Section 2.2.1) ----
+ *
+ * A cell of level l (side 2^-l) at integer position (i, j, k), 0 <= i, j, k < 2^l, l <= 15, is
+ * the key  l << 48 | k << 32 | j << 16 | i.  Leaves must tile the unit cube and be 2:1
+ * balanced across faces, edges and vertices. Points are keyed on the lattice of spacing
+ * 2^-(lmax+1) (lmax = finest leaf level): key = x + Mx (y + Mx z), Mx = 2^(lmax+1) + 1.
+ *
+ * Active space (what stokes_solve, stokes_vmult level -1 and gmg_vcycle act on): the Q2
+ * nodes of the leaves that are not hanging, in increasing key order, component-blocked
+ * velocity [3][nodes]; the Q1 vertices that are not hanging, in increasing key order. A
+ * node of a leaf that lies on a face or edge of a coarser neighbouring leaf, and is not one
+ * of its nodes, is hanging: its value is the coarser leaf's Q2 (velocity) or Q1 (pressure)
+ * interpolant there, resolved inside the operators. Nodes on the cube boundary are
+ * Dirichlet (identity rows, as on uniform meshes).
+ *
+ * Multigrid levels: index 0 = the uniform grid 2^coarsest_level, index li = refinement
+ * level coarsest_level + li, holding every cell of that level (leaf or refined) and its Q2
+ * nodes in increasing key order. Nodes on the boundary of those cells' union but inside the
+ * cube (refinement edge) are ordinary rows of the level operator and are never smoothed.
+ * One V-cycle: the active right-hand side goes to the level of each node's coarsest leaf;
+ * down: degree-k Chebyshev smoothing from zero, residual (edge rows included), restriction
+ * added to the coarser level; dense FP64 solve on level 0; up: prolongation added on every
+ * node, Chebyshev smoothing; each active node takes its value on its level. */
+typedef struct {
+    int coarsest_level;         /* coarsest multigrid level (uniform), <= every leaf's level; its
+                                   free velocity DoFs (dense solve) must number at most 4000 */
+    int64_t n_leaves;
+    const uint64_t* leaf_keys;  /* host, n_leaves keys (any order) */
+} stokes_octree;
+
+/* Leaves of the adaptive sinker mesh: start from the uniform grid 2^base_level; split a leaf
+ * while its level is below the maximum level of a sinker (max_levels[s]) and its distance
+ * interval [min, max |x - c_s|] over the cell meets (shell_radius - shell_half_width,
+ * shell_radius + shell_half_width); then 2:1-balance (faces, edges, vertices). Writes up to
+ * `capacity` sorted keys to `keys` (host; may be NULL with capacity 0 to query the count) and
+ * the count to *n_leaves. Errors: EINVAL (bad argument, or capacity below the count while
+ * keys is given; *n_leaves is set), ENOMEM. */
+stokes_status stokes_octree_sinker_mesh(int base_level, int n_sinkers, const double* centres,
+                                        const int* max_levels, double shell_radius, double shell_half_width,
+                                        uint64_t* keys, int64_t capacity, int64_t* n_leaves);
+
+/* Set up an octree problem: host tables (active DoFs, constraints, levels, copy lists), cell
+ * viscosity (leaf: harmonic average over its Gauss points; refined cell: mean of its
+ * children, Section 2.3), level diagonals, Lanczos estimates per level li >= 1 (start vector
+ * splitmix64 with seed 1907000 + li on the smoothed nodes), the dense inverse of level 0 and
+ * the right-hand side. mu must be kind 0. Synchronous. Errors: EINVAL, EMESH (unbalanced or
+ * malformed leaves, constraint chains), ENOMEM, ECUDA. The context then serves stokes_size,
+ * stokes_vmult, gmg_vcycle, stokes_solve, stokes_solve_host, stokes_get_rhs,
+ * stokes_get_viscosity (level -1: leaves), stokes_get_inv_diagonal, stokes_get_lambda_max,
+ * stokes_precondition, stokes_schur_inverse and stokes_octree_table; the uniform-only entry
+ * points (autotune, batch solve, smooth, transfers, coarse solve) return EMESH. */
+stokes_status stokes_setup_octree(const stokes_octree* mesh, const stokes_mu* mu, const stokes_bc* bc,
+                                  const stokes_options* opt, void* stream, stokes_ctx** out);
+
+/* Host copy of a table of an octree context; returns the entry count (0 for a bad argument)
+ * and writes min(count, capacity) entries to `out` (host; may be NULL):
+ *   0 leaf keys (uint64)                   1 active velocity node keys (uint64)
+ *   2 active pressure vertex keys (uint64) 3 node keys of multigrid level `level` (uint64)
+ *   4 node flags of level `level` (uint8: 1 boundary, 2 refinement edge)
+ *   5 per active velocity node: the multigrid level index it is copied to (int32)
+ *   6 number of hanging velocity nodes, 7 number of hanging pressure vertices (count only) */
+size_t stokes_octree_table(const stokes_ctx* ctx, int which, int level, void* out, size_t capacity);
+
 /* Free everything the context owns (synchronises the device first). NULL is a no-op. */
 void stokes_destroy(stokes_ctx* ctx);
 
@@ -152,14 +215,19 @@ const char* stokes_strerror(stokes_status s);
 const char* stokes_last_error(void);
 
 /* Sizes: what = 0 N_u, 1 N_p, 2 cells, 3 cells per axis, 4 number of levels.
- * level -1 = finest. Returns 0 for a bad argument. */
+ * level -1 = finest. Returns 0 for a bad argument. Octree contexts: level -1 = the active
+ * space (N_u, N_p, leaves; what 3 = finest leaf level), level li = multigrid level li
+ * (3 * nodes, 0, cells; what 3 = its refinement level). */
 size_t stokes_size(const stokes_ctx* ctx, int level, int what);
 
 /* dst = block * src on one level (Section 2.1, eq. stokes_linear_system),
  * matrix-free, sum-factorised on Q2 cells with the level's cell viscosity.
  * level -1 = finest. prec FP32 is available for block A only; the B, B^T,
  * M_p and Stokes blocks are FP64 and finest-level only. src and dst must not
- * overlap. Errors: EINVAL (bad level/block/precision, null pointer), ECUDA. */
+ * overlap. Errors: EINVAL (bad level/block/precision, null pointer), ECUDA.
+ * Octree contexts: level -1 is the active space with hanging-node constraints (FP64, all
+ * blocks, native FP64 arithmetic); level li >= 0 is multigrid level li (block A, FP32 or
+ * FP64; refinement-edge rows are ordinary rows). */
 stokes_status stokes_vmult(stokes_ctx* ctx, int level, int block, int prec,
                            const void* src_dev, void* dst_dev, void* stream);
 
@@ -169,7 +237,8 @@ stokes_status stokes_vmult(stokes_ctx* ctx, int level, int block, int prec,
  * prolongation; exact FP64 solve on level 0. prec selects the arithmetic of
  * the whole cycle (FP32: vectors and kernels in FP32, coarse solve in FP64);
  * rhs and x have that precision and length N_u. x holds rhs on constrained
- * entries. rhs and x must not overlap. */
+ * entries. rhs and x must not overlap. Octree contexts: rhs and x are FP64 active velocity
+ * vectors whatever prec (prec selects the arithmetic of the local-smoothing cycle). */
 stokes_status gmg_vcycle(stokes_ctx* ctx, int prec, const void* rhs_dev, void* x_dev, void* stream);
 
 /* Solve [[A, B^T], [B, 0]] [u; p] = [rhs_u; rhs_p] with right-preconditioned

@@ -15,9 +15,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libstokes_gb300.so")
-SOURCES = ["ops.cu", "vec.cu", "krylov.cu", "brick.cu", "outer.cu", "api.cu", "noalloc.cu", "probe.cu"]
+SOURCES = ["ops.cu", "vec.cu", "krylov.cu", "brick.cu", "outer.cu", "octree.cu", "octree_host.cpp", "api.cu",
+           "noalloc.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC,-ffp-contract=off",
          "-I" + os.path.join(ROOT, "include")]
 
 
@@ -43,7 +44,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
 
     def compile_one(src):
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
         if force or _stale(o, [s] + headers):
             cmd = [cc] + ARCH + FLAGS + ["-c", s, "-o", o]
             r = subprocess.run(cmd, capture_output=True, text=True)

@@ -39,6 +39,10 @@ class stokes_bc(C.Structure):
     _fields_ = [("noslip_faces", C.c_uint32)]
 
 
+class stokes_octree(C.Structure):
+    _fields_ = [("coarsest_level", C.c_int), ("n_leaves", C.c_int64), ("leaf_keys", C.POINTER(C.c_uint64))]
+
+
 class stokes_options(C.Structure):
     _fields_ = [("cheb_degree", C.c_int), ("smoothing_range", C.c_double), ("eig_safety", C.c_double),
                 ("lanczos_steps", C.c_int), ("schur_degree", C.c_int), ("restart", C.c_int),
@@ -87,6 +91,11 @@ _SIGS = {
     "stokes_profile_read": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int]),
     "stokes_launch_count": (C.c_longlong, []),
     "stokes_probe_fma": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "stokes_octree_sinker_mesh": (C.c_int, [C.c_int, C.c_int, _P, _P, C.c_double, C.c_double, _P, C.c_int64,
+                                            C.POINTER(C.c_int64)]),
+    "stokes_setup_octree": (C.c_int, [C.POINTER(stokes_octree), C.POINTER(stokes_mu), C.POINTER(stokes_bc),
+                                      C.POINTER(stokes_options), _P, C.POINTER(_P)]),
+    "stokes_octree_table": (C.c_size_t, [_P, C.c_int, C.c_int, _P, C.c_size_t]),
 }
 
 PROF_CLASSES = ["vmult_A_fp32", "vmult_A_fp64", "stokes_fp64", "bt_fp64", "mass_p", "transfer",
@@ -208,6 +217,68 @@ def stokes_setup_problem(prob, options=None, stream=None) -> Context:
     """stokes_setup from a sinker_inputs.SinkerProblem."""
     return stokes_setup(prob.n, prob.n_levels, prob.centres, prob.mu_min, prob.mu_max, prob.delta, prob.omega,
                         prob.beta, options=options, stream=stream)
+
+
+def stokes_octree_sinker_mesh(base_level, centres, max_levels, shell_radius=0.05, shell_half_width=0.02):
+    """Leaf keys (numpy uint64, sorted) of the refined and 2:1-balanced sinker octree."""
+    import numpy as np
+    lib = load()
+    cen = np.ascontiguousarray(centres, dtype=np.float64).reshape(-1, 3)
+    lv = np.ascontiguousarray(max_levels, dtype=np.int32)
+    n = C.c_int64(0)
+    _check(lib.stokes_octree_sinker_mesh(int(base_level), cen.shape[0], cen.ctypes.data, lv.ctypes.data,
+                                         float(shell_radius), float(shell_half_width), None, 0, C.byref(n)),
+           "stokes_octree_sinker_mesh")
+    keys = np.empty(n.value, dtype=np.uint64)
+    _check(lib.stokes_octree_sinker_mesh(int(base_level), cen.shape[0], cen.ctypes.data, lv.ctypes.data,
+                                         float(shell_radius), float(shell_half_width), keys.ctypes.data,
+                                         keys.size, C.byref(n)), "stokes_octree_sinker_mesh")
+    return keys
+
+
+def stokes_setup_octree(leaf_keys, coarsest_level, centres, mu_min, mu_max, delta=200.0, omega=0.1, beta=10.0,
+                        options=None, stream=None) -> Context:
+    """stokes_setup_octree for the given leaves with the sinker viscosity."""
+    import numpy as np
+    lib = load()
+    keys = np.ascontiguousarray(leaf_keys, dtype=np.uint64)
+    mesh = stokes_octree(int(coarsest_level), keys.size, keys.ctypes.data_as(C.POINTER(C.c_uint64)))
+    cen = np.ascontiguousarray(centres, dtype=np.float64).reshape(-1, 3)
+    mu = stokes_mu()
+    mu.kind = 0
+    mu.n_sinkers = cen.shape[0]
+    mu.centres = cen.ctypes.data_as(C.POINTER(C.c_double)) if cen.size else None
+    mu.mu_min, mu.mu_max, mu.delta, mu.omega, mu.beta = mu_min, mu_max, delta, omega, beta
+    bc = stokes_bc(0x3F)
+    h = C.c_void_p()
+    st = lib.stokes_setup_octree(C.byref(mesh), C.byref(mu), C.byref(bc), C.byref(options) if options else None,
+                                 _stream(stream), C.byref(h))
+    _check(st, "stokes_setup_octree")
+    return Context(h.value)
+
+
+def stokes_setup_octree_problem(prob, options=None, stream=None) -> Context:
+    """Mesh (stokes_octree_sinker_mesh) and set-up for a sinker_inputs.OctreeProblem."""
+    keys = stokes_octree_sinker_mesh(prob.base_level, prob.centres, prob.max_levels, prob.shell_radius,
+                                     prob.shell_half_width)
+    return stokes_setup_octree(keys, prob.coarsest_level, prob.centres, prob.mu_min, prob.mu_max, prob.delta,
+                               prob.omega, prob.beta, options=options, stream=stream)
+
+
+_TABLE_DTYPES = {0: "uint64", 1: "uint64", 2: "uint64", 3: "uint64", 4: "uint8", 5: "int32"}
+
+
+def stokes_octree_table(ctx, which, level=0):
+    """Host copy of an octree table (numpy array), or the count for which = 6, 7."""
+    import numpy as np
+    lib = load()
+    n = int(lib.stokes_octree_table(ctx.handle, which, level, None, 0))
+    if which not in _TABLE_DTYPES:
+        return n
+    out = np.empty(n, dtype=_TABLE_DTYPES[which])
+    if n:
+        lib.stokes_octree_table(ctx.handle, which, level, out.ctypes.data, n)
+    return out
 
 
 def stokes_vmult(ctx, level, block, prec, src, dst, stream=None):

@@ -14,9 +14,12 @@
 #include "../../include/stokes.h"
 #include "brick.cuh"
 #include "internal.cuh"
+#include "octree.cuh"
 #include "prof.cuh"
 
+#include <algorithm>
 #include <chrono>
+#include <type_traits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -137,6 +140,29 @@ template <typename T> T* slots(Level& L);
 template <> double* slots<double>(Level& L) { return L.slots64; }
 template <> float* slots<float>(Level& L) { return L.slots32; }
 
+// One level of the local-smoothing hierarchy of an octree mesh (index 0 = coarsest).
+struct OctLevel {
+    OctLevelDev g;
+    LevelVecs<double> v64;
+    LevelVecs<float> v32;
+    double lam_max = 0.0, lo = 0.0, hi = 0.0;
+    size_t n_copy = 0;                 // active nodes copied to / from this level
+    int32_t* copy_a = nullptr;         // their active indices
+    int32_t* copy_l = nullptr;         // their level indices
+};
+
+// Adaptive (octree) mesh: active space with hanging-node constraints and the level hierarchy.
+struct OctCtx {
+    OctHost host;
+    OctActiveDev act;
+    std::vector<OctLevel> lev;
+    double* leaf_mu = nullptr;
+};
+
+template <typename T> LevelVecs<T>& ovecs(OctLevel& L);
+template <> LevelVecs<double>& ovecs<double>(OctLevel& L) { return L.v64; }
+template <> LevelVecs<float>& ovecs<float>(OctLevel& L) { return L.v32; }
+
 }  // namespace
 
 struct stokes_ctx {
@@ -177,6 +203,7 @@ struct stokes_ctx {
     int cell_block = 128;                            // threads per block of the cell kernel (autotuned)
     float *tune_x = nullptr, *tune_r = nullptr, *tune_b = nullptr;   // autotuner work (FP32, finest level)
     double* tune_up = nullptr;                                        // autotuner solution vector
+    OctCtx* oct = nullptr;                           // set for octree meshes (stokes_setup_octree)
 };
 
 namespace {
@@ -351,8 +378,117 @@ stokes_status vcycle(stokes_ctx* c, const T* rhs, T* x, cudaStream_t s) {
     return STOKES_OK;
 }
 
+// ---------------------------------------------------------------- octree meshes
+// Local smoothing (Section 2.2.1 by citation): level li (0 = coarsest) holds all cells of its
+// refinement level; edge nodes are ordinary rows and columns of A_li but are never smoothed
+// (D^-1 = 0 there), boundary nodes are identity rows.
+
+size_t active_nu(const stokes_ctx* c) { return c->oct ? 3 * c->oct->act.nu_nodes : c->lev[c->L - 1].g.n_u; }
+size_t active_np(const stokes_ctx* c) { return c->oct ? c->oct->act.np : c->lev[c->L - 1].g.n_p; }
+
+// dst = A_li src (boundary rows: identity; boundary entries of src ignored).
+template <typename T>
+stokes_status oct_vmult_level(stokes_ctx* c, int li, const T* src, T* dst, cudaStream_t s) {
+    OctLevel& L = c->oct->lev[li];
+    CK(cudaMemsetAsync(dst, 0, 3 * L.g.nn * sizeof(T), s));
+    CK(launch_oct_level_cells<T>(L.g, ovecs<T>(L).mu, src, dst, s));
+    CK(launch_oct_copy_boundary<T>(L.g, src, dst, s));
+    return STOKES_OK;
+}
+
+template <typename T>
+stokes_status oct_smooth(stokes_ctx* c, int li, const T* b, T* x, bool zero_guess, cudaStream_t s) {
+    OctLevel& L = c->oct->lev[li];
+    LevelVecs<T>& v = ovecs<T>(L);
+    const double theta = 0.5 * (L.hi + L.lo), delta = 0.5 * (L.hi - L.lo), sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    const size_t n = 3 * L.g.nn;
+    auto step = [&](double c1, double c2) -> stokes_status {
+        CK(launch_oct_level_cells<T>(L.g, v.mu, x, v.acc, s));
+        CK(launch_consume<T>(2, n, v.acc, b, v.dinv, v.d, x, c1, c2, s));
+        return STOKES_OK;
+    };
+    if (zero_guess) {
+        CK(launch_cheb_update<T>(n, b, nullptr, v.dinv, v.d, x, 0.0, 1.0 / theta, false, s));
+    } else {
+        CKS(step(0.0, 1.0 / theta));
+    }
+    for (int it = 1; it < c->opt.cheb_degree; ++it) {
+        const double rho_new = 1.0 / (2.0 * sigma - rho);
+        CKS(step(rho_new * rho, 2.0 * rho_new / delta));
+        rho = rho_new;
+    }
+    return STOKES_OK;
+}
+
+template <typename T>
+stokes_status oct_vcycle_level(stokes_ctx* c, int li, cudaStream_t s) {
+    OctLevel& L = c->oct->lev[li];
+    LevelVecs<T>& v = ovecs<T>(L);
+    if (li == 0) {
+        CK(cudaMemsetAsync(v.x, 0, 3 * L.g.nn * sizeof(T), s));
+        CK(launch_coarse_solve<T>(c->nf, c->free_idx, c->Ainv, v.b, v.x, s));
+        return STOKES_OK;
+    }
+    OctLevel& C = c->oct->lev[li - 1];
+    CKS(oct_smooth<T>(c, li, v.b, v.x, true, s));
+    CK(launch_oct_level_cells<T>(L.g, v.mu, v.x, v.acc, s));
+    CK(launch_consume<T>(1, 3 * L.g.nn, v.acc, v.b, nullptr, nullptr, v.r, 0.0, 0.0, s));   // r = b - A x
+    CK(launch_oct_restrict_add<T>(L.g, C.g, v.r, ovecs<T>(C).b, s));
+    CKS(oct_vcycle_level<T>(c, li - 1, s));
+    CK(launch_oct_prolongate<T>(L.g, C.g, ovecs<T>(C).x, v.x, true, s));
+    CKS(oct_smooth<T>(c, li, v.b, v.x, false, s));
+    return STOKES_OK;
+}
+
+// x = V(rhs) on the active velocity space (FP64 vectors, V-cycle arithmetic T); Dirichlet
+// rows act as the identity.
+template <typename T>
+stokes_status oct_vcycle(stokes_ctx* c, const double* rhs, double* x, cudaStream_t s) {
+    OctCtx& o = *c->oct;
+    const size_t nu = o.act.nu_nodes;
+    for (OctLevel& L : o.lev) {
+        CK(cudaMemsetAsync(ovecs<T>(L).b, 0, 3 * L.g.nn * sizeof(T), s));
+        CK(launch_oct_copy_to_level<T>(L.n_copy, L.copy_a, L.copy_l, nu, L.g.nn, rhs, ovecs<T>(L).b, s));
+    }
+    CKS(oct_vcycle_level<T>(c, int(o.lev.size()) - 1, s));
+    for (OctLevel& L : o.lev)
+        CK(launch_oct_copy_from_level<T>(L.n_copy, L.copy_a, L.copy_l, nu, L.g.nn, ovecs<T>(L).x, x, s));
+    CK(launch_oct_identity_rows(o.act, rhs, x, s));
+    return STOKES_OK;
+}
+
+stokes_status oct_schur_inverse(stokes_ctx* c, const double* rp, double* zp, cudaStream_t s) {
+    const size_t np = c->oct->act.np;
+    const double lo = 1.0 / 8.0, hi = 27.0 / 8.0;
+    const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    CK(launch_cheb_update<double>(np, rp, nullptr, c->mp_dinv, c->sp_d, zp, 0.0, 1.0 / theta, false, s));
+    for (int it = 1; it < c->opt.schur_degree; ++it) {
+        CK(launch_oct_mass_p(c->oct->act, zp, c->sp_t, s));
+        const double rho_new = 1.0 / (2.0 * sigma - rho);
+        CK(launch_cheb_update<double>(np, rp, c->sp_t, c->mp_dinv, c->sp_d, zp, rho_new * rho, 2.0 * rho_new / delta,
+                                      true, s));
+        rho = rho_new;
+    }
+    return STOKES_OK;
+}
+
+stokes_status oct_precondition(stokes_ctx* c, int prec, const double* r, double* z, cudaStream_t s) {
+    OctCtx& o = *c->oct;
+    const size_t nu = 3 * o.act.nu_nodes, np = o.act.np;
+    double* zp = z + nu;
+    CKS(oct_schur_inverse(c, r + nu, zp, s));
+    CK(launch_axpby(np, -1.0, zp, 0.0, zp, s));                               // z_p = -S^-1 r_p
+    CK(launch_oct_active(o.act, nullptr, zp, c->tu, nullptr, false, true, false, s));
+    CK(launch_axpby(nu, 1.0, r, -1.0, c->tu, s));                            // t = r_u - B^T z_p
+    if (prec == STOKES_FP64) return oct_vcycle<double>(c, c->tu, z, s);
+    return oct_vcycle<float>(c, c->tu, z, s);
+}
+
 // z_p = S_hat^-1 r_p: Jacobi-Chebyshev on M_p, interval [1/8, 27/8], zero guess.
 stokes_status schur_inverse(stokes_ctx* c, const double* rp, double* zp, cudaStream_t s) {
+    if (c->oct) return oct_schur_inverse(c, rp, zp, s);
     const LevelGeom& g = c->lev[c->L - 1].g;
     const double lo = 1.0 / 8.0, hi = 27.0 / 8.0;
     const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
@@ -370,6 +506,11 @@ stokes_status schur_inverse(stokes_ctx* c, const double* rp, double* zp, cudaStr
 }
 
 stokes_status apply_stokes(stokes_ctx* c, const double* src, double* dst, cudaStream_t s) {
+    if (c->oct) {
+        const size_t nu = 3 * c->oct->act.nu_nodes;
+        CK(launch_oct_active(c->oct->act, src, src + nu, dst, dst + nu, true, true, true, s));
+        return STOKES_OK;
+    }
     Level& F = c->lev[c->L - 1];
     CK(launch_stokes_blocks(F.g, F.v64.mu, src, src + F.g.n_u, dst, dst + F.g.n_u, true, true, true, c->opt.outer_arith == 1, s));
     return STOKES_OK;
@@ -377,6 +518,7 @@ stokes_status apply_stokes(stokes_ctx* c, const double* src, double* dst, cudaSt
 
 // z = P^-1 r (eq. stokes_precond).
 stokes_status precondition(stokes_ctx* c, int prec, const double* r, double* z, cudaStream_t s) {
+    if (c->oct) return oct_precondition(c, prec, r, z, s);
     Level& F = c->lev[c->L - 1];
     const size_t nu = F.g.n_u, np = F.g.n_p;
     double* zp = z + nu;
@@ -398,8 +540,7 @@ stokes_status precondition(stokes_ctx* c, int prec, const double* r, double* z, 
 stokes_status ensure_krylov(stokes_ctx* c) {
     const int m = c->opt.restart;
     if (c->V && c->krylov_restart == m) return STOKES_OK;
-    const LevelGeom& g = c->lev[c->L - 1].g;
-    c->N = g.n_u + g.n_p;
+    c->N = active_nu(c) + active_np(c);
     c->ldv = c->N + (c->N & 1);   // even row stride: 16-byte aligned entry pairs (krylov.cu)
     CKS(dalloc(c, &c->V, size_t(m + 1) * c->ldv));
     CKS(dalloc(c, &c->Z, size_t(m) * c->N));
@@ -411,10 +552,10 @@ stokes_status ensure_krylov(stokes_ctx* c) {
 }
 
 stokes_status remove_pressure_mean(stokes_ctx* c, double* up, cudaStream_t s) {
-    const LevelGeom& g = c->lev[c->L - 1].g;
+    const size_t nu = active_nu(c), np = active_np(c);
     double wp = 0.0;
-    CKS(dot(c, g.n_p, c->p_weights, up + g.n_u, s, &wp));
-    CK(launch_add_scalar(g.n_p, -wp / c->p_wsum, up + g.n_u, s));
+    CKS(dot(c, np, c->p_weights, up + nu, s, &wp));
+    CK(launch_add_scalar(np, -wp / c->p_wsum, up + nu, s));
     return STOKES_OK;
 }
 
@@ -641,6 +782,45 @@ stokes_status fgmres(stokes_ctx* c, int prec, const double* b, double* x, double
     return STOKES_OK;
 }
 
+stokes_status validate_options(const stokes_options& o) {
+    if (o.cheb_degree < 1 || o.smoothing_range <= 1.0 || o.eig_safety <= 0.0 || o.lanczos_steps < 1 ||
+        o.schur_degree < 1 || o.restart < 1 || o.restart > 500 || (o.outer_arith != 0 && o.outer_arith != 1) ||
+        (o.vmult_kernel != 0 && o.vmult_kernel != 1) || (o.graphs != 0 && o.graphs != 1))
+        return fail(STOKES_EINVAL, "bad options");
+    return STOKES_OK;
+}
+
+// Inverse of a dense symmetric positive definite matrix (row-major nf x nf): Cholesky
+// A = R^T R with R upper triangular, then R^T z = e_j and R x = z for every column j.
+stokes_status spd_inverse(const std::vector<double>& A, int nf, std::vector<double>& Ainv) {
+    std::vector<double> R = A;
+    for (int i = 0; i < nf; ++i) {
+        for (int k = 0; k < i; ++k) {
+            const double rki = R[size_t(k) * nf + i];
+            for (int jj = i; jj < nf; ++jj) R[size_t(i) * nf + jj] -= rki * R[size_t(k) * nf + jj];
+        }
+        const double d = R[size_t(i) * nf + i];
+        if (!(d > 0.0)) return fail(STOKES_EINVAL, "coarse matrix is not positive definite");
+        const double sd = std::sqrt(d);
+        for (int jj = i; jj < nf; ++jj) R[size_t(i) * nf + jj] /= sd;
+    }
+    Ainv.assign(size_t(nf) * nf, 0.0);
+    std::vector<double> zz(nf);
+    for (int j = 0; j < nf; ++j) {
+        for (int i = 0; i < nf; ++i) {
+            double t = (i == j) ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) t -= R[size_t(k) * nf + i] * zz[k];
+            zz[i] = t / R[size_t(i) * nf + i];
+        }
+        for (int i = nf - 1; i >= 0; --i) {
+            double t = zz[i];
+            for (int k = i + 1; k < nf; ++k) t -= R[size_t(i) * nf + k] * Ainv[size_t(k) * nf + j];
+            Ainv[size_t(i) * nf + j] = t / R[size_t(i) * nf + i];
+        }
+    }
+    return STOKES_OK;
+}
+
 stokes_status check_level(const stokes_ctx* c, int& level) {
     if (!c) return fail(STOKES_EINVAL, "null context");
     if (level == -1) level = c->L - 1;
@@ -652,10 +832,7 @@ stokes_status setup_impl(const stokes_mesh* mesh, const stokes_mu* mu, const sto
                          const stokes_options* opt, cudaStream_t s, stokes_ctx* c) {
     if (opt) c->opt = *opt; else stokes_default_options(&c->opt);
     const stokes_options& o = c->opt;
-    if (o.cheb_degree < 1 || o.smoothing_range <= 1.0 || o.eig_safety <= 0.0 || o.lanczos_steps < 1 ||
-        o.schur_degree < 1 || o.restart < 1 || o.restart > 500 || (o.outer_arith != 0 && o.outer_arith != 1) ||
-        (o.vmult_kernel != 0 && o.vmult_kernel != 1) || (o.graphs != 0 && o.graphs != 1))
-        return fail(STOKES_EINVAL, "bad options");
+    CKS(validate_options(o));
     CK(brick_configure());
     CK(gs_configure());
     c->n = mesh->n;
@@ -791,31 +968,214 @@ stokes_status setup_impl(const stokes_mesh* mesh, const stokes_mu* mu, const sto
                 CK(cudaStreamSynchronize(s));
                 for (int i = 0; i < nf; ++i) A[size_t(i) * nf + j] = col[idx[i]];
             }
-            // Cholesky A = R^T R (upper R in place), then the inverse column by column.
-            std::vector<double> R = A;
-            for (int i = 0; i < nf; ++i) {
-                for (int k = 0; k < i; ++k) {
-                    const double rki = R[size_t(k) * nf + i];
-                    for (int jj = i; jj < nf; ++jj) R[size_t(i) * nf + jj] -= rki * R[size_t(k) * nf + jj];
-                }
-                const double d = R[size_t(i) * nf + i];
-                if (!(d > 0.0)) return fail(STOKES_EINVAL, "coarse matrix is not positive definite");
-                const double sd = std::sqrt(d);
-                for (int jj = i; jj < nf; ++jj) R[size_t(i) * nf + jj] /= sd;
-            }
-            std::vector<double> Ainv(size_t(nf) * nf), zz(nf);
+            std::vector<double> Ainv;
+            CKS(spd_inverse(A, nf, Ainv));
+            CKS(dalloc(c, &c->Ainv, size_t(nf) * nf));
+            CK(cudaMemcpyAsync(c->Ainv, Ainv.data(), sizeof(double) * nf * nf, cudaMemcpyHostToDevice, s));
+        }
+    }
+    CK(cudaStreamSynchronize(s));
+    return STOKES_OK;
+}
+
+template <typename T>
+stokes_status upload(stokes_ctx* c, T** dev, const std::vector<T>& host, cudaStream_t s) {
+    CKS(dalloc(c, dev, host.size()));
+    if (!host.empty()) CK(cudaMemcpyAsync(*dev, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return STOKES_OK;
+}
+
+// Octree setup: host tables (octree_host.cpp), device copies, level diagonals, Lanczos
+// estimates per level (start vector splitmix64(1907000 + li) on the smoothed nodes), the dense
+// inverse of the coarsest (uniform) level, right-hand side and pressure mass diagonal.
+stokes_status oct_setup_impl(const stokes_octree* mesh, const stokes_mu* mu, const stokes_options* opt,
+                             cudaStream_t s, stokes_ctx* c) {
+    if (opt) c->opt = *opt; else stokes_default_options(&c->opt);
+    CKS(validate_options(c->opt));
+    const stokes_options& o = c->opt;
+    CK(brick_configure());
+    CK(gs_configure());
+    if (mu->kind != 0) return fail(STOKES_EINVAL, "octree meshes take the sinker viscosity (kind 0)");
+    if (mu->n_sinkers < 0 || (mu->n_sinkers > 0 && !mu->centres)) return fail(STOKES_EINVAL, "bad sinker list");
+    c->oct = new (std::nothrow) OctCtx();
+    if (!c->oct) return fail(STOKES_ENOMEM, "host allocation failed");
+    OctCtx& oc = *c->oct;
+    std::vector<uint64_t> leaves(mesh->leaf_keys, mesh->leaf_keys + mesh->n_leaves);
+    OctSinkers sk;
+    sk.n = mu->n_sinkers;
+    sk.centres = mu->centres;
+    sk.mu_min = mu->mu_min;
+    sk.mu_max = mu->mu_max;
+    sk.delta = mu->delta;
+    sk.omega = mu->omega;
+    sk.beta = mu->beta;
+    const std::string err = oct_build(leaves, mesh->coarsest_level, sk, oc.host);
+    if (!err.empty()) return fail(STOKES_EMESH, "octree: " + err);
+    const OctHost& H = oc.host;
+    // ---- active space
+    OctActiveDev& a = oc.act;
+    a.n_leaves = int(H.leaves.size());
+    a.nu_nodes = H.unodes.size();
+    a.np = H.pverts.size();
+    {
+        int32_t *lu, *lp, *un, *pn;
+        double *uw, *pw, *lm;
+        uint8_t *ub, *lv;
+        std::vector<uint8_t> lev8(H.leaves.size());
+        for (size_t n = 0; n < H.leaves.size(); ++n) lev8[n] = uint8_t(oct_l(H.leaves[n]));
+        CKS(upload(c, &lu, H.leaf_u, s));
+        CKS(upload(c, &lp, H.leaf_p, s));
+        CKS(upload(c, &un, H.ucon_node, s));
+        CKS(upload(c, &uw, H.ucon_w, s));
+        CKS(upload(c, &pn, H.pcon_node, s));
+        CKS(upload(c, &pw, H.pcon_w, s));
+        CKS(upload(c, &ub, H.ubnd, s));
+        CKS(upload(c, &lm, H.leaf_mu, s));
+        CKS(upload(c, &lv, lev8, s));
+        CK(cudaStreamSynchronize(s));   // lev8 (pageable, local) consumed
+        a.leaf_u = lu; a.leaf_p = lp; a.ucon_node = un; a.ucon_w = uw; a.pcon_node = pn; a.pcon_w = pw;
+        a.ubnd = ub; a.mu = lm; a.level = lv;
+        oc.leaf_mu = lm;
+    }
+    const size_t nu = 3 * a.nu_nodes, np = a.np;
+    CKS(upload(c, &c->F, H.F, s));
+    {
+        std::vector<double> dinv(np);
+        double wsum = 0.0;
+        for (size_t n = 0; n < np; ++n) {
+            dinv[n] = 1.0 / H.mp_diag[n];
+            wsum += H.p_weights[n];
+        }
+        CKS(upload(c, &c->mp_dinv, dinv, s));
+        CK(cudaStreamSynchronize(s));
+        CKS(upload(c, &c->p_weights, H.p_weights, s));
+        c->p_wsum = wsum;
+    }
+    CKS(dalloc(c, &c->sp_d, np));
+    CKS(dalloc(c, &c->sp_t, np));
+    CKS(dalloc(c, &c->tu, nu));
+    CKS(dalloc(c, &c->partials, size_t(std::max(multidot_blocks(), gs_partials_blocks())) * (o.restart + 8)));
+    CKS(dalloc(c, &c->dots, size_t(o.restart + 8)));
+    CK(cudaMallocHost(&c->dots_host, size_t(2 * (o.restart + 8)) * sizeof(double)));
+    CKS(dalloc(c, &c->ref_diag, 81));
+    CK(launch_ref_diag(c->ref_diag, s));
+    // ---- levels
+    const int NL = int(H.levels.size());
+    oc.lev.resize(NL);
+    std::vector<std::vector<int32_t>> ca(NL), cl(NL);
+    for (size_t n = 0; n < H.unodes.size(); ++n) {
+        if (H.ubnd[n]) continue;
+        const int li = H.copy_level[n] - H.coarsest;
+        ca[li].push_back(int32_t(n));
+        cl[li].push_back(H.copy_index[n]);
+    }
+    for (int li = 0; li < NL; ++li) {
+        const OctLevelHost& LH = H.levels[li];
+        OctLevel& L = oc.lev[li];
+        int32_t* cn;
+        uint8_t* fl;
+        CKS(upload(c, &cn, LH.cell_nodes, s));
+        CKS(upload(c, &fl, LH.flags, s));
+        L.g.n_cells = int(LH.cells.size());
+        L.g.nn = LH.nodes.size();
+        L.g.h = std::ldexp(1.0, -LH.l);
+        L.g.cell_nodes = cn;
+        L.g.flags = fl;
+        if (li > 0) {
+            uint32_t* pa;
+            uint16_t* po;
+            CKS(upload(c, &pa, LH.parent, s));
+            CKS(upload(c, &po, LH.pos, s));
+            L.g.parent = pa;
+            L.g.pos = po;
+        }
+        const size_t n3 = 3 * L.g.nn;
+        for (auto* q : {&L.v64.b, &L.v64.x, &L.v64.r, &L.v64.d, &L.v64.t, &L.v64.dinv, &L.v64.acc}) CKS(dalloc(c, q, n3));
+        for (auto* q : {&L.v32.b, &L.v32.x, &L.v32.r, &L.v32.d, &L.v32.t, &L.v32.dinv, &L.v32.acc}) CKS(dalloc(c, q, n3));
+        CK(cudaMemsetAsync(L.v64.acc, 0, n3 * sizeof(double), s));
+        CK(cudaMemsetAsync(L.v32.acc, 0, n3 * sizeof(float), s));
+        CK(cudaMemsetAsync(L.v64.d, 0, n3 * sizeof(double), s));
+        CK(cudaMemsetAsync(L.v32.d, 0, n3 * sizeof(float), s));
+        CKS(upload(c, &L.v64.mu, LH.mu, s));
+        CKS(dalloc(c, &L.v32.mu, LH.mu.size()));
+        CK(launch_cast_d2f(LH.mu.size(), L.v64.mu, L.v32.mu, s));
+        CK(launch_oct_inv_diag(L.g, L.v64.mu, c->ref_diag, L.v64.t, L.v64.dinv, s));
+        CK(launch_cast_d2f(n3, L.v64.dinv, L.v32.dinv, s));
+        L.n_copy = ca[li].size();
+        CKS(upload(c, &L.copy_a, ca[li], s));
+        CKS(upload(c, &L.copy_l, cl[li], s));
+    }
+    CK(cudaStreamSynchronize(s));   // the local copy lists are consumed
+    // ---- Lanczos estimates of lambda_max(D^-1 A) on the smoothed nodes, levels li >= 1
+    for (int li = 1; li < NL; ++li) {
+        OctLevel& L = oc.lev[li];
+        const size_t n = 3 * L.g.nn;
+        std::vector<double> mask(n);
+        const OctLevelHost& LH = H.levels[li];
+        for (int cc = 0; cc < 3; ++cc)
+            for (size_t t = 0; t < L.g.nn; ++t) mask[cc * L.g.nn + t] = LH.flags[t] == 0 ? 1.0 : 0.0;
+        double *sq = L.v64.r, *v = L.v64.x, *vp = L.v64.d, *w = L.v64.t, *tmp = L.v64.b;
+        CK(cudaMemcpyAsync(tmp, mask.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+        CK(launch_splitmix_vector(n, uint64_t(1907000 + li), tmp, v, s));
+        CK(cudaStreamSynchronize(s));   // mask (pageable) consumed
+        CK(launch_sqrt_vec(n, L.v64.dinv, sq, s));
+        double vv = 0.0;
+        CKS(dot(c, n, v, v, s, &vv));
+        CK(launch_axpby(n, 1.0 / std::sqrt(vv), v, 0.0, v, s));
+        CK(cudaMemsetAsync(vp, 0, n * sizeof(double), s));
+        double beta_prev = 0.0;
+        std::vector<double> al, be;
+        for (int it = 0; it < o.lanczos_steps; ++it) {
+            CK(launch_mul(n, sq, v, tmp, s));
+            CKS(oct_vmult_level<double>(c, li, tmp, w, s));
+            CK(launch_mul(n, sq, w, w, s));
+            double alpha = 0.0;
+            CKS(dot(c, n, w, v, s, &alpha));
+            CK(launch_axpby(n, -alpha, v, 1.0, w, s));
+            CK(launch_axpby(n, -beta_prev, vp, 1.0, w, s));
+            double b2 = 0.0;
+            CKS(dot(c, n, w, w, s, &b2));
+            const double beta = std::sqrt(b2);
+            al.push_back(alpha);
+            if (beta <= 1e-12 * std::fabs(alpha)) break;
+            be.push_back(beta);
+            std::swap(vp, v);
+            CK(launch_axpby(n, 1.0 / beta, w, 0.0, v, s));
+            beta_prev = beta;
+        }
+        L.lam_max = tridiag_max_eig(al, be);
+        L.hi = o.eig_safety * L.lam_max;
+        L.lo = L.hi / o.smoothing_range;
+        CK(cudaMemsetAsync(L.v64.d, 0, n * sizeof(double), s));
+    }
+    // ---- dense inverse of the coarsest level on its free nodes (FP64)
+    {
+        OctLevel& L0 = oc.lev[0];
+        const OctLevelHost& LH = H.levels[0];
+        const size_t nn = L0.g.nn, n3 = 3 * nn;
+        std::vector<int> idx;
+        for (int cc = 0; cc < 3; ++cc)
+            for (size_t t = 0; t < nn; ++t)
+                if (LH.flags[t] == 0) idx.push_back(int(cc * nn + t));
+        const int nf = int(idx.size());
+        if (nf > 4000) return fail(STOKES_EMESH, "coarsest level too large for the dense solve");
+        c->nf = nf;
+        if (nf > 0) {
+            CKS(dalloc(c, &c->free_idx, size_t(nf)));
+            CK(cudaMemcpyAsync(c->free_idx, idx.data(), sizeof(int) * nf, cudaMemcpyHostToDevice, s));
+            std::vector<double> A(size_t(nf) * nf), col(n3);
+            double *e = L0.v64.b, *Ae = L0.v64.t;
+            const double one = 1.0;
             for (int j = 0; j < nf; ++j) {
-                for (int i = 0; i < nf; ++i) {   // R^T z = e_j
-                    double t = (i == j) ? 1.0 : 0.0;
-                    for (int k = 0; k < i; ++k) t -= R[size_t(k) * nf + i] * zz[k];
-                    zz[i] = t / R[size_t(i) * nf + i];
-                }
-                for (int i = nf - 1; i >= 0; --i) {   // R x = z
-                    double t = zz[i];
-                    for (int k = i + 1; k < nf; ++k) t -= R[size_t(i) * nf + k] * Ainv[size_t(k) * nf + j];
-                    Ainv[size_t(i) * nf + j] = t / R[size_t(i) * nf + i];
-                }
+                CK(cudaMemsetAsync(e, 0, n3 * sizeof(double), s));
+                CK(cudaMemcpyAsync(e + idx[j], &one, sizeof(double), cudaMemcpyHostToDevice, s));
+                CKS(oct_vmult_level<double>(c, 0, e, Ae, s));
+                CK(cudaMemcpyAsync(col.data(), Ae, n3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                for (int i = 0; i < nf; ++i) A[size_t(i) * nf + j] = col[idx[i]];
             }
+            std::vector<double> Ainv;
+            CKS(spd_inverse(A, nf, Ainv));
             CKS(dalloc(c, &c->Ainv, size_t(nf) * nf));
             CK(cudaMemcpyAsync(c->Ainv, Ainv.data(), sizeof(double) * nf * nf, cudaMemcpyHostToDevice, s));
         }
@@ -912,11 +1272,110 @@ void stokes_destroy(stokes_ctx* c) {
     if (c->gstream) cudaStreamDestroy(c->gstream);
     for (void* p : c->allocs) cudaFree(p);
     if (c->dots_host) cudaFreeHost(c->dots_host);
+    delete c->oct;
     delete c;
+}
+
+stokes_status stokes_octree_sinker_mesh(int base_level, int n_sinkers, const double* centres, const int* max_levels,
+                                        double shell_radius, double shell_half_width, uint64_t* keys, int64_t capacity,
+                                        int64_t* n_leaves) {
+    g_last_error.clear();
+    if (!n_leaves || base_level < 0 || base_level > 15 || n_sinkers < 0 || (n_sinkers > 0 && (!centres || !max_levels)))
+        return fail(STOKES_EINVAL, "bad argument");
+    for (int i = 0; i < n_sinkers; ++i)
+        if (max_levels[i] > 15) return fail(STOKES_EINVAL, "maximum level above 15");
+    try {
+        const std::vector<uint64_t> leaves =
+            oct_balance(oct_refine_shells(base_level, n_sinkers, centres, max_levels, shell_radius, shell_half_width));
+        *n_leaves = int64_t(leaves.size());
+        if (capacity < int64_t(leaves.size())) {
+            if (keys || capacity != 0) return fail(STOKES_EINVAL, "capacity below the number of leaves");
+            return STOKES_OK;
+        }
+        if (!keys) return fail(STOKES_EINVAL, "null key buffer");
+        std::copy(leaves.begin(), leaves.end(), keys);
+    } catch (const std::bad_alloc&) {
+        return fail(STOKES_ENOMEM, "host allocation failed");
+    }
+    return STOKES_OK;
+}
+
+stokes_status stokes_setup_octree(const stokes_octree* mesh, const stokes_mu* mu, const stokes_bc* bc,
+                                  const stokes_options* opt, void* stream, stokes_ctx** out) {
+    g_last_error.clear();
+    if (!mesh || !mu || !bc || !out || (mesh->n_leaves > 0 && !mesh->leaf_keys))
+        return fail(STOKES_EINVAL, "null argument");
+    *out = nullptr;
+    if (bc->noslip_faces != 0x3Fu) return fail(STOKES_EMESH, "all six walls must be no-slip (0x3F)");
+    if (mesh->n_leaves < 1) return fail(STOKES_EMESH, "no leaves");
+    stokes_ctx* c = new (std::nothrow) stokes_ctx();
+    if (!c) return fail(STOKES_ENOMEM, "host allocation failed");
+    stokes_status st;
+    try {
+        st = oct_setup_impl(mesh, mu, opt, static_cast<cudaStream_t>(stream), c);
+    } catch (const std::bad_alloc&) {
+        st = fail(STOKES_ENOMEM, "host allocation failed");
+    }
+    if (st != STOKES_OK) {
+        const std::string msg = g_last_error;
+        stokes_destroy(c);
+        g_last_error = msg;
+        return st;
+    }
+    *out = c;
+    return STOKES_OK;
+}
+
+size_t stokes_octree_table(const stokes_ctx* c, int which, int level, void* out, size_t capacity) {
+    if (!c || !c->oct) return 0;
+    const OctHost& H = c->oct->host;
+    auto put = [&](const auto& v) -> size_t {
+        using E = typename std::decay<decltype(v)>::type::value_type;
+        if (out) std::memcpy(out, v.data(), std::min(capacity, v.size()) * sizeof(E));
+        return v.size();
+    };
+    const bool lv = level >= 0 && level < int(H.levels.size());
+    switch (which) {
+        case 0: return put(H.leaves);
+        case 1: return put(H.unodes);
+        case 2: return put(H.pverts);
+        case 3: return lv ? put(H.levels[level].nodes) : 0;
+        case 4: return lv ? put(H.levels[level].flags) : 0;
+        case 5: {
+            std::vector<int32_t> li(H.copy_level.size());
+            for (size_t n = 0; n < li.size(); ++n) li[n] = H.copy_level[n] - H.coarsest;
+            return put(li);
+        }
+        case 6: return H.ucon_node.size() / kOctUCon;
+        case 7: return H.pcon_node.size() / kOctPCon;
+    }
+    return 0;
 }
 
 size_t stokes_size(const stokes_ctx* c, int level, int what) {
     if (!c) return 0;
+    if (c->oct) {
+        const OctCtx& o = *c->oct;
+        const int NL = int(o.lev.size());
+        if (what == 4) return size_t(NL);
+        if (level == -1) {
+            switch (what) {
+                case 0: return 3 * o.act.nu_nodes;
+                case 1: return o.act.np;
+                case 2: return size_t(o.act.n_leaves);
+                case 3: return size_t(o.host.lmax);
+            }
+            return 0;
+        }
+        if (level < 0 || level >= NL) return 0;
+        switch (what) {
+            case 0: return 3 * o.lev[level].g.nn;
+            case 1: return 0;
+            case 2: return size_t(o.lev[level].g.n_cells);
+            case 3: return size_t(o.host.levels[level].l);
+        }
+        return 0;
+    }
     if (level == -1) level = c->L - 1;
     if (level < 0 || level >= c->L) return 0;
     const LevelGeom& g = c->lev[level].g;
@@ -930,8 +1389,37 @@ size_t stokes_size(const stokes_ctx* c, int level, int what) {
     return 0;
 }
 
+static stokes_status oct_vmult(stokes_ctx* c, int level, int block, int prec, const void* src, void* dst, cudaStream_t s) {
+    OctCtx& o = *c->oct;
+    if (level >= 0) {
+        if (level >= int(o.lev.size())) return fail(STOKES_EINVAL, "level out of range");
+        if (block != STOKES_BLOCK_A) return fail(STOKES_EINVAL, "multigrid levels have block A only");
+        if (prec == STOKES_FP32)
+            return oct_vmult_level<float>(c, level, static_cast<const float*>(src), static_cast<float*>(dst), s);
+        if (prec == STOKES_FP64)
+            return oct_vmult_level<double>(c, level, static_cast<const double*>(src), static_cast<double*>(dst), s);
+        return fail(STOKES_EINVAL, "bad precision");
+    }
+    if (level != -1) return fail(STOKES_EINVAL, "level out of range");
+    if (prec != STOKES_FP64) return fail(STOKES_EINVAL, "the active-space blocks are FP64 only");
+    const double* sd = static_cast<const double*>(src);
+    double* dd = static_cast<double*>(dst);
+    switch (block) {
+        case STOKES_BLOCK_A: CK(launch_oct_active(o.act, sd, nullptr, dd, nullptr, true, false, false, s)); return STOKES_OK;
+        case STOKES_BLOCK_B: CK(launch_oct_active(o.act, sd, nullptr, nullptr, dd, false, false, true, s)); return STOKES_OK;
+        case STOKES_BLOCK_BT: CK(launch_oct_active(o.act, nullptr, sd, dd, nullptr, false, true, false, s)); return STOKES_OK;
+        case STOKES_BLOCK_MP: CK(launch_oct_mass_p(o.act, sd, dd, s)); return STOKES_OK;
+        case STOKES_BLOCK_STOKES: return apply_stokes(c, sd, dd, s);
+    }
+    return fail(STOKES_EINVAL, "bad block");
+}
+
 stokes_status stokes_vmult(stokes_ctx* c, int level, int block, int prec, const void* src, void* dst,
                            void* stream) {
+    if (c && c->oct) {
+        if (!src || !dst) return fail(STOKES_EINVAL, "null vector");
+        return oct_vmult(c, level, block, prec, src, dst, static_cast<cudaStream_t>(stream));
+    }
     CKS(check_level(c, level));
     if (!src || !dst) return fail(STOKES_EINVAL, "null vector");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -969,6 +1457,11 @@ stokes_status stokes_vmult(stokes_ctx* c, int level, int block, int prec, const 
 stokes_status gmg_vcycle(stokes_ctx* c, int prec, const void* rhs, void* x, void* stream) {
     if (!c || !rhs || !x) return fail(STOKES_EINVAL, "null argument");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (c->oct) {
+        if (prec == STOKES_FP32) return oct_vcycle<float>(c, static_cast<const double*>(rhs), static_cast<double*>(x), s);
+        if (prec == STOKES_FP64) return oct_vcycle<double>(c, static_cast<const double*>(rhs), static_cast<double*>(x), s);
+        return fail(STOKES_EINVAL, "bad precision");
+    }
     if (prec == STOKES_FP32) return vcycle<float>(c, static_cast<const float*>(rhs), static_cast<float*>(x), s);
     if (prec == STOKES_FP64) return vcycle<double>(c, static_cast<const double*>(rhs), static_cast<double*>(x), s);
     return fail(STOKES_EINVAL, "bad precision");
@@ -982,11 +1475,11 @@ stokes_status stokes_solve(stokes_ctx* c, int vcycle_prec, const double* rhs, do
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const auto t0 = std::chrono::steady_clock::now();
     CKS(ensure_krylov(c));
-    const LevelGeom& g = c->lev[c->L - 1].g;
+    const size_t nu = active_nu(c), np = active_np(c);
     const double* b = rhs;
     if (!b) {
-        CK(cudaMemcpyAsync(c->bvec, c->F, g.n_u * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        CK(cudaMemsetAsync(c->bvec + g.n_u, 0, g.n_p * sizeof(double), s));
+        CK(cudaMemcpyAsync(c->bvec, c->F, nu * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemsetAsync(c->bvec + nu, 0, np * sizeof(double), s));
         b = c->bvec;
     }
     stokes_status st = fgmres(c, vcycle_prec, b, up, rtol, max_it, info, s);
@@ -1010,6 +1503,7 @@ static stokes_status drop_graphs(stokes_ctx* c) {
 }
 
 stokes_status stokes_autotune(stokes_ctx* c, int what, void* stream, int* block_out, int* degree_out) {
+    if (c && c->oct) return fail(STOKES_EMESH, "not available for octree meshes");
     if (!c) return fail(STOKES_EINVAL, "null context");
     if (what < 0 || what > 3) return fail(STOKES_EINVAL, "what must be a combination of 1 and 2");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1086,6 +1580,8 @@ stokes_status stokes_batch_solve(int n_problems, stokes_ctx* const* ctxs, int vc
                                  const double* const* rhs_devs, double* const* up_devs, double rtol, int max_it,
                                  stokes_solve_info* infos, void* const* streams) {
     if (n_problems < 1 || !ctxs || !up_devs) return fail(STOKES_EINVAL, "null argument or no problems");
+    for (int i = 0; i < n_problems; ++i)
+        if (ctxs[i] && ctxs[i]->oct) return fail(STOKES_EMESH, "batched solves take uniform meshes");
     if (vcycle_prec != STOKES_FP32 && vcycle_prec != STOKES_FP64) return fail(STOKES_EINVAL, "bad precision");
     if (!(rtol > 0.0) || max_it < 1) return fail(STOKES_EINVAL, "bad rtol or max_it");
     for (int i = 0; i < n_problems; ++i) {
@@ -1136,8 +1632,7 @@ stokes_status stokes_solve_host(stokes_ctx* c, int vcycle_prec, const double* rh
                                 double rtol, int max_it, stokes_solve_info* info, void* stream) {
     if (!c || !up_host) return fail(STOKES_EINVAL, "null argument");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const LevelGeom& g = c->lev[c->L - 1].g;
-    const size_t N = g.n_u + g.n_p;
+    const size_t N = active_nu(c) + active_np(c);
     const auto t0 = std::chrono::steady_clock::now();
     if (!c->h_up_dev) {
         CKS(dalloc(c, &c->h_up_dev, N));
@@ -1158,6 +1653,19 @@ stokes_status stokes_solve_host(stokes_ctx* c, int vcycle_prec, const double* rh
 }
 
 stokes_status stokes_get_viscosity(stokes_ctx* c, int level, double* mu_dev, void* stream) {
+    if (c && c->oct) {
+        if (!mu_dev) return fail(STOKES_EINVAL, "null pointer");
+        OctCtx& o = *c->oct;
+        const double* src = level == -1 ? o.leaf_mu : nullptr;
+        size_t n = level == -1 ? size_t(o.act.n_leaves) : 0;
+        if (level >= 0 && level < int(o.lev.size())) {
+            src = o.lev[level].v64.mu;
+            n = size_t(o.lev[level].g.n_cells);
+        }
+        if (!src) return fail(STOKES_EINVAL, "level out of range");
+        CK(cudaMemcpyAsync(mu_dev, src, n * sizeof(double), cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)));
+        return STOKES_OK;
+    }
     CKS(check_level(c, level));
     if (!mu_dev) return fail(STOKES_EINVAL, "null pointer");
     Level& Lv = c->lev[level];
@@ -1167,6 +1675,14 @@ stokes_status stokes_get_viscosity(stokes_ctx* c, int level, double* mu_dev, voi
 }
 
 stokes_status stokes_get_inv_diagonal(stokes_ctx* c, int level, double* dinv_dev, void* stream) {
+    if (c && c->oct) {
+        if (!dinv_dev) return fail(STOKES_EINVAL, "null pointer");
+        if (level < 0 || level >= int(c->oct->lev.size())) return fail(STOKES_EINVAL, "level out of range");
+        OctLevel& L = c->oct->lev[level];
+        CK(cudaMemcpyAsync(dinv_dev, L.v64.dinv, 3 * L.g.nn * sizeof(double), cudaMemcpyDeviceToDevice,
+                           static_cast<cudaStream_t>(stream)));
+        return STOKES_OK;
+    }
     CKS(check_level(c, level));
     if (!dinv_dev) return fail(STOKES_EINVAL, "null pointer");
     Level& Lv = c->lev[level];
@@ -1176,6 +1692,12 @@ stokes_status stokes_get_inv_diagonal(stokes_ctx* c, int level, double* dinv_dev
 }
 
 stokes_status stokes_get_lambda_max(stokes_ctx* c, int level, double* lam_host) {
+    if (c && c->oct) {
+        if (!lam_host) return fail(STOKES_EINVAL, "null pointer");
+        if (level < 0 || level >= int(c->oct->lev.size())) return fail(STOKES_EINVAL, "level out of range");
+        *lam_host = c->oct->lev[level].lam_max;
+        return STOKES_OK;
+    }
     CKS(check_level(c, level));
     if (!lam_host) return fail(STOKES_EINVAL, "null pointer");
     *lam_host = c->lev[level].lam_max;
@@ -1184,14 +1706,14 @@ stokes_status stokes_get_lambda_max(stokes_ctx* c, int level, double* lam_host) 
 
 stokes_status stokes_get_rhs(stokes_ctx* c, double* F_dev, void* stream) {
     if (!c || !F_dev) return fail(STOKES_EINVAL, "null argument");
-    const LevelGeom& g = c->lev[c->L - 1].g;
-    CK(cudaMemcpyAsync(F_dev, c->F, g.n_u * sizeof(double), cudaMemcpyDeviceToDevice,
+    CK(cudaMemcpyAsync(F_dev, c->F, active_nu(c) * sizeof(double), cudaMemcpyDeviceToDevice,
                        static_cast<cudaStream_t>(stream)));
     return STOKES_OK;
 }
 
 stokes_status stokes_prolongate(stokes_ctx* c, int fine_level, int prec, const void* coarse, void* fine, int add,
                                 void* stream) {
+    if (c && c->oct) return fail(STOKES_EMESH, "not available for octree meshes");
     CKS(check_level(c, fine_level));
     if (fine_level < 1) return fail(STOKES_EINVAL, "fine_level must be >= 1");
     if (!coarse || !fine) return fail(STOKES_EINVAL, "null vector");
@@ -1208,6 +1730,7 @@ stokes_status stokes_prolongate(stokes_ctx* c, int fine_level, int prec, const v
 
 stokes_status stokes_restrict(stokes_ctx* c, int fine_level, int prec, const void* fine, void* coarse,
                               void* stream) {
+    if (c && c->oct) return fail(STOKES_EMESH, "not available for octree meshes");
     CKS(check_level(c, fine_level));
     if (fine_level < 1) return fail(STOKES_EINVAL, "fine_level must be >= 1");
     if (!coarse || !fine) return fail(STOKES_EINVAL, "null vector");
@@ -1224,6 +1747,7 @@ stokes_status stokes_restrict(stokes_ctx* c, int fine_level, int prec, const voi
 
 stokes_status stokes_smooth(stokes_ctx* c, int level, int prec, const void* b, void* x, int zero_guess,
                             void* stream) {
+    if (c && c->oct) return fail(STOKES_EMESH, "not available for octree meshes");
     CKS(check_level(c, level));
     if (level < 1) return fail(STOKES_EINVAL, "smoothing needs level >= 1");
     if (!b || !x) return fail(STOKES_EINVAL, "null vector");
@@ -1236,6 +1760,7 @@ stokes_status stokes_smooth(stokes_ctx* c, int level, int prec, const void* b, v
 }
 
 stokes_status stokes_coarse_solve(stokes_ctx* c, int prec, const void* b, void* x, void* stream) {
+    if (c && c->oct) return fail(STOKES_EMESH, "not available for octree meshes");
     if (!c || !b || !x) return fail(STOKES_EINVAL, "null argument");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (prec == STOKES_FP32) return coarse_solve<float>(c, static_cast<const float*>(b), static_cast<float*>(x), s);

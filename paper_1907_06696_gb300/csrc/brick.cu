@@ -205,6 +205,27 @@ cudaError_t launch_cell_epi(const BrickArgs<T>& a, int epi, T* acc, size_t n_u, 
 
 PlaneLayout brick_layout(int n) { return make_plane_layout(n, kBrickX, kBrickY, kBrickZ); }
 
+template <typename T>
+cudaError_t launch_consume(int epi, size_t n, T* acc, const T* b, const T* dinv, T* d, T* x_or_r, double c1,
+                           double c2, cudaStream_t s) {
+    const size_t per = sizeof(T) == 4 ? 4 : 2;
+    const size_t nb = (n / per + 255) / 256;
+    const unsigned blocks = unsigned(nb < 1 ? 1 : (nb < 4864 ? nb : 4864));
+    auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+    if (epi == EPI_RESID) {
+        const bool vec = al(acc) && al(b) && al(x_or_r);
+        LAUNCH(PROF_SMOOTH_VEC, s, (k_consume_resid<T><<<blocks, 256, 0, s>>>(n, acc, b, x_or_r, vec)));
+    } else {
+        const bool vec = al(acc) && al(b) && al(dinv) && al(d) && al(x_or_r);
+        LAUNCH(PROF_SMOOTH_VEC, s, (k_consume_cheb<T><<<blocks, 256, 0, s>>>(n, acc, b, dinv, d, x_or_r, T(c1), T(c2), vec)));
+    }
+    return cudaGetLastError();
+}
+template cudaError_t launch_consume<float>(int, size_t, float*, const float*, const float*, float*, float*, double,
+                                           double, cudaStream_t);
+template cudaError_t launch_consume<double>(int, size_t, double*, const double*, const double*, double*, double*,
+                                            double, double, cudaStream_t);
+
 cudaError_t brick_configure() {
     cudaError_t e;
     if ((e = configure_epi<float, EPI_PLAIN>()) != cudaSuccess) return e;
