@@ -473,6 +473,25 @@ def run_kernels(args):
     from paper_1907_06696_gb300 import capi
     capi.load()
     import sinker_inputs as si
+    if args.workload.startswith("oct"):
+        # adaptive case: 2 outer applies (constrained FP64 blocks), 3 finest-level FP32 products, 1 V-cycle
+        prob = si.octree_workload(args.workload)
+        ctx = capi.stokes_setup_octree_problem(prob)
+        N = ctx.n_u + ctx.n_p
+        up = torch.rand(N, device="cuda", dtype=torch.float64)
+        out = torch.empty_like(up)
+        for _ in range(2):
+            capi.stokes_vmult(ctx, -1, capi.BLOCK_STOKES, capi.STOKES_FP64, up, out)
+        NL = ctx.size(-1, 4)
+        xf = torch.rand(ctx.size(NL - 1, 0), device="cuda", dtype=torch.float32)
+        yf = torch.empty_like(xf)
+        for _ in range(3):
+            capi.stokes_vmult(ctx, NL - 1, capi.BLOCK_A, capi.STOKES_FP32, xf, yf)
+        xu = torch.empty(ctx.n_u, device="cuda", dtype=torch.float64)
+        capi.gmg_vcycle(ctx, capi.STOKES_FP32, up[:ctx.n_u], xu)
+        torch.cuda.synchronize()
+        print(json.dumps({"kernels": args.workload, "n_u": ctx.n_u, "n_p": ctx.n_p, "leaves": ctx.size(-1, 2)}))
+        return
     prob = si.workload(args.workload)
     ctx = capi.stokes_setup_problem(prob)
     n_u, n_p = ctx.n_u, ctx.n_p
@@ -596,12 +615,127 @@ def run_report(args):
     ctx.close()
 
 
+def run_octree(args):
+    """Adaptive workload (octree mesh refined in shells around the sinkers, hanging nodes,
+    local-smoothing GMG): host mesh and set-up times, FP32- and FP64-V-cycle solves to 1e-8,
+    per-class kernel time of one solve, and the throughput of the active outer operator (FP64,
+    constrained) and of the finest level operator (FP32)."""
+    import torch
+    from paper_1907_06696_gb300 import build as B
+    B.build()
+    from paper_1907_06696_gb300 import capi
+    capi.load()
+    import sinker_inputs as si
+    prob = si.octree_workload(args.workload)
+    t0 = time.perf_counter()
+    keys = capi.stokes_octree_sinker_mesh(prob.base_level, prob.centres, prob.max_levels, prob.shell_radius,
+                                          prob.shell_half_width)
+    mesh_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ctx = capi.stokes_setup_octree(keys, prob.coarsest_level, prob.centres, prob.mu_min, prob.mu_max, prob.delta,
+                                   prob.omega, prob.beta)
+    setup_s = time.perf_counter() - t0
+    n_u, n_p = ctx.n_u, ctx.n_p
+    N = n_u + n_p
+    NL = ctx.size(-1, 4)
+    stream = torch.cuda.current_stream()
+    up = torch.zeros(N, dtype=torch.float64, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def solve(prec):
+        up.zero_()
+        return capi.stokes_solve(ctx, prec, None, up, rtol=RTOL, max_it=5000, stream=stream, check=False)
+
+    for _ in range(max(1, min(args.warmup, 3))):
+        solve(capi.STOKES_FP32)
+    torch.cuda.synchronize()
+    clk, clk_path = clocks_start(torch.cuda.current_device())
+    time.sleep(0.3)
+    l0 = capi.stokes_launch_count()
+    e0.record(stream)
+    its = []
+    for _ in range(args.steps):
+        info = solve(capi.STOKES_FP32)
+        its.append(info.iterations)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = capi.stokes_launch_count() - l0
+    clocks = clocks_stop(clk, clk_path)
+    ms = e0.elapsed_time(e1) / args.steps
+    res32 = info.rel_residual_true
+    st32 = info.status
+    e0.record(stream)
+    info64 = solve(capi.STOKES_FP64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    # one profiled FP32 solve: time per kernel class
+    capi.stokes_profile(1)
+    capi.stokes_profile_read(reset=True)
+    solve(capi.STOKES_FP32)
+    torch.cuda.synchronize()
+    prof = capi.stokes_profile_read(reset=True)
+    capi.stokes_profile(0)
+    tot = sum(v[0] for v in prof.values())
+    shares = {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / tot, 4)} for k, v in prof.items() if v[1]}
+    # operator throughput
+    reps = 10
+    x = torch.rand(N, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    capi.stokes_vmult(ctx, -1, capi.BLOCK_STOKES, capi.STOKES_FP64, x, y, stream=stream)
+    e0.record(stream)
+    for _ in range(reps):
+        capi.stokes_vmult(ctx, -1, capi.BLOCK_STOKES, capi.STOKES_FP64, x, y, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    outer_ms = e0.elapsed_time(e1) / reps
+    nf = ctx.size(NL - 1, 0)
+    xf = torch.rand(nf, dtype=torch.float32, device="cuda")
+    yf = torch.empty_like(xf)
+    capi.stokes_vmult(ctx, NL - 1, capi.BLOCK_A, capi.STOKES_FP32, xf, yf, stream=stream)
+    e0.record(stream)
+    for _ in range(reps):
+        capi.stokes_vmult(ctx, NL - 1, capi.BLOCK_A, capi.STOKES_FP32, xf, yf, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    level_ms = e0.elapsed_time(e1) / reps
+    leaves = ctx.size(-1, 2)
+    pk = peaks()
+    hbm = pk.get("hbm_gbs", 6800.0)
+    level_cells = ctx.size(NL - 1, 2)
+    # algorithmic bytes of the finest level operator: src + dst (FP32) + the 27 node indices and mu per cell
+    lvl_bytes = 2 * 4 * nf + level_cells * (27 * 4 + 4)
+    line = {"metric": "Stokes solve s to 1e-8 rel (FP32 vs FP64 GMG), adaptive octree", "value": N / (ms / 1e3) / 1e9,
+            "unit": "GDoF/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 outer + f32 V-cycle",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "base_level": prob.base_level, "max_levels": [int(v) for v in prob.max_levels],
+                       "sinkers": prob.n_sinkers, "dr": prob.mu_max / prob.mu_min, "leaves": leaves, "n_u": n_u,
+                       "n_p": n_p, "levels": NL, "hanging_u": capi.stokes_octree_table(ctx, 6),
+                       "hanging_p": capi.stokes_octree_table(ctx, 7), "rtol": RTOL,
+                       "mesh_s": mesh_s, "setup_s": setup_s, "parallelism": "1 GPU",
+                       "l2": "working set > L2 (no flush needed)"},
+            "solve": {"fp32_vcycle_s": ms / 1e3, "fp32_vcycle_iterations": its, "fp32_true_rel_residual": res32,
+                      "fp32_status": st32, "fp64_vcycle_s": ms64 / 1e3, "fp64_vcycle_iterations": info64.iterations,
+                      "fp64_true_rel_residual": info64.rel_residual_true, "fp64_status": info64.status,
+                      "fp32_speedup_vs_fp64_gmg": ms64 / ms},
+            "operators": {"outer_fp64_ms": outer_ms, "outer_gdofs": N / (outer_ms / 1e3) / 1e9,
+                          "finest_level_fp32_ms": level_ms, "finest_level_dofs": nf,
+                          "finest_level_gdofs": nf / (level_ms / 1e3) / 1e9,
+                          "finest_level_alg_gbs": lvl_bytes / (level_ms / 1e3) / 1e9, "peak_gbs": hbm},
+            "kernel_share": shares, "gpu_launches": int(launches), "clocks": clocks}
+    print(json.dumps(line))
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.solve_report:
         run_report(args)
         return
-    if args.workload.startswith("batch") and args.impl != "reference":
+    if args.workload.startswith("oct") and args.impl != "reference":
+        run_octree(args)
+    elif args.workload.startswith("batch") and args.impl != "reference":
         run_batch(args)
     elif args.kernels:
         run_kernels(args)

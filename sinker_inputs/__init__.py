@@ -163,12 +163,15 @@ def octree_workload(name: str) -> OctreeProblem:
 
     octree   : base 8^3, 12 sinkers refined to levels 7-9 (drawn per sinker), viscosity ratio 1e6,
                multigrid down to 4^3 (~20M velocity DoFs); seed 1911
+    oct_l    : base 8^3, 6 sinkers, levels 7-8, ratio 1e6 (profiling case, a few million DoFs)
     oct_m    : base 8^3, 4 sinkers, levels 5-6, ratio 1e4 (parity case)
     oct_s    : base 4^3, 2 sinkers, levels 4-5, ratio 1e4 (parity case)
     oct_xs   : base 2^3, 1 sinker, level 4, ratio 1e2 (dense-solve case)
     """
     if name == "octree":
         return octree_problem(3, 2, 12, (7, 8, 9), 1e6, 1911, name)
+    if name == "oct_l":
+        return octree_problem(3, 2, 6, (7, 8), 1e6, 1924, name)
     if name == "oct_m":
         return octree_problem(3, 2, 4, (5, 6), 1e4, 1921, name)
     if name == "oct_s":
