@@ -733,12 +733,12 @@ def main():
     if args.solve_report:
         run_report(args)
         return
-    if args.workload.startswith("oct") and args.impl != "reference":
+    if args.kernels:
+        run_kernels(args)
+    elif args.workload.startswith("oct") and args.impl != "reference":
         run_octree(args)
     elif args.workload.startswith("batch") and args.impl != "reference":
         run_batch(args)
-    elif args.kernels:
-        run_kernels(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
