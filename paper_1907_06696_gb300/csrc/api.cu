@@ -1017,20 +1017,50 @@ stokes_status oct_setup_impl(const stokes_octree* mesh, const stokes_mu* mu, con
     a.n_leaves = int(H.leaves.size());
     a.nu_nodes = H.unodes.size();
     a.np = H.pverts.size();
+    // The active-space kernels visit leaves in Morton (z-curve) order of their lower corner on the
+    // finest lattice, so that neighbouring threads share nodes in cache (the key order keeps the
+    // leaves of different levels apart); numbering (key order) and results are unchanged up to the
+    // order of the atomic additions.
+    auto morton = [&](uint64_t cell) {
+        const int sh = H.lmax - oct_l(cell);
+        const uint64_t x = uint64_t(oct_i(cell)) << sh, y = uint64_t(oct_j(cell)) << sh, z = uint64_t(oct_k(cell)) << sh;
+        uint64_t m = 0;
+        for (int b = 0; b < 16; ++b)
+            m |= (((x >> b) & 1) << (3 * b)) | (((y >> b) & 1) << (3 * b + 1)) | (((z >> b) & 1) << (3 * b + 2));
+        return (m << 4) | uint64_t(oct_l(cell));
+    };
+    auto z_order = [&](const std::vector<uint64_t>& cells) {
+        std::vector<uint64_t> key(cells.size());
+        for (size_t n = 0; n < cells.size(); ++n) key[n] = morton(cells[n]);
+        std::vector<uint32_t> perm(cells.size());
+        for (size_t n = 0; n < perm.size(); ++n) perm[n] = uint32_t(n);
+        std::sort(perm.begin(), perm.end(), [&](uint32_t a, uint32_t b) { return key[a] < key[b]; });
+        return perm;   // perm[new position] = index in key order
+    };
     {
         int32_t *lu, *lp, *un, *pn;
         double *uw, *pw, *lm;
         uint8_t *ub, *lv;
-        std::vector<uint8_t> lev8(H.leaves.size());
-        for (size_t n = 0; n < H.leaves.size(); ++n) lev8[n] = uint8_t(oct_l(H.leaves[n]));
-        CKS(upload(c, &lu, H.leaf_u, s));
-        CKS(upload(c, &lp, H.leaf_p, s));
+        const size_t nl = H.leaves.size();
+        const std::vector<uint32_t> perm = z_order(H.leaves);
+        std::vector<uint8_t> lev8(nl);
+        std::vector<int32_t> zu(nl * 27), zp(nl * 8);
+        std::vector<double> zmu(nl);
+        for (size_t n = 0; n < nl; ++n) {
+            const size_t o = perm[n];
+            lev8[n] = uint8_t(oct_l(H.leaves[o]));
+            zmu[n] = H.leaf_mu[o];
+            std::copy(H.leaf_u.begin() + o * 27, H.leaf_u.begin() + o * 27 + 27, zu.begin() + n * 27);
+            std::copy(H.leaf_p.begin() + o * 8, H.leaf_p.begin() + o * 8 + 8, zp.begin() + n * 8);
+        }
+        CKS(upload(c, &lu, zu, s));
+        CKS(upload(c, &lp, zp, s));
         CKS(upload(c, &un, H.ucon_node, s));
         CKS(upload(c, &uw, H.ucon_w, s));
         CKS(upload(c, &pn, H.pcon_node, s));
         CKS(upload(c, &pw, H.pcon_w, s));
         CKS(upload(c, &ub, H.ubnd, s));
-        CKS(upload(c, &lm, H.leaf_mu, s));
+        CKS(upload(c, &lm, zmu, s));
         CKS(upload(c, &lv, lev8, s));
         CK(cudaStreamSynchronize(s));   // lev8 (pageable, local) consumed
         a.leaf_u = lu; a.leaf_p = lp; a.ucon_node = un; a.ucon_w = uw; a.pcon_node = pn; a.pcon_w = pw;
@@ -1069,12 +1099,27 @@ stokes_status oct_setup_impl(const stokes_octree* mesh, const stokes_mu* mu, con
         ca[li].push_back(int32_t(n));
         cl[li].push_back(H.copy_index[n]);
     }
+    std::vector<std::vector<uint32_t>> inv_perm(NL);   // key-order index -> position visited
     for (int li = 0; li < NL; ++li) {
         const OctLevelHost& LH = H.levels[li];
         OctLevel& L = oc.lev[li];
         int32_t* cn;
         uint8_t* fl;
-        CKS(upload(c, &cn, LH.cell_nodes, s));
+        const size_t ncl = LH.cells.size();
+        // level cells keep key (row) order: it matches the row-major node numbering of the level, so
+        // neighbouring threads read neighbouring nodes (Morton order measured slower here)
+        std::vector<uint32_t> perm(ncl);
+        for (size_t n = 0; n < ncl; ++n) perm[n] = uint32_t(n);
+        inv_perm[li].resize(ncl);
+        std::vector<int32_t> zcn(ncl * 27);
+        std::vector<double> zmu(ncl);
+        for (size_t n = 0; n < ncl; ++n) {
+            inv_perm[li][perm[n]] = uint32_t(n);
+            zmu[n] = LH.mu[perm[n]];
+            std::copy(LH.cell_nodes.begin() + size_t(perm[n]) * 27, LH.cell_nodes.begin() + size_t(perm[n]) * 27 + 27,
+                      zcn.begin() + n * 27);
+        }
+        CKS(upload(c, &cn, zcn, s));
         CKS(upload(c, &fl, LH.flags, s));
         L.g.n_cells = int(LH.cells.size());
         L.g.nn = LH.nodes.size();
@@ -1084,7 +1129,9 @@ stokes_status oct_setup_impl(const stokes_octree* mesh, const stokes_mu* mu, con
         if (li > 0) {
             uint32_t* pa;
             uint16_t* po;
-            CKS(upload(c, &pa, LH.parent, s));
+            std::vector<uint32_t> par(LH.parent.size());
+            for (size_t t = 0; t < par.size(); ++t) par[t] = inv_perm[li - 1][LH.parent[t]];
+            CKS(upload(c, &pa, par, s));
             CKS(upload(c, &po, LH.pos, s));
             L.g.parent = pa;
             L.g.pos = po;
@@ -1096,7 +1143,7 @@ stokes_status oct_setup_impl(const stokes_octree* mesh, const stokes_mu* mu, con
         CK(cudaMemsetAsync(L.v32.acc, 0, n3 * sizeof(float), s));
         CK(cudaMemsetAsync(L.v64.d, 0, n3 * sizeof(double), s));
         CK(cudaMemsetAsync(L.v32.d, 0, n3 * sizeof(float), s));
-        CKS(upload(c, &L.v64.mu, LH.mu, s));
+        CKS(upload(c, &L.v64.mu, zmu, s));
         CKS(dalloc(c, &L.v32.mu, LH.mu.size()));
         CK(launch_cast_d2f(LH.mu.size(), L.v64.mu, L.v32.mu, s));
         CK(launch_oct_inv_diag(L.g, L.v64.mu, c->ref_diag, L.v64.t, L.v64.dinv, s));

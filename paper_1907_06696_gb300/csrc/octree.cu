@@ -141,6 +141,7 @@ __device__ __forceinline__ double gather_u(const OctActiveDev& a, const double* 
     const int32_t* nd = a.ucon_node + size_t(-r - 1) * kOctUCon;
     const double* wt = a.ucon_w + size_t(-r - 1) * kOctUCon;
     double v = 0.0;
+#pragma unroll 1
     for (int t = 0; t < kOctUCon; ++t) {
         const int32_t node = nd[t];
         if (node < 0) break;
@@ -155,6 +156,7 @@ __device__ __forceinline__ void scatter_u(const OctActiveDev& a, double* dst, in
     }
     const int32_t* nd = a.ucon_node + size_t(-r - 1) * kOctUCon;
     const double* wt = a.ucon_w + size_t(-r - 1) * kOctUCon;
+#pragma unroll 1
     for (int t = 0; t < kOctUCon; ++t) {
         const int32_t node = nd[t];
         if (node < 0) break;
@@ -166,6 +168,7 @@ __device__ __forceinline__ double gather_p(const OctActiveDev& a, const double* 
     const int32_t* nd = a.pcon_node + size_t(-r - 1) * kOctPCon;
     const double* wt = a.pcon_w + size_t(-r - 1) * kOctPCon;
     double v = 0.0;
+#pragma unroll 1
     for (int t = 0; t < kOctPCon; ++t) {
         if (nd[t] < 0) break;
         v += wt[t] * src[nd[t]];
@@ -179,6 +182,7 @@ __device__ __forceinline__ void scatter_p(const OctActiveDev& a, double* dst, in
     }
     const int32_t* nd = a.pcon_node + size_t(-r - 1) * kOctPCon;
     const double* wt = a.pcon_w + size_t(-r - 1) * kOctPCon;
+#pragma unroll 1
     for (int t = 0; t < kOctPCon; ++t) {
         if (nd[t] < 0) break;
         atomicAdd(dst + nd[t], wt[t] * v);
