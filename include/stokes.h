@@ -117,6 +117,9 @@ typedef struct {
                                    graph and replay it on a library stream ordered with the caller's
                                    stream by events (default); 0 = launch kernel by kernel. The first
                                    V-cycle of each precision performs the capture. */
+    int precond_kind;           /* 0 = block-triangular P of eq. stokes_precond (default): z_p = -S_hat^-1 r_p,
+                                   z_u = A_hat^-1 (r_u - B^T z_p); 1 = block-diagonal P_D = diag(A, S) of
+                                   Section 2.2 / Table 1: z_u = A_hat^-1 r_u, z_p = S_hat^-1 r_p */
 } stokes_options;
 
 typedef struct {

@@ -19,10 +19,15 @@ from .gmg import chebyshev_smooth
 
 
 class StokesPreconditioner:
-    def __init__(self, ops_fine, gmg, schur_degree=5, exact_A=None, exact_S=None):
+    """kind "triangular": P^-1 of eq. stokes_precond (z_p = -S_hat^-1 r_p, z_u = A_hat^-1 (r_u - B^T z_p)).
+    kind "diagonal": the block-diagonal P_D = diag(A, S) of Section 2.2 / Table 1
+    (z_u = A_hat^-1 r_u, z_p = S_hat^-1 r_p)."""
+
+    def __init__(self, ops_fine, gmg, schur_degree=5, exact_A=None, exact_S=None, kind="triangular"):
         self.ops = ops_fine
         self.gmg = gmg
         self.schur_degree = schur_degree
+        self.kind = kind
         self.Mp_dinv = 1.0 / ops_fine.diag_Mp()
         self.exact_A = exact_A        # optional callables replacing the approximations
         self.exact_S = exact_S
@@ -42,6 +47,8 @@ class StokesPreconditioner:
     def apply(self, r):
         n_u = self.ops.mesh.n_u
         r_u, r_p = r[:n_u], r[n_u:]
+        if self.kind == "diagonal":
+            return np.concatenate([self.velocity_inverse(r_u), self.schur_inverse(r_p)])
         z_p = -self.schur_inverse(r_p)
         t = r_u - self.ops.apply_BT(z_p)
         z_u = self.velocity_inverse(t)

@@ -479,6 +479,10 @@ stokes_status oct_precondition(stokes_ctx* c, int prec, const double* r, double*
     const size_t nu = 3 * o.act.nu_nodes, np = o.act.np;
     double* zp = z + nu;
     CKS(oct_schur_inverse(c, r + nu, zp, s));
+    if (c->opt.precond_kind == 1) {   // P_D: z_p = S_hat^-1 r_p, z_u = A_hat^-1 r_u
+        if (prec == STOKES_FP64) return oct_vcycle<double>(c, r, z, s);
+        return oct_vcycle<float>(c, r, z, s);
+    }
     CK(launch_axpby(np, -1.0, zp, 0.0, zp, s));                               // z_p = -S^-1 r_p
     CK(launch_oct_active(o.act, nullptr, zp, c->tu, nullptr, false, true, false, s));
     CK(launch_axpby(nu, 1.0, r, -1.0, c->tu, s));                            // t = r_u - B^T z_p
@@ -523,6 +527,14 @@ stokes_status precondition(stokes_ctx* c, int prec, const double* r, double* z, 
     const size_t nu = F.g.n_u, np = F.g.n_p;
     double* zp = z + nu;
     CKS(schur_inverse(c, r + nu, zp, s));
+    if (c->opt.precond_kind == 1) {   // P_D: z_p = S_hat^-1 r_p, z_u = A_hat^-1 r_u
+        if (prec == STOKES_FP64) return vcycle<double>(c, r, z, s);
+        CK(launch_cast_d2f(nu, r, c->stage_in, s));
+        CKS(vcycle<float>(c, c->stage_in, c->stage_out, s));
+        CK(launch_cast_f2d(nu, c->stage_out, z, s));
+        CK(launch_copy_boundary<double>(F.g, r, z, s));
+        return STOKES_OK;
+    }
     CK(launch_axpby(np, -1.0, zp, 0.0, zp, s));                               // z_p = -S^-1 r_p
     CK(launch_stokes_blocks(F.g, F.v64.mu, nullptr, zp, c->tu, nullptr, false, true, false, c->opt.outer_arith == 1, s));
     CK(launch_axpby(nu, 1.0, r, -1.0, c->tu, s));                            // t = r_u - B^T z_p
@@ -785,7 +797,8 @@ stokes_status fgmres(stokes_ctx* c, int prec, const double* b, double* x, double
 stokes_status validate_options(const stokes_options& o) {
     if (o.cheb_degree < 1 || o.smoothing_range <= 1.0 || o.eig_safety <= 0.0 || o.lanczos_steps < 1 ||
         o.schur_degree < 1 || o.restart < 1 || o.restart > 500 || (o.outer_arith != 0 && o.outer_arith != 1) ||
-        (o.vmult_kernel != 0 && o.vmult_kernel != 1) || (o.graphs != 0 && o.graphs != 1))
+        (o.vmult_kernel != 0 && o.vmult_kernel != 1) || (o.graphs != 0 && o.graphs != 1) ||
+        (o.precond_kind != 0 && o.precond_kind != 1))
         return fail(STOKES_EINVAL, "bad options");
     return STOKES_OK;
 }
@@ -1246,6 +1259,7 @@ void stokes_default_options(stokes_options* opt) {
     opt->outer_arith = 1;
     opt->vmult_kernel = 0;
     opt->graphs = 1;
+    opt->precond_kind = 0;
 }
 
 const char* stokes_strerror(stokes_status s) {

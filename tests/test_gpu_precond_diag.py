@@ -1,0 +1,97 @@
+"""GPU parity of the block-diagonal preconditioner P_D = diag(A, S) (Section 2.2, Table 1;
+option precond_kind = 1) through the C ABI against the oracle's StokesPreconditioner(kind=
+"diagonal"), and solves with it on a uniform and an adaptive mesh. Tolerances as in
+test_gpu_parity.py (FP64 V-cycle 1e-10, FP32 V-cycle 2e-5) and test_gpu_octree.py."""
+import functools
+
+import numpy as np
+import pytest
+
+import sinker_inputs as si
+from oracle import adaptive, gmg, krylov, mesh, operators, octree, sinker
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def capi():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1907_06696_gb300 import build as B
+    from paper_1907_06696_gb300 import capi as api
+    B.build()
+    api.load()
+    return api
+
+
+@functools.lru_cache(maxsize=None)
+def uniform_oracle(name):
+    p = si.workload(name)
+    m = mesh.Mesh(p.n)
+    mus = sinker.level_viscosities(m, p, p.n_levels)
+    G = gmg.GMG(p.n, p.n_levels, mus)
+    ops = G.levels[-1].ops
+    F = operators.assemble_rhs(m, sinker.forcing(m.quad_points(), p))
+    return p, m, G, ops, F
+
+
+def diag_options(capi):
+    o = capi.stokes_default_options()
+    o.precond_kind = 1
+    return o
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("name", ["cube8", "cube16"])
+def test_precondition_diagonal(capi, name):
+    p, m, G, ops, F = uniform_oracle(name)
+    ctx = capi.stokes_setup_problem(p, options=diag_options(capi))
+    N = m.n_u + m.n_p
+    r = si.uniform(4001, N)
+    ref = krylov.StokesPreconditioner(ops, G, kind="diagonal").apply(r)
+    z = torch.empty(N, dtype=torch.float64, device="cuda")
+    for prec, tol in ((capi.STOKES_FP64, 1e-10), (capi.STOKES_FP32, 2e-5)):
+        capi.stokes_precondition(ctx, prec, torch.from_numpy(r).cuda(), z)
+        assert rel(z.cpu().numpy(), ref) <= tol, prec
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["cube8", "cube16"])
+def test_solve_diagonal(capi, name):
+    p, m, G, ops, F = uniform_oracle(name)
+    b = np.concatenate([F, np.zeros(m.n_p)])
+    _, its_o, _ = krylov.fgmres(ops.apply_stokes, krylov.StokesPreconditioner(ops, G, kind="diagonal").apply, b,
+                                rtol=1e-8, max_it=2000)
+    _, its_t, _ = krylov.fgmres(ops.apply_stokes, krylov.StokesPreconditioner(ops, G).apply, b, rtol=1e-8)
+    ctx = capi.stokes_setup_problem(p, options=diag_options(capi))
+    for prec in (capi.STOKES_FP64, capi.STOKES_FP32):
+        up = torch.zeros(m.n_u + m.n_p, dtype=torch.float64, device="cuda")
+        info = capi.stokes_solve(ctx, prec, None, up, rtol=1e-8, max_it=2000)
+        x = up.cpu().numpy()
+        assert np.linalg.norm(b - ops.apply_stokes(x)) / np.linalg.norm(b) <= 1.5e-8
+        assert abs(info.iterations - its_o) <= max(2, 0.05 * its_o), (prec, info.iterations, its_o)
+    assert its_o > its_t
+    ctx.close()
+
+
+def test_solve_diagonal_octree(capi):
+    p = si.octree_workload("oct_s")
+    lv = octree.balance(octree.refine_shells(p.base_level, p.centres, p.max_levels, p.shell_radius,
+                                             p.shell_half_width))
+    S = adaptive.AdaptiveStokes(octree.Octree(lv, p.coarsest_level), p)
+    ctx = capi.stokes_setup_octree_problem(p, options=diag_options(capi))
+    N = S.n_u + S.n_p
+    r = si.uniform(4002, N)
+    zr = np.concatenate([S.vcycle(r[:S.n_u]), S.schur_inverse(r[S.n_u:])])
+    z = torch.empty(N, dtype=torch.float64, device="cuda")
+    capi.stokes_precondition(ctx, capi.STOKES_FP64, torch.from_numpy(r).cuda(), z)
+    assert rel(z.cpu().numpy(), zr) <= 1e-9
+    up = torch.zeros(N, dtype=torch.float64, device="cuda")
+    capi.stokes_solve(ctx, capi.STOKES_FP32, None, up, rtol=1e-8, max_it=3000)
+    b = np.concatenate([S.F, np.zeros(S.n_p)])
+    assert np.linalg.norm(b - S.apply_stokes(up.cpu().numpy())) / np.linalg.norm(b) <= 2e-8
+    ctx.close()

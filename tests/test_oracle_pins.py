@@ -333,6 +333,45 @@ def test_exact_preconditioner_two_iterations():
     assert its <= 2
 
 
+def test_exact_block_diagonal_preconditioner_three_iterations():
+    """P_D = diag(A, S) with exact blocks: the preconditioned Stokes matrix has the eigenvalues 1 and
+    (1 +- sqrt 5) / 2 only (Murphy, Golub, Wathen, SIAM J. Sci. Comput. 21 (2000)), so FGMRES
+    converges in at most 3 iterations; with -S instead of S the eigenvalues are 1 and (1 +- i sqrt 3)/2,
+    also 3 values, so the sign is pinned by the eigenvalues themselves."""
+    p, m, G, ops, F = _problem("cube2")
+    A = ops.csr_A().toarray()
+    B = ops.csr_B().toarray()
+    Ainv = np.linalg.inv(A)
+    S = B @ Ainv @ B.T
+    Spinv = np.linalg.pinv(S, rcond=1e-10, hermitian=True)
+    Pc = krylov.StokesPreconditioner(ops, G, exact_A=lambda t: Ainv @ t, exact_S=lambda r: Spinv @ r,
+                                     kind="diagonal")
+    b = np.concatenate([F, np.zeros(m.n_p)])
+    _, its, _ = krylov.fgmres(ops.apply_stokes, Pc.apply, b, rtol=1e-12)
+    assert its == 3
+    # eigenvalues of P_D^-1 K on the free velocity DoFs and the non-constant pressures
+    n_u = m.n_u
+    free = np.nonzero(~m.dirichlet)[0]
+    K = np.block([[A[np.ix_(free, free)], B[:, free].T], [B[:, free], np.zeros((m.n_p, m.n_p))]])
+    Pinv = np.block([[np.linalg.inv(A[np.ix_(free, free)]), np.zeros((free.size, m.n_p))],
+                     [np.zeros((m.n_p, free.size)), Spinv]])
+    ev = np.linalg.eigvals(Pinv @ K)
+    ev = ev[np.abs(ev) > 1e-8]                                   # the pressure constant
+    targets = np.array([1.0, (1 + 5 ** 0.5) / 2, (1 - 5 ** 0.5) / 2])
+    assert np.max(np.min(np.abs(ev[:, None] - targets[None, :]), axis=1)) < 1e-8
+
+
+def test_block_diagonal_needs_more_iterations_than_triangular():
+    """Table 1 context: with the GMG blocks, P_D takes more FGMRES iterations than the
+    block-triangular P (the paper reports about twice as many)."""
+    p, m, G, ops, F = _problem("cube4")
+    b = np.concatenate([F, np.zeros(m.n_p)])
+    _, its_t, _ = krylov.fgmres(ops.apply_stokes, krylov.StokesPreconditioner(ops, G).apply, b, rtol=1e-8)
+    _, its_d, _ = krylov.fgmres(ops.apply_stokes, krylov.StokesPreconditioner(ops, G, kind="diagonal").apply, b,
+                                rtol=1e-8)
+    assert its_d > its_t
+
+
 def test_fgmres_gmg_matches_dense_direct_solve():
     p, m, G, ops, F = _problem("cube4")
     Pc = krylov.StokesPreconditioner(ops, G)
