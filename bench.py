@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--solve-report", action="store_true",
                     help="one FP32-V-cycle and one FP64-V-cycle solve of the workload: iterations, times, "
                          "true FP64 residuals and the difference of the two solutions (any size)")
+    ap.add_argument("--outer", default="fgmres", choices=["fgmres", "idr", "both"],
+                    help="with --solve-report: outer solver(s) of the FP32/FP64 V-cycle solves (idr = IDR(2))")
+    ap.add_argument("--fp32-only", action="store_true",
+                    help="with --solve-report: skip the FP64-V-cycle legs (largest problems)")
     ap.add_argument("--precond", default="triangular", choices=["triangular", "both"],
                     help="with --solve-report: 'both' adds FP32-V-cycle solves with the block-diagonal P_D "
                          "(Table 1 comparison)")
@@ -589,13 +593,35 @@ def run_report(args):
     import sinker_inputs as si
     prob = si.workload(args.workload)
     t0 = time.perf_counter()
-    ctx = capi.stokes_setup_problem(prob)
+    opts = capi.stokes_default_options()
+    if args.outer == "idr":
+        opts.outer_solver = 1
+    ctx = capi.stokes_setup_problem(prob, options=opts)
     setup_s = time.perf_counter() - t0
     N = ctx.n_u + ctx.n_p
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    out = {}
+    out = {"outer": "IDR(2)" if args.outer == "idr" else "FGMRES(50)"}
     sols = {}
-    for tag, prec in (("fp32_vcycle", capi.STOKES_FP32), ("fp64_vcycle", capi.STOKES_FP64)):
+    if args.outer == "both":   # IDR(2) legs first, on a context of their own (FGMRES basis not allocated yet)
+        oi = capi.stokes_default_options()
+        oi.outer_solver = 1
+        ci = capi.stokes_setup_problem(prob, options=oi)
+        legs = (("idr_fp32_vcycle", capi.STOKES_FP32),) if args.fp32_only else \
+            (("idr_fp32_vcycle", capi.STOKES_FP32), ("idr_fp64_vcycle", capi.STOKES_FP64))
+        for tag, prec in legs:
+            up = torch.zeros(N, dtype=torch.float64, device="cuda")
+            e0.record()
+            info = capi.stokes_solve(ci, prec, None, up, rtol=RTOL, max_it=5000, check=False)
+            e1.record()
+            torch.cuda.synchronize()
+            out[tag] = {"s": e0.elapsed_time(e1) / 1e3, "iterations": info.iterations, "status": info.status,
+                        "true_rel_residual": info.rel_residual_true}
+            del up
+        ci.close()
+        torch.cuda.empty_cache()
+    legs = (("fp32_vcycle", capi.STOKES_FP32),) if args.fp32_only else \
+        (("fp32_vcycle", capi.STOKES_FP32), ("fp64_vcycle", capi.STOKES_FP64))
+    for tag, prec in legs:
         up = torch.zeros(N, dtype=torch.float64, device="cuda")
         for _ in range(args.warmup):
             up.zero_()
@@ -608,25 +634,26 @@ def run_report(args):
         out[tag] = {"s": e0.elapsed_time(e1) / 1e3, "iterations": info.iterations, "status": info.status,
                     "true_rel_residual": info.rel_residual_true}
         sols[tag] = up
-    u32, u64 = sols["fp32_vcycle"][:ctx.n_u], sols["fp64_vcycle"][:ctx.n_u]
-    p32, p64 = sols["fp32_vcycle"][ctx.n_u:], sols["fp64_vcycle"][ctx.n_u:]
-    if args.precond == "both":
-        o = capi.stokes_default_options()
-        o.precond_kind = 1
-        cd = capi.stokes_setup_problem(prob, options=o)
-        up = torch.zeros(N, dtype=torch.float64, device="cuda")
-        capi.stokes_solve(cd, capi.STOKES_FP32, None, up, rtol=RTOL, max_it=5000, check=False)
-        up.zero_()
-        e0.record()
-        info = capi.stokes_solve(cd, capi.STOKES_FP32, None, up, rtol=RTOL, max_it=5000, check=False)
-        e1.record()
-        torch.cuda.synchronize()
-        out["block_diagonal_fp32_vcycle"] = {"s": e0.elapsed_time(e1) / 1e3, "iterations": info.iterations,
-                                             "status": info.status, "true_rel_residual": info.rel_residual_true}
-        cd.close()
-    out["rel_diff_u"] = float((u32 - u64).norm() / u64.norm())
-    out["rel_diff_p"] = float((p32 - p64).norm() / p64.norm())
-    out["speedup"] = out["fp64_vcycle"]["s"] / out["fp32_vcycle"]["s"]
+    if not args.fp32_only:
+        u32, u64 = sols["fp32_vcycle"][:ctx.n_u], sols["fp64_vcycle"][:ctx.n_u]
+        p32, p64 = sols["fp32_vcycle"][ctx.n_u:], sols["fp64_vcycle"][ctx.n_u:]
+        if args.precond == "both":
+            o = capi.stokes_default_options()
+            o.precond_kind = 1
+            cd = capi.stokes_setup_problem(prob, options=o)
+            up = torch.zeros(N, dtype=torch.float64, device="cuda")
+            capi.stokes_solve(cd, capi.STOKES_FP32, None, up, rtol=RTOL, max_it=5000, check=False)
+            up.zero_()
+            e0.record()
+            info = capi.stokes_solve(cd, capi.STOKES_FP32, None, up, rtol=RTOL, max_it=5000, check=False)
+            e1.record()
+            torch.cuda.synchronize()
+            out["block_diagonal_fp32_vcycle"] = {"s": e0.elapsed_time(e1) / 1e3, "iterations": info.iterations,
+                                                 "status": info.status, "true_rel_residual": info.rel_residual_true}
+            cd.close()
+        out["rel_diff_u"] = float((u32 - u64).norm() / u64.norm())
+        out["rel_diff_p"] = float((p32 - p64).norm() / p64.norm())
+        out["speedup"] = out["fp64_vcycle"]["s"] / out["fp32_vcycle"]["s"]
     print(json.dumps({"report": args.workload, "n_u": ctx.n_u, "n_p": ctx.n_p, "setup_s": setup_s,
                       "sinkers": prob.n_sinkers, "dr": prob.mu_max / prob.mu_min, "rtol": RTOL, **out}))
     ctx.close()

@@ -120,6 +120,11 @@ typedef struct {
     int precond_kind;           /* 0 = block-triangular P of eq. stokes_precond (default): z_p = -S_hat^-1 r_p,
                                    z_u = A_hat^-1 (r_u - B^T z_p); 1 = block-diagonal P_D = diag(A, S) of
                                    Section 2.2 / Table 1: z_u = A_hat^-1 r_u, z_p = S_hat^-1 r_p */
+    int outer_solver;           /* 0 = FGMRES(restart) (default); 1 = IDR(idr_s), the memory-light solver of
+                                   Section 3.5 (van Gijzen & Sonneveld's bi-orthogonal IDR(s) with right
+                                   preconditioning, 3 idr_s + 4 vectors; shadow space from splitmix64
+                                   seeds 1907100 + i, orthonormalised). Not for stokes_batch_solve. */
+    int idr_s;                  /* shadow-space dimension of IDR(s), 1..8 (2) */
 } stokes_options;
 
 typedef struct {

@@ -142,3 +142,90 @@ def dense_stokes_solve(ops, F):
     rhs[:n_u] = F
     sol = np.linalg.solve(K, rhs)
     return sol[:n_u + n_p]
+
+
+def idr_shadow_space(n, s, seed=1907100):
+    """The s shadow vectors of IDR(s): splitmix64 uniforms u01 - 1/2 (seed + i for column i),
+    orthonormalised by Gram-Schmidt, as columns of an (n, s) array."""
+    import sinker_inputs
+    P = np.stack([sinker_inputs.uniform01(seed + i, n) - 0.5 for i in range(s)], axis=1)
+    for i in range(s):
+        for j in range(i):
+            P[:, i] -= (P[:, j] @ P[:, i]) * P[:, j]
+        P[:, i] /= np.linalg.norm(P[:, i])
+    return P
+
+
+def idr_s(apply_K, apply_Pinv, b, s=2, rtol=1e-8, max_it=1000, x0=None, P=None, kappa=0.7):
+    """IDR(s) with bi-orthogonalisation and a preconditioner (M. B. van Gijzen, P. Sonneveld,
+    "Algorithm 913: an elegant IDR(s) variant that efficiently exploits bi-orthogonality
+    properties", ACM TOMS 38 (2011)); the residual-smoothing-free variant with the "maintain the
+    convergence" choice of omega (|cos| of the angle below kappa is lifted to kappa).
+    The memory-light alternative to FGMRES of Section 3.5: 3s + 4 vectors.
+    Stops when the recursively updated residual satisfies ||r|| <= rtol ||b||; if the true
+    residual b - K x is then still above the tolerance (the recursion drifts from it, more so
+    with an inexact preconditioner), IDR restarts from x with r = b - K x (at most 10 times).
+    Returns (x, preconditioned operator applications, list of relative residuals)."""
+    n = b.shape[0]
+    x = np.zeros(n) if x0 is None else x0.copy()
+    bnorm = np.linalg.norm(b)
+    if P is None:
+        P = idr_shadow_space(n, s)
+    its = 0
+    hist = []
+    tol = rtol * bnorm
+    for _ in range(11):
+        r = b - apply_K(x)
+        hist.append(np.linalg.norm(r) / bnorm)
+        if np.linalg.norm(r) <= tol or its >= max_it:
+            break
+        x, its = _idr_cycle(apply_K, apply_Pinv, b, x, r, P, s, tol, its, max_it, kappa, hist)
+    return x, its, hist
+
+
+def _idr_cycle(apply_K, apply_Pinv, b, x, r, P, s, tol, its, max_it, kappa, hist):
+    """IDR(s) from (x, r) until the recursive residual meets tol or max_it is reached."""
+    n = b.shape[0]
+    bnorm = np.linalg.norm(b)
+    G = np.zeros((n, s))
+    U = np.zeros((n, s))
+    Ms = np.eye(s)
+    om = 1.0
+    while np.linalg.norm(r) > tol and its < max_it:
+        f = P.T @ r
+        for k in range(s):
+            # v = r - G[:, k:] c with M[k:, k:] c = f[k:] (lower triangular)
+            c = np.linalg.solve(Ms[k:, k:], f[k:])
+            v = r - G[:, k:] @ c
+            v = apply_Pinv(v)
+            U[:, k] = U[:, k:] @ c + om * v
+            G[:, k] = apply_K(U[:, k])
+            its += 1
+            for i in range(k):                       # G_k orthogonal to p_0 .. p_{k-1}
+                alpha = (P[:, i] @ G[:, k]) / Ms[i, i]
+                G[:, k] -= alpha * G[:, i]
+                U[:, k] -= alpha * U[:, i]
+            Ms[k:, k] = P[:, k:].T @ G[:, k]
+            beta = f[k] / Ms[k, k]
+            r = r - beta * G[:, k]
+            x = x + beta * U[:, k]
+            hist.append(np.linalg.norm(r) / bnorm)
+            if np.linalg.norm(r) <= tol or its >= max_it:
+                break
+            if k + 1 < s:
+                f[k + 1:] = f[k + 1:] - beta * Ms[k + 1:, k]
+        if np.linalg.norm(r) <= tol or its >= max_it:
+            break
+        # dimension-reduction step
+        v = apply_Pinv(r)
+        t = apply_K(v)
+        its += 1
+        tt, tr = t @ t, t @ r
+        om = tr / tt
+        rho = abs(tr) / (np.sqrt(tt) * np.linalg.norm(r))
+        if rho < kappa:
+            om = om * kappa / rho
+        x = x + om * v
+        r = r - om * t
+        hist.append(np.linalg.norm(r) / bnorm)
+    return x, its

@@ -204,6 +204,11 @@ struct stokes_ctx {
     float *tune_x = nullptr, *tune_r = nullptr, *tune_b = nullptr;   // autotuner work (FP32, finest level)
     double* tune_up = nullptr;                                        // autotuner solution vector
     OctCtx* oct = nullptr;                           // set for octree meshes (stokes_setup_octree)
+    // IDR(s) workspace (allocated on the first IDR solve): G, U, P (s vectors each), r, v, t, tmp
+    int idr_alloc_s = 0;
+    double *idr_G = nullptr, *idr_U = nullptr, *idr_P = nullptr, *idr_r = nullptr, *idr_v = nullptr,
+           *idr_t = nullptr, *idr_tmp = nullptr, *idr_c = nullptr;
+    cudaStream_t idr_stream = nullptr;
 };
 
 namespace {
@@ -794,11 +799,166 @@ stokes_status fgmres(stokes_ctx* c, int prec, const double* b, double* x, double
     return STOKES_OK;
 }
 
+// ---------------------------------------------------------------- IDR(s)
+// The memory-light outer solver of Section 3.5: IDR(s) with bi-orthogonalisation and right
+// preconditioning by P^-1 (M. B. van Gijzen, P. Sonneveld, ACM TOMS 38 (2011), Alg. 913), omega
+// by "maintaining the convergence" (kappa = 0.7). 3s + 4 vectors of N instead of FGMRES's 2 m + 1.
+// The shadow space: splitmix64 uniforms u01 - 1/2 with seeds 1907100 + i, orthonormalised.
+// Iterations count preconditioned operator applications, as for FGMRES.
+stokes_status ensure_idr(stokes_ctx* c, int sdim) {
+    c->N = active_nu(c) + active_np(c);
+    const size_t N = c->N;
+    if (c->idr_alloc_s < sdim) {
+        CKS(dalloc(c, &c->idr_G, size_t(sdim) * N));
+        CKS(dalloc(c, &c->idr_U, size_t(sdim) * N));
+        CKS(dalloc(c, &c->idr_P, size_t(sdim) * N));
+        if (!c->idr_r) {
+            for (double** q : {&c->idr_r, &c->idr_v, &c->idr_t, &c->idr_tmp}) CKS(dalloc(c, q, N));
+            CKS(dalloc(c, &c->idr_c, 16));
+        }
+        c->idr_alloc_s = sdim;
+    }
+    if (!c->bvec) CKS(dalloc(c, &c->bvec, N));
+    // shadow space (rebuilt every solve: cheap, and independent of earlier calls)
+    for (int i = 0; i < sdim; ++i) {
+        double* pi = c->idr_P + size_t(i) * N;
+        CK(launch_splitmix_vector(N, uint64_t(1907100 + i), nullptr, pi, c->idr_stream));
+        for (int j = 0; j < i; ++j) {
+            double d = 0.0;
+            CKS(dot(c, N, c->idr_P + size_t(j) * N, pi, c->idr_stream, &d));
+            CK(launch_axpby(N, -d, c->idr_P + size_t(j) * N, 1.0, pi, c->idr_stream));
+        }
+        double nn = 0.0;
+        CKS(dot(c, N, pi, pi, c->idr_stream, &nn));
+        CK(launch_axpby(N, 1.0 / std::sqrt(nn), pi, 0.0, pi, c->idr_stream));
+    }
+    return STOKES_OK;
+}
+
+stokes_status idr_solve(stokes_ctx* c, int prec, const double* b, double* x, double rtol, int max_it,
+                        stokes_solve_info* info, cudaStream_t s) {
+    const int sd = c->opt.idr_s;   // workspace and shadow space: ensure_idr (stokes_solve)
+    const size_t N = c->N;
+    double *G = c->idr_G, *U = c->idr_U, *P = c->idr_P, *r = c->idr_r, *v = c->idr_v, *t = c->idr_t,
+           *tmp = c->idr_tmp;
+    auto col = [&](double* A, int i) { return A + size_t(i) * N; };
+    double bnorm2 = 0.0;
+    CKS(dot(c, N, b, b, s, &bnorm2));
+    const double bnorm = std::sqrt(bnorm2);
+    stokes_status st = STOKES_NOT_CONVERGED;
+    int its = 0;
+    double rnorm = 0.0;
+    if (bnorm == 0.0) {
+        CK(cudaMemsetAsync(x, 0, N * sizeof(double), s));
+        st = STOKES_OK;
+    } else {
+      // passes: IDR(s) from r = b - K x; a new pass starts when the recursively updated residual met
+      // the tolerance but the true one did not (at most 10 restarts)
+      const double tol = rtol * bnorm;
+      for (int pass = 0; pass < 11; ++pass) {
+        CKS(apply_stokes(c, x, r, s));
+        CK(launch_axpby(N, 1.0, b, -1.0, r, s));                              // r = b - K x
+        double rr = 0.0;
+        CKS(dot(c, N, r, r, s, &rr));
+        rnorm = std::sqrt(rr);
+        if (!std::isfinite(rnorm)) { st = STOKES_BREAKDOWN; break; }
+        if (rnorm <= tol) { st = STOKES_OK; break; }
+        if (its >= max_it) { st = STOKES_NOT_CONVERGED; break; }
+        st = STOKES_NOT_CONVERGED;
+        CK(cudaMemsetAsync(G, 0, size_t(sd) * N * sizeof(double), s));
+        CK(cudaMemsetAsync(U, 0, size_t(sd) * N * sizeof(double), s));
+        std::vector<double> Ms(size_t(sd) * sd, 0.0), f(sd), cc(sd), dots(sd + 1);
+        for (int i = 0; i < sd; ++i) Ms[size_t(i) * sd + i] = 1.0;
+        auto M = [&](int i, int j) -> double& { return Ms[size_t(i) * sd + j]; };
+        double om = 1.0;
+        auto multidot = [&](int k, const double* V, const double* w, double* out) -> stokes_status {
+            CK(launch_multidot(N, k, V, N, w, c->partials, c->dots, s));
+            return fetch(c, k, s, out);
+        };
+        bool done = false;
+        while (!done && its < max_it) {
+            CKS(multidot(sd, P, r, f.data()));                                    // f = P^T r
+            for (int k = 0; k < sd && !done; ++k) {
+                // c = M[k:, k:]^-1 f[k:] (lower triangular)
+                for (int i = k; i < sd; ++i) {
+                    double acc = f[i];
+                    for (int j = k; j < i; ++j) acc -= M(i, j) * cc[j - k];
+                    cc[i - k] = acc / M(i, i);
+                }
+                CK(cudaMemcpyAsync(c->idr_c, cc.data(), sizeof(double) * (sd - k), cudaMemcpyHostToDevice, s));
+                CK(cudaMemcpyAsync(v, r, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                CK(launch_multiaxpy(N, sd - k, col(G, k), N, c->idr_c, v, -1.0, s));   // v = r - G c
+                CKS(precondition(c, prec, v, tmp, s));                               // tmp = P^-1 v
+                CK(cudaMemsetAsync(t, 0, N * sizeof(double), s));
+                CK(launch_multiaxpy(N, sd - k, col(U, k), N, c->idr_c, t, 1.0, s));   // t = U[:, k:] c
+                CK(launch_axpby(N, om, tmp, 1.0, t, s));                                // t += om P^-1 v
+                CK(cudaMemcpyAsync(col(U, k), t, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                CKS(apply_stokes(c, col(U, k), col(G, k), s));                          // G_k = K U_k
+                ++its;
+                for (int i = 0; i < k; ++i) {
+                    double pg = 0.0;
+                    CKS(dot(c, N, col(P, i), col(G, k), s, &pg));
+                    const double alpha = pg / M(i, i);
+                    CK(launch_axpby(N, -alpha, col(G, i), 1.0, col(G, k), s));
+                    CK(launch_axpby(N, -alpha, col(U, i), 1.0, col(U, k), s));
+                }
+                CKS(multidot(sd - k, col(P, k), col(G, k), dots.data()));              // M[k:, k] = P^T G_k
+                for (int i = k; i < sd; ++i) M(i, k) = dots[i - k];
+                if (!std::isfinite(M(k, k)) || M(k, k) == 0.0) { st = STOKES_BREAKDOWN; done = true; break; }
+                const double beta = f[k] / M(k, k);
+                CK(launch_axpby(N, -beta, col(G, k), 1.0, r, s));
+                CK(launch_axpby(N, beta, col(U, k), 1.0, x, s));
+                CKS(dot(c, N, r, r, s, &rr));
+                rnorm = std::sqrt(rr);
+                if (!std::isfinite(rnorm)) { st = STOKES_BREAKDOWN; done = true; break; }
+                if (rnorm <= tol) { st = STOKES_OK; done = true; break; }
+                if (its >= max_it) { done = true; break; }
+                for (int i = k + 1; i < sd; ++i) f[i] -= beta * M(i, k);
+            }
+            if (done || its >= max_it) break;
+            // dimension-reduction step
+            CKS(precondition(c, prec, r, v, s));
+            CKS(apply_stokes(c, v, t, s));
+            ++its;
+            double tt = 0.0, tr = 0.0;
+            CKS(dot(c, N, t, t, s, &tt));
+            CKS(dot(c, N, t, r, s, &tr));
+            if (!(tt > 0.0) || !std::isfinite(tt)) { st = STOKES_BREAKDOWN; break; }
+            om = tr / tt;
+            const double rho = std::fabs(tr) / (std::sqrt(tt) * rnorm);
+            if (rho < 0.7) om = om * 0.7 / rho;
+            CK(launch_axpby(N, om, v, 1.0, x, s));
+            CK(launch_axpby(N, -om, t, 1.0, r, s));
+            CKS(dot(c, N, r, r, s, &rr));
+            rnorm = std::sqrt(rr);
+            if (!std::isfinite(rnorm)) { st = STOKES_BREAKDOWN; break; }
+            if (rnorm <= tol) { st = STOKES_OK; break; }
+        }
+        if (st == STOKES_BREAKDOWN) break;
+      }
+    }
+    // pressure with zero mean, true residual
+    CKS(remove_pressure_mean(c, x, s));
+    CKS(apply_stokes(c, x, r, s));
+    CK(launch_axpby(N, 1.0, b, -1.0, r, s));
+    double rt = 0.0;
+    CKS(dot(c, N, r, r, s, &rt));
+    if (info) {
+        info->iterations = its;
+        info->rel_residual = bnorm > 0 ? rnorm / bnorm : 0.0;
+        info->rel_residual_true = bnorm > 0 ? std::sqrt(rt) / bnorm : 0.0;
+        info->status = st;
+    }
+    if (st != STOKES_OK) return fail(st, st == STOKES_BREAKDOWN ? "IDR(s) breakdown" : "IDR(s) reached max_it");
+    return STOKES_OK;
+}
+
 stokes_status validate_options(const stokes_options& o) {
     if (o.cheb_degree < 1 || o.smoothing_range <= 1.0 || o.eig_safety <= 0.0 || o.lanczos_steps < 1 ||
         o.schur_degree < 1 || o.restart < 1 || o.restart > 500 || (o.outer_arith != 0 && o.outer_arith != 1) ||
         (o.vmult_kernel != 0 && o.vmult_kernel != 1) || (o.graphs != 0 && o.graphs != 1) ||
-        (o.precond_kind != 0 && o.precond_kind != 1))
+        (o.precond_kind != 0 && o.precond_kind != 1) || (o.outer_solver != 0 && o.outer_solver != 1) ||
+        o.idr_s < 1 || o.idr_s > 8)
         return fail(STOKES_EINVAL, "bad options");
     return STOKES_OK;
 }
@@ -1260,6 +1420,8 @@ void stokes_default_options(stokes_options* opt) {
     opt->vmult_kernel = 0;
     opt->graphs = 1;
     opt->precond_kind = 0;
+    opt->outer_solver = 0;
+    opt->idr_s = 2;
 }
 
 const char* stokes_strerror(stokes_status s) {
@@ -1535,7 +1697,12 @@ stokes_status stokes_solve(stokes_ctx* c, int vcycle_prec, const double* rhs, do
     if (!(rtol > 0.0) || max_it < 1) return fail(STOKES_EINVAL, "bad rtol or max_it");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const auto t0 = std::chrono::steady_clock::now();
-    CKS(ensure_krylov(c));
+    if (c->opt.outer_solver == 1) {
+        c->idr_stream = s;
+        CKS(ensure_idr(c, c->opt.idr_s));
+    } else {
+        CKS(ensure_krylov(c));
+    }
     const size_t nu = active_nu(c), np = active_np(c);
     const double* b = rhs;
     if (!b) {
@@ -1543,7 +1710,8 @@ stokes_status stokes_solve(stokes_ctx* c, int vcycle_prec, const double* rhs, do
         CK(cudaMemsetAsync(c->bvec + nu, 0, np * sizeof(double), s));
         b = c->bvec;
     }
-    stokes_status st = fgmres(c, vcycle_prec, b, up, rtol, max_it, info, s);
+    stokes_status st = c->opt.outer_solver == 1 ? idr_solve(c, vcycle_prec, b, up, rtol, max_it, info, s)
+                                                 : fgmres(c, vcycle_prec, b, up, rtol, max_it, info, s);
     const auto t1 = std::chrono::steady_clock::now();
     if (info) {
         info->seconds = std::chrono::duration<double>(t1 - t0).count();
@@ -1641,8 +1809,10 @@ stokes_status stokes_batch_solve(int n_problems, stokes_ctx* const* ctxs, int vc
                                  const double* const* rhs_devs, double* const* up_devs, double rtol, int max_it,
                                  stokes_solve_info* infos, void* const* streams) {
     if (n_problems < 1 || !ctxs || !up_devs) return fail(STOKES_EINVAL, "null argument or no problems");
-    for (int i = 0; i < n_problems; ++i)
+    for (int i = 0; i < n_problems; ++i) {
         if (ctxs[i] && ctxs[i]->oct) return fail(STOKES_EMESH, "batched solves take uniform meshes");
+        if (ctxs[i] && ctxs[i]->opt.outer_solver != 0) return fail(STOKES_EINVAL, "batched solves use FGMRES");
+    }
     if (vcycle_prec != STOKES_FP32 && vcycle_prec != STOKES_FP64) return fail(STOKES_EINVAL, "bad precision");
     if (!(rtol > 0.0) || max_it < 1) return fail(STOKES_EINVAL, "bad rtol or max_it");
     for (int i = 0; i < n_problems; ++i) {

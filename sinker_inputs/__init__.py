@@ -96,6 +96,7 @@ def workload(name: str) -> SinkerProblem:
     cube128 : 128^3 cells, 8 levels, 16 sinkers, viscosity ratio 1e6 (~51M velocity DoFs)
     Smaller parity cases: cube16 (16^3, 5 levels, 4 sinkers, DR 1e4), cube32 (32^3, 6 levels, 8 sinkers, DR 1e4).
     Profiling case: cube96 (96^3, 6 levels, 8 sinkers, DR 1e4; FP32 vectors of 86 MB exceed L2).
+    Largest case: cube192 (192^3, 7 levels down to 3^3, 16 sinkers, DR 1e6; ~171M velocity DoFs).
     Sinker centres come from splitmix64 with seed 1907 + k (k = 1, 2, 3 for cube8, cube64, cube128).
     """
     if name == "cube8":
@@ -105,6 +106,8 @@ def workload(name: str) -> SinkerProblem:
         return dr_problem(64, 7, 8, 1e4, 1909, name)
     if name == "cube128":
         return dr_problem(128, 8, 16, 1e6, 1910, name)
+    if name == "cube192":
+        return dr_problem(192, 7, 16, 1e6, 1916, name)
     if name == "cube96":
         return dr_problem(96, 6, 8, 1e4, 1915, name)
     if name == "cube16":

@@ -464,3 +464,63 @@ def test_galerkin_identity_and_symmetric_vcycle_constant_viscosity():
     x = si.uniform(61, free.size) * free
     y = si.uniform(62, free.size) * free
     assert abs(Gm.vcycle(x) @ y - x @ Gm.vcycle(y)) < 1e-12 * abs(Gm.vcycle(x) @ y)
+
+
+def _bicgstab(A, b, rt, steps):
+    """Textbook BiCGSTAB (Saad, Iterative Methods, Alg. 7.7) with shadow vector rt, no preconditioner."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rho = rt @ r
+    for _ in range(steps):
+        Ap = A @ p
+        alpha = rho / (rt @ Ap)
+        sv = r - alpha * Ap
+        As = A @ sv
+        om = (As @ sv) / (As @ As)
+        x = x + alpha * p + om * sv
+        r = sv - om * As
+        rho_new = rt @ r
+        p = r + (rho_new / rho) * (alpha / om) * (p - om * Ap)
+        rho = rho_new
+    return x
+
+
+def test_idr1_equals_bicgstab():
+    """IDR(1) with omega = the local minimiser is BiCGSTAB in exact arithmetic: after 2k operator
+    applications its iterate equals BiCGSTAB's after k steps with the same shadow vector."""
+    rng = np.random.default_rng(11)
+    n = 40
+    A = np.eye(n) * 4 + rng.standard_normal((n, n)) * 0.3
+    b = rng.standard_normal(n)
+    P = krylov.idr_shadow_space(n, 1, seed=77)
+    for k in (1, 2, 3, 5):
+        x_idr, its, _ = krylov.idr_s(lambda v: A @ v, lambda v: v, b, s=1, rtol=1e-30, max_it=2 * k, P=P,
+                                     kappa=0.0)
+        assert its == 2 * k
+        x_bi = _bicgstab(A, b, P[:, 0], k)
+        assert np.linalg.norm(x_idr - x_bi) <= 1e-10 * np.linalg.norm(x_bi)
+
+
+def test_idr_s_finite_termination():
+    """IDR(s) needs at most n + n/s operator applications for an n x n system (exact arithmetic);
+    with s = 4 on n = 24 it reaches 1e-10 within that bound."""
+    rng = np.random.default_rng(12)
+    n, s = 24, 4
+    A = np.diag(np.linspace(1, 10, n)) + 0.2 * rng.standard_normal((n, n))
+    b = rng.standard_normal(n)
+    x, its, _ = krylov.idr_s(lambda v: A @ v, lambda v: v, b, s=s, rtol=1e-10, max_it=400)
+    assert its <= n + n // s + 2
+    assert np.linalg.norm(A @ x - b) <= 1e-9 * np.linalg.norm(b)
+
+
+def test_idr_stokes_matches_fgmres():
+    """IDR(2) with the block-triangular GMG preconditioner reaches the FGMRES solution (cube4)."""
+    p, m, G, ops, F = _problem("cube4")
+    Pc = krylov.StokesPreconditioner(ops, G)
+    b = np.concatenate([F, np.zeros(m.n_p)])
+    xf, _, _ = krylov.fgmres(ops.apply_stokes, Pc.apply, b, rtol=1e-12)
+    xi, its, _ = krylov.idr_s(ops.apply_stokes, Pc.apply, b, s=2, rtol=1e-12, max_it=3000)
+    xf, xi = krylov.zero_mean_pressure(ops, xf), krylov.zero_mean_pressure(ops, xi)
+    assert np.linalg.norm(b - ops.apply_stokes(xi)) <= 1e-10 * np.linalg.norm(b)
+    assert np.abs(xi - xf).max() <= 1e-8 * np.abs(xf).max()
