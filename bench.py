@@ -59,8 +59,9 @@ def parse():
     ap.add_argument("--solve-report", action="store_true",
                     help="one FP32-V-cycle and one FP64-V-cycle solve of the workload: iterations, times, "
                          "true FP64 residuals and the difference of the two solutions (any size)")
-    ap.add_argument("--outer", default="fgmres", choices=["fgmres", "idr", "both"],
-                    help="with --solve-report: outer solver(s) of the FP32/FP64 V-cycle solves (idr = IDR(2))")
+    ap.add_argument("--outer", default="fgmres", choices=["fgmres", "idr", "gmres", "both", "all"],
+                    help="with --solve-report: outer solver(s) of the FP32/FP64 V-cycle solves (idr = IDR(2), "
+                         "gmres = GMRES(50) with the fixed preconditioner; both = idr + fgmres; all = the three)")
     ap.add_argument("--fp32-only", action="store_true",
                     help="with --solve-report: skip the FP64-V-cycle legs (largest problems)")
     ap.add_argument("--precond", default="triangular", choices=["triangular", "both"],
@@ -594,22 +595,27 @@ def run_report(args):
     prob = si.workload(args.workload)
     t0 = time.perf_counter()
     opts = capi.stokes_default_options()
-    if args.outer == "idr":
-        opts.outer_solver = 1
+    solver_id = {"fgmres": 0, "idr": 1, "gmres": 2}
+    names = {0: "FGMRES(50)", 1: "IDR(2)", 2: "GMRES(50)"}
+    opts.outer_solver = solver_id.get(args.outer, 0)
     ctx = capi.stokes_setup_problem(prob, options=opts)
     setup_s = time.perf_counter() - t0
     N = ctx.n_u + ctx.n_p
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    out = {"outer": "IDR(2)" if args.outer == "idr" else "FGMRES(50)"}
+    out = {"outer": names[opts.outer_solver]}
     sols = {}
-    if args.outer == "both":   # IDR(2) legs first, on a context of their own (FGMRES basis not allocated yet)
+    extra = {"both": ("idr",), "all": ("idr", "gmres")}.get(args.outer, ())
+    for other in extra:   # other solvers first, each on a context of its own (main basis not allocated yet)
         oi = capi.stokes_default_options()
-        oi.outer_solver = 1
+        oi.outer_solver = solver_id[other]
         ci = capi.stokes_setup_problem(prob, options=oi)
-        legs = (("idr_fp32_vcycle", capi.STOKES_FP32),) if args.fp32_only else \
-            (("idr_fp32_vcycle", capi.STOKES_FP32), ("idr_fp64_vcycle", capi.STOKES_FP64))
+        legs = ((other + "_fp32_vcycle", capi.STOKES_FP32),) if args.fp32_only else \
+            ((other + "_fp32_vcycle", capi.STOKES_FP32), (other + "_fp64_vcycle", capi.STOKES_FP64))
         for tag, prec in legs:
             up = torch.zeros(N, dtype=torch.float64, device="cuda")
+            for _ in range(min(args.warmup, 1)):
+                capi.stokes_solve(ci, prec, None, up, rtol=RTOL, max_it=5000, check=False)
+                up.zero_()
             e0.record()
             info = capi.stokes_solve(ci, prec, None, up, rtol=RTOL, max_it=5000, check=False)
             e1.record()

@@ -103,7 +103,7 @@ typedef struct {
     double eig_safety;          /* lam_hi = safety * Lanczos estimate of lambda_max(D^-1 A) (1.2) */
     int lanczos_steps;          /* Lanczos steps for lambda_max (12) */
     int schur_degree;           /* Chebyshev degree of S_hat^-1 on M_p, interval [1/8, 27/8] (5) */
-    int restart;                /* FGMRES restart length (50, Section 3.5) */
+    int restart;                /* FGMRES restart length (50, Section 3.4) */
     int outer_arith;            /* arithmetic of the FP64-interface outer operator: 0 = native FP64;
                                    1 = double-float (pairs of floats, ~48-bit significand) on the FP32
                                    units for every block that contains A (default: 1.6 ms vs 1.95 ms at
@@ -121,14 +121,21 @@ typedef struct {
                                    z_u = A_hat^-1 (r_u - B^T z_p); 1 = block-diagonal P_D = diag(A, S) of
                                    Section 2.2 / Table 1: z_u = A_hat^-1 r_u, z_p = S_hat^-1 r_p */
     int outer_solver;           /* 0 = FGMRES(restart) (default); 1 = IDR(idr_s), the memory-light solver of
-                                   Section 3.5 (van Gijzen & Sonneveld's bi-orthogonal IDR(s) with right
+                                   Section 3.4 (van Gijzen & Sonneveld's bi-orthogonal IDR(s) with right
                                    preconditioning, 3 idr_s + 4 vectors; shadow space from splitmix64
-                                   seeds 1907100 + i, orthonormalised). Not for stokes_batch_solve. */
+                                   seeds 1907100 + i, orthonormalised). Not for stokes_batch_solve.
+                                   2 = GMRES(restart) with the preconditioner as one fixed linear map
+                                   (Section 3.4: the V-cycle and S_hat^-1 are fixed polynomials and an
+                                   exact coarse solve): restart + 2 vectors instead of 2 restart + 2; a
+                                   cycle ends with x += P^-1 (V y) (one preconditioner application more
+                                   per cycle, not counted in iterations) and the solve ends when the
+                                   true residual b - K x, recomputed after the cycle, meets rtol. */
     int idr_s;                  /* shadow-space dimension of IDR(s), 1..8 (2) */
 } stokes_options;
 
 typedef struct {
-    int iterations;             /* FGMRES iterations (preconditioner applications) */
+    int iterations;             /* Krylov iterations: FGMRES / GMRES Arnoldi steps, IDR(s) preconditioned
+                                   operator applications */
     double rel_residual;        /* final recurrence estimate |g_k| / ||b|| */
     double rel_residual_true;   /* ||b - K x|| / ||b|| recomputed in FP64 after the solve */
     double seconds;             /* wall time of the solve on the host clock */
@@ -344,8 +351,9 @@ stokes_status stokes_schur_inverse_noalloc(int n, const double* mu_dev, const do
 /* Kernel classes timed by stokes_profile: 0 velocity cell kernel FP32, 1 velocity
  * cell kernel FP64, 2 fused A+B^T+B cell kernel, 3 B^T cell kernel, 4 pressure mass
  * cell kernel, 5 transfers, 6 smoother / residual vector kernels, 7 Krylov vector
- * kernels, 8 coarse solve, 9 precision casts. */
-#define STOKES_PROF_NCLASS 10
+ * kernels, 8 coarse solve, 9 precision casts, 10 the outer operator applied in native FP64
+ * for the solvers' restart and final residuals (uniform meshes). */
+#define STOKES_PROF_NCLASS 11
 /* enable = 1: record a CUDA event pair around every kernel launch the library
  * issues from now on (adds two event records per launch); 0: stop. Process-wide,
  * for single-threaded use. */

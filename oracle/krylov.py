@@ -1,11 +1,12 @@
-"""Outer Stokes solve (Section 2.2): block-triangular preconditioner and FGMRES.
+"""Outer Stokes solve (Section 2.2): block-triangular preconditioner and FGMRES; the
+memory-light alternatives of Section 3.4 (GMRES with a fixed preconditioner, IDR(s)).
 
 P = [[A, B^T], [0, -S]] (eq. stokes_precond); applying P^-1 to r = [r_u; r_p]:
     z_p = -S_hat^-1 r_p,   z_u = A_hat^-1 (r_u - B^T z_p),
 with A_hat^-1 one GMG V-cycle and S_hat^-1 a Jacobi-Chebyshev iteration on the
 1/mu-weighted pressure mass matrix M_p (Section 2.2.2). Because S_hat^-1 is an
 inner iteration the outer method is flexible GMRES, restart 50 (Section 2.2.2,
-Section 3.5). Readings: S_hat^-1 is degree 5 (5 updates, zero initial guess)
+Section 3.4). Readings: S_hat^-1 is degree 5 (5 updates, zero initial guess)
 on the fixed interval [1/8, 27/8] that bounds the spectrum of diag(M_p)^-1 M_p
 for trilinear hexahedra (A. J. Wathen, IMA J. Numer. Anal. 7 (1987), element
 eigenvalue bound: 1D element mass [[2,1],[1,2]] h/6 scaled by its diagonal has
@@ -58,8 +59,9 @@ class StokesPreconditioner:
 def fgmres(apply_K, apply_Pinv, b, rtol=1e-8, restart=50, max_it=1000, x0=None):
     """Right-preconditioned flexible GMRES (Y. Saad, SIAM J. Sci. Comput. 14 (1993);
     Iterative Methods, Alg. 9.6) with modified Gram-Schmidt and Givens rotations.
-    Stops when the recurrence residual |g_{j+1}| <= rtol * ||b||.
-    Returns (x, iterations, list of relative residual estimates)."""
+    A cycle ends when the recurrence residual |g_{j+1}| <= rtol * ||b||; the solve ends when the
+    true residual b - K x, recomputed after the cycle, meets the tolerance too (else a new cycle
+    starts from it). Returns (x, iterations, list of relative residual estimates)."""
     n = b.shape[0]
     x = np.zeros(n) if x0 is None else x0.copy()
     bnorm = np.linalg.norm(b)
@@ -110,9 +112,76 @@ def fgmres(apply_K, apply_Pinv, b, rtol=1e-8, restart=50, max_it=1000, x0=None):
                 break
         y = np.linalg.solve(np.triu(H[:k, :k]), g[:k])
         x = x + Z[:k].T @ y
-        if abs(g[k]) <= rtol * bnorm:
-            break
+        # the loop head recomputes b - K x: the solve ends when the true residual meets rtol
     return x, its, history
+
+
+def gmres(apply_K, apply_Pinv, b, rtol=1e-8, restart=50, max_it=1000, x0=None):
+    """Right-preconditioned GMRES(restart) (Y. Saad, Iterative Methods for Sparse Linear Systems,
+    2nd ed., Alg. 9.5) with modified Gram-Schmidt and Givens rotations: the Arnoldi basis V of
+    K P^-1 is kept, the preconditioned vectors are not, and a cycle ends with x += P^-1 (V y).
+    This needs P^-1 to be one fixed linear map, which holds for the block-triangular P with a
+    V-cycle (Chebyshev smoothing on fixed intervals, exact coarse solve) and a fixed-degree
+    Chebyshev S_hat^-1; it halves the Krylov memory of flexible GMRES (Section 3.4).
+    A cycle ends when the recurrence residual |g_{j+1}| <= rtol ||b||; the next cycle starts
+    from the true residual b - K x and the solve stops only when that meets the tolerance (a
+    P^-1 in lower precision makes the final update differ slightly from the combination the
+    recurrence assumed). Returns (x, Arnoldi iterations, list of relative residual estimates)."""
+    n = b.shape[0]
+    x = np.zeros(n) if x0 is None else x0.copy()
+    bnorm = np.linalg.norm(b)
+    history = []
+    its = 0
+    if bnorm == 0.0:
+        return x, 0, [0.0]
+    while True:
+        r = b - apply_K(x)
+        beta = np.linalg.norm(r)
+        history.append(beta / bnorm)
+        if beta <= rtol * bnorm or its >= max_it:
+            break
+        m = restart
+        V = np.zeros((m + 1, n))
+        H = np.zeros((m + 1, m))
+        g = np.zeros(m + 1)
+        g[0] = beta
+        V[0] = r / beta
+        k = 0
+        for j in range(m):
+            w = apply_K(apply_Pinv(V[j]))
+            for i in range(j + 1):
+                H[i, j] = w @ V[i]
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            if H[j + 1, j] != 0.0:
+                V[j + 1] = w / H[j + 1, j]
+            its += 1
+            k = j + 1
+            # least-squares residual of the (j+2) x (j+1) Hessenberg problem, by Givens rotations
+            R, gk = _givens_triangularise(H[:k + 1, :k], g[:k + 1])
+            history.append(abs(gk[k]) / bnorm)
+            if abs(gk[k]) <= rtol * bnorm or H[j + 1, j] == 0.0 or its >= max_it:
+                break
+        R, gk = _givens_triangularise(H[:k + 1, :k], g[:k + 1])
+        y = np.linalg.solve(np.triu(R[:k, :k]), gk[:k])
+        x = x + apply_Pinv(V[:k].T @ y)
+    return x, its, history
+
+
+def _givens_triangularise(H, g):
+    """Applies the Givens rotations that make the (k+1) x k upper Hessenberg H upper triangular
+    to H and g; returns the rotated copies (the last entry of g is the least-squares residual)."""
+    R = H.copy()
+    g = g.copy()
+    k = R.shape[1]
+    for j in range(k):
+        d = np.hypot(R[j, j], R[j + 1, j])
+        c, s = R[j, j] / d, R[j + 1, j] / d
+        top = c * R[j, :] + s * R[j + 1, :]
+        R[j + 1, :] = -s * R[j, :] + c * R[j + 1, :]
+        R[j, :] = top
+        g[j], g[j + 1] = c * g[j], -s * g[j]
+    return R, g
 
 
 def zero_mean_pressure(ops, up):
@@ -161,7 +230,7 @@ def idr_s(apply_K, apply_Pinv, b, s=2, rtol=1e-8, max_it=1000, x0=None, P=None, 
     "Algorithm 913: an elegant IDR(s) variant that efficiently exploits bi-orthogonality
     properties", ACM TOMS 38 (2011)); the residual-smoothing-free variant with the "maintain the
     convergence" choice of omega (|cos| of the angle below kappa is lifted to kappa).
-    The memory-light alternative to FGMRES of Section 3.5: 3s + 4 vectors.
+    The memory-light alternative to FGMRES of Section 3.4: 3s + 4 vectors.
     Stops when the recursively updated residual satisfies ||r|| <= rtol ||b||; if the true
     residual b - K x is then still above the tolerance (the recursion drifts from it, more so
     with an inexact preconditioner), IDR restarts from x with r = b - K x (at most 10 times).

@@ -100,7 +100,7 @@ _SIGS = {
 }
 
 PROF_CLASSES = ["vmult_A_fp32", "vmult_A_fp64", "stokes_fp64", "bt_fp64", "mass_p", "transfer",
-                "smoother_vec", "krylov_vec", "coarse", "cast"]
+                "smoother_vec", "krylov_vec", "coarse", "cast", "residual_fp64"]
 
 
 def load(path: str = LIB_PATH):

@@ -74,11 +74,13 @@ void prof_begin(int, cudaStream_t s) {
     g_open = take_event();
     cudaEventRecord(g_open, s);
 }
+thread_local int t_override = -1;
+void prof_override(int cls) { t_override = cls; }
 void prof_end(int cls, cudaStream_t s) {
     if (!g_prof_on || !g_open) return;
     cudaEvent_t e = take_event();
     cudaEventRecord(e, s);
-    g_recs.push_back({cls, g_open, e});
+    g_recs.push_back({t_override >= 0 ? t_override : cls, g_open, e});
     g_open = nullptr;
     if (g_recs.size() > 200000) drain();
 }
@@ -514,14 +516,22 @@ stokes_status schur_inverse(stokes_ctx* c, const double* rp, double* zp, cudaStr
     return STOKES_OK;
 }
 
-stokes_status apply_stokes(stokes_ctx* c, const double* src, double* dst, cudaStream_t s) {
+// dst = K src. native: FP64 arithmetic whatever outer_arith says; the solvers use it for the
+// residuals b - K x they restart from and report, so that the ~2^-47 relative rounding of the
+// double-float operator (amplified by the viscosity contrast) enters only the Krylov recurrences,
+// which the restarts correct like iterative refinement.
+stokes_status apply_stokes(stokes_ctx* c, const double* src, double* dst, cudaStream_t s, bool native = false) {
     if (c->oct) {
         const size_t nu = 3 * c->oct->act.nu_nodes;
         CK(launch_oct_active(c->oct->act, src, src + nu, dst, dst + nu, true, true, true, s));
         return STOKES_OK;
     }
     Level& F = c->lev[c->L - 1];
-    CK(launch_stokes_blocks(F.g, F.v64.mu, src, src + F.g.n_u, dst, dst + F.g.n_u, true, true, true, c->opt.outer_arith == 1, s));
+    if (native) prof_override(PROF_RESID_F64);
+    const cudaError_t e = launch_stokes_blocks(F.g, F.v64.mu, src, src + F.g.n_u, dst, dst + F.g.n_u, true, true,
+                                               true, c->opt.outer_arith == 1 && !native, s);
+    prof_override(-1);
+    CK(e);
     return STOKES_OK;
 }
 
@@ -560,7 +570,8 @@ stokes_status ensure_krylov(stokes_ctx* c) {
     c->N = active_nu(c) + active_np(c);
     c->ldv = c->N + (c->N & 1);   // even row stride: 16-byte aligned entry pairs (krylov.cu)
     CKS(dalloc(c, &c->V, size_t(m + 1) * c->ldv));
-    CKS(dalloc(c, &c->Z, size_t(m) * c->N));
+    // flexible GMRES keeps the m preconditioned vectors; GMRES (outer_solver 2) one work vector
+    CKS(dalloc(c, &c->Z, c->opt.outer_solver == 2 ? c->ldv : size_t(m) * c->N));
     CKS(dalloc(c, &c->w, c->N));
     CKS(dalloc(c, &c->bvec, c->N));
     CKS(dalloc(c, &c->hdev, size_t(2 * (m + 4))));
@@ -580,6 +591,13 @@ stokes_status remove_pressure_mean(stokes_ctx* c, double* up, cudaStream_t s) {
 // phase's kernels on the run's stream and a small device->host copy; complete() runs the host
 // part once that stream has finished. One problem (stokes_solve) or many in lock step
 // (stokes_batch_solve) use the same code.
+// With flexible = false it is GMRES(restart) with a fixed preconditioner (outer_solver 2,
+// Section 3.4): P^-1 V_j goes to one work vector instead of the stored Z_j, and a cycle ends with
+// x += P^-1 (V y).
+// The solve ends only when the true residual b - K x, recomputed in the final phase, meets the
+// tolerance; otherwise a new cycle starts from it. The recurrence can run ahead of the true
+// residual: with the FP32 V-cycle P^-1 (V y) differs slightly from the combination GMRES assumed,
+// and at large sizes and viscosity contrasts rounding in K Z = V H lets FGMRES drift too.
 struct FgmresRun {
     enum Phase { P_BNORM, P_RESTART, P_ITER, P_FINAL, P_DONE };
     stokes_ctx* c = nullptr;
@@ -595,6 +613,9 @@ struct FgmresRun {
     int its = 0, j = 0, m = 0;
     double bnorm = 0.0, est = 1.0, hn_prev = 0.0;
     bool next_v = false;   // V_{j} = w / hn_prev still to be formed before iteration j
+    bool flexible = true;
+    bool force_cycle = false;   // the final check sent the run back: iterate at least once
+    int verify_left = 10;       // such returns left
     std::vector<double> H, cs, sn, g, y;
     double& Hij(int i, int jj) { return H[size_t(i) * m + jj]; }
 };
@@ -610,7 +631,7 @@ stokes_status fgmres_enqueue(FgmresRun& r) {
             CK(cudaMemcpyAsync(c->dots_host, c->dots, sizeof(double), cudaMemcpyDeviceToHost, s));
             return STOKES_OK;
         case FgmresRun::P_RESTART:
-            CKS(apply_stokes(c, r.x, c->w, s));
+            CKS(apply_stokes(c, r.x, c->w, s, true));
             CK(launch_axpby(N, 1.0, r.b, -1.0, c->w, s));                              // w = b - K x
             CK(launch_multidot(N, 1, c->w, N, c->w, c->partials, c->dots, s));
             CK(cudaMemcpyAsync(c->dots_host, c->dots, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -620,7 +641,7 @@ stokes_status fgmres_enqueue(FgmresRun& r) {
             double* V = c->V;
             const size_t ldv = c->ldv;
             double* vj = V + size_t(j) * ldv;
-            double* zj = c->Z + size_t(j) * N;
+            double* zj = r.flexible ? c->Z + size_t(j) * N : c->Z;
             const bool df = c->opt.outer_arith == 1 && m <= gs_max_k();   // V as double-float pairs (krylov.cu)
             if (df) {
                 if (r.next_v) CK(launch_df_store_scaled(N, c->w, 1.0 / r.hn_prev, vj, s));   // V_j = w / |w|
@@ -646,7 +667,7 @@ stokes_status fgmres_enqueue(FgmresRun& r) {
         }
         case FgmresRun::P_FINAL:
             CKS(remove_pressure_mean(c, r.x, s));   // synchronous (one dot)
-            CKS(apply_stokes(c, r.x, c->w, s));
+            CKS(apply_stokes(c, r.x, c->w, s, true));
             CK(launch_axpby(N, 1.0, r.b, -1.0, c->w, s));
             CK(launch_multidot(N, 1, c->w, N, c->w, c->partials, c->dots, s));
             CK(cudaMemcpyAsync(c->dots_host, c->dots, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -657,16 +678,37 @@ stokes_status fgmres_enqueue(FgmresRun& r) {
     return STOKES_OK;
 }
 
-// x += Z y for the finished cycle (y from the upper-triangular solve on the host).
+// x += Z y for the finished cycle (y from the upper-triangular solve on the host); without the
+// stored Z: x += P^-1 (V y), with V y formed in w (double-float V: by the projection pass with
+// w = 0 and coefficients -y into the free basis row V_k, then converted to FP64).
 stokes_status fgmres_update_x(FgmresRun& r, int k) {
     stokes_ctx* c = r.c;
+    const size_t N = c->N;
     for (int i = k - 1; i >= 0; --i) {
         double t = r.g[i];
         for (int l = i + 1; l < k; ++l) t -= r.Hij(i, l) * r.y[l];
         r.y[i] = t / r.Hij(i, i);
     }
-    CK(cudaMemcpyAsync(c->hdev, r.y.data(), size_t(k) * sizeof(double), cudaMemcpyHostToDevice, r.s));
-    CK(launch_multiaxpy(c->N, k, c->Z, c->N, c->hdev, r.x, 1.0, r.s));
+    if (r.flexible) {
+        CK(cudaMemcpyAsync(c->hdev, r.y.data(), size_t(k) * sizeof(double), cudaMemcpyHostToDevice, r.s));
+        CK(launch_multiaxpy(N, k, c->Z, N, c->hdev, r.x, 1.0, r.s));
+    } else {
+        const bool df = c->opt.outer_arith == 1 && r.m <= gs_max_k();
+        CK(cudaMemsetAsync(c->w, 0, N * sizeof(double), r.s));
+        if (df) {
+            for (int i = 0; i < k; ++i) r.y[i] = -r.y[i];
+            r.y[k] = 1.0;                                                          // scale
+            CK(cudaMemcpyAsync(c->hdev, r.y.data(), size_t(k + 1) * sizeof(double), cudaMemcpyHostToDevice, r.s));
+            double* vk = c->V + size_t(k) * c->ldv;                               // unused after the cycle
+            CK(launch_gs_project_scale(N, k, c->V, c->ldv, c->hdev, c->w, c->hdev + k, vk, true, r.s));
+            CK(launch_df_to_double(N, vk, c->w, r.s));
+        } else {
+            CK(cudaMemcpyAsync(c->hdev, r.y.data(), size_t(k) * sizeof(double), cudaMemcpyHostToDevice, r.s));
+            CK(launch_multiaxpy(N, k, c->V, c->ldv, c->hdev, c->w, 1.0, r.s));
+        }
+        CKS(precondition(c, r.prec, c->w, c->Z, r.s));
+        CK(launch_axpby(N, 1.0, c->Z, 1.0, r.x, r.s));
+    }
     CK(cudaStreamSynchronize(r.s));   // r.y is pageable host memory
     return STOKES_OK;
 }
@@ -692,7 +734,12 @@ stokes_status fgmres_complete(FgmresRun& r) {
             const double beta = std::sqrt(hd[0]);
             if (!std::isfinite(beta)) { r.st = STOKES_BREAKDOWN; r.phase = FgmresRun::P_FINAL; return STOKES_OK; }
             r.est = beta / r.bnorm;
-            if (beta <= r.rtol * r.bnorm) { r.st = STOKES_OK; r.phase = FgmresRun::P_FINAL; return STOKES_OK; }
+            if (beta <= r.rtol * r.bnorm && !r.force_cycle) {
+                r.st = STOKES_OK;
+                r.phase = FgmresRun::P_FINAL;
+                return STOKES_OK;
+            }
+            r.force_cycle = false;
             if (r.its >= r.max_it) { r.phase = FgmresRun::P_FINAL; return STOKES_OK; }
             std::fill(r.g.begin(), r.g.end(), 0.0);
             r.g[0] = beta;
@@ -734,15 +781,24 @@ stokes_status fgmres_complete(FgmresRun& r) {
             }
             return STOKES_OK;
         }
-        case FgmresRun::P_FINAL:
+        case FgmresRun::P_FINAL: {
+            const double rt = std::sqrt(hd[0]);
+            if (r.st == STOKES_OK && r.bnorm > 0.0 && rt > r.rtol * r.bnorm && r.its < r.max_it && r.verify_left > 0) {
+                --r.verify_left;
+                r.force_cycle = true;
+                r.st = STOKES_NOT_CONVERGED;   // the recurrence ran ahead: continue from b - K x
+                r.phase = FgmresRun::P_RESTART;
+                return STOKES_OK;
+            }
             if (r.info) {
                 r.info->iterations = r.its;
                 r.info->rel_residual = r.est;
-                r.info->rel_residual_true = r.bnorm > 0 ? std::sqrt(hd[0]) / r.bnorm : 0.0;
+                r.info->rel_residual_true = r.bnorm > 0 ? rt / r.bnorm : 0.0;
                 r.info->status = r.st;
             }
             r.phase = FgmresRun::P_DONE;
             return STOKES_OK;
+        }
         case FgmresRun::P_DONE:
             return STOKES_OK;
     }
@@ -761,11 +817,12 @@ stokes_status fgmres_init(FgmresRun& r, stokes_ctx* c, int prec, const double* b
     r.s = s;
     r.info = info;
     r.m = c->opt.restart;
+    r.flexible = c->opt.outer_solver != 2;
     r.H.assign(size_t(r.m + 1) * r.m, 0.0);
     r.cs.assign(r.m, 0.0);
     r.sn.assign(r.m, 0.0);
     r.g.assign(r.m + 1, 0.0);
-    r.y.assign(r.m, 0.0);
+    r.y.assign(r.m + 1, 0.0);
     r.phase = FgmresRun::P_BNORM;
     return STOKES_OK;
 }
@@ -794,13 +851,13 @@ stokes_status fgmres(stokes_ctx* c, int prec, const double* b, double* x, double
     CKS(fgmres_init(runs[0], c, prec, b, x, rtol, max_it, info ? info : &local, s));
     CKS(fgmres_drive(runs));
     const stokes_status st = runs[0].st;
-    if (st != STOKES_OK) return fail(st, st == STOKES_BREAKDOWN ? "FGMRES breakdown (non-finite norm)"
-                                                                 : "FGMRES reached max_it");
+    if (st != STOKES_OK) return fail(st, st == STOKES_BREAKDOWN ? "(F)GMRES breakdown (non-finite norm)"
+                                                                 : "(F)GMRES reached max_it");
     return STOKES_OK;
 }
 
 // ---------------------------------------------------------------- IDR(s)
-// The memory-light outer solver of Section 3.5: IDR(s) with bi-orthogonalisation and right
+// The memory-light outer solver of Section 3.4: IDR(s) with bi-orthogonalisation and right
 // preconditioning by P^-1 (M. B. van Gijzen, P. Sonneveld, ACM TOMS 38 (2011), Alg. 913), omega
 // by "maintaining the convergence" (kappa = 0.7). 3s + 4 vectors of N instead of FGMRES's 2 m + 1.
 // The shadow space: splitmix64 uniforms u01 - 1/2 with seeds 1907100 + i, orthonormalised.
@@ -856,7 +913,7 @@ stokes_status idr_solve(stokes_ctx* c, int prec, const double* b, double* x, dou
       // the tolerance but the true one did not (at most 10 restarts)
       const double tol = rtol * bnorm;
       for (int pass = 0; pass < 11; ++pass) {
-        CKS(apply_stokes(c, x, r, s));
+        CKS(apply_stokes(c, x, r, s, true));
         CK(launch_axpby(N, 1.0, b, -1.0, r, s));                              // r = b - K x
         double rr = 0.0;
         CKS(dot(c, N, r, r, s, &rr));
@@ -939,7 +996,7 @@ stokes_status idr_solve(stokes_ctx* c, int prec, const double* b, double* x, dou
     }
     // pressure with zero mean, true residual
     CKS(remove_pressure_mean(c, x, s));
-    CKS(apply_stokes(c, x, r, s));
+    CKS(apply_stokes(c, x, r, s, true));
     CK(launch_axpby(N, 1.0, b, -1.0, r, s));
     double rt = 0.0;
     CKS(dot(c, N, r, r, s, &rt));
@@ -957,7 +1014,7 @@ stokes_status validate_options(const stokes_options& o) {
     if (o.cheb_degree < 1 || o.smoothing_range <= 1.0 || o.eig_safety <= 0.0 || o.lanczos_steps < 1 ||
         o.schur_degree < 1 || o.restart < 1 || o.restart > 500 || (o.outer_arith != 0 && o.outer_arith != 1) ||
         (o.vmult_kernel != 0 && o.vmult_kernel != 1) || (o.graphs != 0 && o.graphs != 1) ||
-        (o.precond_kind != 0 && o.precond_kind != 1) || (o.outer_solver != 0 && o.outer_solver != 1) ||
+        (o.precond_kind != 0 && o.precond_kind != 1) || o.outer_solver < 0 || o.outer_solver > 2 ||
         o.idr_s < 1 || o.idr_s > 8)
         return fail(STOKES_EINVAL, "bad options");
     return STOKES_OK;
@@ -1811,7 +1868,7 @@ stokes_status stokes_batch_solve(int n_problems, stokes_ctx* const* ctxs, int vc
     if (n_problems < 1 || !ctxs || !up_devs) return fail(STOKES_EINVAL, "null argument or no problems");
     for (int i = 0; i < n_problems; ++i) {
         if (ctxs[i] && ctxs[i]->oct) return fail(STOKES_EMESH, "batched solves take uniform meshes");
-        if (ctxs[i] && ctxs[i]->opt.outer_solver != 0) return fail(STOKES_EINVAL, "batched solves use FGMRES");
+        if (ctxs[i] && ctxs[i]->opt.outer_solver == 1) return fail(STOKES_EINVAL, "batched solves use (F)GMRES");
     }
     if (vcycle_prec != STOKES_FP32 && vcycle_prec != STOKES_FP64) return fail(STOKES_EINVAL, "bad precision");
     if (!(rtol > 0.0) || max_it < 1) return fail(STOKES_EINVAL, "bad rtol or max_it");

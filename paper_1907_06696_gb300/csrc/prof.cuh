@@ -18,13 +18,16 @@ enum ProfClass {
     PROF_KRYLOV = 7,      // multi-dot, multi-axpy, axpby, norms
     PROF_COARSE = 8,      // coarse solve
     PROF_CAST = 9,        // precision casts
-    PROF_NCLASS = 10
+    PROF_RESID_F64 = 10,  // outer operator for the solvers' restart and final residuals (native FP64)
+    PROF_NCLASS = 11
 };
 
 // Called around each launch; cheap no-ops unless profiling is enabled.
 void prof_begin(int cls, cudaStream_t s);
 void prof_end(int cls, cudaStream_t s);
 void prof_count(int launches);
+// Launches of this host thread are recorded under class cls instead of their own while cls >= 0.
+void prof_override(int cls);
 bool prof_enabled();
 long long launch_total();
 

@@ -96,7 +96,9 @@ def workload(name: str) -> SinkerProblem:
     cube128 : 128^3 cells, 8 levels, 16 sinkers, viscosity ratio 1e6 (~51M velocity DoFs)
     Smaller parity cases: cube16 (16^3, 5 levels, 4 sinkers, DR 1e4), cube32 (32^3, 6 levels, 8 sinkers, DR 1e4).
     Profiling case: cube96 (96^3, 6 levels, 8 sinkers, DR 1e4; FP32 vectors of 86 MB exceed L2).
-    Largest case: cube192 (192^3, 7 levels down to 3^3, 16 sinkers, DR 1e6; ~171M velocity DoFs).
+    Largest case: cube192 (192^3, 7 levels down to 3^3, 16 sinkers, DR 1e6; ~171M velocity DoFs);
+    seq24, seq48, seq96: the same sinkers, viscosity ratio and 3^3 coarse grid on 24^3 .. 96^3
+    cells (iteration counts under mesh refinement at a fixed problem).
     Sinker centres come from splitmix64 with seed 1907 + k (k = 1, 2, 3 for cube8, cube64, cube128).
     """
     if name == "cube8":
@@ -110,6 +112,9 @@ def workload(name: str) -> SinkerProblem:
         return dr_problem(192, 7, 16, 1e6, 1916, name)
     if name == "cube96":
         return dr_problem(96, 6, 8, 1e4, 1915, name)
+    if name in ("seq24", "seq48", "seq96"):   # cube192's problem on coarser meshes (3^3 coarsest)
+        n = int(name[3:])
+        return dr_problem(n, {24: 4, 48: 5, 96: 6}[n], 16, 1e6, 1916, name)
     if name == "cube16":
         return dr_problem(16, 5, 4, 1e4, 1911, name)
     if name == "cube32":

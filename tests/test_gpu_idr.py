@@ -1,4 +1,4 @@
-"""GPU parity of the IDR(s) outer solver (option outer_solver = 1, Section 3.5) through the C ABI
+"""GPU parity of the IDR(s) outer solver (option outer_solver = 1, Section 3.4) through the C ABI
 against the oracle's idr_s on the same problems (same shadow space definition): iteration counts
 within 10% (IDR is sensitive to rounding in the operators, which differ in summation order),
 true residuals recomputed by the oracle's operator, solutions equal to the oracle's FGMRES

@@ -331,6 +331,9 @@ def test_exact_preconditioner_two_iterations():
     b = np.concatenate([F, np.zeros(m.n_p)])
     _, its, hist = krylov.fgmres(ops.apply_stokes, Pc.apply, b, rtol=1e-12)
     assert its <= 2
+    x, its, _ = krylov.gmres(ops.apply_stokes, Pc.apply, b, rtol=1e-12)   # the same with GMRES
+    assert its <= 2
+    assert np.linalg.norm(b - ops.apply_stokes(x)) <= 1e-12 * np.linalg.norm(b)
 
 
 def test_exact_block_diagonal_preconditioner_three_iterations():
@@ -524,3 +527,52 @@ def test_idr_stokes_matches_fgmres():
     xf, xi = krylov.zero_mean_pressure(ops, xf), krylov.zero_mean_pressure(ops, xi)
     assert np.linalg.norm(b - ops.apply_stokes(xi)) <= 1e-10 * np.linalg.norm(b)
     assert np.abs(xi - xf).max() <= 1e-8 * np.abs(xf).max()
+
+
+def test_gmres_minimises_residual_over_krylov_space():
+    """GMRES with a right preconditioner M after k steps from x0 = 0 returns the x in
+    M span{b, (A M) b, ..., (A M)^(k-1) b} with the smallest ||b - A x||: brute force by least
+    squares over an explicitly built power basis; flexible GMRES with the same linear M agrees."""
+    rng = np.random.default_rng(13)
+    n = 30
+    A = np.eye(n) + 0.3 * rng.standard_normal((n, n)) / np.sqrt(n)
+    M = np.eye(n) + 0.2 * rng.standard_normal((n, n)) / np.sqrt(n)
+    b = rng.standard_normal(n)
+    for k in range(1, 9):
+        x, its, _ = krylov.gmres(lambda v: A @ v, lambda v: M @ v, b, rtol=1e-30, restart=k, max_it=k)
+        assert its == k
+        K = np.empty((n, k))
+        K[:, 0] = b
+        for i in range(1, k):
+            K[:, i] = A @ (M @ K[:, i - 1])
+        c = np.linalg.lstsq(A @ M @ K, b, rcond=None)[0]
+        x_bf = M @ (K @ c)
+        assert np.linalg.norm(x - x_bf) <= 1e-9 * np.linalg.norm(x_bf)
+        xf, _, _ = krylov.fgmres(lambda v: A @ v, lambda v: M @ v, b, rtol=1e-30, restart=k, max_it=k)
+        assert np.linalg.norm(x - xf) <= 1e-12 * np.linalg.norm(xf)
+
+
+def test_gmres_restarted_converges_to_true_residual():
+    """Restarted GMRES(5) on a system that needs several cycles stops only at the true residual."""
+    rng = np.random.default_rng(14)
+    n = 60
+    A = np.diag(np.linspace(1, 20, n)) + 0.5 * rng.standard_normal((n, n)) / np.sqrt(n)
+    b = rng.standard_normal(n)
+    D = np.diag(1.0 / np.diag(A))
+    x, its, hist = krylov.gmres(lambda v: A @ v, lambda v: D @ v, b, rtol=1e-10, restart=5, max_it=2000)
+    assert its > 5
+    assert np.linalg.norm(b - A @ x) <= 1e-10 * np.linalg.norm(b)
+
+
+def test_gmres_stokes_matches_fgmres():
+    """GMRES(50) with the block-triangular GMG preconditioner (a fixed linear map) takes the
+    FGMRES iteration count and reaches its solution (cube4)."""
+    p, m, G, ops, F = _problem("cube4")
+    Pc = krylov.StokesPreconditioner(ops, G)
+    b = np.concatenate([F, np.zeros(m.n_p)])
+    xf, its_f, _ = krylov.fgmres(ops.apply_stokes, Pc.apply, b, rtol=1e-10)
+    xg, its_g, _ = krylov.gmres(ops.apply_stokes, Pc.apply, b, rtol=1e-10)
+    assert abs(its_g - its_f) <= 1
+    xf, xg = krylov.zero_mean_pressure(ops, xf), krylov.zero_mean_pressure(ops, xg)
+    assert np.linalg.norm(b - ops.apply_stokes(xg)) <= 1e-10 * np.linalg.norm(b)
+    assert np.abs(xg - xf).max() <= 1e-7 * np.abs(xf).max()
