@@ -61,7 +61,8 @@ def parse():
                          "true FP64 residuals and the difference of the two solutions (any size)")
     ap.add_argument("--outer", default="fgmres", choices=["fgmres", "idr", "gmres", "both", "all"],
                     help="with --solve-report: outer solver(s) of the FP32/FP64 V-cycle solves (idr = IDR(2), "
-                         "gmres = GMRES(50) with the fixed preconditioner; both = idr + fgmres; all = the three)")
+                         "gmres = GMRES(50) with the fixed preconditioner; both = idr + fgmres; all = the three). "
+                         "--precond both adds MINRES with P_D next to FGMRES with P_D")
     ap.add_argument("--fp32-only", action="store_true",
                     help="with --solve-report: skip the FP64-V-cycle legs (largest problems)")
     ap.add_argument("--precond", default="triangular", choices=["triangular", "both"],
@@ -656,6 +657,19 @@ def run_report(args):
             torch.cuda.synchronize()
             out["block_diagonal_fp32_vcycle"] = {"s": e0.elapsed_time(e1) / 1e3, "iterations": info.iterations,
                                                  "status": info.status, "true_rel_residual": info.rel_residual_true}
+            cd.close()
+            o.outer_solver = 3   # MINRES with the same P_D
+            cd = capi.stokes_setup_problem(prob, options=o)
+            up.zero_()
+            capi.stokes_solve(cd, capi.STOKES_FP32, None, up, rtol=RTOL, max_it=5000, check=False)
+            up.zero_()
+            e0.record()
+            info = capi.stokes_solve(cd, capi.STOKES_FP32, None, up, rtol=RTOL, max_it=5000, check=False)
+            e1.record()
+            torch.cuda.synchronize()
+            out["minres_block_diagonal_fp32_vcycle"] = {"s": e0.elapsed_time(e1) / 1e3, "iterations": info.iterations,
+                                                        "status": info.status,
+                                                        "true_rel_residual": info.rel_residual_true}
             cd.close()
         out["rel_diff_u"] = float((u32 - u64).norm() / u64.norm())
         out["rel_diff_p"] = float((p32 - p64).norm() / p64.norm())

@@ -129,8 +129,20 @@ typedef struct {
                                    exact coarse solve): restart + 2 vectors instead of 2 restart + 2; a
                                    cycle ends with x += P^-1 (V y) (one preconditioner application more
                                    per cycle, not counted in iterations) and the solve ends when the
-                                   true residual b - K x, recomputed after the cycle, meets rtol. */
+                                   true residual b - K x, recomputed after the cycle, meets rtol.
+                                   3 = MINRES (method (ii)(b) of Section 2.2; Paige & Saunders) with
+                                   the symmetric positive definite P_D: requires precond_kind = 1
+                                   (EINVAL at set-up otherwise); 11 vectors; the 2-norm residual is
+                                   carried by the recurrence and checked against b - K x (a drift
+                                   restarts MINRES from x, at most 10 times). Not for batches. */
     int idr_s;                  /* shadow-space dimension of IDR(s), 1..8 (2) */
+    int gram_schmidt;           /* FGMRES orthogonalisation with the double-float basis (outer_arith 1,
+                                   restart <= 64): 1 = classical Gram-Schmidt twice with the second
+                                   projection of each basis vector delayed into the next step, two
+                                   passes over the basis per iteration; 0 = the same two projections
+                                   in three passes (default). Same Krylov space; the preconditioner
+                                   receives the once-projected vector. GMRES (outer_solver 2) and the
+                                   native FP64 basis always take three passes. */
 } stokes_options;
 
 typedef struct {

@@ -1,5 +1,6 @@
 """Outer Stokes solve (Section 2.2): block-triangular preconditioner and FGMRES; the
-memory-light alternatives of Section 3.4 (GMRES with a fixed preconditioner, IDR(s)).
+memory-light alternatives of Section 3.4 (GMRES with a fixed preconditioner, IDR(s)); MINRES with
+the block-diagonal preconditioner (method (ii)(b) of Section 2.2).
 
 P = [[A, B^T], [0, -S]] (eq. stokes_precond); applying P^-1 to r = [r_u; r_p]:
     z_p = -S_hat^-1 r_p,   z_u = A_hat^-1 (r_u - B^T z_p),
@@ -182,6 +183,78 @@ def _givens_triangularise(H, g):
         R[j, :] = top
         g[j], g[j + 1] = c * g[j], -s * g[j]
     return R, g
+
+
+def minres(apply_K, apply_Pinv, b, rtol=1e-8, max_it=1000, x0=None):
+    """Preconditioned MINRES (C. C. Paige, M. A. Saunders, SIAM J. Numer. Anal. 12 (1975)) for a
+    symmetric K with a symmetric positive definite preconditioner P (here P_D = diag(A_hat, S_hat),
+    method (ii)(b) of Section 2.2): the Lanczos process of P^-1 K in the P-inner product, its
+    tridiagonal matrix reduced by Givens rotations, x updated every step along directions w
+    (three-term recurrence). Short recurrences: a fixed number of vectors.
+    MINRES minimises the P^-1-norm of the residual; the 2-norm residual r = b - K x is carried
+    along by the same recurrences (K w from K z) and the solve stops when ||r|| <= rtol ||b||, then
+    verifies it against b - K x; if the carried residual drifted, MINRES restarts from x (at most
+    10 times). Returns (x, iterations, list of relative residuals)."""
+    n = b.shape[0]
+    x = np.zeros(n) if x0 is None else x0.copy()
+    bnorm = np.linalg.norm(b)
+    hist = []
+    its = 0
+    if bnorm == 0.0:
+        return x, 0, [0.0]
+    tol = rtol * bnorm
+    for _ in range(11):
+        r = b - apply_K(x)
+        hist.append(np.linalg.norm(r) / bnorm)
+        if np.linalg.norm(r) <= tol or its >= max_it:
+            break
+        x, its = _minres_cycle(apply_K, apply_Pinv, x, r, tol, its, max_it, hist, bnorm)
+    return x, its, hist
+
+
+def _minres_cycle(apply_K, apply_Pinv, x, r, tol, its, max_it, hist, bnorm):
+    """MINRES from (x, r = b - K x) until the carried residual meets tol or max_it is reached."""
+    n = x.shape[0]
+    v_old = np.zeros(n)                 # Lanczos vectors of the unpreconditioned space, scaled by gamma
+    v = r.copy()
+    z = apply_Pinv(v)
+    gamma_old, gamma = 1.0, np.sqrt(v @ z)
+    eta = gamma                         # P^-1-norm of the residual, with sign
+    c_old, c, s_old, s = 1.0, 1.0, 0.0, 0.0
+    w_old, w = np.zeros(n), np.zeros(n)     # search directions
+    Kw_old, Kw = np.zeros(n), np.zeros(n)   # K times them
+    r = r.copy()
+    while its < max_it:
+        z = z / gamma
+        q = apply_K(z)
+        delta = q @ z
+        v_new = q - (delta / gamma) * v - (gamma / gamma_old) * v_old
+        z_new = apply_Pinv(v_new)
+        gamma_new = np.sqrt(v_new @ z_new)
+        # new column of the tridiagonal matrix: rotate by the two previous rotations, then
+        # annihilate gamma_new with a new one
+        a0 = c * delta - c_old * s * gamma
+        a1 = np.hypot(a0, gamma_new)
+        a2 = s * delta + c_old * c * gamma
+        a3 = s_old * gamma
+        c_old, s_old = c, s
+        c, s = a0 / a1, gamma_new / a1
+        w_new = (z - a3 * w_old - a2 * w) / a1
+        Kw_new = (q - a3 * Kw_old - a2 * Kw) / a1
+        x = x + (c * eta) * w_new
+        r = r - (c * eta) * Kw_new
+        eta = -s * eta
+        its += 1
+        v_old, v = v, v_new
+        z = z_new
+        gamma_old, gamma = gamma, gamma_new
+        w_old, w = w, w_new
+        Kw_old, Kw = Kw, Kw_new
+        rn = np.linalg.norm(r)
+        hist.append(rn / bnorm)
+        if rn <= tol or gamma == 0.0:
+            break
+    return x, its
 
 
 def zero_mean_pressure(ops, up):

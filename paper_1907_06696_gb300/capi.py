@@ -47,7 +47,7 @@ class stokes_options(C.Structure):
     _fields_ = [("cheb_degree", C.c_int), ("smoothing_range", C.c_double), ("eig_safety", C.c_double),
                 ("lanczos_steps", C.c_int), ("schur_degree", C.c_int), ("restart", C.c_int),
                 ("outer_arith", C.c_int), ("vmult_kernel", C.c_int), ("graphs", C.c_int), ("precond_kind", C.c_int),
-                ("outer_solver", C.c_int), ("idr_s", C.c_int)]
+                ("outer_solver", C.c_int), ("idr_s", C.c_int), ("gram_schmidt", C.c_int)]
 
 
 class stokes_solve_info(C.Structure):

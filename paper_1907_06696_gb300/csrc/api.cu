@@ -211,6 +211,7 @@ struct stokes_ctx {
     double *idr_G = nullptr, *idr_U = nullptr, *idr_P = nullptr, *idr_r = nullptr, *idr_v = nullptr,
            *idr_t = nullptr, *idr_tmp = nullptr, *idr_c = nullptr;
     cudaStream_t idr_stream = nullptr;
+    double* mr[11] = {};   // MINRES work vectors
 };
 
 namespace {
@@ -574,7 +575,7 @@ stokes_status ensure_krylov(stokes_ctx* c) {
     CKS(dalloc(c, &c->Z, c->opt.outer_solver == 2 ? c->ldv : size_t(m) * c->N));
     CKS(dalloc(c, &c->w, c->N));
     CKS(dalloc(c, &c->bvec, c->N));
-    CKS(dalloc(c, &c->hdev, size_t(2 * (m + 4))));
+    CKS(dalloc(c, &c->hdev, size_t(3 * (m + 4))));   // h1, and two step records of the delayed passes
     c->krylov_restart = m;
     return STOKES_OK;
 }
@@ -614,6 +615,8 @@ struct FgmresRun {
     double bnorm = 0.0, est = 1.0, hn_prev = 0.0;
     bool next_v = false;   // V_{j} = w / hn_prev still to be formed before iteration j
     bool flexible = true;
+    bool lag = false;           // delayed re-orthogonalisation (two passes over V per step)
+    double inv_sqrt_s = 1.0;    // 1 / |u_j| for the preconditioner input u_j / |u_j|
     bool force_cycle = false;   // the final check sent the run back: iterate at least once
     int verify_left = 10;       // such returns left
     std::vector<double> H, cs, sn, g, y;
@@ -642,6 +645,24 @@ stokes_status fgmres_enqueue(FgmresRun& r) {
             const size_t ldv = c->ldv;
             double* vj = V + size_t(j) * ldv;
             double* zj = r.flexible ? c->Z + size_t(j) * N : c->Z;
+            if (r.lag) {
+                // Delayed re-orthogonalisation: row j holds u_j, w of the previous step after one
+                // projection; the preconditioner takes u_j / |u_j| (FGMRES allows any z_j: the
+                // relation K z_j = V H e_j holds for the z_j used). Pass A: V^T w with the dot of
+                // row j corrected on the device to v_j . w; pass B: writes the twice-projected
+                // v_j over row j and u_{j+1} = w - V h to row j + 1, with the dots of the record.
+                if (r.next_v) CK(launch_df_store_scaled(N, c->w, 1.0 / r.hn_prev, vj, s));   // V_0
+                CK(launch_df_to_double(N, vj, c->w, s, j == 0 ? 1.0 : r.inv_sqrt_s));
+                CKS(precondition(c, r.prec, c->w, zj, s));
+                CKS(apply_stokes(c, zj, c->w, s));
+                double* h1d = c->hdev;
+                const double* prev = j > 0 ? c->hdev + size_t(m + 4) * (1 + (j & 1)) : nullptr;
+                double* cur = c->hdev + size_t(m + 4) * (1 + ((j + 1) & 1));
+                CK(launch_gs_dot_lag(N, j + 1, V, ldv, c->w, c->partials, h1d, prev, s));
+                CK(launch_gs_lag_project(N, j + 1, V, ldv, h1d, prev, c->w, c->partials, cur, s));
+                CK(cudaMemcpyAsync(c->dots_host, c->hdev, size_t(3 * (m + 4)) * sizeof(double), cudaMemcpyDeviceToHost, s));
+                return STOKES_OK;
+            }
             const bool df = c->opt.outer_arith == 1 && m <= gs_max_k();   // V as double-float pairs (krylov.cu)
             if (df) {
                 if (r.next_v) CK(launch_df_store_scaled(N, c->w, 1.0 / r.hn_prev, vj, s));   // V_j = w / |w|
@@ -751,8 +772,16 @@ stokes_status fgmres_complete(FgmresRun& r) {
         }
         case FgmresRun::P_ITER: {
             const int j = r.j;
-            for (int i = 0; i <= j; ++i) r.Hij(i, j) = hd[i] + hd[m + 4 + i];
-            const double hn = hd[m + 4 + j + 2];   // the norm V_{j+1} was scaled with
+            double hn = 0.0;
+            if (r.lag) {
+                const double* rec = hd + size_t(m + 4) * (1 + ((j + 1) & 1));
+                for (int i = 0; i <= j; ++i) r.Hij(i, j) = hd[i] + rec[i];
+                hn = rec[j + 2];                              // |u_{j+1} - V c|
+                r.inv_sqrt_s = 1.0 / std::sqrt(rec[j + 1]);
+            } else {
+                for (int i = 0; i <= j; ++i) r.Hij(i, j) = hd[i] + hd[m + 4 + i];
+                hn = hd[m + 4 + j + 2];   // the norm V_{j+1} was scaled with
+            }
             if (!std::isfinite(hn)) { r.st = STOKES_BREAKDOWN; r.phase = FgmresRun::P_FINAL; return STOKES_OK; }
             r.Hij(j + 1, j) = hn;
             for (int i = 0; i < j; ++i) {
@@ -818,6 +847,7 @@ stokes_status fgmres_init(FgmresRun& r, stokes_ctx* c, int prec, const double* b
     r.info = info;
     r.m = c->opt.restart;
     r.flexible = c->opt.outer_solver != 2;
+    r.lag = r.flexible && c->opt.gram_schmidt == 1 && c->opt.outer_arith == 1 && r.m <= gs_max_k();
     r.H.assign(size_t(r.m + 1) * r.m, 0.0);
     r.cs.assign(r.m, 0.0);
     r.sn.assign(r.m, 0.0);
@@ -1010,11 +1040,117 @@ stokes_status idr_solve(stokes_ctx* c, int prec, const double* b, double* x, dou
     return STOKES_OK;
 }
 
+// ---------------------------------------------------------------- MINRES
+// Method (ii)(b) of Section 2.2: MINRES (Paige & Saunders, SIAM J. Numer. Anal. 12 (1975)) with
+// the symmetric positive definite block-diagonal P_D = diag(A_hat, S_hat) (precond_kind 1): the
+// Lanczos process of P^-1 K in the P-inner product, its tridiagonal matrix reduced by Givens
+// rotations, x updated every step along three-term directions w. The 2-norm residual is carried
+// by the same recurrence (K w from K z) and checked against b - K x as in IDR(s): a drifted
+// residual restarts MINRES from x (at most 10 times). 11 vectors of N.
+stokes_status minres_solve(stokes_ctx* c, int prec, const double* b, double* x, double rtol, int max_it,
+                           stokes_solve_info* info, cudaStream_t s) {
+    const size_t N = c->N;
+    for (double*& q : c->mr)
+        if (!q) CKS(dalloc(c, &q, N));
+    double *v_old = c->mr[0], *v = c->mr[1], *z = c->mr[2], *q = c->mr[3], *w_old = c->mr[4], *w = c->mr[5],
+           *Kw_old = c->mr[6], *Kw = c->mr[7], *r = c->mr[8];
+    double bnorm2 = 0.0;
+    CKS(dot(c, N, b, b, s, &bnorm2));
+    const double bnorm = std::sqrt(bnorm2);
+    stokes_status st = STOKES_NOT_CONVERGED;
+    int its = 0;
+    double rnorm = 0.0;
+    if (bnorm == 0.0) {
+        CK(cudaMemsetAsync(x, 0, N * sizeof(double), s));
+        st = STOKES_OK;
+    } else {
+      const double tol = rtol * bnorm;
+      for (int pass = 0; pass < 11; ++pass) {
+        CKS(apply_stokes(c, x, r, s, true));
+        CK(launch_axpby(N, 1.0, b, -1.0, r, s));                               // r = b - K x
+        double rr = 0.0;
+        CKS(dot(c, N, r, r, s, &rr));
+        rnorm = std::sqrt(rr);
+        if (!std::isfinite(rnorm)) { st = STOKES_BREAKDOWN; break; }
+        if (rnorm <= tol) { st = STOKES_OK; break; }
+        if (its >= max_it) { st = STOKES_NOT_CONVERGED; break; }
+        st = STOKES_NOT_CONVERGED;
+        for (double* t : {v_old, w_old, w, Kw_old, Kw}) CK(cudaMemsetAsync(t, 0, N * sizeof(double), s));
+        CK(cudaMemcpyAsync(v, r, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CKS(precondition(c, prec, v, z, s));
+        double g2 = 0.0;
+        CKS(dot(c, N, v, z, s, &g2));
+        if (!(g2 > 0.0) || !std::isfinite(g2)) { st = STOKES_BREAKDOWN; break; }
+        double gamma_old = 1.0, gamma = std::sqrt(g2), eta = gamma;
+        double c_old = 1.0, cs = 1.0, s_old = 0.0, sn = 0.0;
+        bool done = false;
+        while (its < max_it) {
+            CK(launch_axpby(N, 0.0, z, 1.0 / gamma, z, s));                    // z /= gamma
+            CKS(apply_stokes(c, z, q, s));                                        // q = K z
+            double delta = 0.0;
+            CKS(dot(c, N, q, z, s, &delta));
+            // rotations of the previous two steps applied to the new column (delta, gamma)
+            const double a0 = cs * delta - c_old * sn * gamma;
+            const double a2 = sn * delta + c_old * cs * gamma;
+            const double a3 = s_old * gamma;
+            // next Lanczos vector (scaled by gamma_new) into v_old; unnormalised w and K w
+            CK(launch_axpby(N, 1.0, q, -gamma / gamma_old, v_old, s));
+            CK(launch_axpby(N, -delta / gamma, v, 1.0, v_old, s));
+            CK(launch_axpby(N, 1.0, q, -a3, Kw_old, s));
+            CK(launch_axpby(N, -a2, Kw, 1.0, Kw_old, s));
+            CK(launch_axpby(N, 1.0, z, -a3, w_old, s));
+            CK(launch_axpby(N, -a2, w, 1.0, w_old, s));
+            CKS(precondition(c, prec, v_old, q, s));                             // z_new into q
+            CKS(dot(c, N, v_old, q, s, &g2));
+            if (!(g2 >= 0.0) || !std::isfinite(g2)) { st = STOKES_BREAKDOWN; done = true; break; }
+            const double gamma_new = std::sqrt(g2);
+            const double a1 = std::hypot(a0, gamma_new);
+            c_old = cs;
+            s_old = sn;
+            cs = a0 / a1;
+            sn = gamma_new / a1;
+            CK(launch_axpby(N, 0.0, w_old, 1.0 / a1, w_old, s));               // w_new
+            CK(launch_axpby(N, 0.0, Kw_old, 1.0 / a1, Kw_old, s));             // K w_new
+            CK(launch_axpby(N, cs * eta, w_old, 1.0, x, s));
+            CK(launch_axpby(N, -cs * eta, Kw_old, 1.0, r, s));
+            eta = -sn * eta;
+            ++its;
+            std::swap(v_old, v);      // v <- v_new, v_old <- v
+            std::swap(z, q);          // z <- z_new
+            std::swap(w_old, w);      // w <- w_new, w_old <- w
+            std::swap(Kw_old, Kw);
+            gamma_old = gamma;
+            gamma = gamma_new;
+            CKS(dot(c, N, r, r, s, &rr));
+            rnorm = std::sqrt(rr);
+            if (!std::isfinite(rnorm)) { st = STOKES_BREAKDOWN; done = true; break; }
+            if (rnorm <= tol || gamma == 0.0) break;
+        }
+        if (done) break;
+      }
+    }
+    CKS(remove_pressure_mean(c, x, s));
+    CKS(apply_stokes(c, x, r, s, true));
+    CK(launch_axpby(N, 1.0, b, -1.0, r, s));
+    double rt = 0.0;
+    CKS(dot(c, N, r, r, s, &rt));
+    if (st == STOKES_NOT_CONVERGED && bnorm > 0.0 && std::sqrt(rt) <= rtol * bnorm) st = STOKES_OK;
+    if (info) {
+        info->iterations = its;
+        info->rel_residual = bnorm > 0 ? rnorm / bnorm : 0.0;
+        info->rel_residual_true = bnorm > 0 ? std::sqrt(rt) / bnorm : 0.0;
+        info->status = st;
+    }
+    if (st != STOKES_OK) return fail(st, st == STOKES_BREAKDOWN ? "MINRES breakdown" : "MINRES reached max_it");
+    return STOKES_OK;
+}
+
 stokes_status validate_options(const stokes_options& o) {
     if (o.cheb_degree < 1 || o.smoothing_range <= 1.0 || o.eig_safety <= 0.0 || o.lanczos_steps < 1 ||
         o.schur_degree < 1 || o.restart < 1 || o.restart > 500 || (o.outer_arith != 0 && o.outer_arith != 1) ||
         (o.vmult_kernel != 0 && o.vmult_kernel != 1) || (o.graphs != 0 && o.graphs != 1) ||
-        (o.precond_kind != 0 && o.precond_kind != 1) || o.outer_solver < 0 || o.outer_solver > 2 ||
+        (o.precond_kind != 0 && o.precond_kind != 1) || o.outer_solver < 0 || o.outer_solver > 3 || (o.gram_schmidt != 0 && o.gram_schmidt != 1) ||
+        (o.outer_solver == 3 && o.precond_kind != 1) ||
         o.idr_s < 1 || o.idr_s > 8)
         return fail(STOKES_EINVAL, "bad options");
     return STOKES_OK;
@@ -1100,7 +1236,7 @@ stokes_status setup_impl(const stokes_mesh* mesh, const stokes_mu* mu, const sto
     CKS(dalloc(c, &c->stage_out, gf.n_u));
     CKS(dalloc(c, &c->partials, size_t(std::max(multidot_blocks(), gs_partials_blocks())) * (o.restart + 8)));
     CKS(dalloc(c, &c->dots, size_t(o.restart + 8)));
-    CK(cudaMallocHost(&c->dots_host, size_t(2 * (o.restart + 8)) * sizeof(double)));
+    CK(cudaMallocHost(&c->dots_host, size_t(3 * (o.restart + 8)) * sizeof(double)));
     // ---- viscosity (Section 2.3) and right-hand side (Section 3.2)
     double* centres = nullptr;
     if (mu->kind == 0) {
@@ -1316,7 +1452,7 @@ stokes_status oct_setup_impl(const stokes_octree* mesh, const stokes_mu* mu, con
     CKS(dalloc(c, &c->tu, nu));
     CKS(dalloc(c, &c->partials, size_t(std::max(multidot_blocks(), gs_partials_blocks())) * (o.restart + 8)));
     CKS(dalloc(c, &c->dots, size_t(o.restart + 8)));
-    CK(cudaMallocHost(&c->dots_host, size_t(2 * (o.restart + 8)) * sizeof(double)));
+    CK(cudaMallocHost(&c->dots_host, size_t(3 * (o.restart + 8)) * sizeof(double)));
     CKS(dalloc(c, &c->ref_diag, 81));
     CK(launch_ref_diag(c->ref_diag, s));
     // ---- levels
@@ -1479,6 +1615,7 @@ void stokes_default_options(stokes_options* opt) {
     opt->precond_kind = 0;
     opt->outer_solver = 0;
     opt->idr_s = 2;
+    opt->gram_schmidt = 0;
 }
 
 const char* stokes_strerror(stokes_status s) {
@@ -1757,6 +1894,9 @@ stokes_status stokes_solve(stokes_ctx* c, int vcycle_prec, const double* rhs, do
     if (c->opt.outer_solver == 1) {
         c->idr_stream = s;
         CKS(ensure_idr(c, c->opt.idr_s));
+    } else if (c->opt.outer_solver == 3) {
+        c->N = active_nu(c) + active_np(c);   // MINRES vectors: minres_solve
+        if (!c->bvec) CKS(dalloc(c, &c->bvec, c->N));
     } else {
         CKS(ensure_krylov(c));
     }
@@ -1767,8 +1907,9 @@ stokes_status stokes_solve(stokes_ctx* c, int vcycle_prec, const double* rhs, do
         CK(cudaMemsetAsync(c->bvec + nu, 0, np * sizeof(double), s));
         b = c->bvec;
     }
-    stokes_status st = c->opt.outer_solver == 1 ? idr_solve(c, vcycle_prec, b, up, rtol, max_it, info, s)
-                                                 : fgmres(c, vcycle_prec, b, up, rtol, max_it, info, s);
+    stokes_status st = c->opt.outer_solver == 1   ? idr_solve(c, vcycle_prec, b, up, rtol, max_it, info, s)
+                       : c->opt.outer_solver == 3 ? minres_solve(c, vcycle_prec, b, up, rtol, max_it, info, s)
+                                                  : fgmres(c, vcycle_prec, b, up, rtol, max_it, info, s);
     const auto t1 = std::chrono::steady_clock::now();
     if (info) {
         info->seconds = std::chrono::duration<double>(t1 - t0).count();
@@ -1868,7 +2009,8 @@ stokes_status stokes_batch_solve(int n_problems, stokes_ctx* const* ctxs, int vc
     if (n_problems < 1 || !ctxs || !up_devs) return fail(STOKES_EINVAL, "null argument or no problems");
     for (int i = 0; i < n_problems; ++i) {
         if (ctxs[i] && ctxs[i]->oct) return fail(STOKES_EMESH, "batched solves take uniform meshes");
-        if (ctxs[i] && ctxs[i]->opt.outer_solver == 1) return fail(STOKES_EINVAL, "batched solves use (F)GMRES");
+        if (ctxs[i] && (ctxs[i]->opt.outer_solver == 1 || ctxs[i]->opt.outer_solver == 3))
+            return fail(STOKES_EINVAL, "batched solves use (F)GMRES");
     }
     if (vcycle_prec != STOKES_FP32 && vcycle_prec != STOKES_FP64) return fail(STOKES_EINVAL, "bad precision");
     if (!(rtol > 0.0) || max_it < 1) return fail(STOKES_EINVAL, "bad rtol or max_it");

@@ -124,6 +124,17 @@ cudaError_t launch_gs_project_scale(size_t n, int k, const double* V, size_t ld,
                                     const double* scale, double* y, bool df, cudaStream_t s);
 // y = w * scale stored as double-float pairs; x = double-float pairs v as FP64.
 cudaError_t launch_df_store_scaled(size_t n, const double* w, double scale, double* y, cudaStream_t s);
-cudaError_t launch_df_to_double(size_t n, const double* v, double* x, cudaStream_t s);
+cudaError_t launch_df_to_double(size_t n, const double* v, double* x, cudaStream_t s, double scale = 1.0);
+// FGMRES with delayed re-orthogonalisation (two passes over the basis per step instead of three):
+//   launch_gs_dot_lag:     out[i] = V_i . w, i < k; with lag (the record below of the previous step,
+//                          j = k - 1, row j holding u_j): out[j] = v_j . w for the corrected v_j
+//   launch_gs_lag_project: v_j = (u_j - V_{<j} c) / alpha over row j (lag null: row j is final);
+//                          w1 = w - V_{<=j} h into row j + 1 (double-float); record of this step:
+//                          out[0..j] = V_{<=j}^T w1 (= c of the next), out[j+1] = |w1|^2,
+//                          out[j+2] = alpha = sqrt(|w1|^2 - |c|^2), out[j+3] = 1 / alpha
+cudaError_t launch_gs_dot_lag(size_t n, int k, const double* V, size_t ld, const double* w, double* partials,
+                              double* out, const double* lag, cudaStream_t s);
+cudaError_t launch_gs_lag_project(size_t n, int k, double* V, size_t ld, const double* h, const double* lag,
+                                  const double* w, double* partials, double* out, cudaStream_t s);
 
 }  // namespace stk

@@ -54,7 +54,7 @@ constexpr int kGsThreads = 128;
 constexpr int kGsMaxK = 64;                 // largest basis of the double-float passes
 constexpr int kGsMaxBlocks = 2432;          // 16 per SM on 152 SMs; the partials buffer is sized for this
 
-enum GsMode { GS_DOT = 0, GS_PROJECT_DOT = 1, GS_PROJECT_SCALE = 2 };
+enum GsMode { GS_DOT = 0, GS_PROJECT_DOT = 1, GS_PROJECT_SCALE = 2, GS_LAG = 3 };
 
 // An entry pair is handled by TPE = KB / RB threads (adjacent lanes), each owning RB <= 16
 // basis rows: one thread up to KB = 8, two up to 32, four at 64 (measured: more rows per
@@ -67,9 +67,11 @@ struct GsShape {
     static constexpr int PPB = kGsThreads / TPE;   // entry pairs per CTA and sweep
 };
 
-// per thread: two buffers of RB rows x 16 bytes (an entry pair), then coefficients and sums
+// per thread: two buffers of RB rows x 16 bytes (an entry pair), then coefficients (two sets
+// for GS_LAG) and sums
 inline size_t gs_smem(int mode, int kb) {
-    return (4 * size_t(gs_rb(mode, kb)) * kGsThreads + size_t(kb) + 4 * (size_t(kb) + 1)) * sizeof(double);
+    return (4 * size_t(gs_rb(mode, kb)) * kGsThreads + size_t(kb) * (mode == GS_LAG ? 2 : 1) + 4 * (size_t(kb) + 1)) *
+           sizeof(double);
 }
 
 // 16-byte asynchronous copy global -> shared, not cached in L1.
@@ -93,12 +95,17 @@ __device__ __forceinline__ df64 shfl_xor_df(const df64& v, int o) {
 // MODE GS_DOT:           partials <- V^T w                           (rows 0..k-1)
 // MODE GS_PROJECT_DOT:   w <- w - V h; partials <- V^T w, w . w      (rows 0..k)
 // MODE GS_PROJECT_SCALE: y <- (w - V h) * scale[0], y double-float   (no partials)
+// MODE GS_LAG (delayed re-orthogonalisation; j = k - 1, row j holds u_j, the once-projected
+//   vector of the previous step, and scale = its record c = V_{<j}^T u_j, |u_j|^2, alpha,
+//   1 / alpha with alpha = |u_j - V_{<j} c|, or null for j = 0 where row 0 is final):
+//   v_j = (u_j - V_{<j} c) / alpha is written over row j; w1 = w - V_{<=j} h with v_j in row j,
+//   written as double-float to row j + 1 (y = V); partials <- V_{<=j}^T w1 (row j: v_j), w1 . w1.
 // KB >= k is the compile-time bound on the basis size (8, 16, 32 or 64). A thread handles the
 // entry pair (2p, 2p + 1): one 16-byte copy per row.
 template <int MODE, int KB>
 __global__ void __launch_bounds__(kGsThreads) k_gs_df(size_t n, int k, const double* __restrict__ V, size_t ld,
                                                       const double* __restrict__ h, double* __restrict__ w,
-                                                      const double* __restrict__ scale, double* __restrict__ y,
+                                                      const double* __restrict__ scale, double* y,
                                                       double* __restrict__ partials) {
     using S = GsShape<MODE, KB>;
     constexpr int RB = S::RB, TPE = S::TPE, PPB = S::PPB;
@@ -109,17 +116,30 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_df(size_t n, int k, const dou
     const int rb = (k + TPE - 1) / TPE;   // rows per group (<= RB), balanced over the groups
     const int r0 = g * rb;
     float4* col = reinterpret_cast<float4*>(smem) + tid;                       // [2][RB][kGsThreads], own column
+    constexpr int NH = MODE == GS_LAG ? 2 : 1;
     df64* hs = reinterpret_cast<df64*>(smem + 4 * RB * kGsThreads);            // split coefficients
-    df64* red = reinterpret_cast<df64*>(smem + 4 * RB * kGsThreads + KB);      // [4][KB + 1] warp sums
-    if (MODE != GS_DOT)
+    df64* hb = hs + KB;                                                        // GS_LAG: those of v_j
+    df64* red = reinterpret_cast<df64*>(smem + 4 * RB * kGsThreads + NH * KB); // [4][KB + 1] warp sums
+    if constexpr (MODE == GS_LAG) {
+        // w1 = w - sum_{i<j} h_i v_i - h_j v_j with v_j = (u_j - sum_{i<j} c_i v_i) / alpha, as one
+        // combination of the stored rows (a) and v_j itself (b)
+        const int j = k - 1;
+        const double ia = scale ? scale[j + 2] : 1.0;
+        for (int i = tid; i < k; i += kGsThreads) {
+            const double ci = (scale && i < j) ? scale[i] : 0.0;
+            hs[i] = q2::split_double(i < j ? h[i] - h[j] * ci * ia : h[j] * ia);
+            hb[i] = q2::split_double(i < j ? -ci * ia : ia);
+        }
+    } else if constexpr (MODE != GS_DOT) {
         for (int i = tid; i < k; i += kGsThreads) hs[i] = q2::split_double(h[i]);
+    }
     __syncthreads();
     const df64 sc = MODE == GS_PROJECT_SCALE ? q2::split_double(scale[0]) : df64();
     constexpr int NA = MODE == GS_PROJECT_SCALE ? 1 : RB;
     df64 acc[NA];
 #pragma unroll
     for (int r = 0; r < NA; ++r) acc[r] = df64();
-    df64 self;
+    df64 self, vdot;
     // Every lane of a warp runs the same number of sweeps (pairs past the end are masked), so
     // that the full-warp shuffles below are always convergent. The copies of sweep s + 1 are
     // issued before sweep s is computed (two buffers per thread).
@@ -171,6 +191,52 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_df(size_t n, int k, const dou
                     q2::mac(acc[r], df64(v.x, v.y), w0);
                     q2::mac(acc[r], df64(v.z, v.w), w1);
                 }
+        } else if constexpr (MODE == GS_LAG) {
+            df64 s0, s1, t0, t1;
+#pragma unroll
+            for (int r = 0; r < RB; ++r)
+                if (r < rb && in && r0 + r < k) {
+                    const float4 v = cv[r * kGsThreads];
+                    q2::mac(s0, hs[r0 + r], df64(v.x, v.y));
+                    q2::mac(s1, hs[r0 + r], df64(v.z, v.w));
+                    q2::mac(t0, hb[r0 + r], df64(v.x, v.y));
+                    q2::mac(t1, hb[r0 + r], df64(v.z, v.w));
+                }
+            q2::renorm(s0);
+            q2::renorm(s1);
+            q2::renorm(t0);
+            q2::renorm(t1);
+#pragma unroll
+            for (int o = 1; o < TPE; o <<= 1) {
+                s0 += shfl_xor_df(s0, o);
+                s1 += shfl_xor_df(s1, o);
+                t0 += shfl_xor_df(t0, o);
+                t1 += shfl_xor_df(t1, o);
+            }
+            w0 = w0 - s0;
+            w1 = w1 - s1;
+            if (in && g == 0) {
+                float4* vj = reinterpret_cast<float4*>(y + size_t(k - 1) * ld);
+                float4* uk = reinterpret_cast<float4*>(y + size_t(k) * ld);
+                if (in1) {
+                    vj[p] = make_float4(t0.hi, t0.lo, t1.hi, t1.lo);
+                    uk[p] = make_float4(w0.hi, w0.lo, w1.hi, w1.lo);
+                } else {
+                    reinterpret_cast<df64*>(vj)[2 * p] = t0;
+                    reinterpret_cast<df64*>(uk)[2 * p] = w0;
+                }
+                q2::mac(self, w0, w0);
+                q2::mac(self, w1, w1);
+                q2::mac(vdot, t0, w0);
+                q2::mac(vdot, t1, w1);
+            }
+#pragma unroll
+            for (int r = 0; r < RB; ++r)
+                if (r < rb && in && r0 + r < k - 1) {
+                    const float4 v = cv[r * kGsThreads];
+                    q2::mac(acc[r], df64(v.x, v.y), w0);
+                    q2::mac(acc[r], df64(v.z, v.w), w1);
+                }
         } else {
             df64 s0, s1;
 #pragma unroll
@@ -215,6 +281,7 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_df(size_t n, int k, const dou
 #pragma unroll
             for (int r = 0; r < NA; ++r) q2::renorm(acc[r]);
             q2::renorm(self);
+            if constexpr (MODE == GS_LAG) q2::renorm(vdot);
         }
         base += stride;
     }
@@ -223,19 +290,25 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_df(size_t n, int k, const dou
 #pragma unroll
         for (int r = 0; r < RB; ++r) q2::renorm(acc[r]);
         q2::renorm(self);
+        q2::renorm(vdot);
         // sums over the warp's entries (lanes with the same g), then over the CTA's 4 warps
 #pragma unroll
         for (int r = 0; r < RB; ++r)
             for (int o = 16; o >= TPE; o >>= 1) acc[r] += shfl_down_df(acc[r], o);
         for (int o = 16; o >= TPE; o >>= 1) self += shfl_down_df(self, o);
+        if constexpr (MODE == GS_LAG)
+            for (int o = 16; o >= TPE; o >>= 1) vdot += shfl_down_df(vdot, o);
+        // GS_LAG: row j's sum is vdot (v_j is not in shared memory)
+        const int kd = MODE == GS_LAG ? k - 1 : k;
         if (lane < TPE) {
 #pragma unroll
             for (int r = 0; r < RB; ++r)
-                if (r < rb && r0 + r < k) red[wid * (KB + 1) + r0 + r] = acc[r];
+                if (r < rb && r0 + r < kd) red[wid * (KB + 1) + r0 + r] = acc[r];
             if (g == 0) red[wid * (KB + 1) + k] = self;
+            if (MODE == GS_LAG && g == 0) red[wid * (KB + 1) + k - 1] = vdot;
         }
         __syncthreads();
-        const int rows = MODE == GS_PROJECT_DOT ? k + 1 : k;
+        const int rows = MODE == GS_PROJECT_DOT || MODE == GS_LAG ? k + 1 : k;
         for (int row = tid; row < rows; row += kGsThreads) {
             df64 v = red[row];
 #pragma unroll
@@ -247,14 +320,26 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_df(size_t n, int k, const dou
 
 // out[row] = sum over the nb CTA partials of `row`, for rows < rows; with hn: out[rows] = hn and
 // out[rows + 1] = 1 / hn, hn = sqrt(max(out[rows-1] - sum_{i < rows-1} out[i]^2, 0)).
+// With lag (the record of GS_LAG's previous step, j = rows - 1): out[j] = u_j . w becomes
+// v_j . w = (out[j] - sum_{i<j} c_i out[i]) / alpha.
 __global__ void __launch_bounds__(1024) k_gs_final(int rows, int nb, const double* __restrict__ partials,
-                                                   double* __restrict__ out, int with_hn) {
+                                                   double* __restrict__ out, int with_hn,
+                                                   const double* __restrict__ lag) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int row = wid; row < rows; row += 32) {
         double v = 0.0;
         for (int b = lane; b < nb; b += 32) v += partials[size_t(row) * nb + b];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) out[row] = v;
+    }
+    if (lag) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int j = rows - 1;
+            double t = out[j];
+            for (int i = 0; i < j; ++i) t = fma(-lag[i], out[i], t);
+            out[j] = t * lag[j + 2];
+        }
     }
     if (!with_hn) return;
     __syncthreads();
@@ -268,7 +353,7 @@ __global__ void __launch_bounds__(1024) k_gs_final(int rows, int nb, const doubl
 }
 
 // Blocks per launch: as many CTAs as fit on the GPU at once (at most kGsMaxBlocks), per KB.
-int gs_blocks[3][4];
+int gs_blocks[4][4];
 int gs_device = -1;
 
 inline int kb_index(int k) { return k <= 8 ? 0 : k <= 16 ? 1 : k <= 32 ? 2 : 3; }
@@ -345,9 +430,9 @@ __global__ void k_df_store_scaled(size_t n, const double* __restrict__ w, double
     for (size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += size_t(gridDim.x) * blockDim.x)
         y[e] = q2::split_double(w[e]) * sc;
 }
-__global__ void k_df_to_double(size_t n, const df64* __restrict__ v, double* __restrict__ x) {
+__global__ void k_df_to_double(size_t n, const df64* __restrict__ v, double scale, double* __restrict__ x) {
     for (size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += size_t(gridDim.x) * blockDim.x)
-        x[e] = v[e].to_double();
+        x[e] = v[e].to_double() * scale;
 }
 
 inline unsigned stride_blocks(size_t n) {
@@ -364,8 +449,8 @@ cudaError_t launch_df_store_scaled(size_t n, const double* w, double scale, doub
     LAUNCH(PROF_KRYLOV, s, (k_df_store_scaled<<<stride_blocks(n), 256, 0, s>>>(n, w, scale, reinterpret_cast<df64*>(y))));
     return cudaGetLastError();
 }
-cudaError_t launch_df_to_double(size_t n, const double* v, double* x, cudaStream_t s) {
-    LAUNCH(PROF_KRYLOV, s, (k_df_to_double<<<stride_blocks(n), 256, 0, s>>>(n, reinterpret_cast<const df64*>(v), x)));
+cudaError_t launch_df_to_double(size_t n, const double* v, double* x, cudaStream_t s, double scale) {
+    LAUNCH(PROF_KRYLOV, s, (k_df_to_double<<<stride_blocks(n), 256, 0, s>>>(n, reinterpret_cast<const df64*>(v), scale, x)));
     return cudaGetLastError();
 }
 
@@ -379,6 +464,7 @@ cudaError_t gs_configure() {
     if ((e = configure_mode<GS_DOT>(sms)) != cudaSuccess) return e;
     if ((e = configure_mode<GS_PROJECT_DOT>(sms)) != cudaSuccess) return e;
     if ((e = configure_mode<GS_PROJECT_SCALE>(sms)) != cudaSuccess) return e;
+    if ((e = configure_mode<GS_LAG>(sms)) != cudaSuccess) return e;
     gs_device = dev;
     return cudaSuccess;
 }
@@ -389,7 +475,7 @@ cudaError_t launch_gs_dot(size_t n, int k, const double* V, size_t ld, const dou
     if (df && k > kGsMaxK) return cudaErrorInvalidValue;
     if (!df) return launch_multidot(n, k, V, ld, w, partials, out, s, false);
     const int nb = launch_df<GS_DOT>(n, k, V, ld, nullptr, const_cast<double*>(w), nullptr, nullptr, partials, s);
-    LAUNCH(PROF_KRYLOV, s, (k_gs_final<<<1, 1024, 0, s>>>(k, nb, partials, out, 0)));
+    LAUNCH(PROF_KRYLOV, s, (k_gs_final<<<1, 1024, 0, s>>>(k, nb, partials, out, 0, nullptr)));
     return cudaGetLastError();
 }
 
@@ -405,7 +491,7 @@ cudaError_t launch_gs_project_dot(size_t n, int k, const double* V, size_t ld, c
         return cudaGetLastError();
     }
     const int nb = launch_df<GS_PROJECT_DOT>(n, k, V, ld, h, w, nullptr, nullptr, partials, s);
-    LAUNCH(PROF_KRYLOV, s, (k_gs_final<<<1, 1024, 0, s>>>(k + 1, nb, partials, out, 1)));
+    LAUNCH(PROF_KRYLOV, s, (k_gs_final<<<1, 1024, 0, s>>>(k + 1, nb, partials, out, 1, nullptr)));
     return cudaGetLastError();
 }
 
@@ -420,6 +506,26 @@ cudaError_t launch_gs_project_scale(size_t n, int k, const double* V, size_t ld,
         return cudaGetLastError();
     }
     launch_df<GS_PROJECT_SCALE>(n, k, V, ld, h, const_cast<double*>(w), scale, y, nullptr, s);
+    return cudaGetLastError();
+}
+
+}  // namespace stk
+
+namespace stk {
+
+cudaError_t launch_gs_dot_lag(size_t n, int k, const double* V, size_t ld, const double* w, double* partials,
+                              double* out, const double* lag, cudaStream_t s) {
+    if (k <= 0 || k > kGsMaxK) return cudaErrorInvalidValue;
+    const int nb = launch_df<GS_DOT>(n, k, V, ld, nullptr, const_cast<double*>(w), nullptr, nullptr, partials, s);
+    LAUNCH(PROF_KRYLOV, s, (k_gs_final<<<1, 1024, 0, s>>>(k, nb, partials, out, 0, lag)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gs_lag_project(size_t n, int k, double* V, size_t ld, const double* h, const double* lag,
+                                  const double* w, double* partials, double* out, cudaStream_t s) {
+    if (k <= 0 || k > kGsMaxK) return cudaErrorInvalidValue;
+    const int nb = launch_df<GS_LAG>(n, k, V, ld, h, const_cast<double*>(w), lag, V, partials, s);
+    LAUNCH(PROF_KRYLOV, s, (k_gs_final<<<1, 1024, 0, s>>>(k + 1, nb, partials, out, 1, nullptr)));
     return cudaGetLastError();
 }
 

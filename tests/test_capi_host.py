@@ -58,3 +58,19 @@ def test_null_arguments(lib):
     assert lib.gmg_vcycle(None, 0, None, None, None) == capi.STOKES_EINVAL
     assert lib.stokes_size(None, 0, 0) == 0
     lib.stokes_destroy(None)
+
+
+@pytest.mark.parametrize("field,value", [("outer_solver", 4), ("outer_solver", -1), ("idr_s", 9),
+                                         ("precond_kind", 2), ("outer_solver", 3)])
+def test_option_validation(lib, field, value):
+    """Options are checked before any device work: out-of-range solvers, and MINRES (outer_solver 3)
+    without the symmetric positive definite P_D (precond_kind 1), are EINVAL."""
+    mesh = capi.stokes_mesh(0, 8, 4)
+    mu = capi.stokes_mu()
+    mu.kind = 0
+    o = capi.stokes_default_options()
+    setattr(o, field, value)
+    out = C.c_void_p()
+    st = lib.stokes_setup(C.byref(mesh), C.byref(mu), C.byref(capi.stokes_bc(0x3F)), C.byref(o), None, C.byref(out))
+    assert st == capi.STOKES_EINVAL
+    assert out.value is None

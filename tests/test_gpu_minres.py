@@ -1,0 +1,93 @@
+"""GPU parity of MINRES with the block-diagonal preconditioner P_D (option outer_solver = 3,
+method (ii)(b) of Section 2.2) through the C ABI against the oracle's minres on the same problems:
+iteration counts (FP64 V-cycle) within 10% of the oracle's, true residuals recomputed by the
+oracle's operator, solutions equal to the oracle's FGMRES solution to the accuracy the tolerance
+allows; the option is refused without P_D and by batched solves."""
+import functools
+
+import numpy as np
+import pytest
+
+import sinker_inputs as si
+from oracle import adaptive, gmg, krylov, mesh, operators, octree, sinker
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def capi():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1907_06696_gb300 import build as B
+    from paper_1907_06696_gb300 import capi as api
+    B.build()
+    api.load()
+    return api
+
+
+@functools.lru_cache(maxsize=None)
+def uniform_oracle(name):
+    p = si.workload(name)
+    m = mesh.Mesh(p.n)
+    mus = sinker.level_viscosities(m, p, p.n_levels)
+    G = gmg.GMG(p.n, p.n_levels, mus)
+    ops = G.levels[-1].ops
+    F = operators.assemble_rhs(m, sinker.forcing(m.quad_points(), p))
+    return p, m, G, ops, F
+
+
+def minres_options(capi):
+    o = capi.stokes_default_options()
+    o.outer_solver = 3
+    o.precond_kind = 1
+    return o
+
+
+@pytest.mark.parametrize("name", ["cube8", "cube16"])
+def test_minres_solve(capi, name):
+    p, m, G, ops, F = uniform_oracle(name)
+    b = np.concatenate([F, np.zeros(m.n_p)])
+    Pd = krylov.StokesPreconditioner(ops, G, kind="diagonal")
+    _, its_o, _ = krylov.minres(ops.apply_stokes, Pd.apply, b, rtol=1e-8, max_it=5000)
+    xf, _, _ = krylov.fgmres(ops.apply_stokes, krylov.StokesPreconditioner(ops, G).apply, b, rtol=1e-10)
+    xf = krylov.zero_mean_pressure(ops, xf)
+    ctx = capi.stokes_setup_problem(p, options=minres_options(capi))
+    for prec in (capi.STOKES_FP64, capi.STOKES_FP32):
+        for _ in range(2):      # the workspace is reused by the second solve
+            up = torch.zeros(m.n_u + m.n_p, dtype=torch.float64, device="cuda")
+            info = capi.stokes_solve(ctx, prec, None, up, rtol=1e-8, max_it=5000)
+            x = up.cpu().numpy()
+            true = np.linalg.norm(b - ops.apply_stokes(x)) / np.linalg.norm(b)
+            assert true <= 1e-8, (prec, true)
+            assert abs(info.rel_residual_true - true) <= 1e-3 * true + 1e-14
+            assert np.abs(x - xf).max() <= 1e-5 * np.abs(xf).max()
+            if prec == capi.STOKES_FP64:
+                assert abs(info.iterations - its_o) <= max(2, 0.1 * its_o), (info.iterations, its_o)
+    ctx.close()
+
+
+def test_minres_octree(capi):
+    p = si.octree_workload("oct_s")
+    lv = octree.balance(octree.refine_shells(p.base_level, p.centres, p.max_levels, p.shell_radius,
+                                             p.shell_half_width))
+    S = adaptive.AdaptiveStokes(octree.Octree(lv, p.coarsest_level), p)
+    ctx = capi.stokes_setup_octree_problem(p, options=minres_options(capi))
+    up = torch.zeros(S.n_u + S.n_p, dtype=torch.float64, device="cuda")
+    capi.stokes_solve(ctx, capi.STOKES_FP32, None, up, rtol=1e-8, max_it=5000)
+    b = np.concatenate([S.F, np.zeros(S.n_p)])
+    assert np.linalg.norm(b - S.apply_stokes(up.cpu().numpy())) / np.linalg.norm(b) <= 1e-8
+    ctx.close()
+
+
+def test_minres_refusals(capi):
+    p, m, G, ops, F = uniform_oracle("cube8")
+    o = capi.stokes_default_options()
+    o.outer_solver = 3                 # block-triangular P is not symmetric: refused at set-up
+    with pytest.raises(capi.StokesError):
+        capi.stokes_setup_problem(p, options=o)
+    ctx = capi.stokes_setup_problem(p, options=minres_options(capi))
+    up = torch.zeros(m.n_u + m.n_p, dtype=torch.float64, device="cuda")
+    with pytest.raises(capi.StokesError):
+        capi.stokes_batch_solve([ctx], capi.STOKES_FP32, [up])
+    ctx.close()
