@@ -155,18 +155,23 @@ def recorded_traffic(kernel, workload):
     return e.get("bytes_per_launch")
 
 
-def krylov_alg_bytes(N, its, m):
+def krylov_alg_bytes(N, its, m, delayed=True):
     """Algorithmic HBM bytes of the FGMRES vector kernels over a solve of `its` iterations with
     restart m: per cycle the residual (w = b - K x: 3 vectors, |w|: 1) and V_0 = w / beta (2);
-    per iteration with k = j + 1 basis vectors the FP64 copy of V_j for the preconditioner (2),
-    the three Gram-Schmidt passes, (k + 1) + (k + 2) vectors and (k + 2) more when V_k is
-    formed (k < m); x += Z y, k + 2; and the final residual."""
+    per iteration with k = j + 1 basis vectors the FP64 copy of row j for the preconditioner (2)
+    and the Gram-Schmidt passes: delayed re-orthogonalisation (option gram_schmidt 1) reads the
+    k rows and w twice and writes rows j and j + 1, (k + 1) + (k + 3); three passes read them
+    three times, (k + 1) + (k + 2) and (k + 2) more when V_k is formed (k < m); x += Z y, k + 2;
+    and the final residual."""
     vecs, left = N, its   # |b|
     while left > 0:
         kc = min(m, left)
         vecs += 6 * N
         for k in range(1, kc + 1):
-            vecs += (2 * k + 5) * N + ((k + 2) * N if k < m else 0)
+            if delayed:
+                vecs += (2 * k + 6) * N
+            else:
+                vecs += (2 * k + 5) * N + ((k + 2) * N if k < m else 0)
         vecs += (kc + 2) * N
         left -= kc
     vecs += 4 * N
@@ -417,7 +422,9 @@ def run_ours(args):
 
     # class-level roofline of the FGMRES vector kernels: algorithmic bytes of their passes over
     # the profiled solve / their summed time
-    kb = krylov_alg_bytes(N, its[-1], capi.stokes_default_options().restart)
+    dopt = capi.stokes_default_options()
+    kb = krylov_alg_bytes(N, its[-1], dopt.restart,
+                          dopt.gram_schmidt == 1 and dopt.outer_arith == 1 and dopt.restart <= 64)
     kt = prof["krylov_vec"][0] / 1e3
     line["roofline_krylov"] = {"kernels": "k_gs_df (Gram-Schmidt passes), k_gs_final, k_df_*, k_axpby, norms",
                                "bound": "hbm", "achieved": kb / kt / 1e9, "peak": hbm, "unit": "GB/s",

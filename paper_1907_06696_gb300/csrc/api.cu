@@ -1615,7 +1615,7 @@ void stokes_default_options(stokes_options* opt) {
     opt->precond_kind = 0;
     opt->outer_solver = 0;
     opt->idr_s = 2;
-    opt->gram_schmidt = 0;
+    opt->gram_schmidt = 1;
 }
 
 const char* stokes_strerror(stokes_status s) {
