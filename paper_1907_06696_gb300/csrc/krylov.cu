@@ -56,10 +56,17 @@ constexpr int kGsMaxBlocks = 2432;          // 16 per SM on 152 SMs; the partial
 
 enum GsMode { GS_DOT = 0, GS_PROJECT_DOT = 1, GS_PROJECT_SCALE = 2, GS_LAG = 3 };
 
-// An entry pair is handled by TPE = KB / RB threads (adjacent lanes), each owning RB <= 16
-// basis rows: one thread up to KB = 8, two up to 32, four at 64 (measured: more rows per
-// thread is slower).
-__host__ __device__ constexpr int gs_rb(int /*mode*/, int kb) { return kb <= 8 ? kb : kb / 2 > 16 ? 16 : kb / 2; }
+// An entry pair is handled by TPE = KB / RB threads (adjacent lanes), each owning RB <= STK_GS_RB
+// basis rows: with 16, one thread up to KB = 8, two up to 32, four at 64. Measured on whole 64^3
+// and 96^3 solves: 32 rows per thread is slower, and so are 8 (Krylov kernels +10% / +13%) and 4
+// (+69% / +84%): fewer rows per thread add shuffles and partial sums faster than the higher
+// occupancy hides latency.
+#ifndef STK_GS_RB
+#define STK_GS_RB 16
+#endif
+__host__ __device__ constexpr int gs_rb(int /*mode*/, int kb) {
+    return kb <= 8 ? kb : kb / 2 > STK_GS_RB ? STK_GS_RB : kb / 2;
+}
 template <int MODE, int KB>
 struct GsShape {
     static constexpr int RB = gs_rb(MODE, KB);
