@@ -65,6 +65,8 @@ def parse():
                          "--precond both adds MINRES with P_D next to FGMRES with P_D")
     ap.add_argument("--fp32-only", action="store_true",
                     help="with --solve-report: skip the FP64-V-cycle legs (largest problems)")
+    ap.add_argument("--schur-degree", type=int, default=None,
+                    help="with --solve-report: S_hat^-1 Chebyshev degree of the main solver (0 = diag(M_p))")
     ap.add_argument("--precond", default="triangular", choices=["triangular", "both"],
                     help="with --solve-report: 'both' adds FP32-V-cycle solves with the block-diagonal P_D "
                          "(Table 1 comparison)")
@@ -606,11 +608,13 @@ def run_report(args):
     solver_id = {"fgmres": 0, "idr": 1, "gmres": 2}
     names = {0: "FGMRES(50)", 1: "IDR(2)", 2: "GMRES(50)"}
     opts.outer_solver = solver_id.get(args.outer, 0)
+    if args.schur_degree is not None:
+        opts.schur_degree = args.schur_degree
     ctx = capi.stokes_setup_problem(prob, options=opts)
     setup_s = time.perf_counter() - t0
     N = ctx.n_u + ctx.n_p
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    out = {"outer": names[opts.outer_solver]}
+    out = {"outer": names[opts.outer_solver], "schur_degree": opts.schur_degree}
     sols = {}
     extra = {"both": ("idr",), "all": ("idr", "gmres")}.get(args.outer, ())
     for other in extra:   # other solvers first, each on a context of its own (main basis not allocated yet)

@@ -102,7 +102,8 @@ typedef struct {
     double smoothing_range;     /* eigenvalue interval [lam_hi / range, lam_hi] (15) */
     double eig_safety;          /* lam_hi = safety * Lanczos estimate of lambda_max(D^-1 A) (1.2) */
     int lanczos_steps;          /* Lanczos steps for lambda_max (12) */
-    int schur_degree;           /* Chebyshev degree of S_hat^-1 on M_p, interval [1/8, 27/8] (5) */
+    int schur_degree;           /* Chebyshev degree of S_hat^-1 on M_p, interval [1/8, 27/8] (5); 0 = S_hat =
+                                   diag(M_p) itself (Section 3.4; degree 1 is (4/7) diag(M_p)^-1) */
     int restart;                /* FGMRES restart length (50, Section 3.4) */
     int outer_arith;            /* arithmetic of the FP64-interface outer operator: 0 = native FP64;
                                    1 = double-float (pairs of floats, ~48-bit significand) on the FP32

@@ -315,6 +315,8 @@ class AdaptiveStokes:
         return np.where(self.dirichlet, b_active, x)
 
     def schur_inverse(self, r_p, degree=5):
+        if degree == 0:                         # S_hat = diag(M_p)
+            return r_p / self.Mp_diag
         return chebyshev_smooth(self.apply_Mp, 1.0 / self.Mp_diag, r_p, None, degree, 1.0 / 8.0, 27.0 / 8.0, True)
 
     def precondition(self, r):

@@ -35,9 +35,12 @@ class StokesPreconditioner:
         self.exact_S = exact_S
 
     def schur_inverse(self, r_p):
-        """S_hat^-1 r_p: Jacobi-Chebyshev on M_p, interval [1/8, 27/8], zero guess."""
+        """S_hat^-1 r_p: Jacobi-Chebyshev on M_p, interval [1/8, 27/8], zero guess; degree 0 is
+        S_hat = diag(M_p) itself, the fixed approximation Section 3.4 names for non-flexible GMRES."""
         if self.exact_S is not None:
             return self.exact_S(r_p)
+        if self.schur_degree == 0:
+            return self.Mp_dinv * r_p
         return chebyshev_smooth(self.ops.apply_Mp, self.Mp_dinv, r_p, None,
                                 self.schur_degree, 1.0 / 8.0, 27.0 / 8.0, True)
 

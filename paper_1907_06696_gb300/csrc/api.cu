@@ -471,7 +471,9 @@ stokes_status oct_schur_inverse(stokes_ctx* c, const double* rp, double* zp, cud
     const double lo = 1.0 / 8.0, hi = 27.0 / 8.0;
     const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
     double rho = 1.0 / sigma;
-    CK(launch_cheb_update<double>(np, rp, nullptr, c->mp_dinv, c->sp_d, zp, 0.0, 1.0 / theta, false, s));
+    // degree 0: S_hat = diag(M_p) itself (Section 3.4); otherwise the first Chebyshev step
+    const double c0 = c->opt.schur_degree == 0 ? 1.0 : 1.0 / theta;
+    CK(launch_cheb_update<double>(np, rp, nullptr, c->mp_dinv, c->sp_d, zp, 0.0, c0, false, s));
     for (int it = 1; it < c->opt.schur_degree; ++it) {
         CK(launch_oct_mass_p(c->oct->act, zp, c->sp_t, s));
         const double rho_new = 1.0 / (2.0 * sigma - rho);
@@ -506,7 +508,9 @@ stokes_status schur_inverse(stokes_ctx* c, const double* rp, double* zp, cudaStr
     const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
     double rho = 1.0 / sigma;
     const double* mu = c->lev[c->L - 1].v64.mu;
-    CK(launch_cheb_update<double>(g.n_p, rp, nullptr, c->mp_dinv, c->sp_d, zp, 0.0, 1.0 / theta, false, s));
+    // degree 0: S_hat = diag(M_p) itself (Section 3.4); otherwise the first Chebyshev step
+    const double c0 = c->opt.schur_degree == 0 ? 1.0 : 1.0 / theta;
+    CK(launch_cheb_update<double>(g.n_p, rp, nullptr, c->mp_dinv, c->sp_d, zp, 0.0, c0, false, s));
     for (int it = 1; it < c->opt.schur_degree; ++it) {
         CK(launch_mass_p(g, mu, zp, c->sp_t, s));
         const double rho_new = 1.0 / (2.0 * sigma - rho);
@@ -1147,7 +1151,7 @@ stokes_status minres_solve(stokes_ctx* c, int prec, const double* b, double* x, 
 
 stokes_status validate_options(const stokes_options& o) {
     if (o.cheb_degree < 1 || o.smoothing_range <= 1.0 || o.eig_safety <= 0.0 || o.lanczos_steps < 1 ||
-        o.schur_degree < 1 || o.restart < 1 || o.restart > 500 || (o.outer_arith != 0 && o.outer_arith != 1) ||
+        o.schur_degree < 0 || o.restart < 1 || o.restart > 500 || (o.outer_arith != 0 && o.outer_arith != 1) ||
         (o.vmult_kernel != 0 && o.vmult_kernel != 1) || (o.graphs != 0 && o.graphs != 1) ||
         (o.precond_kind != 0 && o.precond_kind != 1) || o.outer_solver < 0 || o.outer_solver > 3 || (o.gram_schmidt != 0 && o.gram_schmidt != 1) ||
         (o.outer_solver == 3 && o.precond_kind != 1) ||

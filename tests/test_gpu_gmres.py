@@ -93,3 +93,28 @@ def test_gmres_batch(capi):
         assert np.linalg.norm(b - ops.apply_stokes(up.cpu().numpy())) / np.linalg.norm(b) <= 1e-8
     for c in ctxs:
         c.close()
+
+
+def test_gmres_diagonal_schur(capi):
+    """S_hat = diag(M_p) (schur_degree = 0, the fixed approximation Section 3.4 names for GMRES):
+    the Schur inverse equals diag(M_p)^-1 r to rounding, and GMRES with it converges with the
+    oracle's iteration count."""
+    p, m, G, ops, F = uniform_oracle("cube16")
+    o = gmres_options(capi)
+    o.schur_degree = 0
+    ctx = capi.stokes_setup_problem(p, options=o)
+    rng = np.random.default_rng(3)
+    rp = rng.uniform(-1, 1, m.n_p)
+    zp = torch.zeros(m.n_p, dtype=torch.float64, device="cuda")
+    capi.stokes_schur_inverse(ctx, torch.tensor(rp, device="cuda"), zp)
+    Pc = krylov.StokesPreconditioner(ops, G, schur_degree=0)
+    ref = Pc.schur_inverse(rp)
+    assert np.abs(zp.cpu().numpy() - ref).max() <= 1e-13 * np.abs(ref).max()
+    b = np.concatenate([F, np.zeros(m.n_p)])
+    _, its_o, _ = krylov.gmres(ops.apply_stokes, Pc.apply, b, rtol=1e-8, max_it=5000)
+    up = torch.zeros(m.n_u + m.n_p, dtype=torch.float64, device="cuda")
+    info = capi.stokes_solve(ctx, capi.STOKES_FP64, None, up, rtol=1e-8, max_it=5000)
+    x = up.cpu().numpy()
+    assert np.linalg.norm(b - ops.apply_stokes(x)) / np.linalg.norm(b) <= 1e-8
+    assert abs(info.iterations - its_o) <= 1, (info.iterations, its_o)
+    ctx.close()
