@@ -80,6 +80,22 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def max_over_ranks(value, dist=None, device="cpu"):
+    """The largest `value` over all ranks (every rank gets it); `value` itself without a process
+    group. The replicas' step time is the slowest rank's."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, n_dofs, ms):
+    """Whole-job GDoF/s of `world` replicas that each solve n_dofs in `ms` (the slowest rank's time)."""
+    return world * n_dofs / (ms / 1e3) / 1e9
+
+
 # ----------------------------------------------------------------- clocks
 CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
            "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -303,13 +319,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     launches = capi.stokes_launch_count() - l0
     clocks = clocks_stop(clk, clk_path)
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, "cuda")
     if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
-    value = world * N / (ms / 1e3) / 1e9
+    value = replica_throughput(world, N, ms)
     true_res32 = info.rel_residual_true
     if rank != 0:
         return
