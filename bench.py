@@ -35,17 +35,22 @@ sys.path.insert(0, ROOT)
 
 METRIC = "vmult GDoF/s & %HBM peak; Stokes solve s to 1e-8 rel (FP32 vs FP64 GMG)"
 RTOL = 1e-8
-# Algorithmic flops per cell of the FP64 outer operator [A B^T; B 0] as implemented
-# (multiply-add = 2 flops): A by sum factorisation 2916 MACs; B^T and B as tensor
-# products of 3x2 moment matrices, 3 components x 114 MACs each.
-STOKES_FLOP_PER_CELL = 2 * (2916 + 342 + 342)
+# Algorithmic flops per cell of the velocity operator A by sum factorisation as implemented
+# (multiply-add = 2 flops): 36 sweeps of 9 lines. Interpolations and their transposes (18
+# sweeps): 3 outputs x 3 MACs per line. Derivatives (9 sweeps): the outer outputs 3 MACs, the
+# middle one a difference times a constant (the derivative matrix at symmetric Gauss points is
+# antisymmetric, its centre 0), 2 flops. Transposed derivatives (9): 3 MACs, and a difference
+# and one MAC, 3 flops.
+A_FLOP_PER_CELL = 18 * 9 * 18 + 9 * 9 * (12 + 2) + 9 * 9 * (12 + 3)
+# Outer operator [A B^T; B 0]: B^T and B as tensor products of 3x2 moment matrices, 3
+# components x 114 MACs each.
+STOKES_FLOP_PER_CELL = A_FLOP_PER_CELL + 2 * (342 + 342)
 # FP32 instructions per cell of the double-float outer operator (estimate from the implemented
-# sweeps): 729 three-term outputs at ~31 instructions (interpolations, derivatives), 243
-# accumulating outputs at ~38 (transposed derivatives), 81 products at 7 (mu h scaling), and the
-# B/B^T moments, 684 multiply-adds at ~18.
-DF64_OPS_PER_CELL = 729 * 31 + 243 * 38 + 81 * 7 + 684 * 18
-# Same for the velocity operator alone.
-A_FLOP_PER_CELL = 2 * 2916
+# sweeps and the double-float primitives): 648 three-term outputs at 31 instructions (dot3), 81
+# middle derivative outputs at 18 (difference 11, product 7), 162 accumulating outputs at 39
+# (dot3_acc) and 81 middle ones at 29 (transposed derivatives), 81 products at 7 (mu h
+# scaling), and the B/B^T moments, 684 multiply-adds at ~18.
+DF64_OPS_PER_CELL = 648 * 31 + 81 * 18 + 162 * 39 + 81 * 29 + 81 * 7 + 684 * 18
 
 
 def parse():

@@ -97,6 +97,10 @@ __host__ __device__ __forceinline__ void interpT(T* x) {
         }
 }
 
+// The Gauss points are symmetric about 1/2, so DC(2-q, 2-m) = -DC(q, m): the middle row and
+// column of DC are DC(1,0) (1, 0, -1) and DC(0,1) (1, 0, -1) (DC(1,1) = 0), and gw(0) = gw(2).
+// The sweeps use that for the middle output (two operations instead of three multiply-adds).
+
 // g (+)= DC x along AX (collocation derivative at the Gauss points).
 template <int AX, bool ADD, typename T>
 __host__ __device__ __forceinline__ void deriv(const T* x, T* g) {
@@ -107,7 +111,8 @@ __host__ __device__ __forceinline__ void deriv(const T* x, T* g) {
             const T a0 = x[lin<AX>(0, o1, o2)], a1 = x[lin<AX>(1, o1, o2)], a2 = x[lin<AX>(2, o1, o2)];
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                const T v = T(DC(q, 0)) * a0 + T(DC(q, 1)) * a1 + T(DC(q, 2)) * a2;
+                const T v = q == 1 ? T(DC(1, 0)) * (a0 - a2)
+                                   : T(DC(q, 0)) * a0 + T(DC(q, 1)) * a1 + T(DC(q, 2)) * a2;
                 if (ADD) g[lin<AX>(q, o1, o2)] += v; else g[lin<AX>(q, o1, o2)] = v;
             }
         }
@@ -124,8 +129,11 @@ __host__ __device__ __forceinline__ void derivT_w(const T* g, T* w) {
 #pragma unroll
             for (int m = 0; m < 3; ++m) {
                 const double wl = gw(o1) * gw(o2) * double(S);
-                w[lin<AX>(m, o1, o2)] += T(DC(0, m) * gw(0) * wl) * a0 + T(DC(1, m) * gw(1) * wl) * a1 +
-                                         T(DC(2, m) * gw(2) * wl) * a2;
+                if (m == 1)
+                    w[lin<AX>(1, o1, o2)] += T(DC(0, 1) * gw(0) * wl) * (a0 - a2);
+                else
+                    w[lin<AX>(m, o1, o2)] += T(DC(0, m) * gw(0) * wl) * a0 + T(DC(1, m) * gw(1) * wl) * a1 +
+                                             T(DC(2, m) * gw(2) * wl) * a2;
             }
         }
 }
@@ -167,8 +175,11 @@ __host__ __device__ __forceinline__ void deriv(const df64* x, df64* g) {
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 df64& out = g[lin<AX>(q, o1, o2)];
-                out = ADD ? dot3_acc(out, df64(DC(q, 0)), a0, df64(DC(q, 1)), a1, df64(DC(q, 2)), a2)
-                          : dot3(df64(DC(q, 0)), a0, df64(DC(q, 1)), a1, df64(DC(q, 2)), a2);
+                if (q == 1)
+                    out = ADD ? out + df64(DC(1, 0)) * (a0 - a2) : df64(DC(1, 0)) * (a0 - a2);
+                else
+                    out = ADD ? dot3_acc(out, df64(DC(q, 0)), a0, df64(DC(q, 1)), a1, df64(DC(q, 2)), a2)
+                              : dot3(df64(DC(q, 0)), a0, df64(DC(q, 1)), a1, df64(DC(q, 2)), a2);
             }
         }
 }
@@ -183,8 +194,11 @@ __host__ __device__ __forceinline__ void derivT_w(const df64* g, df64* w) {
             for (int m = 0; m < 3; ++m) {
                 const double wl = gw(o1) * gw(o2) * double(S);
                 df64& out = w[lin<AX>(m, o1, o2)];
-                out = dot3_acc(out, df64(DC(0, m) * gw(0) * wl), a0, df64(DC(1, m) * gw(1) * wl), a1,
-                               df64(DC(2, m) * gw(2) * wl), a2);
+                if (m == 1)
+                    out = out + df64(DC(0, 1) * gw(0) * wl) * (a0 - a2);
+                else
+                    out = dot3_acc(out, df64(DC(0, m) * gw(0) * wl), a0, df64(DC(1, m) * gw(1) * wl), a1,
+                                   df64(DC(2, m) * gw(2) * wl), a2);
             }
         }
 }
