@@ -16,13 +16,18 @@ namespace stk {
 namespace {
 
 template <bool DO_A, bool DO_BT, bool DO_B>
-__global__ void __launch_bounds__(kOuterThreads, 3) k_outer_df64(OuterArgs a) {
+__global__ void __launch_bounds__(kOuterThreads, 4) k_outer_df64(OuterArgs a) {
     extern __shared__ __align__(16) unsigned char outer_smem[];
     OuterShared& sh = *reinterpret_cast<OuterShared*>(outer_smem);
     const int c = threadIdx.x / kOuterCells, g = threadIdx.x % kOuterCells;
     {
-        q2::df64 U[27];
-        outer_phase1<DO_A, DO_B>(a, c, blockIdx.x, g, sh, U);
+        q2::df64 T2[27];
+        {
+            q2::df64 U[27];
+            outer_phase1<DO_A, DO_B>(a, c, blockIdx.x, g, sh, U, T2);
+        }
+        __syncthreads();
+        outer_phase1b<DO_A>(a, c, blockIdx.x, g, sh, T2);
     }
     __syncthreads();
     q2::df64 W[27];

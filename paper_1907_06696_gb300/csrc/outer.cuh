@@ -8,7 +8,10 @@
 //   W_c  = 2 DC_c^T (w .* DC_c U_c)                          (diagonal term)
 //        + sum_{d != c} DC_d^T (w .* (DC_d U_c + DC_c U_d))   (symmetric pairs)
 // The products DC_d U_c (d != c) and DC_c U_c are exchanged through shared
-// memory so that each thread only keeps its own component. Then
+// memory so that each thread only keeps its own component: the symmetric pair of
+// components c and c+1 (mod 3) has one slot, which warp c writes and warp c+1 adds to
+// after a barrier (three pair slots instead of six ordered ones: 41.5 KB of shared memory
+// per CTA, four CTAs per SM). Then
 // out_c = mu h V^T W_c - h^2 (moments of B^T) p, and B's moments of u_c are
 // added into the pressure output per component.
 // The phases are plain functions of the thread index so that a host program
@@ -34,14 +37,12 @@ struct OuterArgs {
     double* dst_p;
 };
 
-// Shared exchange buffer: X[pair(c,d)][q][g] over the 6 ordered pairs c != d, and the
-// diagonal term Dg[c][q][g] = DC_c U_c (so that phase 1 holds only U and one temporary).
+// Shared exchange buffer: X[c][q][g] = DC_{c+1} U_c + DC_c U_{c+1} (indices mod 3), the
+// symmetric pair of components c and c+1, and the diagonal term Dg[c][q][g] = DC_c U_c.
 struct OuterShared {
-    q2::df64 X[6][27][kOuterCells];
+    q2::df64 X[3][27][kOuterCells];
     q2::df64 Dg[3][27][kOuterCells];
 };
-
-__host__ __device__ __forceinline__ constexpr int outer_pair(int c, int d) { return 2 * c + (d > c ? d - 1 : d); }
 
 __host__ __device__ __forceinline__ bool outer_bnd(int g, int M) { return g == 0 || g == M - 1; }
 
@@ -97,10 +98,11 @@ __host__ __device__ __forceinline__ int outer_gq(const OuterFrame& f, int q) {
 }
 
 // Phase 1: gather own component, B moments, interpolation, and the diagonal derivative
-// DC_0 U and the two cross products DC_1 U, DC_2 U (local axes) into shared memory.
+// DC_0 U and the cross product DC_1 U (local axes) into shared memory; the other cross product
+// DC_2 U is left in T2 for phase 1b.
 template <bool DO_A, bool DO_B>
 __host__ __device__ __forceinline__ void outer_phase1(const OuterArgs& a, int C, int blk, int g, OuterShared& sh,
-                                                      q2::df64 (&U)[27]) {
+                                                      q2::df64 (&U)[27], q2::df64 (&T2)[27]) {
     using q2::df64;
     const size_t cells = size_t(a.n) * a.n * a.n;
     const size_t cell = size_t(blk) * kOuterCells + g;
@@ -150,10 +152,27 @@ __host__ __device__ __forceinline__ void outer_phase1(const OuterArgs& a, int C,
     for (int q = 0; q < 27; ++q) sh.Dg[C][outer_gq(f, q)][g] = T[q];
     q2::deriv<1, false>(U, T);
 #pragma unroll
-    for (int q = 0; q < 27; ++q) sh.X[outer_pair(C, D1)][outer_gq(f, q)][g] = T[q];
-    q2::deriv<2, false>(U, T);
+    for (int q = 0; q < 27; ++q) sh.X[C][outer_gq(f, q)][g] = T[q];     // pair (C, D1): writer
+    q2::deriv<2, false>(U, T2);
+    (void)D1;
+    (void)D2;
+}
+
+// Phase 1b (after a barrier): add this thread's DC_2 U (local axis 2 = global axis D2), i.e.
+// DC_{D2} U_C, into the slot of the pair (D2, C), which warp D2 wrote with DC_C U_{D2}.
+template <bool DO_A>
+__host__ __device__ __forceinline__ void outer_phase1b(const OuterArgs& a, int C, int blk, int g, OuterShared& sh,
+                                                       const q2::df64 (&T2)[27]) {
+    if (!DO_A) return;
+    const size_t cells = size_t(a.n) * a.n * a.n;
+    const size_t cell = size_t(blk) * kOuterCells + g;
+    const OuterFrame f = outer_frame(a, C, cell < cells ? cell : 0);
+    const int D2 = f.D2;
 #pragma unroll
-    for (int q = 0; q < 27; ++q) sh.X[outer_pair(C, D2)][outer_gq(f, q)][g] = T[q];
+    for (int q = 0; q < 27; ++q) {
+        q2::df64& x = sh.X[D2][outer_gq(f, q)][g];
+        x = x + T2[q];
+    }
 }
 
 // Phase 2 (after a barrier): diagonal and symmetric pairs, transposed interpolation,
@@ -175,17 +194,12 @@ __host__ __device__ __forceinline__ void outer_phase2(const OuterArgs& a, int C,
         for (int q = 0; q < 27; ++q) T[q] = sh.Dg[C][outer_gq(f, q)][g];
         q2::derivT_w<0, 2>(T, W);
 #pragma unroll
-        for (int q = 0; q < 27; ++q) {
-            const int gq = outer_gq(f, q);
-            T[q] = sh.X[outer_pair(C, D1)][gq][g] + sh.X[outer_pair(D1, C)][gq][g];
-        }
+        for (int q = 0; q < 27; ++q) T[q] = sh.X[C][outer_gq(f, q)][g];    // pair (C, D1)
         q2::derivT_w<1, 1>(T, W);
 #pragma unroll
-        for (int q = 0; q < 27; ++q) {
-            const int gq = outer_gq(f, q);
-            T[q] = sh.X[outer_pair(C, D2)][gq][g] + sh.X[outer_pair(D2, C)][gq][g];
-        }
+        for (int q = 0; q < 27; ++q) T[q] = sh.X[D2][outer_gq(f, q)][g];   // pair (D2, C)
         q2::derivT_w<2, 1>(T, W);
+        (void)D1;
         q2::interpT<0>(W);
         q2::interpT<1>(W);
         q2::interpT<2>(W);

