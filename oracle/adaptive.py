@@ -12,7 +12,8 @@ weights. Dirichlet rows and columns of A are replaced by the identity, B drops D
 velocity columns and B^T has zero Dirichlet rows, as on the uniform mesh.
 
 Local smoothing (parity unpinned beyond "oracle = the same algorithm": the paper cites the
-method). Level l holds all cells of level l; its operator A_l is assembled from them with
+method; pinned by equality with the uniform GMG on a uniform octree, by the symmetry of the
+V-cycle with variable viscosity, and by a handful of iterations for constant viscosity). Level l holds all cells of level l; its operator A_l is assembled from them with
 the level viscosity (a leaf's harmonic average, a refined cell's mean over its children)
 and identity rows on the cube boundary, edge nodes kept as ordinary rows and columns.
 Smoothing touches only nodes that are neither on the cube boundary nor on the refinement
