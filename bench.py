@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cube64")
     ap.add_argument("--no-extras", action="store_true", help="skip the sweep/profile/e2e/cpu legs")
+    ap.add_argument("--vmult-sweep", action="store_true",
+                    help="finest-level velocity operator A, FP32 and FP64, on uniform meshes of 16..128 cells per "
+                         "axis (8 sinkers, viscosity ratio 1e4); one JSON line per size")
     ap.add_argument("--solve-report", action="store_true",
                     help="one FP32-V-cycle and one FP64-V-cycle solve of the workload: iterations, times, "
                          "true FP64 residuals and the difference of the two solutions (any size)")
@@ -821,8 +824,72 @@ def run_octree(args):
     ctx.close()
 
 
+SWEEP_SIZES = ((16, 5), (32, 6), (48, 5), (64, 7), (96, 6), (128, 8))   # (n, multigrid levels), n = c 2^(L-1)
+
+
+def run_vmult_sweep(args):
+    """Standalone velocity operator A on the finest level across mesh sizes: CUDA-event time per
+    call (median of 20 after 3 warm-ups), the kernel's own time from the class profile, GDoF/s,
+    algorithmic GB/s ((2 N_u + cells) x word size) and its fraction of the measured HBM peak (only
+    meaningful where the vectors exceed L2, flagged), and GFLOP/s. Sources are U(0, 1)."""
+    import statistics
+    import torch
+    from paper_1907_06696_gb300 import build as B
+    B.build()
+    from paper_1907_06696_gb300 import capi
+    capi.load()
+    import sinker_inputs as si
+    torch.cuda.set_device(0)
+    pk = peaks()
+    hbm = pk.get("hbm_gbs", 6800.0)
+    l2 = getattr(torch.cuda.get_device_properties(0), "L2_cache_size", 129 * 2 ** 20)
+    stream = torch.cuda.current_stream()
+    for n, levels in SWEEP_SIZES:
+        prob = si.dr_problem(n, levels, 8, 1e4, 1930 + n, "sweep%d" % n)
+        ctx = capi.stokes_setup_problem(prob, stream=stream)
+        n_u, cells = ctx.n_u, n ** 3
+        out = {"sweep": "vmult_A", "n": n, "n_u": n_u, "peak_gbs": hbm,
+               "peak_note": "of measured" if "hbm_gbs" in pk else "of fallback"}
+        for tag, dtype, word in (("fp32", torch.float32, 4), ("fp64", torch.float64, 8)):
+            prec = capi.STOKES_FP32 if tag == "fp32" else capi.STOKES_FP64
+            x = torch.rand(n_u, device="cuda", dtype=dtype)
+            y = torch.empty_like(x)
+            for _ in range(3):
+                capi.stokes_vmult(ctx, -1, capi.BLOCK_A, prec, x, y, stream=stream)
+            ts = []
+            for _ in range(20):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                capi.stokes_vmult(ctx, -1, capi.BLOCK_A, prec, x, y, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1) / 1e3)
+            capi.stokes_profile(1)
+            capi.stokes_profile_read(reset=True)
+            for _ in range(5):
+                capi.stokes_vmult(ctx, -1, capi.BLOCK_A, prec, x, y, stream=stream)
+            torch.cuda.synchronize()
+            prof = capi.stokes_profile_read(reset=True)
+            capi.stokes_profile(0)
+            kname = "vmult_A_" + tag
+            t_call = statistics.median(ts)
+            t_kern = (prof[kname][0] + prof["smoother_vec"][0]) / max(prof[kname][1], 1) / 1e3
+            bytes_alg = (2 * n_u + cells) * word
+            out[tag] = {"call_ms": t_call * 1e3, "gdofs": n_u / t_call / 1e9, "kernel_ms": t_kern * 1e3,
+                        "kernel_gdofs": n_u / t_kern / 1e9, "achieved_gbs": bytes_alg / t_kern / 1e9,
+                        "hbm_frac": bytes_alg / t_kern / 1e9 / hbm, "exceeds_l2": 2 * n_u * word > l2,
+                        "gflops": cells * A_FLOP_PER_CELL / t_kern / 1e9}
+            del x, y
+        ctx.close()
+        torch.cuda.empty_cache()
+        print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.vmult_sweep:
+        run_vmult_sweep(args)
+        return
     if args.solve_report:
         run_report(args)
         return
