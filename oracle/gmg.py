@@ -7,7 +7,7 @@ recursive coarse correction, prolongation. Level operators are the
 rediscretised fully coupled operators with the level viscosity (Section 2.3);
 the coarsest level is solved exactly (dense, FP64).
 
-Readings of points the paper leaves open (listed in the design doc as well):
+Readings of points the paper leaves open:
 * degree k = k applications of D^-1 A in the error polynomial; the
   eigenvalue interval is [beta/15, beta] with beta = 1.2 lambda_max(D^-1 A),
   lambda_max from 12 Lanczos steps on D^-1/2 A D^-1/2 started from a seeded
