@@ -272,12 +272,15 @@ stokes_status gmg_vcycle(stokes_ctx* ctx, int prec, const void* rhs_dev, void* x
 
 /* Solve [[A, B^T], [B, 0]] [u; p] = [rhs_u; rhs_p] with right-preconditioned
  * FP64 FGMRES(restart) (Section 2.2.2) and P^-1 of eq. stokes_precond:
- * z_p = -S_hat^-1 r_p, z_u = V(r_u - B^T z_p), the V-cycle in `vcycle_prec`.
- * rhs_dev = NULL uses the sinker right-hand side [F; 0]. up_dev: in = initial
- * guess, out = solution with zero-mean pressure. Stops when the recurrence
- * residual <= rtol ||b||. Host-synchronous (one small device->host read per
- * iteration). Errors: NOT_CONVERGED (max_it reached; up holds the last
- * iterate), BREAKDOWN, EINVAL, ENOMEM, ECUDA. */
+ * z_p = -S_hat^-1 r_p, z_u = V(r_u - B^T z_p), the V-cycle in `vcycle_prec`
+ * (options outer_solver and precond_kind select GMRES, IDR(s) or MINRES and the
+ * block-diagonal P_D instead). rhs_dev = NULL uses the sinker right-hand side
+ * [F; 0]. up_dev: in = initial guess, out = solution with zero-mean pressure.
+ * Stops when the recurrence residual <= rtol ||b|| and the true residual
+ * b - K x, recomputed with the native FP64 operator, is too; otherwise the
+ * method restarts from x (at most 10 times). Host-synchronous (small
+ * device->host reads per iteration). Errors: NOT_CONVERGED (max_it reached; up
+ * holds the last iterate), BREAKDOWN, EINVAL, ENOMEM, ECUDA. */
 stokes_status stokes_solve(stokes_ctx* ctx, int vcycle_prec, const double* rhs_dev, double* up_dev,
                            double rtol, int max_it, stokes_solve_info* info, void* stream);
 
