@@ -285,8 +285,9 @@ stokes_status stokes_solve(stokes_ctx* ctx, int vcycle_prec, const double* rhs_d
                            double rtol, int max_it, stokes_solve_info* info, void* stream);
 
 /* Solve n_problems independent Stokes systems together (each context from its own stokes_setup,
- * any sizes): the same FGMRES as stokes_solve, with the iterations of all unconverged problems
- * advancing in lock step. Each problem's kernels run on its own stream (streams[i]; streams = NULL:
+ * any sizes): the same FGMRES (or GMRES, per context option outer_solver 0 or 2) as stokes_solve,
+ * with the iterations of all unconverged problems advancing in lock step; contexts set up for IDR(s)
+ * or MINRES are EINVAL. Each problem's kernels run on its own stream (streams[i]; streams = NULL:
  * library-created streams), so small problems share the GPU, and each problem's V-cycle is replayed
  * as its captured graph. rhs_devs = NULL or rhs_devs[i] = NULL: the sinker right-hand side [F; 0].
  * up_devs[i]: in = initial guess, out = solution (zero-mean pressure). infos[i] (optional) per
