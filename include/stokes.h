@@ -227,6 +227,24 @@ stokes_status stokes_octree_sinker_mesh(int base_level, int n_sinkers, const dou
 stokes_status stokes_setup_octree(const stokes_octree* mesh, const stokes_mu* mu, const stokes_bc* bc,
                                   const stokes_options* opt, void* stream, stokes_ctx** out);
 
+/* Adaptive refinement by a gradient indicator (Section 3.3: each new mesh refines about 1/7 of the
+ * cells chosen by a gradient-based estimator, so that the cell count about doubles; the estimator
+ * is not specified). Indicator of leaf K of side h: eta_K = h^(5/2) |grad u_h(x_K)|_F, the
+ * Frobenius norm of the Q2 velocity's gradient at the leaf centre (there d/dx u is the difference
+ * of the two face-centre values over h), the leaf's values taken from the active vector through
+ * the hanging-node constraints with Dirichlet values read as 0. The floor(n fraction + 1/2) leaves
+ * with the largest eta (equal eta: smaller key first) are split into their 8 children; the result
+ * is 2:1 balanced. mesh: the current leaves (any order) and coarsest level; u_host: host, the
+ * active velocity [3][active nodes] of that mesh (the first 3 x nodes entries of a stokes_solve
+ * result on a context set up from it); fraction in (0, 1] (1/7 in the paper). eta (host, may be
+ * NULL): n_leaves indicators in increasing key order. Writes up to `capacity` sorted new keys to
+ * `keys` (may be NULL with capacity 0 to query the count) and the count to *n_leaves. Host only,
+ * synchronous. Errors: EINVAL (bad argument, non-finite velocity, a leaf beyond level 15, capacity
+ * below the count while keys is given; *n_leaves is set), EMESH (leaves not a balanced tiling),
+ * ENOMEM. */
+stokes_status stokes_octree_refine_gradient(const stokes_octree* mesh, const double* u_host, double fraction,
+                                            double* eta, uint64_t* keys, int64_t capacity, int64_t* n_leaves);
+
 /* Host copy of a table of an octree context; returns the entry count (0 for a bad argument)
  * and writes min(count, capacity) entries to `out` (host; may be NULL):
  *   0 leaf keys (uint64)                   1 active velocity node keys (uint64)

@@ -97,6 +97,8 @@ _SIGS = {
     "stokes_setup_octree": (C.c_int, [C.POINTER(stokes_octree), C.POINTER(stokes_mu), C.POINTER(stokes_bc),
                                       C.POINTER(stokes_options), _P, C.POINTER(_P)]),
     "stokes_octree_table": (C.c_size_t, [_P, C.c_int, C.c_int, _P, C.c_size_t]),
+    "stokes_octree_refine_gradient": (C.c_int, [C.POINTER(stokes_octree), _P, C.c_double, _P, _P, C.c_int64,
+                                                C.POINTER(C.c_int64)]),
 }
 
 PROF_CLASSES = ["vmult_A_fp32", "vmult_A_fp64", "stokes_fp64", "bt_fp64", "mass_p", "transfer",
@@ -264,6 +266,24 @@ def stokes_setup_octree_problem(prob, options=None, stream=None) -> Context:
                                      prob.shell_half_width)
     return stokes_setup_octree(keys, prob.coarsest_level, prob.centres, prob.mu_min, prob.mu_max, prob.delta,
                                prob.omega, prob.beta, options=options, stream=stream)
+
+
+def stokes_octree_refine_gradient(leaf_keys, coarsest_level, u_active, fraction=1.0 / 7.0):
+    """Gradient-indicator refinement on the host: (new sorted leaf keys, indicators of the given
+    leaves in increasing key order). u_active: host array, the active velocity of that mesh."""
+    import numpy as np
+    lib = load()
+    keys = np.ascontiguousarray(leaf_keys, dtype=np.uint64)
+    mesh = stokes_octree(int(coarsest_level), keys.size, keys.ctypes.data_as(C.POINTER(C.c_uint64)))
+    u = np.ascontiguousarray(u_active, dtype=np.float64)
+    eta = np.empty(keys.size, dtype=np.float64)
+    n = C.c_int64(0)
+    _check(lib.stokes_octree_refine_gradient(C.byref(mesh), u.ctypes.data, float(fraction), eta.ctypes.data, None, 0,
+                                             C.byref(n)), "stokes_octree_refine_gradient")
+    out = np.empty(n.value, dtype=np.uint64)
+    _check(lib.stokes_octree_refine_gradient(C.byref(mesh), u.ctypes.data, float(fraction), None, out.ctypes.data,
+                                             out.size, C.byref(n)), "stokes_octree_refine_gradient")
+    return out, eta
 
 
 _TABLE_DTYPES = {0: "uint64", 1: "uint64", 2: "uint64", 3: "uint64", 4: "uint8", 5: "int32"}

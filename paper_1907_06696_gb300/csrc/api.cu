@@ -1721,6 +1721,39 @@ stokes_status stokes_octree_sinker_mesh(int base_level, int n_sinkers, const dou
     return STOKES_OK;
 }
 
+stokes_status stokes_octree_refine_gradient(const stokes_octree* mesh, const double* u_host, double fraction,
+                                            double* eta, uint64_t* keys, int64_t capacity, int64_t* n_leaves) {
+    g_last_error.clear();
+    if (!mesh || !u_host || !n_leaves || mesh->n_leaves < 1 || !mesh->leaf_keys || !(fraction > 0.0) ||
+        fraction > 1.0)
+        return fail(STOKES_EINVAL, "bad argument");
+    try {
+        const std::vector<uint64_t> leaves(mesh->leaf_keys, mesh->leaf_keys + mesh->n_leaves);
+        OctSinkers sk;   // the tables of the active space do not depend on the viscosity
+        OctHost o;
+        const std::string err = oct_build(leaves, mesh->coarsest_level, sk, o);
+        if (!err.empty()) return fail(STOKES_EMESH, err);
+        for (size_t i = 0; i < 3 * o.unodes.size(); ++i)
+            if (!std::isfinite(u_host[i])) return fail(STOKES_EINVAL, "non-finite velocity");
+        std::vector<double> ind;
+        oct_gradient_indicator(o, u_host, ind);
+        if (eta) std::copy(ind.begin(), ind.end(), eta);
+        const std::vector<uint64_t> out = oct_refine_by_indicator(o.leaves, ind, fraction);
+        for (uint64_t c : out)
+            if (oct_l(c) > 15) return fail(STOKES_EINVAL, "refinement beyond level 15");
+        *n_leaves = int64_t(out.size());
+        if (capacity < int64_t(out.size())) {
+            if (keys || capacity != 0) return fail(STOKES_EINVAL, "capacity below the number of leaves");
+            return STOKES_OK;
+        }
+        if (!keys) return fail(STOKES_EINVAL, "null key buffer");
+        std::copy(out.begin(), out.end(), keys);
+    } catch (const std::bad_alloc&) {
+        return fail(STOKES_ENOMEM, "host allocation failed");
+    }
+    return STOKES_OK;
+}
+
 stokes_status stokes_setup_octree(const stokes_octree* mesh, const stokes_mu* mu, const stokes_bc* bc,
                                   const stokes_options* opt, void* stream, stokes_ctx** out) {
     g_last_error.clear();

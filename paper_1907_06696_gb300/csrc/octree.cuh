@@ -79,6 +79,14 @@ struct OctSinkers {
 // the reason (unbalanced mesh, constraint chain, bad keys).
 std::string oct_build(const std::vector<uint64_t>& leaves, int coarsest, const OctSinkers& sk, OctHost& out);
 
+// Gradient indicator of every leaf (sorted order): eta_K = h^(5/2) |grad u_h(x_K)|_F from the active
+// velocity u (component-blocked [3][unodes], Dirichlet values read as 0); and the refinement that
+// splits the floor(n fraction + 1/2) leaves with the largest eta (ties: smaller key), then 2:1
+// balances (Section 3.3, gradient-based adaptive refinement).
+void oct_gradient_indicator(const OctHost& o, const double* u, std::vector<double>& eta);
+std::vector<uint64_t> oct_refine_by_indicator(const std::vector<uint64_t>& leaves, const std::vector<double>& eta,
+                                              double fraction);
+
 // ---- device side (octree.cu) ----
 
 struct OctLevelDev {

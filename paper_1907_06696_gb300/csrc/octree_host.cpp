@@ -566,4 +566,63 @@ std::string oct_build(const std::vector<uint64_t>& leaves_in, int coarsest, cons
     return "";
 }
 
+// Gradient indicator (Section 3.3: a gradient-based estimator refines about 1/7 of the cells per
+// cycle; the estimator is not specified). Reading: eta_K = h^(5/2) |grad u_h(x_K)|_F, the Q2
+// velocity's gradient at the leaf centre, where the basis reduces d/dx u to the difference of the
+// two face-centre values over h (local nodes 12 and 14 along x, 10 and 16 along y, 4 and 22 along
+// z). Leaf values come from the active vector through the hanging-node constraints; Dirichlet
+// values are read as 0 (the wall condition), whatever the vector holds there.
+void oct_gradient_indicator(const OctHost& o, const double* u, std::vector<double>& eta) {
+    static const int kPairs[3][2] = {{12, 14}, {10, 16}, {4, 22}};
+    const size_t nn = o.unodes.size(), nl = o.leaves.size();
+    eta.assign(nl, 0.0);
+    auto value = [&](int c, int32_t ref) {
+        if (ref >= 0) return o.ubnd[size_t(ref)] ? 0.0 : u[size_t(c) * nn + size_t(ref)];
+        const size_t h = size_t(-(ref + 1));
+        double v = 0.0;
+        for (int t = 0; t < kOctUCon; ++t) {
+            const int32_t node = o.ucon_node[h * kOctUCon + t];
+            if (node >= 0 && !o.ubnd[size_t(node)]) v += o.ucon_w[h * kOctUCon + t] * u[size_t(c) * nn + size_t(node)];
+        }
+        return v;
+    };
+    parallel_for(nl, [&](size_t n) {
+        const double h = o.leaf_h[n];
+        double sq = 0.0;
+        for (int c = 0; c < 3; ++c)
+            for (const auto& pr : kPairs) {
+                const double d = (value(c, o.leaf_u[n * 27 + pr[1]]) - value(c, o.leaf_u[n * 27 + pr[0]])) / h;
+                sq += d * d;
+            }
+        eta[n] = h * h * std::sqrt(h) * std::sqrt(sq);
+    });
+}
+
+// Split the floor(n fraction + 1/2) leaves with the largest eta (equal eta: smaller key first),
+// then 2:1 balance. `leaves` sorted, eta in the same order; returns the sorted new leaves.
+std::vector<uint64_t> oct_refine_by_indicator(const std::vector<uint64_t>& leaves, const std::vector<double>& eta,
+                                              double fraction) {
+    const size_t n = leaves.size();
+    std::vector<size_t> order(n);
+    for (size_t i = 0; i < n; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+        return eta[a] != eta[b] ? eta[a] > eta[b] : leaves[a] < leaves[b];
+    });
+    const size_t m = std::min(n, size_t(std::floor(double(n) * fraction + 0.5)));
+    std::vector<uint8_t> mark(n, 0);
+    for (size_t i = 0; i < m; ++i) mark[order[i]] = 1;
+    std::vector<uint64_t> out;
+    out.reserve(n + 7 * m);
+    for (size_t i = 0; i < n; ++i) {
+        if (!mark[i]) {
+            out.push_back(leaves[i]);
+            continue;
+        }
+        uint64_t ch[8];
+        children_of(leaves[i], ch);
+        out.insert(out.end(), ch, ch + 8);
+    }
+    return oct_balance(out);
+}
+
 }  // namespace stk
