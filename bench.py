@@ -711,6 +711,57 @@ def run_report(args):
     ctx.close()
 
 
+def run_adapt(args):
+    """Solve-estimate-refine loop (Section 3.3: from 4 global refinements, each cycle refines about
+    1/7 of the cells by a gradient-based estimator): per cycle the host-side set-up time, the FP32-
+    V-cycle FGMRES solve to 1e-8 on the GPU (CUDA events, after one warm-up solve), its iterations
+    and true residual, and the host refinement time (stokes_octree_refine_gradient on the solved
+    velocity). One JSON line per cycle, then a summary line."""
+    import torch
+    from paper_1907_06696_gb300 import build as B
+    B.build()
+    from paper_1907_06696_gb300 import capi
+    capi.load()
+    import sinker_inputs as si
+    prob, cycles = si.adaptive_loop_workload(args.workload)
+    keys = capi.stokes_octree_sinker_mesh(prob.base_level, prob.centres, prob.max_levels, prob.shell_radius,
+                                          prob.shell_half_width)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for cycle in range(cycles + 1):
+        t0 = time.perf_counter()
+        ctx = capi.stokes_setup_octree(keys, prob.coarsest_level, prob.centres, prob.mu_min, prob.mu_max,
+                                       prob.delta, prob.omega, prob.beta, stream=stream)
+        setup_s = time.perf_counter() - t0
+        n_u, n_p = ctx.n_u, ctx.n_p
+        up = torch.zeros(n_u + n_p, dtype=torch.float64, device="cuda")
+        capi.stokes_solve(ctx, capi.STOKES_FP32, None, up, rtol=RTOL, max_it=5000, stream=stream, check=False)
+        up.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = capi.stokes_solve(ctx, capi.STOKES_FP32, None, up, rtol=RTOL, max_it=5000, stream=stream,
+                                 check=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        row = {"adapt": args.workload, "cycle": cycle, "leaves": int(keys.size), "n_u": n_u, "n_p": n_p,
+               "setup_s": setup_s, "solve_s": e0.elapsed_time(e1) / 1e3, "iterations": info.iterations,
+               "status": info.status, "true_rel_residual": info.rel_residual_true}
+        if cycle < cycles:
+            u = up[:n_u].cpu().numpy()
+            t0 = time.perf_counter()
+            keys, _ = capi.stokes_octree_refine_gradient(keys, prob.coarsest_level, u)
+            row["refine_s"] = time.perf_counter() - t0
+        ctx.close()
+        del up
+        torch.cuda.empty_cache()
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    print(json.dumps({"adapt": args.workload, "cycles": cycles, "sinkers": prob.n_sinkers,
+                      "dr": prob.mu_max / prob.mu_min, "leaves": [r["leaves"] for r in rows],
+                      "dofs": [r["n_u"] + r["n_p"] for r in rows], "iterations": [r["iterations"] for r in rows],
+                      "solve_s": [r["solve_s"] for r in rows]}))
+
+
 def run_octree(args):
     """Adaptive workload (octree mesh refined in shells around the sinkers, hanging nodes,
     local-smoothing GMG): host mesh and set-up times, FP32- and FP64-V-cycle solves to 1e-8,
@@ -897,6 +948,8 @@ def main():
         run_kernels(args)
     elif args.workload.startswith("oct") and args.impl != "reference":
         run_octree(args)
+    elif args.workload.startswith("adapt") and args.impl != "reference":
+        run_adapt(args)
     elif args.workload.startswith("batch") and args.impl != "reference":
         run_batch(args)
     elif args.impl == "reference":

@@ -189,6 +189,22 @@ def octree_workload(name: str) -> OctreeProblem:
     raise KeyError(name)
 
 
+def adaptive_loop_workload(name: str):
+    """(OctreeProblem, cycles) of a solve-estimate-refine loop: the start mesh is the uniform grid
+    2^base_level (every sinker's maximum level equals base_level, so no shell is refined) and each
+    cycle refines by the gradient indicator.
+
+    adapt    : 16^3 start (4 global refinements, as in Section 3.3), 4 sinkers, viscosity ratio 1e4,
+               multigrid down to 4^3, 5 cycles; seed 1926
+    adapt_xs : 4^3 start, 1 sinker, ratio 1e2, down to 2^3, 2 cycles (oracle-sized)
+    """
+    if name == "adapt":
+        return octree_problem(4, 2, 4, (4,), 1e4, 1926, name), 5
+    if name == "adapt_xs":
+        return octree_problem(2, 1, 1, (2,), 1e2, 1927, name), 2
+    raise KeyError(name)
+
+
 BATCH_SIZES = ((16, 5), (24, 4), (32, 6), (48, 5))   # (cells per axis, levels): coarsest 1 or 3 cells
 
 
