@@ -278,12 +278,17 @@ def stokes_octree_refine_gradient(leaf_keys, coarsest_level, u_active, fraction=
     u = np.ascontiguousarray(u_active, dtype=np.float64)
     eta = np.empty(keys.size, dtype=np.float64)
     n = C.c_int64(0)
-    _check(lib.stokes_octree_refine_gradient(C.byref(mesh), u.ctypes.data, float(fraction), eta.ctypes.data, None, 0,
-                                             C.byref(n)), "stokes_octree_refine_gradient")
-    out = np.empty(n.value, dtype=np.uint64)
-    _check(lib.stokes_octree_refine_gradient(C.byref(mesh), u.ctypes.data, float(fraction), None, out.ctypes.data,
-                                             out.size, C.byref(n)), "stokes_octree_refine_gradient")
-    return out, eta
+    # each leaf is split at most once by the refinement and its balance (refining every leaf once
+    # gives a balanced tree that contains the minimal one), so 8 n keys suffice
+    out = np.empty(8 * keys.size, dtype=np.uint64)
+    st = lib.stokes_octree_refine_gradient(C.byref(mesh), u.ctypes.data, float(fraction), eta.ctypes.data,
+                                           out.ctypes.data, out.size, C.byref(n))
+    if st == STOKES_EINVAL and n.value > out.size:
+        out = np.empty(n.value, dtype=np.uint64)
+        st = lib.stokes_octree_refine_gradient(C.byref(mesh), u.ctypes.data, float(fraction), eta.ctypes.data,
+                                               out.ctypes.data, out.size, C.byref(n))
+    _check(st, "stokes_octree_refine_gradient")
+    return out[:n.value].copy(), eta
 
 
 _TABLE_DTYPES = {0: "uint64", 1: "uint64", 2: "uint64", 3: "uint64", 4: "uint8", 5: "int32"}

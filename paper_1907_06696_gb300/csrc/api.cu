@@ -1731,7 +1731,7 @@ stokes_status stokes_octree_refine_gradient(const stokes_octree* mesh, const dou
         const std::vector<uint64_t> leaves(mesh->leaf_keys, mesh->leaf_keys + mesh->n_leaves);
         OctSinkers sk;   // the tables of the active space do not depend on the viscosity
         OctHost o;
-        const std::string err = oct_build(leaves, mesh->coarsest_level, sk, o);
+        const std::string err = oct_build(leaves, mesh->coarsest_level, sk, o, true);
         if (!err.empty()) return fail(STOKES_EMESH, err);
         for (size_t i = 0; i < 3 * o.unodes.size(); ++i)
             if (!std::isfinite(u_host[i])) return fail(STOKES_EINVAL, "non-finite velocity");

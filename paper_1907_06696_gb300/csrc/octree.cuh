@@ -75,9 +75,11 @@ struct OctSinkers {
     double mu_min = 1, mu_max = 1, delta = 200, omega = 0.1, beta = 10;
 };
 
-// Builds every table from a 2:1-balanced leaf set. Returns an empty string on success, else
+// Builds every table from a 2:1-balanced leaf set (active_only: the sorted leaves, their sizes
+// and the velocity space with its constraints only). Returns an empty string on success, else
 // the reason (unbalanced mesh, constraint chain, bad keys).
-std::string oct_build(const std::vector<uint64_t>& leaves, int coarsest, const OctSinkers& sk, OctHost& out);
+std::string oct_build(const std::vector<uint64_t>& leaves, int coarsest, const OctSinkers& sk, OctHost& out,
+                      bool active_only = false);
 
 // Gradient indicator of every leaf (sorted order): eta_K = h^(5/2) |grad u_h(x_K)|_F from the active
 // velocity u (component-blocked [3][unodes], Dirichlet values read as 0); and the refinement that

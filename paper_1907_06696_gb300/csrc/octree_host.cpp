@@ -35,11 +35,15 @@ void children_of(uint64_t c, uint64_t out[8]) {
     for (int q = 0; q < 8; ++q) out[q] = oct_key(l + 1, 2 * i + (q & 1), 2 * j + ((q >> 1) & 1), 2 * k + (q >> 2));
 }
 
-template <typename F>
-void parallel_for(size_t n, F f) {
+unsigned host_threads() {
     unsigned nt = std::thread::hardware_concurrency();
     if (nt == 0) nt = 1;
-    if (nt > 32) nt = 32;
+    return nt > 32 ? 32 : nt;
+}
+
+template <typename F>
+void parallel_for(size_t n, F f) {
+    unsigned nt = host_threads();
     if (n < 4096) nt = 1;
     std::vector<std::thread> th;
     for (unsigned t = 0; t < nt; ++t)
@@ -47,6 +51,47 @@ void parallel_for(size_t n, F f) {
             for (size_t i = n * t / nt; i < n * (t + 1) / nt; ++i) f(i);
         });
     for (auto& x : th) x.join();
+}
+
+// Sort with the host threads: chunks sorted in parallel, then merged pairwise. For a total order
+// (elements that compare equal are identical) the result equals std::sort's.
+template <typename T, typename Less = std::less<T>>
+void par_sort(std::vector<T>& v, Less less = Less()) {
+    size_t P = 1;
+    while (2 * P <= host_threads()) P *= 2;
+    if (P == 1 || v.size() < (size_t(1) << 16)) {
+        std::sort(v.begin(), v.end(), less);
+        return;
+    }
+    std::vector<size_t> b(P + 1);
+    for (size_t i = 0; i <= P; ++i) b[i] = v.size() * i / P;
+    {
+        std::vector<std::thread> th;
+        for (size_t i = 0; i < P; ++i) th.emplace_back([&, i] { std::sort(v.begin() + b[i], v.begin() + b[i + 1], less); });
+        for (auto& x : th) x.join();
+    }
+    std::vector<T> tmp(v.size());
+    for (size_t w = 1; w < P; w *= 2) {
+        std::vector<std::thread> th;
+        for (size_t i = 0; i < P; i += 2 * w)
+            th.emplace_back([&, i] {
+                const size_t lo = b[i], mid = b[std::min(i + w, P)], hi = b[std::min(i + 2 * w, P)];
+                std::merge(v.begin() + lo, v.begin() + mid, v.begin() + mid, v.begin() + hi, tmp.begin() + lo, less);
+            });
+        for (auto& x : th) x.join();
+        v.swap(tmp);
+    }
+}
+
+// Runs f(i) for i < n on the host threads; f returns an error message or nullptr. Returns the
+// message of the smallest failing i (the one a sequential loop would report), or nullptr.
+template <typename F>
+const char* parallel_check(size_t n, F f) {
+    std::vector<const char*> err(n, nullptr);
+    parallel_for(n, [&](size_t i) { err[i] = f(i); });
+    for (size_t i = 0; i < n; ++i)
+        if (err[i]) return err[i];
+    return nullptr;
 }
 
 // Quadratic Lagrange basis on {0, 1/2, 1} at the lattice positions 0, 1/4, 1/2, 3/4, 1.
@@ -99,7 +144,7 @@ std::vector<uint64_t> oct_refine_shells(int base_level, int n_sinkers, const dou
         }
         leaves.swap(nxt);
     }
-    std::sort(leaves.begin(), leaves.end());
+    par_sort(leaves);
     return leaves;
 }
 
@@ -137,15 +182,16 @@ std::vector<uint64_t> oct_balance(const std::vector<uint64_t>& in) {
         }
     }
     std::vector<uint64_t> out(leaves.begin(), leaves.end());
-    std::sort(out.begin(), out.end());
+    par_sort(out);
     return out;
 }
 
-std::string oct_build(const std::vector<uint64_t>& leaves_in, int coarsest, const OctSinkers& sk, OctHost& o) {
+std::string oct_build(const std::vector<uint64_t>& leaves_in, int coarsest, const OctSinkers& sk, OctHost& o,
+                      bool active_only) {
     o = OctHost();
     if (leaves_in.empty()) return "no leaves";
     o.leaves = leaves_in;
-    std::sort(o.leaves.begin(), o.leaves.end());
+    par_sort(o.leaves);
     if (std::adjacent_find(o.leaves.begin(), o.leaves.end()) != o.leaves.end()) return "duplicate leaves";
     std::unordered_set<uint64_t> leafset(o.leaves.begin(), o.leaves.end()), cells;
     int lmax = 0, lmin = 99;
@@ -218,7 +264,7 @@ std::string oct_build(const std::vector<uint64_t>& leaves_in, int coarsest, cons
                     for (int ii = 0; ii < 3; ++ii)
                         all.push_back({pkey(oct_i(c) * s + ii * h2, oct_j(c) * s + jj * h2, oct_k(c) * s + kk * h2), l});
         }
-        std::sort(all.begin(), all.end());
+        par_sort(all);
         std::vector<std::pair<uint64_t, int>> nodes;   // key, coarsest leaf level
         for (auto& p : all)
             if (nodes.empty() || nodes.back().first != p.first) nodes.push_back(p);
@@ -236,7 +282,7 @@ std::string oct_build(const std::vector<uint64_t>& leaves_in, int coarsest, cons
                 hang.push_back({pkey(x, y, z), e.coarse});
             }
         }
-        std::sort(hang.begin(), hang.end());
+        par_sort(hang);
         hang.erase(std::unique(hang.begin(), hang.end(),
                                [](const auto& a, const auto& b) { return a.first == b.first; }),
                    hang.end());
@@ -249,17 +295,17 @@ std::string oct_build(const std::vector<uint64_t>& leaves_in, int coarsest, cons
         }
         const size_t nu = o.unodes.size();
         o.ubnd.resize(nu);
-        for (size_t n = 0; n < nu; ++n) {
+        parallel_for(nu, [&](size_t n) {
             const uint64_t kx = o.unodes[n] % Mx, ky = (o.unodes[n] / Mx) % Mx, kz = o.unodes[n] / (Mx * Mx);
             o.ubnd[n] = on_bnd(int64_t(kx), int64_t(ky), int64_t(kz)) ? 1 : 0;
-        }
+        });
         auto uidx = [&](uint64_t key) -> int64_t {
             auto it = std::lower_bound(o.unodes.begin(), o.unodes.end(), key);
             return (it != o.unodes.end() && *it == key) ? int64_t(it - o.unodes.begin()) : -1;
         };
         o.ucon_node.assign(hang.size() * kOctUCon, -1);
         o.ucon_w.assign(hang.size() * kOctUCon, 0.0);
-        for (size_t h = 0; h < hang.size(); ++h) {
+        const char* err = parallel_check(hang.size(), [&](size_t h) -> const char* {
             const uint64_t key = hang[h].first, C = hang[h].second;
             const int64_t px = int64_t(key % Mx), py = int64_t((key / Mx) % Mx), pz = int64_t(key / (Mx * Mx));
             const int64_t s = S(oct_l(C)), q4 = s / 4;   // coarse cell side s, nodes every s/2
@@ -277,9 +323,11 @@ std::string oct_build(const std::vector<uint64_t>& leaves_in, int coarsest, cons
                 o.ucon_w[h * kOctUCon + t] = w;
                 ++t;
             }
-        }
+            return nullptr;
+        });
+        if (err) return err;
         o.leaf_u.resize(nl * 27);
-        for (size_t n = 0; n < nl; ++n) {
+        err = parallel_check(nl, [&](size_t n) -> const char* {
             const uint64_t c = o.leaves[n];
             const int64_t s = S(oct_l(c)), h2 = s / 2;
             for (int a = 0; a < 27; ++a) {
@@ -294,7 +342,14 @@ std::string oct_build(const std::vector<uint64_t>& leaves_in, int coarsest, cons
                     o.leaf_u[n * 27 + a] = -int32_t(it - hang.begin()) - 1;
                 }
             }
-        }
+            return nullptr;
+        });
+        if (err) return err;
+    }
+    if (active_only) {   // the velocity space and leaf sizes are all the gradient indicator needs
+        o.leaf_h.resize(nl);
+        for (size_t n = 0; n < nl; ++n) o.leaf_h[n] = std::ldexp(1.0, -oct_l(o.leaves[n]));
+        return "";
     }
 
     // ---- pressure vertices
@@ -306,7 +361,7 @@ std::string oct_build(const std::vector<uint64_t>& leaves_in, int coarsest, cons
             for (int a = 0; a < 8; ++a)
                 all.push_back(pkey((oct_i(c) + (a & 1)) * s, (oct_j(c) + ((a >> 1) & 1)) * s, (oct_k(c) + (a >> 2)) * s));
         }
-        std::sort(all.begin(), all.end());
+        par_sort(all);
         all.erase(std::unique(all.begin(), all.end()), all.end());
         std::vector<std::pair<uint64_t, uint64_t>> hang;
         for (const CN& e : cn) {
@@ -320,7 +375,7 @@ std::string oct_build(const std::vector<uint64_t>& leaves_in, int coarsest, cons
                 hang.push_back({pkey(x, y, z), e.coarse});
             }
         }
-        std::sort(hang.begin(), hang.end());
+        par_sort(hang);
         hang.erase(std::unique(hang.begin(), hang.end(),
                                [](const auto& a, const auto& b) { return a.first == b.first; }),
                    hang.end());
@@ -336,7 +391,7 @@ std::string oct_build(const std::vector<uint64_t>& leaves_in, int coarsest, cons
         };
         o.pcon_node.assign(hang.size() * kOctPCon, -1);
         o.pcon_w.assign(hang.size() * kOctPCon, 0.0);
-        for (size_t h = 0; h < hang.size(); ++h) {
+        const char* err = parallel_check(hang.size(), [&](size_t h) -> const char* {
             const uint64_t key = hang[h].first, C = hang[h].second;
             const int64_t px = int64_t(key % Mx), py = int64_t((key / Mx) % Mx), pz = int64_t(key / (Mx * Mx));
             const int64_t s = S(oct_l(C)), half = s / 2;
@@ -358,9 +413,11 @@ std::string oct_build(const std::vector<uint64_t>& leaves_in, int coarsest, cons
                 o.pcon_w[h * kOctPCon + t] = w;
                 ++t;
             }
-        }
+            return nullptr;
+        });
+        if (err) return err;
         o.leaf_p.resize(nl * 8);
-        for (size_t n = 0; n < nl; ++n) {
+        err = parallel_check(nl, [&](size_t n) -> const char* {
             const uint64_t c = o.leaves[n];
             const int64_t s = S(oct_l(c));
             for (int a = 0; a < 8; ++a) {
@@ -374,7 +431,9 @@ std::string oct_build(const std::vector<uint64_t>& leaves_in, int coarsest, cons
                     o.leaf_p[n * 8 + a] = -int32_t(it - hang.begin()) - 1;
                 }
             }
-        }
+            return nullptr;
+        });
+        if (err) return err;
     }
 
     // ---- leaf viscosity (harmonic average over the Gauss points, Section 2.3) and F (Section 3.2)
@@ -480,7 +539,7 @@ std::string oct_build(const std::vector<uint64_t>& leaves_in, int coarsest, cons
     for (size_t n = 0; n < nl; ++n) mu_cell[o.leaves[n]] = o.leaf_mu[n];
     std::vector<std::vector<uint64_t>> by_level(lmax + 1);
     for (uint64_t c : cells) by_level[oct_l(c)].push_back(c);
-    for (auto& v : by_level) std::sort(v.begin(), v.end());
+    for (auto& v : by_level) par_sort(v);
     for (int l = lmax; l >= 0; --l)
         for (uint64_t c : by_level[l])
             if (!mu_cell.count(c)) {
@@ -503,20 +562,21 @@ std::string oct_build(const std::vector<uint64_t>& leaves_in, int coarsest, cons
                 keys.push_back(pkey(oct_i(c) * s + (a % 3) * h2, oct_j(c) * s + ((a / 3) % 3) * h2, oct_k(c) * s + (a / 9) * h2));
         L.cell_nodes.resize(keys.size());
         std::vector<uint64_t> sorted = keys;
-        std::sort(sorted.begin(), sorted.end());
+        par_sort(sorted);
         sorted.erase(std::unique(sorted.begin(), sorted.end()), sorted.end());
         L.nodes = sorted;
-        for (size_t t = 0; t < keys.size(); ++t)
+        parallel_for(keys.size(), [&](size_t t) {
             L.cell_nodes[t] = int32_t(std::lower_bound(L.nodes.begin(), L.nodes.end(), keys[t]) - L.nodes.begin());
+        });
         L.mu.resize(L.cells.size());
-        for (size_t n = 0; n < L.cells.size(); ++n) L.mu[n] = mu_cell.at(L.cells[n]);
+        parallel_for(L.cells.size(), [&](size_t n) { L.mu[n] = mu_cell.at(L.cells[n]); });
         const int N = 1 << l;
         L.flags.assign(L.nodes.size(), 0);
-        for (size_t t = 0; t < L.nodes.size(); ++t) {
+        parallel_for(L.nodes.size(), [&](size_t t) {
             const int64_t p[3] = {int64_t(L.nodes[t] % Mx), int64_t((L.nodes[t] / Mx) % Mx), int64_t(L.nodes[t] / (Mx * Mx))};
             if (on_bnd(p[0], p[1], p[2])) {
                 L.flags[t] = 1;
-                continue;
+                return;
             }
             int lo[3], hi[3];
             for (int d = 0; d < 3; ++d) {
@@ -531,7 +591,7 @@ std::string oct_build(const std::vector<uint64_t>& leaves_in, int coarsest, cons
                         if (ci >= 0 && cj >= 0 && ck >= 0 && ci < N && cj < N && ck < N && !cells.count(oct_key(l, ci, cj, ck)))
                             edge = true;
             if (edge) L.flags[t] = 2;
-        }
+        });
         if (l > coarsest) {
             const OctLevelHost& C = o.levels[l - 1 - coarsest];
             L.parent.assign(L.nodes.size(), 0xFFFFFFFFu);
@@ -555,14 +615,16 @@ std::string oct_build(const std::vector<uint64_t>& leaves_in, int coarsest, cons
     }
     // ---- copy indices: each active node to its coarsest leaf's level
     o.copy_index.resize(o.unodes.size());
-    for (size_t n = 0; n < o.unodes.size(); ++n) {
+    const char* err = parallel_check(o.unodes.size(), [&](size_t n) -> const char* {
         const int l = o.copy_level[n];
         const OctLevelHost& L = o.levels[l - coarsest];
         const auto it = std::lower_bound(L.nodes.begin(), L.nodes.end(), o.unodes[n]);
         if (it == L.nodes.end() || *it != o.unodes[n]) return "active node missing on its level";
         o.copy_index[n] = int32_t(it - L.nodes.begin());
         if (L.flags[o.copy_index[n]] == 2) return "active node on the refinement edge of its level";
-    }
+        return nullptr;
+    });
+    if (err) return err;
     return "";
 }
 
@@ -605,7 +667,7 @@ std::vector<uint64_t> oct_refine_by_indicator(const std::vector<uint64_t>& leave
     const size_t n = leaves.size();
     std::vector<size_t> order(n);
     for (size_t i = 0; i < n; ++i) order[i] = i;
-    std::sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+    par_sort(order, [&](size_t a, size_t b) {   // a total order: keys are unique
         return eta[a] != eta[b] ? eta[a] > eta[b] : leaves[a] < leaves[b];
     });
     const size_t m = std::min(n, size_t(std::floor(double(n) * fraction + 0.5)));
