@@ -254,16 +254,15 @@ std::string oct_build(const std::vector<uint64_t>& leaves_in, int coarsest, cons
 
     // ---- velocity nodes
     {
-        std::vector<std::pair<uint64_t, int>> all;
-        all.reserve(nl * 27);
-        for (uint64_t c : o.leaves) {
+        std::vector<std::pair<uint64_t, int>> all(nl * 27);
+        parallel_for(nl, [&](size_t n) {
+            const uint64_t c = o.leaves[n];
             const int l = oct_l(c);
             const int64_t s = S(l), h2 = s / 2;
-            for (int kk = 0; kk < 3; ++kk)
-                for (int jj = 0; jj < 3; ++jj)
-                    for (int ii = 0; ii < 3; ++ii)
-                        all.push_back({pkey(oct_i(c) * s + ii * h2, oct_j(c) * s + jj * h2, oct_k(c) * s + kk * h2), l});
-        }
+            for (int a = 0; a < 27; ++a)
+                all[n * 27 + a] = {pkey(oct_i(c) * s + (a % 3) * h2, oct_j(c) * s + ((a / 3) % 3) * h2,
+                                        oct_k(c) * s + (a / 9) * h2), l};
+        });
         par_sort(all);
         std::vector<std::pair<uint64_t, int>> nodes;   // key, coarsest leaf level
         for (auto& p : all)
@@ -354,13 +353,13 @@ std::string oct_build(const std::vector<uint64_t>& leaves_in, int coarsest, cons
 
     // ---- pressure vertices
     {
-        std::vector<uint64_t> all;
-        all.reserve(nl * 8);
-        for (uint64_t c : o.leaves) {
+        std::vector<uint64_t> all(nl * 8);
+        parallel_for(nl, [&](size_t n) {
+            const uint64_t c = o.leaves[n];
             const int64_t s = S(oct_l(c));
             for (int a = 0; a < 8; ++a)
-                all.push_back(pkey((oct_i(c) + (a & 1)) * s, (oct_j(c) + ((a >> 1) & 1)) * s, (oct_k(c) + (a >> 2)) * s));
-        }
+                all[n * 8 + a] = pkey((oct_i(c) + (a & 1)) * s, (oct_j(c) + ((a >> 1) & 1)) * s, (oct_k(c) + (a >> 2)) * s);
+        });
         par_sort(all);
         all.erase(std::unique(all.begin(), all.end()), all.end());
         std::vector<std::pair<uint64_t, uint64_t>> hang;
@@ -500,7 +499,14 @@ std::string oct_build(const std::vector<uint64_t>& leaves_in, int coarsest, cons
         const size_t np = o.pverts.size();
         o.mp_diag.assign(np, 0.0);
         o.p_weights.assign(np, 0.0);
-        for (size_t n = 0; n < nl; ++n) {
+        // The terms each leaf adds (to int psi_a and to the diagonal of M_p) are found in parallel
+        // and then added in leaf order, so the sums equal those of a sequential loop bit for bit.
+        struct Term {
+            int32_t idx;
+            double v;
+        };
+        auto leaf_terms = [&](size_t n, Term* pw, Term* md, uint32_t& npw, uint32_t& nmd) {
+            npw = nmd = 0;
             const double h = o.leaf_h[n], sc = h * h * h / o.leaf_mu[n];
             int32_t idx[8][kOctPCon];
             double w[8][kOctPCon];
@@ -521,7 +527,10 @@ std::string oct_build(const std::vector<uint64_t>& leaves_in, int coarsest, cons
                     }
                 }
                 for (int t = 0; t < kOctPCon; ++t)
-                    if (idx[a][t] >= 0) o.p_weights[idx[a][t]] += w[a][t] * h * h * h / 8.0;
+                    if (idx[a][t] >= 0) {
+                        if (pw) pw[npw] = {idx[a][t], w[a][t] * h * h * h / 8.0};
+                        ++npw;
+                    }
             }
             for (int a = 0; a < 8; ++a)
                 for (int b = 0; b < 8; ++b) {
@@ -529,9 +538,26 @@ std::string oct_build(const std::vector<uint64_t>& leaves_in, int coarsest, cons
                     for (int d = 0; d < 3; ++d) m *= (((a >> d) & 1) == ((b >> d) & 1)) ? 1.0 / 3.0 : 1.0 / 6.0;
                     for (int t = 0; t < kOctPCon; ++t)
                         for (int u = 0; u < kOctPCon; ++u)
-                            if (idx[a][t] >= 0 && idx[a][t] == idx[b][u]) o.mp_diag[idx[a][t]] += sc * m * w[a][t] * w[b][u];
+                            if (idx[a][t] >= 0 && idx[a][t] == idx[b][u]) {
+                                if (md) md[nmd] = {idx[a][t], sc * m * w[a][t] * w[b][u]};
+                                ++nmd;
+                            }
                 }
+        };
+        std::vector<uint32_t> cpw(nl), cmd(nl);
+        parallel_for(nl, [&](size_t n) { leaf_terms(n, nullptr, nullptr, cpw[n], cmd[n]); });
+        std::vector<size_t> opw(nl + 1, 0), omd(nl + 1, 0);
+        for (size_t n = 0; n < nl; ++n) {
+            opw[n + 1] = opw[n] + cpw[n];
+            omd[n + 1] = omd[n] + cmd[n];
         }
+        std::vector<Term> tpw(opw[nl]), tmd(omd[nl]);
+        parallel_for(nl, [&](size_t n) {
+            uint32_t a, b;
+            leaf_terms(n, tpw.data() + opw[n], tmd.data() + omd[n], a, b);
+        });
+        for (const Term& t : tpw) o.p_weights[size_t(t.idx)] += t.v;
+        for (const Term& t : tmd) o.mp_diag[size_t(t.idx)] += t.v;
     }
 
     // ---- levels coarsest .. lmax
@@ -555,11 +581,13 @@ std::string oct_build(const std::vector<uint64_t>& leaves_in, int coarsest, cons
         L.l = l;
         L.cells = by_level[l];
         const int64_t s = S(l), h2 = s / 2;
-        std::vector<uint64_t> keys;
-        keys.reserve(L.cells.size() * 27);
-        for (uint64_t c : L.cells)
+        std::vector<uint64_t> keys(L.cells.size() * 27);
+        parallel_for(L.cells.size(), [&](size_t n) {
+            const uint64_t c = L.cells[n];
             for (int a = 0; a < 27; ++a)
-                keys.push_back(pkey(oct_i(c) * s + (a % 3) * h2, oct_j(c) * s + ((a / 3) % 3) * h2, oct_k(c) * s + (a / 9) * h2));
+                keys[n * 27 + a] = pkey(oct_i(c) * s + (a % 3) * h2, oct_j(c) * s + ((a / 3) % 3) * h2,
+                                        oct_k(c) * s + (a / 9) * h2);
+        });
         L.cell_nodes.resize(keys.size());
         std::vector<uint64_t> sorted = keys;
         par_sort(sorted);
