@@ -156,17 +156,29 @@ std::vector<uint64_t> oct_balance(const std::vector<uint64_t>& in) {
         uint64_t a = c;
         while (cells.insert(a).second && oct_l(a) > 0) a = parent_key(a);
     }
+    // Finest level first: every level-(l-1) cell that touches a level-l leaf must exist; a missing
+    // one is created by splitting its nearest existing ancestor (recursively). Splits only create
+    // cells of level < l, so the scan of level l reads the sets while they are unchanged (in
+    // parallel) and the splits follow in the scan's order. The result is the unique coarsest
+    // balanced refinement of the input.
     for (int l = lmax; l >= 2; --l) {
         std::vector<uint64_t> cur;
         for (uint64_t c : leaves)
             if (oct_l(c) == l) cur.push_back(c);
-        std::sort(cur.begin(), cur.end());
+        par_sort(cur);
         const int n = 1 << l;
-        for (uint64_t c : cur) {
+        std::vector<std::vector<uint64_t>> miss(cur.size());
+        parallel_for(cur.size(), [&](size_t t) {
+            const uint64_t c = cur[t];
             for (const auto& d : kDirs) {
                 const int ni = oct_i(c) + d[0], nj = oct_j(c) + d[1], nk = oct_k(c) + d[2];
                 if (ni < 0 || nj < 0 || nk < 0 || ni >= n || nj >= n || nk >= n) continue;
                 const uint64_t target = oct_key(l - 1, ni >> 1, nj >> 1, nk >> 1);
+                if (!cells.count(target)) miss[t].push_back(target);
+            }
+        });
+        for (const auto& list : miss)
+            for (uint64_t target : list)
                 while (!cells.count(target)) {
                     uint64_t anc = parent_key(target);
                     while (!cells.count(anc)) anc = parent_key(anc);
@@ -178,8 +190,6 @@ std::vector<uint64_t> oct_balance(const std::vector<uint64_t>& in) {
                         cells.insert(x);
                     }
                 }
-            }
-        }
     }
     std::vector<uint64_t> out(leaves.begin(), leaves.end());
     par_sort(out);
