@@ -107,8 +107,8 @@ def lanczos_lambda_max(apply_A, Dinv, free_mask, seed, steps=12):
 
 
 class Level:
-    def __init__(self, n, mu_cells, level_index):
-        self.mesh = Mesh(n)
+    def __init__(self, n, mu_cells, level_index, noslip_faces=0x3F):
+        self.mesh = Mesh(n, noslip_faces)
         self.ops = Operators(self.mesh, mu_cells)
         self.free = (~self.mesh.dirichlet).astype(np.float64)
         d = self.ops.diag_A()
@@ -125,12 +125,12 @@ class GMG:
     """V-cycle hierarchy: levels[0] is the coarsest (n_coarse cells per axis)."""
 
     def __init__(self, n_finest, n_levels, mu_levels, degree=4, smoothing_range=15.0,
-                 safety=1.2, lanczos_steps=12):
+                 safety=1.2, lanczos_steps=12, noslip_faces=0x3F):
         self.degree = degree
         self.levels = []
         for l in range(n_levels):
             n = n_finest >> (n_levels - 1 - l)
-            self.levels.append(Level(n, mu_levels[l], l))
+            self.levels.append(Level(n, mu_levels[l], l, noslip_faces))
         self.P = [None] + [prolongation(self.levels[l - 1].mesh.n) for l in range(1, n_levels)]
         for lev in self.levels[1:]:
             lev.lam_max = lanczos_lambda_max(lev.A, lev.Dinv, lev.free,

@@ -7,7 +7,11 @@ component-blocked: DoF (c, node) has index c M^3 + node, so N_u = 3 M^3
 vertex (i,j,k) -> i + (n+1) j + (n+1)^2 k. Cell (ci,cj,ck) -> ci + n cj + n^2 ck.
 
 Homogeneous Dirichlet data on all six walls (eq. stokes): every velocity DoF on
-a boundary node is constrained.
+a boundary node is constrained. The walls can instead carry the no-normal-flux
+condition the paper names as an extension (Section 2: u . n = 0 with zero
+tangential traction, the latter natural in the weak form): face f = 2 axis + side
+(side 0 at coordinate 0, side 1 at 1) is no-slip if bit f of `noslip_faces` is
+set, else only the velocity component along its normal is constrained there.
 """
 from __future__ import annotations
 
@@ -15,8 +19,9 @@ import numpy as np
 
 
 class Mesh:
-    def __init__(self, n: int):
+    def __init__(self, n: int, noslip_faces: int = 0x3F):
         self.n = n
+        self.noslip_faces = noslip_faces
         self.h = 1.0 / n
         self.M = 2 * n + 1
         self.n_nodes = self.M ** 3
@@ -48,7 +53,18 @@ class Mesh:
         I, J, K = np.meshgrid(idx, idx, idx, indexing="ij")
         on_b = (I == 0) | (I == M - 1) | (J == 0) | (J == M - 1) | (K == 0) | (K == M - 1)
         self.boundary_node = on_b.transpose(2, 1, 0).ravel()
-        self.dirichlet = np.concatenate([self.boundary_node] * 3)
+        face = []                                   # node masks of faces 0..5, node order
+        for A in (I, J, K):
+            face.append((A == 0).transpose(2, 1, 0).ravel())
+            face.append((A == M - 1).transpose(2, 1, 0).ravel())
+        comp = []
+        for c in range(3):
+            m = np.zeros(self.n_nodes, dtype=bool)
+            for f in range(6):
+                if (noslip_faces >> f) & 1 or f // 2 == c:
+                    m |= face[f]
+            comp.append(m)
+        self.dirichlet = np.concatenate(comp)
         self.interior = ~self.dirichlet
 
     def node_coords(self):
