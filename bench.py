@@ -45,12 +45,6 @@ A_FLOP_PER_CELL = 18 * 9 * 18 + 9 * 9 * (12 + 2) + 9 * 9 * (12 + 3)
 # Outer operator [A B^T; B 0]: B^T and B as tensor products of 3x2 moment matrices, 3
 # components x 114 MACs each.
 STOKES_FLOP_PER_CELL = A_FLOP_PER_CELL + 2 * (342 + 342)
-# FP32 instructions per cell of the double-float outer operator (estimate from the implemented
-# sweeps and the double-float primitives): 648 three-term outputs at 31 instructions (dot3), 81
-# middle derivative outputs at 18 (difference 11, product 7), 162 accumulating outputs at 39
-# (dot3_acc) and 81 middle ones at 29 (transposed derivatives), 81 products at 7 (mu h
-# scaling), and the B/B^T moments, 684 multiply-adds at ~18.
-DF64_OPS_PER_CELL = 648 * 31 + 81 * 18 + 162 * 39 + 81 * 29 + 81 * 7 + 684 * 18
 
 
 def parse():
@@ -61,6 +55,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cube64")
     ap.add_argument("--no-extras", action="store_true", help="skip the sweep/profile/e2e/cpu legs")
+    ap.add_argument("--no-large", action="store_true", help="skip the 128^3 vmult and solve leg")
     ap.add_argument("--vmult-sweep", action="store_true",
                     help="finest-level velocity operator A, FP32 and FP64, on uniform meshes of 16..128 cells per "
                          "axis (8 sinkers, viscosity ratio 1e4); one JSON line per size")
@@ -224,6 +219,59 @@ def cpu_threads():
 
 
 # ----------------------------------------------------------------- reference arm
+def workload_config(prob, n_u, n_p):
+    """The workload and method, shared by both arms' `config` (implementation details of our arm
+    go to its `impl_config`)."""
+    return {"workload": prob.name, "n": prob.n, "levels": prob.n_levels, "sinkers": prob.n_sinkers,
+            "dr": prob.mu_max / prob.mu_min, "n_u": int(n_u), "n_p": int(n_p), "rtol": RTOL,
+            "vcycle": "fp32", "outer": "fp64 FGMRES(50)", "cheb_degree": 4, "schur": "Chebyshev degree 5 on M_p"}
+
+
+# basis rows the Gram-Schmidt step of the timed oracle iteration runs against: the mean over a
+# restart cycle of FGMRES(50) (iteration j projects against j + 1 rows)
+ORACLE_GS_ROWS = 25
+
+
+def _oracle_setup(prob):
+    import numpy as np
+    from oracle import gmg, krylov, mesh, operators, sinker
+    m = mesh.Mesh(prob.n)
+    mus = sinker.level_viscosities(m, prob, prob.n_levels)
+    G = gmg.GMG(prob.n, prob.n_levels, mus)
+    ops = G.levels[-1].ops
+    Pc = krylov.StokesPreconditioner(ops, G)
+    N = m.n_u + m.n_p
+    V = np.empty((ORACLE_GS_ROWS, N))
+    for i in range(ORACLE_GS_ROWS):
+        V[i] = np.sin(np.arange(N) * (0.37 + 0.11 * i))
+        V[i] /= np.linalg.norm(V[i])
+    return ops, Pc, V, N
+
+
+def _oracle_iteration(ops, Pc, V, v):
+    """One iteration of the oracle's FGMRES (krylov.fgmres): z = P^-1 v (V-cycle, S_hat^-1,
+    B^T), w = K z, modified Gram-Schmidt of w against the basis rows, its norm."""
+    import numpy as np
+    z = Pc.apply(v)
+    w = ops.apply_stokes(z)
+    for i in range(V.shape[0]):
+        w = w - (w @ V[i]) * V[i]
+    return np.linalg.norm(w)
+
+
+def _oracle_steps(prob, warmup, steps):
+    """Mean seconds of one oracle FGMRES iteration on the full workload (set-up untimed)."""
+    ops, Pc, V, N = _oracle_setup(prob)
+    v = V[0].copy()
+    ts = []
+    for i in range(warmup + steps):
+        t = time.perf_counter()
+        _oracle_iteration(ops, Pc, V, v)
+        if i >= warmup:
+            ts.append(time.perf_counter() - t)
+    return ts, N
+
+
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
@@ -235,41 +283,25 @@ def run_reference(args):
         print(json.dumps({"impl": "reference", "unavailable": "no recorded oracle iteration count for %s "
                           "(run python -m oracle.solve_workload %s)" % (args.workload, args.workload)}))
         return
-    # each step: one FGMRES iteration of the oracle on the full workload (one shared set-up),
-    # scaled by the oracle's recorded iteration count for the whole solve
-    t_it, ndof = _oracle_steps(prob, args.warmup, args.steps)
-    solve_s = t_it * its
-    value = ndof / solve_s / 1e9
+    # each step: one FGMRES iteration of the oracle on the full workload (one shared set-up); the
+    # solve throughput scales the measured mean by the oracle's recorded iteration count
+    ts, ndof = _oracle_steps(prob, args.warmup, args.steps)
+    t_it = statistics.mean(ts)
+    value = ndof / (t_it * its) / 1e9
+    sample = ("1 FGMRES iteration of the numpy/scipy FP64 oracle per step on the full %s workload: "
+              "P^-1 (V-cycle, S_hat^-1, B^T), K z, modified Gram-Schmidt against %d basis rows; "
+              "value = N / (mean step time x the oracle's recorded %d iterations)"
+              % (args.workload, ORACLE_GS_ROWS, its))
     line = {"metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": solve_s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": t_it * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": args.workload, "n": prob.n, "levels": prob.n_levels, "sinkers": prob.n_sinkers,
-                       "dr": prob.mu_max / prob.mu_min, "rtol": RTOL},
+            "config": workload_config(prob, si.n_velocity(prob.n), si.n_pressure(prob.n)),
+            "extrapolation": {"iterations_per_solve": its, "solve_s": t_it * its,
+                              "step_ms": [round(t * 1e3, 1) for t in ts]},
             "cpu_baseline": {"value": value, "unit": "GDoF/s", "cores": cpu_threads(), "kind": "oracle",
-                             "sample": "1 FGMRES iteration of the oracle per step on the full %s workload "
-                                       "(numpy/scipy FP64), scaled by the oracle's recorded %d iterations"
-                                       % (args.workload, its)},
+                             "sample": sample},
             "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
-
-
-def _oracle_steps(prob, warmup, steps):
-    import numpy as np
-    from oracle import gmg, krylov, mesh, operators, sinker
-    m = mesh.Mesh(prob.n)
-    mus = sinker.level_viscosities(m, prob, prob.n_levels)
-    G = gmg.GMG(prob.n, prob.n_levels, mus)
-    ops = G.levels[-1].ops
-    F = operators.assemble_rhs(m, sinker.forcing(m.quad_points(), prob))
-    b = np.concatenate([F, np.zeros(m.n_p)])
-    Pc = krylov.StokesPreconditioner(ops, G)
-    ts = []
-    for i in range(warmup + steps):
-        t = time.perf_counter()
-        krylov.fgmres(ops.apply_stokes, Pc.apply, b, rtol=1e-30, max_it=1)
-        if i >= warmup:
-            ts.append(time.perf_counter() - t)
-    return statistics.mean(ts), m.n_u + m.n_p
 
 
 # ----------------------------------------------------------------- our arm
@@ -337,14 +369,16 @@ def run_ours(args):
     pk = peaks()
     hbm = pk.get("hbm_gbs", 6800.0)
     hbm_src = "of measured" if "hbm_gbs" in pk else "of fallback"
+    dopt = capi.stokes_default_options()
     line = {"metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64 outer + f32 V-cycle", "data": "synthetic",
-            "config": {"workload": args.workload, "n": prob.n, "levels": prob.n_levels, "sinkers": prob.n_sinkers,
-                       "dr": prob.mu_max / prob.mu_min, "n_u": n_u, "n_p": n_p, "rtol": RTOL,
-                       "vcycle": "fp32", "outer": "fp64 FGMRES(50)", "parallelism": "replicas" if world > 1 else "1 GPU",
-                       "cheb_degree": 4, "cell_block": tuned_block,
-                       "l2": "working set %.1f GB > L2 (no flush needed)" % (N * 8 * 103 / 1e9)},
+            "vs_baseline": None, "dtype": "df64 outer (FP64 true residual) + f32 V-cycle", "data": "synthetic",
+            "config": workload_config(prob, n_u, n_p),
+            "impl_config": {"parallelism": "replicas" if world > 1 else "1 GPU", "cell_block": tuned_block,
+                            "vmult_kernel": VMULT_KERNELS.get(dopt.vmult_kernel, dopt.vmult_kernel),
+                            "outer_arith": "double-float on FP32 pipes (~47-bit significand), restart and final "
+                                           "residuals native FP64" if dopt.outer_arith == 1 else "native FP64",
+                            "l2": "working set %.1f GB > L2 (no flush needed)" % (N * 8 * 103 / 1e9)},
             "solve": {"fp32_vcycle_s": ms / 1e3, "fp32_vcycle_iterations": its,
                       "fp32_true_rel_residual": true_res32},
             "gpu_launches": int(launches), "clocks": clocks}
@@ -352,7 +386,8 @@ def run_ours(args):
         print(json.dumps(line))
         return
 
-    # --- FP64 V-cycle solve (same FGMRES), one timed solve
+    # --- FP64 V-cycle solve (same FGMRES), one timed solve; the two solutions' difference
+    sol32 = up.clone()
     e0.record(stream)
     info64 = solve(FP64)
     e1.record(stream)
@@ -360,41 +395,16 @@ def run_ours(args):
     line["solve"].update({"fp64_vcycle_s": e0.elapsed_time(e1) / 1e3, "fp64_vcycle_iterations": info64.iterations,
                           "fp64_true_rel_residual": info64.rel_residual_true})
     line["solve"]["fp32_speedup_vs_fp64_gmg"] = line["solve"]["fp64_vcycle_s"] / line["solve"]["fp32_vcycle_s"]
+    line["accuracy"] = {args.workload + "_fp32_vs_fp64_vcycle": solution_difference(sol32, up, n_u)}
+    del sol32
 
-    # --- standalone vmult (finest level), FP32 and FP64
-    x32 = torch.rand(n_u, device="cuda", dtype=torch.float32)
-    y32 = torch.empty_like(x32)
-    x64 = x32.double()
-    y64 = torch.empty_like(x64)
-    cells = prob.n ** 3
-    vm = {}
-    for tag, prec, x, y, s in (("fp32", FP32, x32, y32, 4), ("fp64", FP64, x64, y64, 8)):
-        reps = 20 if tag == "fp32" else 5
-        for _ in range(3):
-            capi.stokes_vmult(ctx, -1, capi.BLOCK_A, prec, x, y, stream=stream)
-        capi.stokes_profile(1)
-        capi.stokes_profile_read(reset=True)
-        e0.record(stream)
-        for _ in range(reps):
-            capi.stokes_vmult(ctx, -1, capi.BLOCK_A, prec, x, y, stream=stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        prof = capi.stokes_profile_read(reset=True)
-        capi.stokes_profile(0)
-        t_call = e0.elapsed_time(e1) / reps / 1e3
-        kname = "vmult_A_" + tag
-        # one operator application = the brick kernel + the brick-plane kernel
-        t_kern = (prof[kname][0] + prof["smoother_vec"][0]) / max(prof[kname][1], 1) / 1e3
-        bytes_alg = (2 * n_u + cells) * s
-        vm[tag] = {"gdofs": n_u / t_call / 1e9, "call_ms": t_call * 1e3, "kernel_ms": t_kern * 1e3,
-                   "kernel_gdofs": n_u / t_kern / 1e9, "algorithmic_bytes": bytes_alg,
-                   "achieved_gbs": bytes_alg / t_kern / 1e9, "hbm_frac": bytes_alg / t_kern / 1e9 / hbm,
-                   "gflops": cells * A_FLOP_PER_CELL / t_kern / 1e9}
-    line["vmult"] = vm
-    line["vmult"]["peak_gbs"] = hbm
-    line["vmult"]["peak_note"] = hbm_src
+    # --- standalone vmult (finest level) at the bench workload: vectors of 64^3 fit in L2
+    vm64 = time_vmult(capi, ctx, prob.n, n_u, stream, hbm)
+    line["vmult_l2_resident"] = dict(vm64, workload=args.workload,
+                                     note="src + dst fit in the 126 MB L2: an L2 figure, not an HBM one")
 
     # --- profiled solve: time share per kernel class inside the step
+    cells = prob.n ** 3
     capi.stokes_profile(1)
     capi.stokes_profile_read(reset=True)
     solve(FP32)
@@ -404,48 +414,13 @@ def run_ours(args):
     tot = sum(v[0] for v in prof.values())
     line["kernel_share"] = {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / tot, 4)}
                             for k, v in prof.items() if v[1]}
-    # the dominant single kernel: the classes below hold one kernel each (the Krylov and smoother
-    # classes hold many small ones and get their own class-level roofline)
-    single = ("stokes_fp64", "vmult_A_fp32")
-    dom = max(single, key=lambda k: prof.get(k, (0.0, 0))[0])
-    # live FMA peaks of this GPU (FMA-chain probe), for the ALU-bound kernels
+    # live FMA peaks of this GPU (FMA-chain probe), for the ALU side of the roofline
     f32_peak, f64_peak = capi.stokes_probe_fma()
     line["alu_peaks_tflops"] = {"fp32": f32_peak, "fp64": f64_peak, "how": "stokes_probe_fma: 8 FMA chains/thread"}
-    for tag, pk in (("fp32", f32_peak), ("fp64", f64_peak)):
-        vm[tag]["alu_frac"] = vm[tag]["gflops"] / (pk * 1e3)
-    outer_arith = capi.stokes_default_options().outer_arith
-    line["config"]["outer_arith"] = "double-float on FP32 pipes" if outer_arith == 1 else "native FP64"
-    if dom == "stokes_fp64":
-        # time of the outer operator alone, averaged over the profiled solve's launches
-        dms = prof[dom][0] / max(prof[dom][1], 1)
-        fl = cells * STOKES_FLOP_PER_CELL
-        ach = fl / (dms / 1e3) / 1e9
-        if outer_arith == 1:
-            # double-float kernel: bound by the FP32 pipe; FP32 instructions per cell estimated from
-            # the implemented sweeps (DF64_OPS_PER_CELL), peak = FFMA probe / 2 (instructions/s)
-            ips = cells * DF64_OPS_PER_CELL / (dms / 1e3)
-            line["roofline"] = {"kernel": "k_outer_df64<1,1,1> (outer [A B^T; B 0], double-float)", "bound": "alu",
-                                "achieved": ips / 1e9, "peak": f32_peak / 2 * 1e3, "unit": "G FP32-instr/s",
-                                "frac": ips / (f32_peak / 2 * 1e12),
-                                "traffic": recorded_traffic("stokes_df64", args.workload),
-                                "peak_note": "of measured (FFMA probe, this run; FMA counted as 1 instruction)",
-                                "per_launch": "%d cells x ~%d FP32 instructions" % (cells, DF64_OPS_PER_CELL),
-                                "fp64_equivalent_gflops": ach, "fp64_dfma_peak_gflops": f64_peak * 1e3}
-        else:
-            line["roofline"] = {"kernel": "k_stokes_blocks<double,1,1,1> (outer [A B^T; B 0], FP64)", "bound": "alu",
-                                "achieved": ach, "peak": f64_peak * 1e3, "unit": "GFLOP/s",
-                                "frac": ach / (f64_peak * 1e3), "traffic": recorded_traffic("stokes_fp64", args.workload),
-                                "peak_note": "of measured (DFMA probe, this run)",
-                                "per_launch": "%d cells x %d flop" % (cells, STOKES_FLOP_PER_CELL)}
-    else:
-        k = vm["fp32"] if dom == "vmult_A_fp32" else vm["fp64"]
-        line["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": k["achieved_gbs"], "peak": hbm, "unit": "GB/s",
-                            "frac": k["hbm_frac"], "traffic": recorded_traffic(dom, args.workload),
-                            "peak_note": hbm_src}
+    line["roofline"] = dominant_roofline(prof, dopt, cells, n_u, N, hbm, hbm_src, f32_peak, f64_peak, args.workload)
 
     # class-level roofline of the FGMRES vector kernels: algorithmic bytes of their passes over
     # the profiled solve / their summed time
-    dopt = capi.stokes_default_options()
     kb = krylov_alg_bytes(N, its[-1], dopt.restart,
                           dopt.gram_schmidt == 1 and dopt.outer_arith == 1 and dopt.restart <= 64)
     kt = prof["krylov_vec"][0] / 1e3
@@ -485,24 +460,176 @@ def run_ours(args):
     line["e2e"] = {"value": N / (ems / 1e3) / 1e9, "unit": "GDoF/s", "ms_per_step": ems,
                    "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8}
     ctx.close()
-    del up, x32, y32, x64, y64
+    del up
     torch.cuda.empty_cache()
+
+    # --- each result's error against the FP64 oracle's solution where the oracle can solve
+    for name in ("cube8", "cube16"):
+        ref = stored_oracle_solution(name)
+        if ref is None:
+            continue
+        sp = si.workload(name)
+        sctx = capi.stokes_setup_problem(sp, stream=stream)
+        acc = {}
+        for tag, prec in (("fp32_vcycle", FP32), ("fp64_vcycle", FP64)):
+            x = torch.zeros(sctx.n_u + sctx.n_p, dtype=torch.float64, device="cuda")
+            inf = capi.stokes_solve(sctx, prec, None, x, rtol=RTOL, max_it=2000, stream=stream)
+            acc[tag] = dict(solution_difference(x, torch.from_numpy(ref).cuda(), sctx.n_u),
+                            iterations=inf.iterations, true_rel_residual=inf.rel_residual_true)
+        line["accuracy"][name + "_vs_oracle_solution"] = acc
+        sctx.close()
+    line["accuracy"]["note"] = ("relative 2-norm differences of velocity and pressure; the oracle's FGMRES "
+                                "solution to 1e-12 (oracle/solutions/, written by oracle/solve_workload.py)")
+
+    # --- the 128^3 configuration: above-L2 vmult (the HBM figure) and one FP32-V-cycle solve
+    if not args.no_large:
+        line.update(run_large(capi, si, torch, stream, hbm, hbm_src))
 
     # --- CPU oracle baseline: bounded sample, scaled to a solve
     its_ref = oracle_iterations(args.workload)
     try:
-        t_it, ndof = _oracle_steps(prob, 0, 2)
+        ts, ndof = _oracle_steps(prob, 0, 3)
+        t_it = statistics.mean(ts)
         n_it = its_ref if its_ref else its[-1]
         line["cpu_baseline"] = {"value": ndof / (t_it * n_it) / 1e9, "unit": "GDoF/s", "cores": cpu_threads(),
                                 "kind": "oracle",
-                                "sample": "2 FGMRES iterations of the numpy/scipy FP64 oracle on the full %s "
-                                          "workload (set-up untimed), %.2f s each, scaled by %d iterations%s"
-                                          % (args.workload, t_it, n_it,
+                                "sample": "3 FGMRES iterations of the numpy/scipy FP64 oracle on the full %s "
+                                          "workload (set-up untimed; P^-1, K z, modified Gram-Schmidt against %d "
+                                          "basis rows), %.2f s each, scaled by %d iterations%s"
+                                          % (args.workload, ORACLE_GS_ROWS, t_it, n_it,
                                              " (oracle's recorded count)" if its_ref else " (GPU FP32 count)")}
     except MemoryError as e:
         line["cpu_baseline"] = {"value": None, "unit": "GDoF/s", "cores": cpu_threads(), "kind": "oracle",
                                 "sample": "failed: %s" % e}
     print(json.dumps(line))
+
+
+VMULT_KERNELS = {0: "k_cell_atomic (one thread per cell, FP32 pipes, atomic scatter)",
+                 1: "k_brick + k_planes (brick-tiled, deterministic)"}
+
+
+def solution_difference(x, ref, n_u):
+    """Relative 2-norm differences of the velocity and pressure parts of two solutions."""
+    import torch
+    du = torch.linalg.vector_norm(x[:n_u] - ref[:n_u]) / torch.linalg.vector_norm(ref[:n_u])
+    dp = torch.linalg.vector_norm(x[n_u:] - ref[n_u:]) / torch.linalg.vector_norm(ref[n_u:])
+    return {"u_rel": float(du), "p_rel": float(dp)}
+
+
+def stored_oracle_solution(name):
+    import numpy as np
+    path = os.path.join(ROOT, "oracle", "solutions", name + ".npy")
+    return np.load(path) if os.path.exists(path) else None
+
+
+def time_vmult(capi, ctx, n, n_u, stream, hbm, reps=(20, 5)):
+    """Finest-level dst = A src, FP32 and FP64: CUDA-event time of the whole call (zeroing the
+    output, the operator kernel, the identity rows) and of the operator kernel alone (profiled
+    class), algorithmic bytes (2 N_u + cells) x size / kernel time against the HBM peak."""
+    import torch
+    cells = n ** 3
+    x32 = torch.rand(n_u, device="cuda", dtype=torch.float32)
+    y32 = torch.empty_like(x32)
+    x64 = x32.double()
+    y64 = torch.empty_like(x64)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    for tag, prec, x, y, sz, r in (("fp32", capi.STOKES_FP32, x32, y32, 4, reps[0]),
+                                   ("fp64", capi.STOKES_FP64, x64, y64, 8, reps[1])):
+        for _ in range(3):
+            capi.stokes_vmult(ctx, -1, capi.BLOCK_A, prec, x, y, stream=stream)
+        capi.stokes_profile(1)
+        capi.stokes_profile_read(reset=True)
+        e0.record(stream)
+        for _ in range(r):
+            capi.stokes_vmult(ctx, -1, capi.BLOCK_A, prec, x, y, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = capi.stokes_profile_read(reset=True)
+        capi.stokes_profile(0)
+        t_call = e0.elapsed_time(e1) / r / 1e3
+        kname = "vmult_A_" + tag
+        # one operator application = the cell kernel (+ the brick-plane kernel of the brick variant)
+        t_kern = (prof[kname][0] + prof["smoother_vec"][0]) / max(prof[kname][1], 1) / 1e3
+        bytes_alg = (2 * n_u + cells) * sz
+        out[tag] = {"gdofs": n_u / t_call / 1e9, "call_ms": t_call * 1e3, "kernel_ms": t_kern * 1e3,
+                    "kernel_gdofs": n_u / t_kern / 1e9, "algorithmic_bytes": bytes_alg,
+                    "achieved_gbs": bytes_alg / t_kern / 1e9, "hbm_frac": bytes_alg / t_kern / 1e9 / hbm,
+                    "call_hbm_frac": bytes_alg / t_call / 1e9 / hbm,
+                    "gflops": cells * A_FLOP_PER_CELL / t_kern / 1e9}
+    out["peak_gbs"] = hbm
+    return out
+
+
+def dominant_roofline(prof, dopt, cells, n_u, N, hbm, hbm_src, f32_peak, f64_peak, workload):
+    """Roofline of the single kernel with the largest time in the profiled solve. achieved =
+    algorithmic bytes per launch / its mean launch time, against the measured HBM peak; the ALU
+    side (method flops against the FMA probe) beside it."""
+    single = ("stokes_fp64", "vmult_A_fp32")
+    dom = max(single, key=lambda k: prof.get(k, (0.0, 0))[0])
+    dms = prof[dom][0] / max(prof[dom][1], 1)
+    if dom == "stokes_fp64":
+        bytes_alg = (2 * N + cells) * 8
+        fl = cells * STOKES_FLOP_PER_CELL
+        df = dopt.outer_arith == 1
+        r = {"kernel": "k_outer_df64<1,1,1> (outer [A B^T; B 0], double-float)" if df else
+                       "k_stokes_blocks<double,1,1,1> (outer [A B^T; B 0], FP64)",
+             "bound": "hbm", "achieved": bytes_alg / (dms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+             "frac": bytes_alg / (dms / 1e3) / 1e9 / hbm,
+             "traffic": recorded_traffic("stokes_df64" if df else "stokes_fp64", workload),
+             "peak_note": hbm_src, "launch_ms": dms,
+             "per_launch": "(2 (N_u + N_p) + cells) x 8 B = %d B (u, p read and written in FP64, cell viscosity)"
+                           % bytes_alg}
+        alu_peak = f32_peak if df else f64_peak
+        r["alu"] = {"method_flop_per_cell": STOKES_FLOP_PER_CELL, "achieved_gflops": fl / (dms / 1e3) / 1e9,
+                    "peak_gflops": alu_peak * 1e3, "frac": fl / (dms / 1e3) / 1e9 / (alu_peak * 1e3),
+                    "peak_note": "of measured (%s probe, this run); the FP64 method flops %s"
+                                 % ("FFMA" if df else "DFMA",
+                                    "run as double-float on the FP32 pipes, several FP32 instructions each"
+                                    if df else "on the FP64 pipe")}
+        inst = recorded_traffic("stokes_df64_inst" if df else "stokes_fp64_inst", workload)
+        if inst:
+            ips = inst / (dms / 1e3)
+            r["issue"] = {"fp32_pipe_inst_per_launch": inst, "frac": ips / (f32_peak / 2 * 1e12),
+                          "note": "FP32-pipe instructions per launch from ncu against half the FFMA probe "
+                                  "(instructions/s)"}
+        return r
+    bytes_alg = (2 * n_u + cells) * 4
+    return {"kernel": dom, "bound": "hbm", "achieved": bytes_alg / (dms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+            "frac": bytes_alg / (dms / 1e3) / 1e9 / hbm, "traffic": recorded_traffic(dom, workload),
+            "peak_note": hbm_src, "launch_ms": dms,
+            "per_launch": "finest-level (2 N_u + cells) x 4 B = %d B (mean over the solve's levels is lower)"
+                          % bytes_alg}
+
+
+def run_large(capi, si, torch, stream, hbm, hbm_src, name="cube128"):
+    """The 128^3 configuration (16 sinkers, viscosity ratio 1e6, 8 levels): the standalone vmult with
+    vectors far above L2 (the HBM figure) and one FP32-V-cycle FGMRES solve to 1e-8 with its true
+    residual from the native FP64 operator."""
+    prob = si.workload(name)
+    t0 = time.perf_counter()
+    ctx = capi.stokes_setup_problem(prob, stream=stream)
+    setup_s = time.perf_counter() - t0
+    n_u, n_p = ctx.n_u, ctx.n_p
+    vm = time_vmult(capi, ctx, prob.n, n_u, stream, hbm)
+    vm.update({"workload": name, "peak_note": hbm_src,
+               "note": "src + dst = %.0f MB FP32, above the 126 MB L2" % (2 * n_u * 4 / 1e6)})
+    up = torch.zeros(n_u + n_p, dtype=torch.float64, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    info = capi.stokes_solve(ctx, capi.STOKES_FP32, None, up, rtol=RTOL, max_it=3000, stream=stream, check=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    solve = {"workload": name, "n_u": n_u, "n_p": n_p, "levels": prob.n_levels, "dr": prob.mu_max / prob.mu_min,
+             "sinkers": prob.n_sinkers, "setup_s": setup_s, "fp32_vcycle_s": e0.elapsed_time(e1) / 1e3,
+             "iterations": info.iterations, "status": info.status,
+             "true_rel_residual": info.rel_residual_true,
+             "note": "first solve on the context (includes the V-cycle graph capture); true residual from the "
+                     "library's native FP64 operator"}
+    ctx.close()
+    del up
+    torch.cuda.empty_cache()
+    return {"vmult": vm, "solve_" + name: solve}
 
 
 def run_kernels(args):

@@ -60,7 +60,7 @@ typedef enum {
     STOKES_EINVAL = 1,          /* bad argument (size, level, precision, null pointer) */
     STOKES_ENOMEM = 2,          /* device or host allocation failed */
     STOKES_ECUDA = 3,           /* a CUDA runtime call or kernel launch failed */
-    STOKES_NOT_CONVERGED = 4,   /* stokes_solve hit max_it before rtol */
+    STOKES_NOT_CONVERGED = 4,   /* a solve ended with its true residual above rtol */
     STOKES_BREAKDOWN = 5,       /* NaN/Inf or a zero Krylov norm in stokes_solve */
     STOKES_TIMEOUT = 6,         /* reserved: a bounded device wait gave up */
     STOKES_EMESH = 7            /* unsupported mesh description */
@@ -78,7 +78,7 @@ typedef enum {
 
 typedef struct {
     int kind;                   /* 0 = uniform n^3 grid of the unit cube (the only kind) */
-    int n;                      /* cells per axis on the finest level, n = c * 2^(n_levels-1), 1 <= c <= 4 */
+    int n;                      /* cells per axis on the finest level, n = c * 2^(n_levels-1), 1 <= c <= 6 */
     int n_levels;               /* multigrid levels, >= 1 */
 } stokes_mesh;
 
@@ -168,7 +168,7 @@ void stokes_default_options(stokes_options* opt);
  * M_p, and the right-hand side F (kind 0 only; F = 0 for kind 1).
  * Synchronous on `stream`. On success *out owns all of it. Errors: EINVAL
  * (null pointer, n or n_levels out of range), EMESH (kind != 0, n not
- * c*2^(L-1), bc != 0x3F), ENOMEM, ECUDA. */
+ * c*2^(L-1) with c <= 6, bc != 0x3F), ENOMEM, ECUDA. */
 stokes_status stokes_setup(const stokes_mesh* mesh, const stokes_mu* mu, const stokes_bc* bc,
                            const stokes_options* opt /* NULL = defaults */, void* stream,
                            stokes_ctx** out);
@@ -296,9 +296,12 @@ stokes_status gmg_vcycle(stokes_ctx* ctx, int prec, const void* rhs_dev, void* x
  * [F; 0]. up_dev: in = initial guess, out = solution with zero-mean pressure.
  * Stops when the recurrence residual <= rtol ||b|| and the true residual
  * b - K x, recomputed with the native FP64 operator, is too; otherwise the
- * method restarts from x (at most 10 times). Host-synchronous (small
- * device->host reads per iteration). Errors: NOT_CONVERGED (max_it reached; up
- * holds the last iterate), BREAKDOWN, EINVAL, ENOMEM, ECUDA. */
+ * method restarts from x (at most 10 times). The returned status follows that
+ * true residual: OK only if it is <= rtol ||b||, NOT_CONVERGED otherwise
+ * (max_it reached, or the restarts used up; up holds the last iterate and
+ * info->rel_residual_true its true residual). Host-synchronous (small
+ * device->host reads per iteration). Errors: NOT_CONVERGED, BREAKDOWN, EINVAL,
+ * ENOMEM, ECUDA. */
 stokes_status stokes_solve(stokes_ctx* ctx, int vcycle_prec, const double* rhs_dev, double* up_dev,
                            double rtol, int max_it, stokes_solve_info* info, void* stream);
 
@@ -375,10 +378,12 @@ stokes_status stokes_autotune(stokes_ctx* ctx, int what, void* stream, int* bloc
  * stokes_ctx, and calls no cudaMalloc/cudaFree. Its three work vectors live in
  * one fixed device array of 3 * STOKES_NOALLOC_MAX_NP doubles (~0.86 MB) that
  * every GPU loading the library holds until exit. The first call on a device
- * looks up that array's address (make it before any stream capture). All
- * calls share the array: calls that overlap on the GPU race; serialise them.
- * rp_dev and zp_dev hold (n+1)^3 doubles and must not overlap. Errors: EINVAL
- * (null pointer, n < 1, degree < 1, (n+1)^3 > STOKES_NOALLOC_MAX_NP), ECUDA. */
+ * looks up that array's address (make it before any stream capture); later
+ * calls on a stream that is not capturing look it up again. All calls share
+ * the array: calls that overlap on the GPU race; serialise them. degree 0 is
+ * S_hat = diag(M_p), as for the context's schur_degree = 0. rp_dev and zp_dev
+ * hold (n+1)^3 doubles and must not overlap. Errors: EINVAL (null pointer,
+ * n < 1, n > 32, i.e. (n+1)^3 > STOKES_NOALLOC_MAX_NP, degree < 0), ECUDA. */
 stokes_status stokes_schur_inverse_noalloc(int n, const double* mu_dev, const double* rp_dev, double* zp_dev,
                                            int degree, void* stream);
 

@@ -24,6 +24,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 using namespace stk;
@@ -823,6 +824,10 @@ stokes_status fgmres_complete(FgmresRun& r) {
                 r.phase = FgmresRun::P_RESTART;
                 return STOKES_OK;
             }
+            // the status follows the true residual, whatever ended the iteration (max_it, the
+            // recurrence, or no verification returns left); only a breakdown keeps its own status
+            if (r.st != STOKES_BREAKDOWN && r.bnorm > 0.0)
+                r.st = rt <= r.rtol * r.bnorm ? STOKES_OK : STOKES_NOT_CONVERGED;
             if (r.info) {
                 r.info->iterations = r.its;
                 r.info->rel_residual = r.est;
@@ -886,7 +891,7 @@ stokes_status fgmres(stokes_ctx* c, int prec, const double* b, double* x, double
     CKS(fgmres_drive(runs));
     const stokes_status st = runs[0].st;
     if (st != STOKES_OK) return fail(st, st == STOKES_BREAKDOWN ? "(F)GMRES breakdown (non-finite norm)"
-                                                                 : "(F)GMRES reached max_it");
+                                                                 : "(F)GMRES: true residual above rtol (max_it or restarts used up)");
     return STOKES_OK;
 }
 
@@ -1034,13 +1039,17 @@ stokes_status idr_solve(stokes_ctx* c, int prec, const double* b, double* x, dou
     CK(launch_axpby(N, 1.0, b, -1.0, r, s));
     double rt = 0.0;
     CKS(dot(c, N, r, r, s, &rt));
+    // the status follows the true residual (a recurrence that met the tolerance on the last
+    // allowed restart is not enough); only a breakdown keeps its own status
+    if (st != STOKES_BREAKDOWN && bnorm > 0.0) st = std::sqrt(rt) <= rtol * bnorm ? STOKES_OK : STOKES_NOT_CONVERGED;
     if (info) {
         info->iterations = its;
         info->rel_residual = bnorm > 0 ? rnorm / bnorm : 0.0;
         info->rel_residual_true = bnorm > 0 ? std::sqrt(rt) / bnorm : 0.0;
         info->status = st;
     }
-    if (st != STOKES_OK) return fail(st, st == STOKES_BREAKDOWN ? "IDR(s) breakdown" : "IDR(s) reached max_it");
+    if (st != STOKES_OK)
+        return fail(st, st == STOKES_BREAKDOWN ? "IDR(s) breakdown" : "IDR(s): true residual above rtol (max_it or restarts used up)");
     return STOKES_OK;
 }
 
@@ -1138,14 +1147,15 @@ stokes_status minres_solve(stokes_ctx* c, int prec, const double* b, double* x, 
     CK(launch_axpby(N, 1.0, b, -1.0, r, s));
     double rt = 0.0;
     CKS(dot(c, N, r, r, s, &rt));
-    if (st == STOKES_NOT_CONVERGED && bnorm > 0.0 && std::sqrt(rt) <= rtol * bnorm) st = STOKES_OK;
+    // the status follows the true residual; only a breakdown keeps its own status
+    if (st != STOKES_BREAKDOWN && bnorm > 0.0) st = std::sqrt(rt) <= rtol * bnorm ? STOKES_OK : STOKES_NOT_CONVERGED;
     if (info) {
         info->iterations = its;
         info->rel_residual = bnorm > 0 ? rnorm / bnorm : 0.0;
         info->rel_residual_true = bnorm > 0 ? std::sqrt(rt) / bnorm : 0.0;
         info->status = st;
     }
-    if (st != STOKES_OK) return fail(st, st == STOKES_BREAKDOWN ? "MINRES breakdown" : "MINRES reached max_it");
+    if (st != STOKES_OK) return fail(st, st == STOKES_BREAKDOWN ? "MINRES breakdown" : "MINRES: true residual above rtol (max_it or restarts used up)");
     return STOKES_OK;
 }
 
@@ -1160,34 +1170,74 @@ stokes_status validate_options(const stokes_options& o) {
     return STOKES_OK;
 }
 
-// Inverse of a dense symmetric positive definite matrix (row-major nf x nf): Cholesky
-// A = R^T R with R upper triangular, then R^T z = e_j and R x = z for every column j.
+// Runs f(i) for i < n on the host threads, i interleaved over the threads (balances the
+// triangular loops below).
+template <typename F>
+void host_parallel_rows(int n, F f) {
+    unsigned nt = std::thread::hardware_concurrency();
+    nt = nt < 1 ? 1 : (nt > 32 ? 32 : nt);
+    if (n < 64 || nt == 1) {
+        for (int i = 0; i < n; ++i) f(i);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t)
+        th.emplace_back([&, t] {
+            for (int i = int(t); i < n; i += int(nt)) f(i);
+        });
+    for (auto& x : th) x.join();
+}
+
+// Inverse of a dense symmetric positive definite matrix (row-major nf x nf): blocked Cholesky
+// A = L L^T (row panels of kBlk columns; every inner loop a contiguous dot product), then
+// W = L^-1 column by column (stored transposed, W[j][i] = (L^-1)_ij), then A^-1 = L^-T L^-1,
+// entry (a, b) = sum_{i >= max(a, b)} W[a][i] W[b][i]. Rows and columns are spread over the
+// host threads; the result does not depend on their number.
 stokes_status spd_inverse(const std::vector<double>& A, int nf, std::vector<double>& Ainv) {
-    std::vector<double> R = A;
-    for (int i = 0; i < nf; ++i) {
-        for (int k = 0; k < i; ++k) {
-            const double rki = R[size_t(k) * nf + i];
-            for (int jj = i; jj < nf; ++jj) R[size_t(i) * nf + jj] -= rki * R[size_t(k) * nf + jj];
+    constexpr int kBlk = 64;
+    std::vector<double> L = A;   // lower triangle overwritten by the factor
+    auto Lr = [&](int i) { return L.data() + size_t(i) * nf; };
+    auto dotn = [](const double* x, const double* y, int n) {
+        double t = 0.0;
+        for (int k = 0; k < n; ++k) t += x[k] * y[k];
+        return t;
+    };
+    for (int kb = 0; kb < nf; kb += kBlk) {
+        const int ke = std::min(kb + kBlk, nf);
+        // diagonal block (earlier panels already subtracted by the trailing updates)
+        for (int j = kb; j < ke; ++j) {
+            const double d = Lr(j)[j] - dotn(Lr(j) + kb, Lr(j) + kb, j - kb);
+            if (!(d > 0.0)) return fail(STOKES_EINVAL, "coarse matrix is not positive definite");
+            Lr(j)[j] = std::sqrt(d);
+            for (int i = j + 1; i < ke; ++i) Lr(i)[j] = (Lr(i)[j] - dotn(Lr(i) + kb, Lr(j) + kb, j - kb)) / Lr(j)[j];
         }
-        const double d = R[size_t(i) * nf + i];
-        if (!(d > 0.0)) return fail(STOKES_EINVAL, "coarse matrix is not positive definite");
-        const double sd = std::sqrt(d);
-        for (int jj = i; jj < nf; ++jj) R[size_t(i) * nf + jj] /= sd;
+        // panel below the block, then the trailing lower triangle
+        host_parallel_rows(nf - ke, [&](int t) {
+            double* ri = Lr(ke + t);
+            for (int j = kb; j < ke; ++j) ri[j] = (ri[j] - dotn(ri + kb, Lr(j) + kb, j - kb)) / Lr(j)[j];
+        });
+        host_parallel_rows(nf - ke, [&](int t) {
+            const int i = ke + t;
+            double* ri = Lr(i);
+            for (int j = ke; j <= i; ++j) ri[j] -= dotn(ri + kb, Lr(j) + kb, ke - kb);
+        });
     }
+    std::vector<double> W(size_t(nf) * nf, 0.0);
+    host_parallel_rows(nf, [&](int j) {
+        double* x = W.data() + size_t(j) * nf;   // x[i] = (L^-1)_ij, i >= j
+        x[j] = 1.0 / Lr(j)[j];
+        for (int i = j + 1; i < nf; ++i) x[i] = -dotn(Lr(i) + j, x + j, i - j) / Lr(i)[i];
+    });
     Ainv.assign(size_t(nf) * nf, 0.0);
-    std::vector<double> zz(nf);
-    for (int j = 0; j < nf; ++j) {
-        for (int i = 0; i < nf; ++i) {
-            double t = (i == j) ? 1.0 : 0.0;
-            for (int k = 0; k < i; ++k) t -= R[size_t(k) * nf + i] * zz[k];
-            zz[i] = t / R[size_t(i) * nf + i];
+    host_parallel_rows(nf, [&](int a) {
+        const double* wa = W.data() + size_t(a) * nf;
+        for (int b = 0; b <= a; ++b) {
+            const double* wb = W.data() + size_t(b) * nf;
+            Ainv[size_t(a) * nf + b] = dotn(wa + a, wb + a, nf - a);
         }
-        for (int i = nf - 1; i >= 0; --i) {
-            double t = zz[i];
-            for (int k = i + 1; k < nf; ++k) t -= R[size_t(i) * nf + k] * Ainv[size_t(k) * nf + j];
-            Ainv[size_t(i) * nf + j] = t / R[size_t(i) * nf + i];
-        }
-    }
+    });
+    for (int a = 0; a < nf; ++a)
+        for (int b = a + 1; b < nf; ++b) Ainv[size_t(a) * nf + b] = Ainv[size_t(b) * nf + a];
     return STOKES_OK;
 }
 
@@ -1669,7 +1719,10 @@ stokes_status stokes_setup(const stokes_mesh* mesh, const stokes_mu* mu, const s
     const int cdiv = 1 << (mesh->n_levels - 1);
     if (mesh->n % cdiv != 0) return fail(STOKES_EMESH, "n must be c * 2^(n_levels-1)");
     const int coarse = mesh->n / cdiv;
-    if (coarse > 4) return fail(STOKES_EMESH, "coarsest level must have at most 4 cells per axis");
+    // the dense coarse inverse holds the 3 (2c - 1)^3 free DoFs of a c^3 coarsest mesh: at most
+    // 4,000 of them (c <= 6), the same limit as on octree meshes
+    if (3 * (2 * coarse - 1) * (2 * coarse - 1) * (2 * coarse - 1) > 4000)
+        return fail(STOKES_EMESH, "coarsest level must have at most 6 cells per axis (dense FP64 solve)");
     stokes_ctx* c = new (std::nothrow) stokes_ctx();
     if (!c) return fail(STOKES_ENOMEM, "host allocation failed");
     stokes_status st = setup_impl(mesh, mu, bc, opt, static_cast<cudaStream_t>(stream), c);

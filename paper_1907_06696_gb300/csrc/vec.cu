@@ -145,11 +145,15 @@ __global__ void k_cast_f2d(size_t n, const float* __restrict__ in, double* __res
 template <typename T>
 __global__ void k_coarse_solve(int nf, const int* __restrict__ idx, const double* __restrict__ Ainv,
                                const T* __restrict__ b, T* __restrict__ x) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nf) return;
+    // one warp per row of the inverse: coalesced row reads, lane sums reduced in a fixed order
+    const int r = int((size_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5), lane = int(threadIdx.x & 31);
+    if (r >= nf) return;   // whole warps leave together
+    const double* row = Ainv + size_t(r) * nf;
     double s = 0.0;
-    for (int j = 0; j < nf; ++j) s += Ainv[size_t(r) * nf + j] * double(b[idx[j]]);
-    x[idx[r]] = T(s);
+    for (int j = lane; j < nf; j += 32) s += row[j] * double(b[idx[j]]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) x[idx[r]] = T(s);
 }
 
 __global__ void k_axpby(size_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
@@ -315,7 +319,7 @@ cudaError_t launch_cast_f2d(size_t n, const float* in, double* out, cudaStream_t
 template <typename T>
 cudaError_t launch_coarse_solve(int nf, const int* free_idx, const double* Ainv, const T* b, T* x, cudaStream_t s) {
     if (nf <= 0) return cudaSuccess;
-    LAUNCH(PROF_COARSE, s, k_coarse_solve<T><<<blocks_for(size_t(nf), 128), 128, 0, s>>>(nf, free_idx, Ainv, b, x));
+    LAUNCH(PROF_COARSE, s, k_coarse_solve<T><<<blocks_for(size_t(nf) * 32, 128), 128, 0, s>>>(nf, free_idx, Ainv, b, x));
     return cudaGetLastError();
 }
 template cudaError_t launch_coarse_solve<float>(int, const int*, const double*, const float*, float*, cudaStream_t);

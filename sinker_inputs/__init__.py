@@ -205,12 +205,13 @@ def adaptive_loop_workload(name: str):
     raise KeyError(name)
 
 
-BATCH_SIZES = ((16, 5), (24, 4), (32, 6), (48, 5))   # (cells per axis, levels): coarsest 1 or 3 cells
+# (cells per axis, levels): coarsest 1, 3 or 5 cells per axis
+BATCH_SIZES = ((16, 5), (20, 3), (24, 4), (32, 6), (40, 4), (48, 5))
 
 
 def batch_workload(count: int = 64, seed: int = 1907 + 5):
-    """Batched sinker problems: size drawn uniformly from BATCH_SIZES (16^3..48^3 with a
-    coarsest mesh of at most 3^3 cells), 1-8 sinkers, viscosity ratio log-uniform in [1e2, 1e6];
+    """Batched sinker problems: size drawn uniformly from BATCH_SIZES ({16, 20, 24, 32, 40, 48}^3
+    with a coarsest mesh of at most 5^3 cells), 1-8 sinkers, viscosity ratio log-uniform in [1e2, 1e6];
     all draws from splitmix64 with `seed` (problem i uses seed * 1000 + i for its centres)."""
     u = uniform01(seed, 3 * count)
     probs = []

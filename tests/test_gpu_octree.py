@@ -10,8 +10,10 @@
 * V-cycle: FP64 <= 1e-9 (Lanczos estimates agree to rounding, so the Chebyshev coefficients
   differ at 1e-14 and the cycle propagates that); FP32 <= 1e-4 (FP32 rounding through the
   recursion of up to 5 levels);
-* solves: the oracle's own operator confirms the GPU solution's true residual (<= 2e-8 with
-  rtol 1e-8), iteration counts within 20% of the oracle's FGMRES.
+* solves: status OK and the oracle's own operator confirms the GPU solution's true residual:
+  <= 1e-8 (1 + 1e-3) with rtol 1e-8 (the library stops on its own native-FP64 true residual;
+  the two evaluations of b - K x differ by ~1e-12 ||b||, ~1e-4 of that residual), iteration
+  counts within 20% of the oracle's FGMRES.
 """
 import functools
 
@@ -172,8 +174,9 @@ def test_solve(capi, name, prec):
     x = up.cpu().numpy()
     b = np.concatenate([S.F, np.zeros(S.n_p)])
     res = np.linalg.norm(b - S.apply_stokes(x)) / np.linalg.norm(b)
-    assert res <= 2e-8
-    assert info.rel_residual_true <= 1e-8 * 1.0001
+    assert info.status == capi.STOKES_OK
+    assert res <= 1e-8 * 1.001
+    assert info.rel_residual_true <= 1e-8
     its_ref = oracle_solve(name)
     assert abs(info.iterations - its_ref) <= max(3, 0.2 * its_ref), (info.iterations, its_ref)
     w = S.pressure_weights()

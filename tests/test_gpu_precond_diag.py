@@ -72,7 +72,10 @@ def test_solve_diagonal(capi, name):
         up = torch.zeros(m.n_u + m.n_p, dtype=torch.float64, device="cuda")
         info = capi.stokes_solve(ctx, prec, None, up, rtol=1e-8, max_it=2000)
         x = up.cpu().numpy()
-        assert np.linalg.norm(b - ops.apply_stokes(x)) / np.linalg.norm(b) <= 1.5e-8
+        # the library stops on its own native-FP64 true residual <= 1e-8; the oracle's recomputation
+        # differs from it by ~1e-5 of that (the FP64 operator parity bound over a 1e-8 residual)
+        assert info.status == capi.STOKES_OK
+        assert np.linalg.norm(b - ops.apply_stokes(x)) / np.linalg.norm(b) <= 1e-8 * 1.001
         assert abs(info.iterations - its_o) <= max(2, 0.05 * its_o), (prec, info.iterations, its_o)
     assert its_o > its_t
     ctx.close()
@@ -91,7 +94,8 @@ def test_solve_diagonal_octree(capi):
     capi.stokes_precondition(ctx, capi.STOKES_FP64, torch.from_numpy(r).cuda(), z)
     assert rel(z.cpu().numpy(), zr) <= 1e-9
     up = torch.zeros(N, dtype=torch.float64, device="cuda")
-    capi.stokes_solve(ctx, capi.STOKES_FP32, None, up, rtol=1e-8, max_it=3000)
+    info = capi.stokes_solve(ctx, capi.STOKES_FP32, None, up, rtol=1e-8, max_it=3000)
     b = np.concatenate([S.F, np.zeros(S.n_p)])
-    assert np.linalg.norm(b - S.apply_stokes(up.cpu().numpy())) / np.linalg.norm(b) <= 2e-8
+    assert info.status == capi.STOKES_OK
+    assert np.linalg.norm(b - S.apply_stokes(up.cpu().numpy())) / np.linalg.norm(b) <= 1e-8 * 1.001
     ctx.close()

@@ -165,6 +165,27 @@ def test_global_A_rigid_modes_and_constraints():
     assert np.array_equal(y[m.dirichlet], xr[m.dirichlet])
 
 
+@pytest.mark.parametrize("n", [8, 12])
+def test_row_evaluator_equals_element_operator_on_every_row(n):
+    """operators.apply_A_rows (the row-by-row A_c x that the full-size GPU checks use, with no
+    global cell tables) equals the element-by-element Operators.apply_A, itself pinned above by
+    quadratic reproduction, rigid modes and the constraints, on every row of an 8^3 and a 12^3
+    mesh: interior rows, rows next to each wall, edge and corner, and the identity rows on the
+    walls. Cell viscosity varies by cell (1..100) and x is non-zero on constrained entries, so a
+    wrong cell index, local index, boundary mask or mu lookup fails it."""
+    m = mesh.Mesh(n)
+    mu = 1.0 + 99.0 * si.uniform01(11 + n, m.n_cells)
+    x = si.uniform(12 + n, m.n_u)
+    ref = operators.Operators(m, mu).apply_A(x)
+    got = operators.apply_A_rows(n, mu, x, np.arange(m.n_u))
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+    # the comparison sees a boundary-mask mistake: rows that also took the constrained entries
+    # of x (the unconstrained operator) differ from it by far more than rounding
+    wrong = operators.Operators(m, mu).apply_A_unconstrained(x)
+    free = ~m.dirichlet
+    assert np.abs(wrong[free] - got[free]).max() > 1e-3 * np.abs(ref).max()
+
+
 def test_BT_of_linear_pressure_and_adjointness():
     """(B^T p)_(c,node) = -int d_c phi p = int phi d_c p for interior nodes; for p = x that is
     int phi on the x component and 0 elsewhere. And (B u, p) = (u, B^T p)."""

@@ -31,14 +31,23 @@ def capi():
     return api
 
 
-@pytest.mark.parametrize("name", ["cube8", "cube16"])
-def test_noalloc_schur_matches_context_entry_point(capi, name):
-    p = si.workload(name)
-    ctx = capi.stokes_setup_problem(p)
+def problem(name):
+    # n32: 32^3 cells, the largest size the fixed array holds (33^3 = STOKES_NOALLOC_MAX_NP pressure DoFs)
+    return si.dr_problem(32, 4, 4, 1e4, 7032, "n32") if name == "n32" else si.workload(name)
+
+
+@pytest.mark.parametrize("name,degree", [("cube8", None), ("cube16", None), ("cube8", 0), ("cube16", 3),
+                                         ("n32", None)])
+def test_noalloc_schur_matches_context_entry_point(capi, name, degree):
+    p = problem(name)
+    opt = capi.stokes_default_options()
+    if degree is not None:
+        opt.schur_degree = degree
+    degree = opt.schur_degree
+    ctx = capi.stokes_setup_problem(p, options=opt)
     n_p = ctx.n_p
     mu = torch.empty(p.n ** 3, dtype=torch.float64, device="cuda")
     capi.stokes_get_viscosity(ctx, -1, mu)
-    degree = capi.stokes_default_options().schur_degree
     for call in range(2):
         rp = torch.tensor(si.uniform(7000 + call, n_p), dtype=torch.float64, device="cuda")
         ref = torch.empty_like(rp)
@@ -55,7 +64,8 @@ def test_noalloc_schur_matches_context_entry_point(capi, name):
 def test_noalloc_rejects_sizes_beyond_its_array(capi):
     lib = capi.load()
     x = torch.zeros(8, dtype=torch.float64, device="cuda")
-    # 33^3 = 35937 pressure DoFs fit; 34^3 do not
-    assert lib.stokes_schur_inverse_noalloc(33, x.data_ptr(), x.data_ptr(), x.data_ptr(), 5, None) == capi.STOKES_EINVAL
-    assert lib.stokes_schur_inverse_noalloc(0, x.data_ptr(), x.data_ptr(), x.data_ptr(), 5, None) == capi.STOKES_EINVAL
+    # 33^3 = 35937 pressure DoFs fit; 34^3 do not; sizes whose (n + 1)^3 overflows are refused too
+    for n in (33, 0, -1, 2 ** 31 - 1):
+        assert lib.stokes_schur_inverse_noalloc(n, x.data_ptr(), x.data_ptr(), x.data_ptr(), 5, None) == capi.STOKES_EINVAL
+    assert lib.stokes_schur_inverse_noalloc(4, x.data_ptr(), x.data_ptr(), x.data_ptr(), -1, None) == capi.STOKES_EINVAL
     assert lib.stokes_schur_inverse_noalloc(4, None, x.data_ptr(), x.data_ptr(), 5, None) == capi.STOKES_EINVAL
