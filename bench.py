@@ -505,7 +505,8 @@ def run_ours(args):
 
 
 VMULT_KERNELS = {0: "k_cell_atomic (one thread per cell, FP32 pipes, atomic scatter)",
-                 1: "k_brick + k_planes (brick-tiled, deterministic)"}
+                 1: "k_brick + k_planes (brick-tiled, deterministic)",
+                 2: "k_cell_tc (cell products on the tensor cores, tcgen05 kind::f16, shared-memory node tile)"}
 
 
 def solution_difference(x, ref, n_u):

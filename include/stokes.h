@@ -62,7 +62,7 @@ typedef enum {
     STOKES_ECUDA = 3,           /* a CUDA runtime call or kernel launch failed */
     STOKES_NOT_CONVERGED = 4,   /* a solve ended with its true residual above rtol */
     STOKES_BREAKDOWN = 5,       /* NaN/Inf or a zero Krylov norm in stokes_solve */
-    STOKES_TIMEOUT = 6,         /* reserved: a bounded device wait gave up */
+    STOKES_TIMEOUT = 6,         /* a bounded wait inside a kernel gave up (options.wait_limit_s) */
     STOKES_EMESH = 7            /* unsupported mesh description */
 } stokes_status;
 
@@ -112,8 +112,12 @@ typedef struct {
                                    run in native FP64, which is faster for them. Both match the FP64
                                    oracle to 1e-12. */
     int vmult_kernel;           /* level operator of the V-cycle: 0 = one thread per cell with atomic adds
-                                   and a separate epilogue pass (default, fastest); 1 = brick-tiled,
-                                   atomic-free and deterministic, epilogue fused */
+                                   and a separate epilogue pass (default); 1 = brick-tiled, atomic-free
+                                   and deterministic, epilogue fused; 2 = FP32 levels: the brick-tiled
+                                   scatter of 1 with the cell products on the tensor cores (A_cell =
+                                   mu_c h A_hat with 5400 A_hat exact in f16; each cell's values scaled
+                                   by a power of two and split into two f16 terms, 22 significant bits;
+                                   f32 accumulation), FP64 levels as 0 */
     int graphs;                 /* 1 = capture the V-cycle's level recursion once per precision as a CUDA
                                    graph and replay it on a library stream ordered with the caller's
                                    stream by events (default); 0 = launch kernel by kernel. The first
@@ -145,6 +149,11 @@ typedef struct {
                                    0 = the same two projections in three passes. Same Krylov space; the preconditioner
                                    receives the once-projected vector. GMRES (outer_solver 2) and the
                                    native FP64 basis always take three passes. */
+    double wait_limit_s;        /* bound, in seconds of the GPU's global timer, of every wait inside the
+                                   library's kernels (the tensor-core operator's wait for its MMAs; 1.0).
+                                   A wait that runs out records STOKES_TIMEOUT in the context's device
+                                   status word (see stokes_device_status) and its kernel leaves, with
+                                   undefined output; 0 gives up at once (exercises that path). */
 } stokes_options;
 
 typedef struct {
@@ -364,6 +373,12 @@ stokes_status stokes_precondition(stokes_ctx* ctx, int vcycle_prec, const double
  * Note: the paper's smoother degree is 4; a tuned degree trades smoothing work per V-cycle against
  * the outer iteration count. */
 stokes_status stokes_autotune(stokes_ctx* ctx, int what, void* stream, int* block_out, int* degree_out);
+
+/* Synchronise `stream`, then read and clear the context's device status word: TIMEOUT if a
+ * bounded wait inside one of the library's kernels gave up since the last check (the output of
+ * that call is undefined; the context stays usable), OK otherwise. stokes_solve checks the word
+ * itself before it returns. No counterpart in the paper. */
+stokes_status stokes_device_status(stokes_ctx* ctx, void* stream);
 
 /* ---- allocation-free entry point (no counterpart in the paper) ---- */
 

@@ -47,7 +47,8 @@ class stokes_options(C.Structure):
     _fields_ = [("cheb_degree", C.c_int), ("smoothing_range", C.c_double), ("eig_safety", C.c_double),
                 ("lanczos_steps", C.c_int), ("schur_degree", C.c_int), ("restart", C.c_int),
                 ("outer_arith", C.c_int), ("vmult_kernel", C.c_int), ("graphs", C.c_int), ("precond_kind", C.c_int),
-                ("outer_solver", C.c_int), ("idr_s", C.c_int), ("gram_schmidt", C.c_int)]
+                ("outer_solver", C.c_int), ("idr_s", C.c_int), ("gram_schmidt", C.c_int),
+                ("wait_limit_s", C.c_double)]
 
 
 class stokes_solve_info(C.Structure):
@@ -87,6 +88,7 @@ _SIGS = {
     "stokes_schur_inverse": (C.c_int, [_P, _P, _P, _P]),
     "stokes_precondition": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "stokes_schur_inverse_noalloc": (C.c_int, [C.c_int, _P, _P, _P, C.c_int, _P]),
+    "stokes_device_status": (C.c_int, [_P, _P]),
     "stokes_autotune": (C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "stokes_profile": (C.c_int, [C.c_int]),
     "stokes_profile_read": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int]),
@@ -392,6 +394,12 @@ def stokes_schur_inverse(ctx, rp, zp, stream=None):
 def stokes_precondition(ctx, vcycle_prec, r, z, stream=None):
     _check(load().stokes_precondition(ctx.handle, vcycle_prec, _ptr(r), _ptr(z), _stream(stream)),
            "stokes_precondition")
+
+
+def stokes_device_status(ctx, stream=None):
+    """Synchronise the stream, read and clear the context's device status word (raises
+    StokesError with STOKES_TIMEOUT if a bounded wait inside a kernel gave up)."""
+    _check(load().stokes_device_status(ctx.handle, _stream(stream)), "stokes_device_status")
 
 
 def stokes_schur_inverse_noalloc(n, mu, rp, zp, degree=5, stream=None):

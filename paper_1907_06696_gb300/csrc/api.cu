@@ -213,6 +213,11 @@ struct stokes_ctx {
            *idr_t = nullptr, *idr_tmp = nullptr, *idr_c = nullptr;
     cudaStream_t idr_stream = nullptr;
     double* mr[11] = {};   // MINRES work vectors
+    // tensor-core level operator: f16 table of 5400 A_hat; device status word (bit 0: a bounded
+    // wait inside a kernel gave up), checked by stokes_device_status and at the end of a solve
+    void* tc_table = nullptr;
+    unsigned* dev_status = nullptr;
+    TcArgs tc{};
 };
 
 namespace {
@@ -270,14 +275,15 @@ double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& 
     return 0.5 * (lo + hi);
 }
 
-// Level-operator selector for launch_level_op: 1 = brick kernel, else the cell kernel's block size.
-int level_kernel(const stokes_ctx* c) { return c->opt.vmult_kernel == 1 ? 1 : c->cell_block; }
+// Level-operator selector for launch_level_op: 1 = brick kernel, 2 = tensor-core brick kernel
+// (FP32 levels), else the cell kernel's block size.
+int level_kernel(const stokes_ctx* c) { return c->opt.vmult_kernel == 1 || c->opt.vmult_kernel == 2 ? c->opt.vmult_kernel : c->cell_block; }
 
 template <typename T>
 stokes_status vmult_level(stokes_ctx* c, int l, const T* src, T* dst, cudaStream_t s) {
     Level& L = c->lev[l];
     CK(launch_level_op<T>(level_kernel(c), L.g, L.planes, EPI_PLAIN, vecs<T>(L).mu, src, dst, nullptr, nullptr,
-                          nullptr, 0.0, 0.0, slots<T>(L), vecs<T>(L).acc, s));
+                          nullptr, 0.0, 0.0, slots<T>(L), vecs<T>(L).acc, s, &c->tc));
     return STOKES_OK;
 }
 
@@ -287,7 +293,7 @@ stokes_status cheb_step(stokes_ctx* c, int l, const T* b, T* x, double c1, doubl
     Level& L = c->lev[l];
     LevelVecs<T>& v = vecs<T>(L);
     CK(launch_level_op<T>(level_kernel(c), L.g, L.planes, EPI_CHEB, v.mu, x, nullptr, b, v.dinv, v.d, c1, c2,
-                          slots<T>(L), v.acc, s));
+                          slots<T>(L), v.acc, s, &c->tc));
     return STOKES_OK;
 }
 
@@ -330,7 +336,7 @@ stokes_status vcycle_level(stokes_ctx* c, int l, cudaStream_t s) {
     LevelVecs<T>& vc = vecs<T>(c->lev[l - 1]);
     CKS(smooth<T>(c, l, v.b, v.x, true, s));
     CK(launch_level_op<T>(level_kernel(c), L.g, L.planes, EPI_RESID, v.mu, v.x, v.r, v.b, nullptr, nullptr, 0.0,
-                          0.0, slots<T>(L), v.acc, s));
+                          0.0, slots<T>(L), v.acc, s, &c->tc));
     CK(launch_restrict<T>(L.g, v.r, vc.b, s));
     CKS(vcycle_level<T>(c, l - 1, s));
     CK(launch_prolongate<T>(L.g, vc.x, v.x, true, s));
@@ -1159,10 +1165,45 @@ stokes_status minres_solve(stokes_ctx* c, int prec, const double* b, double* x, 
     return STOKES_OK;
 }
 
+// The context's device status word, and for vmult_kernel 2 the tensor-core operator's f16 table
+// (5400 A_hat from the library's own sum-factorised cell operator, checked to be exact in f16).
+stokes_status setup_device_status(stokes_ctx* c, cudaStream_t s) {
+    CKS(dalloc(c, &c->dev_status, 1));
+    CK(cudaMemsetAsync(c->dev_status, 0, sizeof(unsigned), s));
+    c->tc.status = c->dev_status;
+    c->tc.wait_ns = (unsigned long long)(c->opt.wait_limit_s * 1e9);
+    if (c->opt.vmult_kernel != 2) return STOKES_OK;
+    CK(tc_configure());
+    unsigned char* table = nullptr;
+    int* flag = nullptr;
+    CKS(dalloc(c, &table, tc_table_bytes()));
+    CKS(dalloc(c, &flag, 1));
+    CK(tc_build_table(table, flag, s));
+    int hflag = 0;
+    CK(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hflag != 0) return fail(STOKES_ECUDA, "5400 A_hat is not exact in f16 (tensor-core operator)");
+    c->tc_table = table;
+    c->tc.table = table;
+    return STOKES_OK;
+}
+
+// Read and clear the device status word (synchronises s): TIMEOUT if a bounded device wait gave up.
+stokes_status take_device_status(stokes_ctx* c, cudaStream_t s) {
+    if (!c->dev_status) return STOKES_OK;
+    unsigned w = 0;
+    CK(cudaMemcpyAsync(&w, c->dev_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemsetAsync(c->dev_status, 0, sizeof(unsigned), s));
+    CK(cudaStreamSynchronize(s));
+    if (w != 0) return fail(STOKES_TIMEOUT, "a bounded wait inside a kernel gave up (wait_limit_s)");
+    return STOKES_OK;
+}
+
 stokes_status validate_options(const stokes_options& o) {
     if (o.cheb_degree < 1 || o.smoothing_range <= 1.0 || o.eig_safety <= 0.0 || o.lanczos_steps < 1 ||
         o.schur_degree < 0 || o.restart < 1 || o.restart > 500 || (o.outer_arith != 0 && o.outer_arith != 1) ||
-        (o.vmult_kernel != 0 && o.vmult_kernel != 1) || (o.graphs != 0 && o.graphs != 1) ||
+        o.vmult_kernel < 0 || o.vmult_kernel > 2 || (o.graphs != 0 && o.graphs != 1) || !(o.wait_limit_s >= 0.0) ||
+        o.wait_limit_s > 1e6 ||
         (o.precond_kind != 0 && o.precond_kind != 1) || o.outer_solver < 0 || o.outer_solver > 3 || (o.gram_schmidt != 0 && o.gram_schmidt != 1) ||
         (o.outer_solver == 3 && o.precond_kind != 1) ||
         o.idr_s < 1 || o.idr_s > 8)
@@ -1261,6 +1302,7 @@ stokes_status setup_impl(const stokes_mesh* mesh, const stokes_mu* mu, const sto
     c->lev.resize(L);
     for (int l = 0; l < L; ++l) c->lev[l].g = make_geom(mesh->n >> (L - 1 - l));
     const LevelGeom& gf = c->lev[L - 1].g;
+    CKS(setup_device_status(c, s));
     // ---- per-level storage
     for (int l = 0; l < L; ++l) {
         Level& Lv = c->lev[l];
@@ -1670,6 +1712,7 @@ void stokes_default_options(stokes_options* opt) {
     opt->outer_solver = 0;
     opt->idr_s = 2;
     opt->gram_schmidt = 1;
+    opt->wait_limit_s = 1.0;
 }
 
 const char* stokes_strerror(stokes_status s) {
@@ -2000,12 +2043,19 @@ stokes_status stokes_solve(stokes_ctx* c, int vcycle_prec, const double* rhs, do
     stokes_status st = c->opt.outer_solver == 1   ? idr_solve(c, vcycle_prec, b, up, rtol, max_it, info, s)
                        : c->opt.outer_solver == 3 ? minres_solve(c, vcycle_prec, b, up, rtol, max_it, info, s)
                                                   : fgmres(c, vcycle_prec, b, up, rtol, max_it, info, s);
+    const stokes_status dst = take_device_status(c, s);
+    if (dst != STOKES_OK && st != STOKES_ECUDA) st = dst;
     const auto t1 = std::chrono::steady_clock::now();
     if (info) {
         info->seconds = std::chrono::duration<double>(t1 - t0).count();
         info->status = st;
     }
     return st;
+}
+
+stokes_status stokes_device_status(stokes_ctx* c, void* stream) {
+    if (!c) return fail(STOKES_EINVAL, "null context");
+    return take_device_status(c, static_cast<cudaStream_t>(stream));
 }
 
 // Drop the captured V-cycle graphs (after a change of the smoother); they are recaptured on next use.
@@ -2039,7 +2089,7 @@ stokes_status stokes_autotune(stokes_ctx* c, int what, void* stream, int* block_
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     stokes_status st = STOKES_OK;
-    if ((what & 1) && c->opt.vmult_kernel != 1) {
+    if ((what & 1) && c->opt.vmult_kernel == 0) {   // only the cell kernel has a block size
         // threads per block of the cell kernel: the fastest FP32 level operator on the finest level
         float best = 1e30f;
         int best_bs = c->cell_block;
@@ -2088,7 +2138,7 @@ stokes_status stokes_autotune(stokes_ctx* c, int what, void* stream, int* block_
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != STOKES_OK) return st;
-    if (block_out) *block_out = c->opt.vmult_kernel == 1 ? 0 : c->cell_block;
+    if (block_out) *block_out = c->opt.vmult_kernel != 0 ? 0 : c->cell_block;
     if (degree_out) *degree_out = c->opt.cheb_degree;
     return STOKES_OK;
 }

@@ -172,18 +172,28 @@ cudaError_t launch_cell(const BrickArgs<T>& a, T* acc, int bs, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Accumulate A src into acc: the cell kernel, or (FP32 with tc given) the tensor-core kernel.
 template <typename T>
-cudaError_t launch_cell_epi(const BrickArgs<T>& a, int epi, T* acc, size_t n_u, int bs, cudaStream_t s) {
+cudaError_t accumulate(const BrickArgs<T>& a, T* acc, int bs, const TcArgs* tc, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        if (tc) return launch_cell_tc(a, acc, *tc, s);
+    }
+    return launch_cell<T>(a, acc, bs, s);
+}
+
+template <typename T>
+cudaError_t launch_cell_epi(const BrickArgs<T>& a, int epi, T* acc, size_t n_u, int bs, cudaStream_t s,
+                            const TcArgs* tc = nullptr) {
     if (epi == EPI_PLAIN) {
         // dst = A src: accumulate straight into the zeroed dst, identity rows afterwards
         cudaError_t e = cudaMemsetAsync(a.dst, 0, n_u * sizeof(T), s);
         if (e != cudaSuccess) return e;
-        e = launch_cell<T>(a, a.dst, bs, s);
+        e = accumulate<T>(a, a.dst, bs, tc, s);
         if (e != cudaSuccess) return e;
         LevelGeom g = make_geom(a.n);
         return launch_copy_boundary<T>(g, a.src, a.dst, s);
     }
-    cudaError_t e = launch_cell<T>(a, acc, bs, s);
+    cudaError_t e = accumulate<T>(a, acc, bs, tc, s);
     if (e != cudaSuccess) return e;
     const size_t per = sizeof(T) == 4 ? 4 : 2;
     const size_t b = (n_u / per + 255) / 256;
@@ -239,7 +249,7 @@ cudaError_t brick_configure() {
 template <typename T>
 cudaError_t launch_level_op(int kernel, const LevelGeom& g, const PlaneLayout& L, int epi, const T* mu, const T* src,
                             T* dst, const T* b, const T* dinv, T* d, double c1, double c2, T* slots, T* acc,
-                            cudaStream_t s) {
+                            cudaStream_t s, const TcArgs* tc) {
     BrickArgs<T> a;
     a.n = g.n;
     a.M = g.M;
@@ -255,6 +265,14 @@ cudaError_t launch_level_op(int kernel, const LevelGeom& g, const PlaneLayout& L
     a.c2 = T(c2);
     a.slots = slots;
     a.L = L;
+    if (kernel == 2) {
+        if constexpr (sizeof(T) == 4) {
+            if (!tc || !tc->table || !tc->status) return cudaErrorInvalidValue;
+            return launch_cell_epi<T>(a, epi, acc, g.n_u, 128, s, tc);
+        } else {
+            kernel = 128;   // no FP64 tensor-core path
+        }
+    }
     if (kernel == 0 || kernel == 64 || kernel == 128 || kernel == 256)
         return launch_cell_epi<T>(a, epi, acc, g.n_u, kernel == 0 ? 128 : kernel, s);
     switch (epi) {
@@ -267,9 +285,9 @@ cudaError_t launch_level_op(int kernel, const LevelGeom& g, const PlaneLayout& L
 
 template cudaError_t launch_level_op<float>(int, const LevelGeom&, const PlaneLayout&, int, const float*,
                                             const float*, float*, const float*, const float*, float*, double, double,
-                                            float*, float*, cudaStream_t);
+                                            float*, float*, cudaStream_t, const TcArgs*);
 template cudaError_t launch_level_op<double>(int, const LevelGeom&, const PlaneLayout&, int, const double*,
                                              const double*, double*, const double*, const double*, double*, double,
-                                             double, double*, double*, cudaStream_t);
+                                             double, double*, double*, cudaStream_t, const TcArgs*);
 
 }  // namespace stk

@@ -345,15 +345,33 @@ inline size_t plane_threads(const PlaneLayout& L) {
 PlaneLayout brick_layout(int n);
 // Shared-memory opt-in of every brick kernel instantiation (call once before any launch or capture).
 cudaError_t brick_configure();
+// Tensor-core level operator (brick_tc.cu): the f16 table of 5400 A_hat in the layout its
+// kernel reads (tc_table_bytes() bytes, built once by tc_build_table), a device status word
+// (bit 0: a bounded wait for the MMAs gave up) and that wait's limit in nanoseconds.
+struct TcArgs {
+    const void* table;
+    unsigned* status;
+    unsigned long long wait_ns;
+};
+cudaError_t tc_configure();
+size_t tc_table_bytes();
+// flag (device int) != 0 afterwards if an entry of 5400 A_hat is not an integer f16 holds exactly.
+cudaError_t tc_build_table(void* table, int* flag, cudaStream_t s);
+// acc += A src on the nodes that are not on the domain boundary (acc zero there on entry, as for
+// the cell kernel); the epilogue kernels of launch_level_op consume it.
+cudaError_t launch_cell_tc(const BrickArgs<float>& a, float* acc, const TcArgs& t, cudaStream_t s);
+
 // A x with an epilogue (EPI_PLAIN: dst = A x; EPI_RESID: dst = b - A x;
 // EPI_CHEB: d = c1 d + c2 dinv (b - A x), src += d in place).
 // kernel 0, 64, 128, 256: one thread per cell (blocks of 128, 64, 128, 256 threads) with atomic
 //           adds into acc (n_u entries, zero on entry and on return) and a consumer kernel for the
 //           epilogue;
-// kernel 1: the brick-tiled kernel with the epilogue fused (slots: brick_layout(n).total entries).
+// kernel 1: the brick-tiled kernel with the epilogue fused (slots: brick_layout(n).total entries);
+// kernel 2: FP32: the cell products on the tensor cores, accumulated like kernel 0 (tc must be
+//           given); FP64: kernel 128.
 template <typename T>
 cudaError_t launch_level_op(int kernel, const LevelGeom& g, const PlaneLayout& L, int epi, const T* mu, const T* src,
                             T* dst, const T* b, const T* dinv, T* d, double c1, double c2, T* slots, T* acc,
-                            cudaStream_t s);
+                            cudaStream_t s, const TcArgs* tc = nullptr);
 
 }  // namespace stk

@@ -73,7 +73,8 @@ _ctx_cache = {}
 
 def gpu_ctx(capi, name, kernel=0):
     """Context of a named problem; kernel selects the V-cycle level operator
-    (0 = cell-parallel with atomic adds, 1 = brick-tiled deterministic)."""
+    (0 = cell-parallel with atomic adds, 1 = brick-tiled deterministic, 2 = brick-tiled with the
+    FP32 cell products on the tensor cores)."""
     key = (name, kernel)
     if key not in _ctx_cache:
         p = oracle_problem(name)[0]
@@ -129,7 +130,7 @@ def test_inverse_diagonal_and_lambda(capi, name):
 
 
 # ----------------------------------------------------------------- operators
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 @pytest.mark.parametrize("name", ["cube8", "n12", "cube16", "n24"])
 def test_vmult_A_all_levels(capi, name, kernel):
     p, m, mus, G, ops, F = oracle_problem(name)
@@ -194,7 +195,7 @@ def test_transfers(capi, name):
             assert_close(host(outc), ref_r, tol)
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 @pytest.mark.parametrize("name", ["cube8", "n12"])
 def test_chebyshev_smoother(capi, name, kernel):
     p, m, mus, G, ops, F = oracle_problem(name)
@@ -225,7 +226,7 @@ def test_coarse_solve(capi, name):
         assert_close(host(x), ref, tol)
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 @pytest.mark.parametrize("name", ["cube8", "n12", "cube16", "n24", "n10c5", "n12c6"])
 def test_vcycle(capi, name, kernel):
     p, m, mus, G, ops, F = oracle_problem(name)
@@ -257,10 +258,11 @@ def test_schur_and_block_preconditioner(capi, name):
     assert_close(host(z), ref, F32_CYCLE_TOL)
 
 
+@pytest.mark.parametrize("kernel", [0, 2])
 @pytest.mark.parametrize("name", ["cube8", "n12", "n10c5"])
-def test_solve_fp64_and_fp32_vcycle(capi, name):
+def test_solve_fp64_and_fp32_vcycle(capi, name, kernel):
     p, m, mus, G, ops, F = oracle_problem(name)
-    ctx = gpu_ctx(capi, name)
+    ctx = gpu_ctx(capi, name, kernel)
     b = np.concatenate([F, np.zeros(m.n_p)])
     Pc = krylov.StokesPreconditioner(ops, G)
     xo, its_o, _ = krylov.fgmres(ops.apply_stokes, Pc.apply, b, rtol=1e-8)
@@ -329,12 +331,41 @@ def test_status_follows_true_residual_at_max_it(capi, solver):
 
 
 # ----------------------------------------------------------------- edge cases
-@pytest.mark.parametrize("kernel", [0, 1])
+def test_tensor_core_operator_wait_timeout(capi):
+    """A bounded device wait that runs out: with wait_limit_s = 0 the tensor-core operator gives up
+    on its MMAs at once, records STOKES_TIMEOUT in the context's status word (read and cleared by
+    stokes_device_status, and by stokes_solve) and leaves; the context and the device stay usable
+    and the next call with a normal limit is correct."""
+    p, m, mus, G, ops, F = oracle_problem("n12")
+    opt = capi.stokes_default_options()
+    opt.vmult_kernel = 2
+    opt.wait_limit_s = 0.0
+    ctx = capi.stokes_setup_problem(p, options=opt)
+    x = si.uniform(310, m.n_u)
+    src = dev(x, torch.float32)
+    dst = torch.empty_like(src)
+    capi.stokes_vmult(ctx, -1, capi.BLOCK_A, capi.STOKES_FP32, src, dst)
+    with pytest.raises(capi.StokesError) as e:
+        capi.stokes_device_status(ctx)
+    assert e.value.status == capi.STOKES_TIMEOUT
+    capi.stokes_device_status(ctx)          # cleared
+    up = torch.zeros(m.n_u + m.n_p, dtype=torch.float64, device="cuda")
+    info = capi.stokes_solve(ctx, capi.STOKES_FP32, None, up, rtol=1e-8, max_it=20, check=False)
+    assert info.status == capi.STOKES_TIMEOUT
+    ctx.close()
+    ok = gpu_ctx(capi, "n12", 2)
+    capi.stokes_vmult(ok, -1, capi.BLOCK_A, capi.STOKES_FP32, src, dst)
+    capi.stokes_device_status(ok)
+    assert_close(host(dst), G.levels[-1].ops.apply_A(x), F32_TOL)
+
+
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 @pytest.mark.parametrize("prec", [0, 1])
 def test_graph_replay_matches_kernel_launches(capi, prec, kernel):
     """The captured V-cycle graph runs the same kernels in the same order, over two replays with
-    different right-hand sides: bitwise equal output with the deterministic brick operator; with
-    the atomic operator (summation order varies from run to run) equal to rounding."""
+    different right-hand sides: bitwise equal output with the deterministic brick operator (1); with
+    the atomic operators (0; 2, whose shared and global atomic adds vary their order from run to
+    run) equal to rounding."""
     p = oracle_problem("n12")[0]
     outs = []
     for graphs in (0, 1):
@@ -485,6 +516,17 @@ def test_full_size_vmult_sampled_rows(capi, name):
         got = host(dst)[rows]
         assert np.abs(got - ref).max() <= tol * 10 * np.abs(ref).max(), (prec, np.abs(got - ref).max())
         del src, dst
+    # the tensor-core FP32 operator (vmult_kernel 2), launched as the benchmark launches it
+    opt = capi.stokes_default_options()
+    opt.vmult_kernel = 2
+    tctx = capi.stokes_setup_problem(p, options=opt)
+    src = dev(x, torch.float32)
+    dst = torch.empty_like(src)
+    capi.stokes_vmult(tctx, -1, capi.BLOCK_A, capi.STOKES_FP32, src, dst)
+    capi.stokes_device_status(tctx)
+    got = host(dst)[rows]
+    assert np.abs(got - ref).max() <= F32_TOL * 10 * np.abs(ref).max(), np.abs(got - ref).max()
+    tctx.close()
 
 
 _full_cache = {}
