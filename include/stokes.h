@@ -417,6 +417,11 @@ stokes_status stokes_profile(int enable);
 /* Milliseconds and launches accumulated for class `cls` (synchronises the device);
  * reset = 1 clears all classes afterwards. */
 stokes_status stokes_profile_read(int cls, double* ms, long long* launches, int reset);
+/* Test hook: from now on the library's device allocations fail with ENOMEM once they would take
+ * more than `bytes` in total (freed bytes are not counted back); bytes < 0 removes the limit.
+ * Exercises the allocation-failure paths of set-up and solve (a failed set-up frees what it had
+ * allocated). Process-wide, for single-threaded use. */
+stokes_status stokes_debug_alloc_limit(long long bytes);
 /* Number of kernel launches the library has issued since it was loaded. */
 long long stokes_launch_count(void);
 /* FP32 and FP64 FMA throughput of the current device in TFLOP/s (eight independent FMA

@@ -89,6 +89,7 @@ _SIGS = {
     "stokes_precondition": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "stokes_schur_inverse_noalloc": (C.c_int, [C.c_int, _P, _P, _P, C.c_int, _P]),
     "stokes_device_status": (C.c_int, [_P, _P]),
+    "stokes_debug_alloc_limit": (C.c_int, [C.c_longlong]),
     "stokes_autotune": (C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "stokes_profile": (C.c_int, [C.c_int]),
     "stokes_profile_read": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int]),

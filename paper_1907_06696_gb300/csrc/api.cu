@@ -222,8 +222,17 @@ struct stokes_ctx {
 
 namespace {
 
+// Test hook (stokes_debug_alloc_limit): bytes the library may still allocate on the device; < 0 =
+// no limit.
+long long g_alloc_left = -1;
+
 template <typename T>
 stokes_status dalloc(stokes_ctx* c, T** p, size_t count) {
+    const size_t bytes = count * sizeof(T) > 0 ? count * sizeof(T) : 16;
+    if (g_alloc_left >= 0) {
+        if ((long long)bytes > g_alloc_left) return fail(STOKES_ENOMEM, "device allocation limit reached (test hook)");
+        g_alloc_left -= (long long)bytes;
+    }
     void* q = nullptr;
     cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
     if (e != cudaSuccess) return fail(STOKES_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
@@ -1165,6 +1174,32 @@ stokes_status minres_solve(stokes_ctx* c, int prec, const double* b, double* x, 
     return STOKES_OK;
 }
 
+// Viscosity description (Sections 2.3, 3.2), checked on the host before any device work: kind 0
+// (sinker formula) needs finite sinker centres, 0 < mu_min, mu_max < inf and finite delta, omega,
+// beta; kind 1 needs cells x 27 finite, positive quadrature-point values (the harmonic average
+// and the 1/mu pressure mass need mu > 0).
+stokes_status validate_mu(const stokes_mu* mu, size_t cells) {
+    if (mu->kind == 0) {
+        if (mu->n_sinkers < 0 || (mu->n_sinkers > 0 && !mu->centres)) return fail(STOKES_EINVAL, "bad sinker list");
+        for (int i = 0; i < 3 * mu->n_sinkers; ++i)
+            if (!std::isfinite(mu->centres[i])) return fail(STOKES_EINVAL, "non-finite sinker centre");
+        if (!(mu->mu_min > 0.0) || !(mu->mu_max > 0.0) || !std::isfinite(mu->mu_min) || !std::isfinite(mu->mu_max))
+            return fail(STOKES_EINVAL, "mu_min and mu_max must be finite and positive");
+        if (!std::isfinite(mu->delta) || !std::isfinite(mu->omega) || !std::isfinite(mu->beta) || mu->delta < 0.0 ||
+            mu->omega < 0.0)
+            return fail(STOKES_EINVAL, "delta, omega must be finite and >= 0, beta finite");
+        return STOKES_OK;
+    }
+    if (mu->kind == 1) {
+        if (!mu->mu_q) return fail(STOKES_EINVAL, "mu_q is null");
+        for (size_t i = 0; i < 27 * cells; ++i)
+            if (!(mu->mu_q[i] > 0.0) || !std::isfinite(mu->mu_q[i]))
+                return fail(STOKES_EINVAL, "quadrature-point viscosity must be finite and positive");
+        return STOKES_OK;
+    }
+    return fail(STOKES_EINVAL, "unknown viscosity kind");
+}
+
 // The context's device status word, and for vmult_kernel 2 the tensor-core operator's f16 table
 // (5400 A_hat from the library's own sum-factorised cell operator, checked to be exact in f16).
 stokes_status setup_device_status(stokes_ctx* c, cudaStream_t s) {
@@ -1455,10 +1490,8 @@ stokes_status oct_setup_impl(const stokes_octree* mesh, const stokes_mu* mu, con
     if (opt) c->opt = *opt; else stokes_default_options(&c->opt);
     CKS(validate_options(c->opt));
     const stokes_options& o = c->opt;
-    CK(brick_configure());
-    CK(gs_configure());
     if (mu->kind != 0) return fail(STOKES_EINVAL, "octree meshes take the sinker viscosity (kind 0)");
-    if (mu->n_sinkers < 0 || (mu->n_sinkers > 0 && !mu->centres)) return fail(STOKES_EINVAL, "bad sinker list");
+    CKS(validate_mu(mu, 0));
     c->oct = new (std::nothrow) OctCtx();
     if (!c->oct) return fail(STOKES_ENOMEM, "host allocation failed");
     OctCtx& oc = *c->oct;
@@ -1471,8 +1504,11 @@ stokes_status oct_setup_impl(const stokes_octree* mesh, const stokes_mu* mu, con
     sk.delta = mu->delta;
     sk.omega = mu->omega;
     sk.beta = mu->beta;
+    // host tables first: a malformed or unbalanced leaf set is refused before any device work
     const std::string err = oct_build(leaves, mesh->coarsest_level, sk, oc.host);
     if (!err.empty()) return fail(STOKES_EMESH, "octree: " + err);
+    CK(brick_configure());
+    CK(gs_configure());
     const OctHost& H = oc.host;
     // ---- active space
     OctActiveDev& a = oc.act;
@@ -1766,6 +1802,7 @@ stokes_status stokes_setup(const stokes_mesh* mesh, const stokes_mu* mu, const s
     // 4,000 of them (c <= 6), the same limit as on octree meshes
     if (3 * (2 * coarse - 1) * (2 * coarse - 1) * (2 * coarse - 1) > 4000)
         return fail(STOKES_EMESH, "coarsest level must have at most 6 cells per axis (dense FP64 solve)");
+    CKS(validate_mu(mu, size_t(mesh->n) * mesh->n * mesh->n));
     stokes_ctx* c = new (std::nothrow) stokes_ctx();
     if (!c) return fail(STOKES_ENOMEM, "host allocation failed");
     stokes_status st = setup_impl(mesh, mu, bc, opt, static_cast<cudaStream_t>(stream), c);
@@ -2051,6 +2088,11 @@ stokes_status stokes_solve(stokes_ctx* c, int vcycle_prec, const double* rhs, do
         info->status = st;
     }
     return st;
+}
+
+stokes_status stokes_debug_alloc_limit(long long bytes) {
+    g_alloc_left = bytes < 0 ? -1 : bytes;
+    return STOKES_OK;
 }
 
 stokes_status stokes_device_status(stokes_ctx* c, void* stream) {

@@ -1,9 +1,12 @@
 """GPU parity of the IDR(s) outer solver (option outer_solver = 1, Section 3.4) through the C ABI
-against the oracle's idr_s on the same problems (same shadow space definition): iteration counts
-within 20% (at least 4): IDR(s) is not a minimal-residual method, and its iteration count moves
-with rounding-level changes of the operators, which differ from the oracle's in summation order
-and, through the atomic scatters of the cell kernels, from one run to the next (cube8, s = 2: 35
-in the oracle, 31 to 35 on the GPU),
+against the oracle's idr_s on the same problems (same shadow space definition): FP64-V-cycle
+iteration counts within 10% of the oracle's (at least 3). IDR(s) is not a minimal-residual method,
+and its count moves with rounding-level changes of the operators, which differ from the oracle's
+in summation order and, through the FP64 atomic scatters of the outer operator and the pressure
+mass matrix, from one run to the next (with either level operator). Measured over 8 runs each
+with the atomic (vmult_kernel 0) and the deterministic brick (1) level operators, oracle count in
+brackets: cube8 s = 1: 33-35 [35]; s = 2: 33-35 [34]; s = 4: 31-32 [31]; cube16 s = 2: 102-106
+[104].
 true residuals recomputed by the oracle's operator, solutions equal to the oracle's FGMRES
 solution to the accuracy the tolerance allows."""
 import functools
@@ -70,7 +73,7 @@ def test_idr_solve(capi, name, sdim):
             # of its largest entry (measured 1.03e-5 on cube8, s = 2), FGMRES iterates by ~4e-6
             assert np.abs(x - xf).max() <= 2e-5 * np.abs(xf).max()
             if prec == capi.STOKES_FP64:
-                assert abs(info.iterations - its_o) <= max(4, 0.2 * its_o), (info.iterations, its_o)
+                assert abs(info.iterations - its_o) <= max(3, 0.1 * its_o), (info.iterations, its_o)
     ctx.close()
 
 

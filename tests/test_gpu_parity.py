@@ -330,6 +330,67 @@ def test_status_follows_true_residual_at_max_it(capi, solver):
     ctx.close()
 
 
+def test_allocation_failure_frees_what_it_took(capi):
+    """Device allocations that fail (the stokes_debug_alloc_limit hook) give ENOMEM from set-up and
+    from the first solve (which allocates the Krylov basis); the failed set-up frees what it had
+    taken, and the same calls succeed once the limit is lifted."""
+    p = oracle_problem("cube8")[0]
+    lib = capi.load()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    try:
+        for limit in (0, 1 << 12, 1 << 20):
+            assert lib.stokes_debug_alloc_limit(limit) == capi.STOKES_OK
+            with pytest.raises(capi.StokesError) as e:
+                capi.stokes_setup_problem(p)
+            assert e.value.status == capi.STOKES_ENOMEM
+        lib.stokes_debug_alloc_limit(-1)
+        ctx = capi.stokes_setup_problem(p)
+        lib.stokes_debug_alloc_limit(0)
+        up = torch.zeros(ctx.n_u + ctx.n_p, dtype=torch.float64, device="cuda")
+        with pytest.raises(capi.StokesError) as e:
+            capi.stokes_solve(ctx, capi.STOKES_FP32, None, up, rtol=1e-8, max_it=200)
+        assert e.value.status == capi.STOKES_ENOMEM
+    finally:
+        lib.stokes_debug_alloc_limit(-1)
+    info = capi.stokes_solve(ctx, capi.STOKES_FP32, None, up, rtol=1e-8, max_it=200)
+    assert info.status == capi.STOKES_OK
+    ctx.close()
+    del up
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] >= free0 - (8 << 20)
+
+
+def test_double_float_outer_operator_wide_scale_spread(capi):
+    """The double-float outer operator (float exponent range, ~47-bit significands, the unchecked
+    addition of its hi/lo pairs) against the native FP64 kernel at h = 1/128 with the cell viscosity
+    log-uniform over 1e-12..1e12 and inputs log-uniform over 1e-6..1e6 in magnitude: relative
+    2-norm difference <= 1e-12 on [A B^T; B 0] and on each block."""
+    n, L = 128, 6
+    cells = n ** 3
+    mu_c = 10.0 ** (24.0 * si.uniform01(3300, cells) - 12.0)
+    mu_q = np.repeat(mu_c, 27)
+    outs = []
+    N = si.n_velocity(n) + si.n_pressure(n)
+    mag = 10.0 ** (12.0 * si.uniform01(3301, N) - 6.0)
+    up = dev(si.uniform(3302, N) * mag)
+    for arith in (1, 0):
+        opt = capi.stokes_default_options()
+        opt.outer_arith = arith
+        ctx = capi.stokes_setup(n, L, mu_q=mu_q, options=opt)
+        out = torch.empty_like(up)
+        capi.stokes_vmult(ctx, -1, capi.BLOCK_STOKES, capi.STOKES_FP64, up, out)
+        outs.append(host(out))
+        ctx.close()
+        del out
+        torch.cuda.empty_cache()
+    got, ref = outs
+    n_u = si.n_velocity(n)
+    assert rel(got, ref) <= F64_TOL, rel(got, ref)
+    assert rel(got[:n_u], ref[:n_u]) <= F64_TOL and rel(got[n_u:], ref[n_u:]) <= F64_TOL
+    assert np.all(np.isfinite(got))
+
+
 # ----------------------------------------------------------------- edge cases
 def test_tensor_core_operator_wait_timeout(capi):
     """A bounded device wait that runs out: with wait_limit_s = 0 the tensor-core operator gives up
