@@ -684,60 +684,77 @@ def run_kernels(args):
 
 def run_batch(args):
     """Batched workload: many independent sinker problems of uneven sizes solved together with the
-    FP32 V-cycle (stokes_batch_solve), against the same problems solved one after the other with the
-    FP64 V-cycle."""
+    FP32 V-cycle (stokes_batch_solve) -- one captured V-cycle graph per problem (batch_vcycle 0, the
+    default, timed over the steps) and the V-cycles as one persistent launch per round
+    (batch_vcycle 1) -- against the same problems solved one after the other with the FP32 and with
+    the FP64 V-cycle. batch64s draws the sizes 16^3..24^3 only."""
     import torch
     from paper_1907_06696_gb300 import build as B
     B.build()
     from paper_1907_06696_gb300 import capi
     capi.load()
     import sinker_inputs as si
-    count = int(args.workload[len("batch"):] or 64)
-    probs = si.batch_workload(count)
+    small = args.workload.endswith("s")
+    count = int(args.workload[len("batch"):].rstrip("s") or 64)
+    probs = si.batch_workload(count, sizes=si.BATCH_SIZES_SMALL if small else si.BATCH_SIZES)
     ctxs = [capi.stokes_setup_problem(p) for p in probs]
-    blocks = [capi.stokes_autotune(c, 1)[0] for c in ctxs]     # launch shape per problem size
     ups = [torch.zeros(c.n_u + c.n_p, dtype=torch.float64, device="cuda") for c in ctxs]
     ndof = sum(c.n_u + c.n_p for c in ctxs)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-    def batch():
+    def batch(mode):
+        for c in ctxs:
+            capi.stokes_set_batch_vcycle(c, mode)
         for u in ups:
             u.zero_()
         return capi.stokes_batch_solve(ctxs, capi.STOKES_FP32, ups, rtol=RTOL, max_it=3000)
 
+    # the default: one captured V-cycle graph per problem on its own stream
     for _ in range(max(args.warmup, 1)):
-        batch()
+        batch(0)
     torch.cuda.synchronize()
     clk, clk_path = clocks_start(torch.cuda.current_device())
     l0 = capi.stokes_launch_count()
     e0.record()
     for _ in range(args.steps):
-        infos = batch()
+        infos = batch(0)
     e1.record()
     torch.cuda.synchronize()
     launches = capi.stokes_launch_count() - l0
     clocks = clocks_stop(clk, clk_path)
     ms = e0.elapsed_time(e1) / args.steps
-    # reference: the same problems solved one after the other with the FP64 V-cycle
+    # the same batch with the persistent batched V-cycle kernel (batch_vcycle 1)
+    batch(1)
+    torch.cuda.synchronize()
     e0.record()
-    seq_its = []
-    for c, u in zip(ctxs, ups):
-        u.zero_()
-        seq_its.append(capi.stokes_solve(c, capi.STOKES_FP64, None, u, rtol=RTOL, max_it=3000).iterations)
+    kinfos = batch(1)
     e1.record()
     torch.cuda.synchronize()
-    seq_ms = e0.elapsed_time(e1)
+    kernel_ms = e0.elapsed_time(e1)
+    # the same problems one after the other, FP32 and FP64 V-cycle
+    seq = {}
+    for tag, prec in (("fp32", capi.STOKES_FP32), ("fp64", capi.STOKES_FP64)):
+        its = []
+        e0.record()
+        for c, u in zip(ctxs, ups):
+            u.zero_()
+            its.append(capi.stokes_solve(c, prec, None, u, rtol=RTOL, max_it=3000).iterations)
+        e1.record()
+        torch.cuda.synchronize()
+        seq[tag] = (e0.elapsed_time(e1), its)
     line = {"metric": METRIC, "value": ndof / (ms / 1e3) / 1e9, "unit": "GDoF/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64 outer + f32 V-cycle", "data": "synthetic",
+            "vs_baseline": None, "dtype": "df64 outer (FP64 true residual) + f32 V-cycle", "data": "synthetic",
             "config": {"workload": args.workload, "problems": count,
-                       "sizes": sorted(set(p.n for p in probs)), "total_dofs": ndof, "rtol": RTOL,
-                       "cell_blocks": {str(n): sorted(set(b for p, b in zip(probs, blocks) if p.n == n))
-                                       for n in sorted(set(p.n for p in probs))}},
-            "batch": {"fp32_batch_s": ms / 1e3, "iterations": [i.iterations for i in infos],
+                       "sizes": sorted(set(p.n for p in probs)), "total_dofs": ndof, "rtol": RTOL},
+            "batch": {"fp32_batch_graphs_s": ms / 1e3, "iterations": [i.iterations for i in infos],
                       "max_true_rel_residual": max(i.rel_residual_true for i in infos),
-                      "fp64_sequential_s": seq_ms / 1e3, "fp64_sequential_iterations": seq_its,
-                      "speedup": seq_ms / ms},
+                      "fp32_batch_kernel_s": kernel_ms / 1e3, "kernel_iterations": [i.iterations for i in kinfos],
+                      "fp32_sequential_s": seq["fp32"][0] / 1e3, "fp32_sequential_iterations": seq["fp32"][1],
+                      "fp64_sequential_s": seq["fp64"][0] / 1e3, "fp64_sequential_iterations": seq["fp64"][1],
+                      "batching_gain_vs_sequential_fp32": seq["fp32"][0] / ms,
+                      "kernel_gain_vs_graphs": ms / kernel_ms,
+                      "speedup_vs_sequential_fp64": seq["fp64"][0] / ms},
             "gpu_launches": int(launches), "clocks": clocks}
     for c in ctxs:
         c.close()

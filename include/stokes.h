@@ -154,6 +154,14 @@ typedef struct {
                                    A wait that runs out records STOKES_TIMEOUT in the context's device
                                    status word (see stokes_device_status) and its kernel leaves, with
                                    undefined output; 0 gives up at once (exercises that path). */
+    int batch_vcycle;           /* stokes_batch_solve with FP32 V-cycles inside FGMRES: 0 = one captured
+                                   V-cycle graph per problem, replayed on the problem's own stream
+                                   (default; measured faster); 1 = in a round where at least eight
+                                   problems reach their preconditioner, their V-cycles run as one
+                                   persistent cooperative launch (work queue of (problem, tile) items
+                                   per phase, grid barriers bounded by wait_limit_s, the other problems
+                                   masked out), other rounds as 0. Read from the first context of the
+                                   batch. */
 } stokes_options;
 
 typedef struct {
@@ -373,6 +381,11 @@ stokes_status stokes_precondition(stokes_ctx* ctx, int vcycle_prec, const double
  * Note: the paper's smoother degree is 4; a tuned degree trades smoothing work per V-cycle against
  * the outer iteration count. */
 stokes_status stokes_autotune(stokes_ctx* ctx, int what, void* stream, int* block_out, int* degree_out);
+
+/* Change options.batch_vcycle of a context (0 or 1; see stokes_options): how stokes_batch_solve
+ * runs the FP32 V-cycles when this context comes first in the batch. Errors: EINVAL. No counterpart
+ * in the paper. */
+stokes_status stokes_set_batch_vcycle(stokes_ctx* ctx, int mode);
 
 /* Synchronise `stream`, then read and clear the context's device status word: TIMEOUT if a
  * bounded wait inside one of the library's kernels gave up since the last check (the output of

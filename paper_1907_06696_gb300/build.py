@@ -15,8 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libstokes_gb300.so")
-SOURCES = ["ops.cu", "vec.cu", "krylov.cu", "brick.cu", "brick_tc.cu", "outer.cu", "octree.cu", "octree_host.cpp",
-           "api.cu", "noalloc.cu", "probe.cu"]
+SOURCES = ["ops.cu", "vec.cu", "krylov.cu", "brick.cu", "brick_tc.cu", "batch.cu", "outer.cu", "octree.cu",
+           "octree_host.cpp", "api.cu", "noalloc.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC,-ffp-contract=off",
          "-I" + os.path.join(ROOT, "include")]

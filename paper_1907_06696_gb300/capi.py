@@ -48,7 +48,7 @@ class stokes_options(C.Structure):
                 ("lanczos_steps", C.c_int), ("schur_degree", C.c_int), ("restart", C.c_int),
                 ("outer_arith", C.c_int), ("vmult_kernel", C.c_int), ("graphs", C.c_int), ("precond_kind", C.c_int),
                 ("outer_solver", C.c_int), ("idr_s", C.c_int), ("gram_schmidt", C.c_int),
-                ("wait_limit_s", C.c_double)]
+                ("wait_limit_s", C.c_double), ("batch_vcycle", C.c_int)]
 
 
 class stokes_solve_info(C.Structure):
@@ -90,6 +90,7 @@ _SIGS = {
     "stokes_schur_inverse_noalloc": (C.c_int, [C.c_int, _P, _P, _P, C.c_int, _P]),
     "stokes_device_status": (C.c_int, [_P, _P]),
     "stokes_debug_alloc_limit": (C.c_int, [C.c_longlong]),
+    "stokes_set_batch_vcycle": (C.c_int, [_P, C.c_int]),
     "stokes_autotune": (C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "stokes_profile": (C.c_int, [C.c_int]),
     "stokes_profile_read": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int]),
@@ -395,6 +396,12 @@ def stokes_schur_inverse(ctx, rp, zp, stream=None):
 def stokes_precondition(ctx, vcycle_prec, r, z, stream=None):
     _check(load().stokes_precondition(ctx.handle, vcycle_prec, _ptr(r), _ptr(z), _stream(stream)),
            "stokes_precondition")
+
+
+def stokes_set_batch_vcycle(ctx, mode):
+    """How stokes_batch_solve runs the FP32 V-cycles when ctx comes first: 1 = one persistent launch
+    for all problems per round, 0 = one captured graph per problem."""
+    _check(load().stokes_set_batch_vcycle(ctx.handle, int(mode)), "stokes_set_batch_vcycle")
 
 
 def stokes_device_status(ctx, stream=None):

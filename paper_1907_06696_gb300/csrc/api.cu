@@ -12,6 +12,7 @@
 // each pass one fused multi-dot and one fused multi-axpy, one host
 // synchronisation per iteration.
 #include "../../include/stokes.h"
+#include "batch.cuh"
 #include "brick.cuh"
 #include "internal.cuh"
 #include "octree.cuh"
@@ -557,31 +558,43 @@ stokes_status apply_stokes(stokes_ctx* c, const double* src, double* dst, cudaSt
 }
 
 // z = P^-1 r (eq. stokes_precond).
-stokes_status precondition(stokes_ctx* c, int prec, const double* r, double* z, cudaStream_t s) {
+// Parts of the preconditioner for the batched driver (uniform meshes, FP32 V-cycle): PREC_PRE
+// runs everything up to the right-hand side of the finest FP32 level, PREC_POST everything after
+// the level recursion (which the batched kernel runs for many problems at once); PREC_ALL both
+// with the recursion in between.
+enum PrecPart { PREC_ALL = 0, PREC_PRE = 1, PREC_POST = 2 };
+
+stokes_status precondition(stokes_ctx* c, int prec, const double* r, double* z, cudaStream_t s,
+                           int part = PREC_ALL) {
     if (c->oct) return oct_precondition(c, prec, r, z, s);
     Level& F = c->lev[c->L - 1];
     const size_t nu = F.g.n_u, np = F.g.n_p;
     double* zp = z + nu;
-    CKS(schur_inverse(c, r + nu, zp, s));
-    if (c->opt.precond_kind == 1) {   // P_D: z_p = S_hat^-1 r_p, z_u = A_hat^-1 r_u
-        if (prec == STOKES_FP64) return vcycle<double>(c, r, z, s);
-        CK(launch_cast_d2f(nu, r, c->stage_in, s));
-        CKS(vcycle<float>(c, c->stage_in, c->stage_out, s));
+    const double* rin = c->opt.precond_kind == 1 ? r : c->tu;   // the V-cycle's right-hand side
+    if (part == PREC_POST) {   // the tail of vcycle<float>, then back to FP64
+        CK(cudaMemcpyAsync(c->stage_out, F.v32.x, nu * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        CK(launch_copy_boundary<float>(F.g, c->stage_in, c->stage_out, s));
         CK(launch_cast_f2d(nu, c->stage_out, z, s));
-        CK(launch_copy_boundary<double>(F.g, r, z, s));
+        CK(launch_copy_boundary<double>(F.g, rin, z, s));
         return STOKES_OK;
     }
-    CK(launch_axpby(np, -1.0, zp, 0.0, zp, s));                               // z_p = -S^-1 r_p
-    CK(launch_stokes_blocks(F.g, F.v64.mu, nullptr, zp, c->tu, nullptr, false, true, false, c->opt.outer_arith == 1, s));
-    CK(launch_axpby(nu, 1.0, r, -1.0, c->tu, s));                            // t = r_u - B^T z_p
-    if (prec == STOKES_FP64) {
-        CKS(vcycle<double>(c, c->tu, z, s));
-    } else {
-        CK(launch_cast_d2f(nu, c->tu, c->stage_in, s));
-        CKS(vcycle<float>(c, c->stage_in, c->stage_out, s));
-        CK(launch_cast_f2d(nu, c->stage_out, z, s));
-        CK(launch_copy_boundary<double>(F.g, c->tu, z, s));
+    CKS(schur_inverse(c, r + nu, zp, s));
+    if (c->opt.precond_kind != 1) {
+        CK(launch_axpby(np, -1.0, zp, 0.0, zp, s));                           // z_p = -S^-1 r_p
+        CK(launch_stokes_blocks(F.g, F.v64.mu, nullptr, zp, c->tu, nullptr, false, true, false,
+                                c->opt.outer_arith == 1, s));
+        CK(launch_axpby(nu, 1.0, r, -1.0, c->tu, s));                        // t = r_u - B^T z_p
+    }   // else P_D: z_p = S_hat^-1 r_p, z_u = A_hat^-1 r_u
+    if (prec == STOKES_FP64) return vcycle<double>(c, rin, z, s);
+    CK(launch_cast_d2f(nu, rin, c->stage_in, s));
+    if (part == PREC_PRE) {    // the head of vcycle<float>
+        CK(cudaMemcpyAsync(F.v32.b, c->stage_in, nu * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        CK(launch_zero_boundary<float>(F.g, F.v32.b, s));
+        return STOKES_OK;
     }
+    CKS(vcycle<float>(c, c->stage_in, c->stage_out, s));
+    CK(launch_cast_f2d(nu, c->stage_out, z, s));
+    CK(launch_copy_boundary<double>(F.g, rin, z, s));
     return STOKES_OK;
 }
 
@@ -639,9 +652,30 @@ struct FgmresRun {
     double inv_sqrt_s = 1.0;    // 1 / |u_j| for the preconditioner input u_j / |u_j|
     bool force_cycle = false;   // the final check sent the run back: iterate at least once
     int verify_left = 10;       // such returns left
+    bool batched = false;       // the batched driver runs the FP32 level recursion of P^-1
+    int batch_stage = 0;        // 1: P_ITER stopped before the level recursion (pin, zj kept)
+    const double* pin = nullptr;
+    double* zj = nullptr;
     std::vector<double> H, cs, sn, g, y;
     double& Hij(int i, int jj) { return H[size_t(i) * m + jj]; }
 };
+
+// Batched driver: P_ITER runs the preconditioner up to the finest FP32 right-hand side and stops
+// (batch_stage 1); the driver runs the level recursion of every such problem in one launch; the
+// next enqueue resumes after it.
+stokes_status fgmres_stop_before_levels(FgmresRun& r, const double* pin, double* zj) {
+    CKS(precondition(r.c, r.prec, pin, zj, r.s, PREC_PRE));
+    r.pin = pin;
+    r.zj = zj;
+    r.batch_stage = 1;
+    return STOKES_OK;
+}
+
+stokes_status fgmres_resume_after_levels(FgmresRun& r) {
+    CKS(precondition(r.c, r.prec, r.pin, r.zj, r.s, PREC_POST));
+    r.batch_stage = 0;
+    return STOKES_OK;
+}
 
 stokes_status fgmres_enqueue(FgmresRun& r) {
     stokes_ctx* c = r.c;
@@ -671,9 +705,14 @@ stokes_status fgmres_enqueue(FgmresRun& r) {
                 // relation K z_j = V H e_j holds for the z_j used). Pass A: V^T w with the dot of
                 // row j corrected on the device to v_j . w; pass B: writes the twice-projected
                 // v_j over row j and u_{j+1} = w - V h to row j + 1, with the dots of the record.
-                if (r.next_v) CK(launch_df_store_scaled(N, c->w, 1.0 / r.hn_prev, vj, s));   // V_0
-                CK(launch_df_to_double(N, vj, c->w, s, j == 0 ? 1.0 : r.inv_sqrt_s));
-                CKS(precondition(c, r.prec, c->w, zj, s));
+                if (r.batch_stage == 0) {
+                    if (r.next_v) CK(launch_df_store_scaled(N, c->w, 1.0 / r.hn_prev, vj, s));   // V_0
+                    CK(launch_df_to_double(N, vj, c->w, s, j == 0 ? 1.0 : r.inv_sqrt_s));
+                    if (r.batched) return fgmres_stop_before_levels(r, c->w, zj);
+                    CKS(precondition(c, r.prec, c->w, zj, s));
+                } else {
+                    CKS(fgmres_resume_after_levels(r));
+                }
                 CKS(apply_stokes(c, zj, c->w, s));
                 double* h1d = c->hdev;
                 const double* prev = j > 0 ? c->hdev + size_t(m + 4) * (1 + (j & 1)) : nullptr;
@@ -684,12 +723,16 @@ stokes_status fgmres_enqueue(FgmresRun& r) {
                 return STOKES_OK;
             }
             const bool df = c->opt.outer_arith == 1 && m <= gs_max_k();   // V as double-float pairs (krylov.cu)
-            if (df) {
+            if (r.batch_stage == 1) {
+                CKS(fgmres_resume_after_levels(r));
+            } else if (df) {
                 if (r.next_v) CK(launch_df_store_scaled(N, c->w, 1.0 / r.hn_prev, vj, s));   // V_j = w / |w|
                 CK(launch_df_to_double(N, vj, c->w, s));
+                if (r.batched) return fgmres_stop_before_levels(r, c->w, zj);
                 CKS(precondition(c, r.prec, c->w, zj, s));
             } else {
                 if (r.next_v) CK(launch_axpby(N, 1.0 / r.hn_prev, c->w, 0.0, vj, s));
+                if (r.batched) return fgmres_stop_before_levels(r, vj, zj);
                 CKS(precondition(c, r.prec, vj, zj, s));
             }
             CKS(apply_stokes(c, zj, c->w, s));
@@ -895,6 +938,214 @@ stokes_status fgmres_drive(std::vector<FgmresRun>& runs) {
             if (r.phase != FgmresRun::P_DONE) active = true;
         }
     }
+    return STOKES_OK;
+}
+
+// Device state of the batched V-cycle: the problems' level tables, the phase list and per-phase
+// tile offsets of the work queue (rebuilt each round for the problems that take part), the queue
+// counters, the mask of those problems, the status word; a stream for the launch and events that
+// order it with the problems' streams.
+struct BatchVcycle {
+    std::vector<void*> mem;
+    BatchLaunch bl{};
+    std::vector<BatchProblem> probs;   // host copy (sizes for the tile counts)
+    std::vector<int> levels;
+    int degree = 0, max_phases = 0;
+    int* active_host = nullptr;          // pinned, with the round's phases and tile offsets
+    BatchPhase* phases_host = nullptr;
+    unsigned* prefix_host = nullptr;
+    int* active_dev = nullptr;
+    BatchPhase* phases_dev = nullptr;
+    unsigned* prefix_dev = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev_out = nullptr;
+    std::vector<cudaEvent_t> ev_in;
+    ~BatchVcycle() {
+        for (cudaEvent_t e : ev_in) cudaEventDestroy(e);
+        if (ev_out) cudaEventDestroy(ev_out);
+        if (s) cudaStreamDestroy(s);
+        for (void* h : {static_cast<void*>(active_host), static_cast<void*>(phases_host),
+                        static_cast<void*>(prefix_host)})
+            if (h) cudaFreeHost(h);
+        for (void* p : mem) cudaFree(p);
+    }
+    template <typename T>
+    stokes_status upload(T** dev, const T* host, size_t count) {
+        void* p = nullptr;
+        CK(cudaMalloc(&p, std::max<size_t>(count * sizeof(T), 16)));
+        mem.push_back(p);
+        if (host && count) CK(cudaMemcpy(p, host, count * sizeof(T), cudaMemcpyHostToDevice));
+        *dev = static_cast<T*>(p);
+        return STOKES_OK;
+    }
+};
+
+// Rounds with fewer problems at their preconditioner than this replay each problem's own captured
+// V-cycle graph instead (a launch with few items still pays every grid barrier).
+constexpr int kBatchKernelMinProblems = 8;
+
+// True if the runs can share one batched V-cycle launch: FP32 V-cycles of uniform meshes inside
+// FGMRES, one smoother degree, supported level counts, a device that runs cooperative launches.
+bool batch_vcycle_eligible(const std::vector<FgmresRun>& runs) {
+    if (runs.empty() || runs[0].prec != STOKES_FP32 || runs[0].c->opt.batch_vcycle != 1) return false;
+    const int deg = runs[0].c->opt.cheb_degree;
+    if (deg > kBatchMaxDegree) return false;
+    for (const FgmresRun& r : runs)
+        if (r.c->oct || !r.flexible || r.c->L > kBatchMaxLevels || r.c->opt.cheb_degree != deg) return false;
+    return batch_grid_blocks() > 0;
+}
+
+stokes_status batch_vcycle_setup(BatchVcycle& B, const std::vector<FgmresRun>& runs) {
+    const int P = int(runs.size());
+    const int deg = runs[0].c->opt.cheb_degree;
+    B.degree = deg;
+    B.probs.assign(P, BatchProblem{});
+    B.levels.assign(P, 0);
+    double wait_s = 1e6;
+    for (int p = 0; p < P; ++p) {
+        stokes_ctx* c = runs[p].c;
+        BatchProblem& bp = B.probs[p];
+        bp.L = c->L;
+        bp.nf = c->nf;
+        bp.free_idx = c->free_idx;
+        bp.Ainv = c->Ainv;
+        for (int l = 0; l < c->L; ++l) {
+            const Level& Lv = c->lev[l];
+            BatchLevel& bl = bp.lev[l];
+            bl.n = Lv.g.n;
+            bl.M = Lv.g.M;
+            bl.nodes = Lv.g.nodes;
+            bl.n_u = Lv.g.n_u;
+            bl.h = float(Lv.g.h);
+            bl.mu = Lv.v32.mu;
+            bl.dinv = Lv.v32.dinv;
+            bl.b = Lv.v32.b;
+            bl.x = Lv.v32.x;
+            bl.r = Lv.v32.r;
+            bl.d = Lv.v32.d;
+            bl.acc = Lv.v32.acc;
+            // the coefficients smooth() uses: step 0 (0, 1/theta), then the three-term recurrence
+            const double theta = 0.5 * (Lv.hi + Lv.lo), delta = 0.5 * (Lv.hi - Lv.lo), sigma = theta / delta;
+            double rho = 1.0 / sigma;
+            bl.c1[0] = 0.0f;
+            bl.c2[0] = float(1.0 / theta);
+            for (int k = 1; k < deg; ++k) {
+                const double rho_new = 1.0 / (2.0 * sigma - rho);
+                bl.c1[k] = float(rho_new * rho);
+                bl.c2[k] = float(2.0 * rho_new / delta);
+                rho = rho_new;
+            }
+        }
+        B.levels[p] = c->L;
+        wait_s = std::min(wait_s, c->opt.wait_limit_s);
+    }
+    // every round's phase list (a subset of the problems) is no longer than the full batch's
+    B.max_phases = batch_build_phases(B.levels.data(), P, deg, nullptr, 0);
+    BatchProblem* dprob = nullptr;
+    unsigned* dctr = nullptr;
+    unsigned* dstatus = nullptr;
+    CKS(B.upload(&dprob, B.probs.data(), size_t(P)));
+    CKS(B.upload(&B.phases_dev, static_cast<const BatchPhase*>(nullptr), size_t(B.max_phases)));
+    CKS(B.upload(&B.prefix_dev, static_cast<const unsigned*>(nullptr), size_t(B.max_phases) * (P + 1)));
+    CKS(B.upload(&dctr, static_cast<const unsigned*>(nullptr), size_t(B.max_phases + 2)));
+    CKS(B.upload(&dstatus, static_cast<const unsigned*>(nullptr), 1));
+    CK(cudaMemset(dstatus, 0, sizeof(unsigned)));
+    CKS(B.upload(&B.active_dev, static_cast<const int*>(nullptr), size_t(P)));
+    CK(cudaMallocHost(reinterpret_cast<void**>(&B.active_host), sizeof(int) * P));
+    CK(cudaMallocHost(reinterpret_cast<void**>(&B.phases_host), sizeof(BatchPhase) * B.max_phases));
+    CK(cudaMallocHost(reinterpret_cast<void**>(&B.prefix_host), sizeof(unsigned) * B.max_phases * (P + 1)));
+    CK(cudaStreamCreateWithFlags(&B.s, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&B.ev_out, cudaEventDisableTiming));
+    B.ev_in.resize(P, nullptr);
+    for (cudaEvent_t& e : B.ev_in) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    B.bl = BatchLaunch{dprob, P, B.phases_dev, 0, B.prefix_dev, dctr, B.active_dev, dstatus,
+                       (unsigned long long)(wait_s * 1e9)};
+    return STOKES_OK;
+}
+
+// Phase list and tile offsets of one round for the problems in the mask (pinned host buffers,
+// copied on the batch stream); returns the number of tiles of the largest phase.
+stokes_status batch_vcycle_round(BatchVcycle& B, unsigned* widest) {
+    const int P = int(B.probs.size());
+    std::vector<int> lv;
+    for (int p = 0; p < P; ++p)
+        if (B.active_host[p]) lv.push_back(B.levels[p]);
+    const int nph = batch_build_phases(lv.data(), int(lv.size()), B.degree, B.phases_host, B.max_phases);
+    if (nph > B.max_phases) return fail(STOKES_ECUDA, "batched V-cycle: phase list overflow");
+    *widest = 0;
+    for (int i = 0; i < nph; ++i) {
+        const size_t per_tile = size_t(kBatchThreads) * batch_items_per_thread(B.phases_host[i].op);
+        unsigned t = 0;
+        unsigned* pre = B.prefix_host + size_t(i) * (P + 1);
+        for (int p = 0; p < P; ++p) {
+            pre[p] = t;
+            if (!B.active_host[p]) continue;
+            const size_t tiles = (batch_items(B.probs[p], B.phases_host[i]) + per_tile - 1) / per_tile;
+            if (size_t(t) + tiles > 0xFFFFFFF0u) return fail(STOKES_EINVAL, "batch too large for the work queue");
+            *widest = std::max(*widest, unsigned(tiles));
+            t += unsigned(tiles);
+        }
+        pre[P] = t;
+        *widest = std::max(*widest, t);
+    }
+    B.bl.n_phases = nph;
+    CK(cudaMemcpyAsync(B.active_dev, B.active_host, sizeof(int) * P, cudaMemcpyHostToDevice, B.s));
+    CK(cudaMemcpyAsync(B.phases_dev, B.phases_host, sizeof(BatchPhase) * nph, cudaMemcpyHostToDevice, B.s));
+    CK(cudaMemcpyAsync(B.prefix_dev, B.prefix_host, sizeof(unsigned) * size_t(nph) * (P + 1),
+                       cudaMemcpyHostToDevice, B.s));
+    return STOKES_OK;
+}
+
+// Lock-step FGMRES of all runs. In a round where at least kBatchKernelMinProblems runs reached
+// their preconditioner, one batched V-cycle launch runs all of their level recursions; in other
+// rounds each replays its own captured V-cycle graph on its stream. Returns TIMEOUT if a grid
+// barrier of the batched kernel gave up.
+stokes_status fgmres_drive_batched(std::vector<FgmresRun>& runs, BatchVcycle& B) {
+    const int P = int(runs.size());
+    bool active = true;
+    while (active) {
+        active = false;
+        for (FgmresRun& r : runs)
+            if (r.phase != FgmresRun::P_DONE) CKS(fgmres_enqueue(r));
+        int count = 0;
+        for (int p = 0; p < P; ++p) {
+            B.active_host[p] = runs[p].phase != FgmresRun::P_DONE && runs[p].batch_stage == 1;
+            count += B.active_host[p];
+        }
+        if (count >= kBatchKernelMinProblems) {
+            unsigned widest = 0;
+            CKS(batch_vcycle_round(B, &widest));
+            for (int p = 0; p < P; ++p)
+                if (B.active_host[p]) {
+                    CK(cudaEventRecord(B.ev_in[p], runs[p].s));
+                    CK(cudaStreamWaitEvent(B.s, B.ev_in[p], 0));
+                }
+            CK(launch_batch_vcycle(B.bl, int(widest), B.s));
+            CK(cudaEventRecord(B.ev_out, B.s));
+            for (int p = 0; p < P; ++p)
+                if (B.active_host[p]) {
+                    CK(cudaStreamWaitEvent(runs[p].s, B.ev_out, 0));
+                    CKS(fgmres_enqueue(runs[p]));   // resumes after the level recursion
+                }
+            // the pinned round buffers are rewritten next round: their copies must have run
+            CK(cudaStreamSynchronize(B.s));
+        } else if (count > 0) {
+            for (int p = 0; p < P; ++p)
+                if (B.active_host[p]) {
+                    CKS(run_levels<float>(runs[p].c, runs[p].s));
+                    CKS(fgmres_enqueue(runs[p]));
+                }
+        }
+        for (FgmresRun& r : runs) {
+            if (r.phase == FgmresRun::P_DONE) continue;
+            CK(cudaStreamSynchronize(r.s));
+            CKS(fgmres_complete(r));
+            if (r.phase != FgmresRun::P_DONE) active = true;
+        }
+    }
+    unsigned w = 0;
+    CK(cudaMemcpy(&w, B.bl.status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (w != 0) return fail(STOKES_TIMEOUT, "a grid barrier of the batched V-cycle gave up (wait_limit_s)");
     return STOKES_OK;
 }
 
@@ -1238,6 +1489,7 @@ stokes_status validate_options(const stokes_options& o) {
     if (o.cheb_degree < 1 || o.smoothing_range <= 1.0 || o.eig_safety <= 0.0 || o.lanczos_steps < 1 ||
         o.schur_degree < 0 || o.restart < 1 || o.restart > 500 || (o.outer_arith != 0 && o.outer_arith != 1) ||
         o.vmult_kernel < 0 || o.vmult_kernel > 2 || (o.graphs != 0 && o.graphs != 1) || !(o.wait_limit_s >= 0.0) ||
+        (o.batch_vcycle != 0 && o.batch_vcycle != 1) ||
         o.wait_limit_s > 1e6 ||
         (o.precond_kind != 0 && o.precond_kind != 1) || o.outer_solver < 0 || o.outer_solver > 3 || (o.gram_schmidt != 0 && o.gram_schmidt != 1) ||
         (o.outer_solver == 3 && o.precond_kind != 1) ||
@@ -1749,6 +2001,7 @@ void stokes_default_options(stokes_options* opt) {
     opt->idr_s = 2;
     opt->gram_schmidt = 1;
     opt->wait_limit_s = 1.0;
+    opt->batch_vcycle = 0;
 }
 
 const char* stokes_strerror(stokes_status s) {
@@ -2090,6 +2343,12 @@ stokes_status stokes_solve(stokes_ctx* c, int vcycle_prec, const double* rhs, do
     return st;
 }
 
+stokes_status stokes_set_batch_vcycle(stokes_ctx* c, int mode) {
+    if (!c || (mode != 0 && mode != 1)) return fail(STOKES_EINVAL, "null context or bad mode");
+    c->opt.batch_vcycle = mode;
+    return STOKES_OK;
+}
+
 stokes_status stokes_debug_alloc_limit(long long bytes) {
     g_alloc_left = bytes < 0 ? -1 : bytes;
     return STOKES_OK;
@@ -2227,7 +2486,19 @@ stokes_status stokes_batch_solve(int n_problems, stokes_ctx* const* ctxs, int vc
         }
         st = fgmres_init(runs[i], c, vcycle_prec, b, up_devs[i], rtol, max_it, infos ? &infos[i] : &local[i], s);
     }
-    if (st == STOKES_OK) st = fgmres_drive(runs);
+    if (st == STOKES_OK) {
+        if (batch_vcycle_eligible(runs)) {
+            // one persistent launch per round runs the FP32 V-cycles of all problems
+            BatchVcycle B;
+            st = batch_vcycle_setup(B, runs);
+            for (FgmresRun& r : runs) r.batched = true;
+            if (st == STOKES_OK) st = fgmres_drive_batched(runs, B);
+            if (st == STOKES_TIMEOUT)
+                for (int i = 0; i < n_problems; ++i) (infos ? infos[i] : local[i]).status = STOKES_TIMEOUT;
+        } else {
+            st = fgmres_drive(runs);
+        }
+    }
     for (cudaStream_t s : own) cudaStreamDestroy(s);
     if (st != STOKES_OK) return st;
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

@@ -207,16 +207,18 @@ def adaptive_loop_workload(name: str):
 
 # (cells per axis, levels): coarsest 1, 3 or 5 cells per axis
 BATCH_SIZES = ((16, 5), (20, 3), (24, 4), (32, 6), (40, 4), (48, 5))
+# the small end of the same range: many problems that each leave most of the GPU idle
+BATCH_SIZES_SMALL = ((16, 5), (20, 3), (24, 4))
 
 
-def batch_workload(count: int = 64, seed: int = 1907 + 5):
+def batch_workload(count: int = 64, seed: int = 1907 + 5, sizes=BATCH_SIZES):
     """Batched sinker problems: size drawn uniformly from BATCH_SIZES ({16, 20, 24, 32, 40, 48}^3
     with a coarsest mesh of at most 5^3 cells), 1-8 sinkers, viscosity ratio log-uniform in [1e2, 1e6];
     all draws from splitmix64 with `seed` (problem i uses seed * 1000 + i for its centres)."""
     u = uniform01(seed, 3 * count)
     probs = []
     for i in range(count):
-        n, L = BATCH_SIZES[min(int(u[3 * i] * len(BATCH_SIZES)), len(BATCH_SIZES) - 1)]
+        n, L = sizes[min(int(u[3 * i] * len(sizes)), len(sizes) - 1)]
         k = 1 + min(int(u[3 * i + 1] * 8), 7)
         dr = 10.0 ** (2.0 + 4.0 * u[3 * i + 2])
         probs.append(dr_problem(n, L, k, dr, seed * 1000 + i, "batch%d" % i))
