@@ -75,7 +75,11 @@ def parse():
                          "(Table 1 comparison)")
     ap.add_argument("--kernels", action="store_true",
                     help="profiling case: set up the workload, run 3 FP32 vmults, 2 FP64 Stokes applies, "
-                         "1 FP32 V-cycle, print one line and exit (for ncu)")
+                         "1 FP32 V-cycle, print one line and exit (for ncu); no Krylov basis is allocated")
+    ap.add_argument("--kernels-gs", action="store_true",
+                    help="with --kernels: also 40 FGMRES iterations (Gram-Schmidt passes up to a 40-vector basis)")
+    ap.add_argument("--vmult-kernel", type=int, default=None,
+                    help="with --kernels: level operator (0 cell kernel, 1 brick, 2 tensor cores)")
     return ap.parse_args()
 
 
@@ -484,6 +488,7 @@ def run_ours(args):
     # --- the 128^3 configuration: above-L2 vmult (the HBM figure) and one FP32-V-cycle solve
     if not args.no_large:
         line.update(run_large(capi, si, torch, stream, hbm, hbm_src))
+        line["refinement"] = run_refinement(capi, si, torch, stream)
 
     # --- CPU oracle baseline: bounded sample, scaled to a solve
     its_ref = oracle_iterations(args.workload)
@@ -603,6 +608,29 @@ def dominant_roofline(prof, dopt, cells, n_u, N, hbm, hbm_src, f32_peak, f64_pea
                           % bytes_alg}
 
 
+def run_refinement(capi, si, torch, stream):
+    """One problem (16 sinkers, viscosity ratio 1e6, 3^3 coarsest mesh) on 24^3, 48^3, 96^3 cells:
+    FP32-V-cycle FGMRES(50) iterations, time and true residual per mesh (Section 3.5: iteration
+    counts stay constant under refinement)."""
+    rows = []
+    for name in ("seq24", "seq48", "seq96"):
+        p = si.workload(name)
+        ctx = capi.stokes_setup_problem(p, stream=stream)
+        up = torch.zeros(ctx.n_u + ctx.n_p, dtype=torch.float64, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = capi.stokes_solve(ctx, capi.STOKES_FP32, None, up, rtol=RTOL, max_it=3000, stream=stream, check=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rows.append({"workload": name, "n": p.n, "dofs": ctx.n_u + ctx.n_p, "iterations": info.iterations,
+                     "s": e0.elapsed_time(e1) / 1e3, "status": info.status,
+                     "true_rel_residual": info.rel_residual_true})
+        ctx.close()
+        del up
+        torch.cuda.empty_cache()
+    return {"meshes": rows, "note": "first solve on each context (includes the V-cycle graph capture)"}
+
+
 def run_large(capi, si, torch, stream, hbm, hbm_src, name="cube128"):
     """The 128^3 configuration (16 sinkers, viscosity ratio 1e6, 8 levels): the standalone vmult with
     vectors far above L2 (the HBM figure) and one FP32-V-cycle FGMRES solve to 1e-8 with its true
@@ -660,7 +688,10 @@ def run_kernels(args):
         print(json.dumps({"kernels": args.workload, "n_u": ctx.n_u, "n_p": ctx.n_p, "leaves": ctx.size(-1, 2)}))
         return
     prob = si.workload(args.workload)
-    ctx = capi.stokes_setup_problem(prob)
+    opt = capi.stokes_default_options()
+    if args.vmult_kernel is not None:
+        opt.vmult_kernel = args.vmult_kernel
+    ctx = capi.stokes_setup_problem(prob, options=opt)
     n_u, n_p = ctx.n_u, ctx.n_p
     x = torch.rand(n_u, device="cuda", dtype=torch.float32)
     y = torch.empty_like(x)
@@ -671,13 +702,15 @@ def run_kernels(args):
     for _ in range(2):
         capi.stokes_vmult(ctx, -1, capi.BLOCK_STOKES, capi.STOKES_FP64, up, out)
     capi.gmg_vcycle(ctx, capi.STOKES_FP32, x, y)
-    # 40 FGMRES iterations: Gram-Schmidt passes up to a 40-vector basis
-    up.zero_()
-    try:
-        capi.stokes_solve(ctx, capi.STOKES_FP32, None, up, rtol=1e-14, max_it=40)
-    except capi.StokesError as e:
-        if e.status != capi.STOKES_NOT_CONVERGED:
-            raise
+    if args.kernels_gs:
+        # 40 FGMRES iterations: Gram-Schmidt passes up to a 40-vector basis
+        up.zero_()
+        try:
+            capi.stokes_solve(ctx, capi.STOKES_FP32, None, up, rtol=1e-14, max_it=40)
+        except capi.StokesError as e:
+            if e.status != capi.STOKES_NOT_CONVERGED:
+                raise
+    capi.stokes_device_status(ctx)
     torch.cuda.synchronize()
     print(json.dumps({"kernels": args.workload, "n_u": n_u, "n_p": n_p}))
 
