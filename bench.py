@@ -155,6 +155,7 @@ def peaks():
 # while these files are unchanged).
 KERNEL_SOURCES = {
     "stokes_df64": ("q2_basis.cuh", "df64.cuh", "outer.cuh", "outer.cu"),
+    "stokes_df64_inst": ("q2_basis.cuh", "df64.cuh", "outer.cuh", "outer.cu"),
     "stokes_fp64": ("q2_basis.cuh", "ops.cu"),
     "vmult_A_fp32": ("q2_basis.cuh", "brick.cuh", "brick.cu"),
     "krylov_vec": ("krylov.cu", "vec.cu"),
@@ -596,9 +597,10 @@ def dominant_roofline(prof, dopt, cells, n_u, N, hbm, hbm_src, f32_peak, f64_pea
         inst = recorded_traffic("stokes_df64_inst" if df else "stokes_fp64_inst", workload)
         if inst:
             ips = inst / (dms / 1e3)
-            r["issue"] = {"fp32_pipe_inst_per_launch": inst, "frac": ips / (f32_peak / 2 * 1e12),
-                          "note": "FP32-pipe instructions per launch from ncu against half the FFMA probe "
-                                  "(instructions/s)"}
+            r["issue"] = {"thread_inst_per_launch": inst, "frac": ips / (f32_peak / 2 * 1e12),
+                          "note": "instructions per launch (ncu smsp__inst_executed.sum x 32) against the "
+                                  "FFMA probe's instruction rate (FMA = 1 instruction): the issue efficiency "
+                                  "of the double-float code"}
         return r
     bytes_alg = (2 * n_u + cells) * 4
     return {"kernel": dom, "bound": "hbm", "achieved": bytes_alg / (dms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
