@@ -435,6 +435,22 @@ stokes_status stokes_profile_read(int cls, double* ms, long long* launches, int 
  * Exercises the allocation-failure paths of set-up and solve (a failed set-up frees what it had
  * allocated). Process-wide, for single-threaded use. */
 stokes_status stokes_debug_alloc_limit(long long bytes);
+/* 1 if this library was built with STOKES_DEBUG (index-map checks), else 0. In such a build
+ * every kernel of the octree path checks each entry it reads from a host-built index map
+ * (table numbers: 0 cell -> level nodes, 1 node -> parent cell, 2 node -> position in the parent,
+ * 3 leaf -> velocity nodes or constraints, 4 velocity constraint -> nodes, 5 leaf -> pressure
+ * vertices or constraints, 6 pressure constraint -> vertices, 7 copy list -> active node,
+ * 8 copy list -> level node) against the size of what it indexes. A bad entry is skipped, never
+ * trapped on, and recorded in the context's status words; the call that ran the kernel
+ * (stokes_setup_octree, stokes_vmult, gmg_vcycle, stokes_schur_inverse, stokes_precondition,
+ * stokes_solve; each synchronises its stream in such a build) then returns STOKES_EMESH and
+ * stokes_last_error() names the table and the entry's position in it. */
+int stokes_debug_build(void);
+/* Test hook of STOKES_DEBUG builds: from now on the checks of `table` on this octree context
+ * accept only entries below (true bound - cut), so that the last `cut` valid entries read as bad
+ * and exercise the path above without any out-of-range access. Drops the captured V-cycle
+ * graphs. Errors: EINVAL (release build, uniform-mesh context, bad table, cut < 0), ECUDA. */
+stokes_status stokes_debug_index_cut(stokes_ctx* ctx, int table, long long cut);
 /* Number of kernel launches the library has issued since it was loaded. */
 long long stokes_launch_count(void);
 /* FP32 and FP64 FMA throughput of the current device in TFLOP/s (eight independent FMA

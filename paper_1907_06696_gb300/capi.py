@@ -12,6 +12,8 @@ import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libstokes_gb300.so")
+# the same library built with STOKES_DEBUG (index-map checks on the octree path)
+DEBUG_LIB_PATH = os.path.join(HERE, "libstokes_gb300_debug.so")
 
 STOKES_OK, STOKES_EINVAL, STOKES_ENOMEM, STOKES_ECUDA = 0, 1, 2, 3
 STOKES_NOT_CONVERGED, STOKES_BREAKDOWN, STOKES_TIMEOUT, STOKES_EMESH = 4, 5, 6, 7
@@ -90,6 +92,8 @@ _SIGS = {
     "stokes_schur_inverse_noalloc": (C.c_int, [C.c_int, _P, _P, _P, C.c_int, _P]),
     "stokes_device_status": (C.c_int, [_P, _P]),
     "stokes_debug_alloc_limit": (C.c_int, [C.c_longlong]),
+    "stokes_debug_build": (C.c_int, []),
+    "stokes_debug_index_cut": (C.c_int, [_P, C.c_int, C.c_longlong]),
     "stokes_set_batch_vcycle": (C.c_int, [_P, C.c_int]),
     "stokes_autotune": (C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "stokes_profile": (C.c_int, [C.c_int]),
@@ -109,20 +113,43 @@ PROF_CLASSES = ["vmult_A_fp32", "vmult_A_fp64", "stokes_fp64", "bt_fp64", "mass_
                 "smoother_vec", "krylov_vec", "coarse", "cast", "residual_fp64"]
 
 
-def load(path: str = LIB_PATH):
-    """Load the library (raises if it has not been built)."""
-    global _lib
-    if _lib is not None:
-        return _lib
+def open_library(path: str):
+    """Open one build of the library with the signatures set (raises if it is missing)."""
     if not os.path.exists(path):
-        raise RuntimeError("libstokes_gb300.so not found at %s; run __graft_entry__.build() first" % path)
+        raise RuntimeError("%s not found; run __graft_entry__.build() first" % path)
     lib = C.CDLL(path)
     for name, (res, args) in _SIGS.items():
         f = getattr(lib, name)
         f.restype = res
         f.argtypes = args
-    _lib = lib
     return lib
+
+
+def load(path: str = LIB_PATH):
+    """Load the library that every function of this module calls (once per process)."""
+    global _lib
+    if _lib is None:
+        _lib = open_library(path)
+    return _lib
+
+
+class use_library:
+    """Context manager: the functions of this module call `lib` (from open_library) inside the
+    block, e.g. the STOKES_DEBUG build in its tests. A Context is destroyed by the build that made it."""
+
+    def __init__(self, lib):
+        self.lib = lib
+
+    def __enter__(self):
+        global _lib
+        load()
+        self.saved, _lib = _lib, self.lib
+        return self.lib
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
 
 
 def _ptr(x):
@@ -157,10 +184,11 @@ class Context:
 
     def __init__(self, handle):
         self.handle = handle
+        self.lib = load()   # the build that made the handle destroys it
 
     def close(self):
         if self.handle:
-            load().stokes_destroy(self.handle)
+            self.lib.stokes_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
@@ -170,7 +198,7 @@ class Context:
             pass
 
     def size(self, level=-1, what=0):
-        return int(load().stokes_size(self.handle, level, what))
+        return int(self.lib.stokes_size(self.handle, level, what))
 
     @property
     def n_u(self):

@@ -474,11 +474,11 @@ stokes_status oct_vcycle(stokes_ctx* c, const double* rhs, double* x, cudaStream
     const size_t nu = o.act.nu_nodes;
     for (OctLevel& L : o.lev) {
         CK(cudaMemsetAsync(ovecs<T>(L).b, 0, 3 * L.g.nn * sizeof(T), s));
-        CK(launch_oct_copy_to_level<T>(L.n_copy, L.copy_a, L.copy_l, nu, L.g.nn, rhs, ovecs<T>(L).b, s));
+        CK(launch_oct_copy_to_level<T>(L.n_copy, L.copy_a, L.copy_l, nu, L.g.nn, rhs, ovecs<T>(L).b, L.g.dbg, s));
     }
     CKS(oct_vcycle_level<T>(c, int(o.lev.size()) - 1, s));
     for (OctLevel& L : o.lev)
-        CK(launch_oct_copy_from_level<T>(L.n_copy, L.copy_a, L.copy_l, nu, L.g.nn, ovecs<T>(L).x, x, s));
+        CK(launch_oct_copy_from_level<T>(L.n_copy, L.copy_a, L.copy_l, nu, L.g.nn, ovecs<T>(L).x, x, L.g.dbg, s));
     CK(launch_oct_identity_rows(o.act, rhs, x, s));
     return STOKES_OK;
 }
@@ -1454,8 +1454,8 @@ stokes_status validate_mu(const stokes_mu* mu, size_t cells) {
 // The context's device status word, and for vmult_kernel 2 the tensor-core operator's f16 table
 // (5400 A_hat from the library's own sum-factorised cell operator, checked to be exact in f16).
 stokes_status setup_device_status(stokes_ctx* c, cudaStream_t s) {
-    CKS(dalloc(c, &c->dev_status, 1));
-    CK(cudaMemsetAsync(c->dev_status, 0, sizeof(unsigned), s));
+    CKS(dalloc(c, &c->dev_status, kStatusWords));
+    CK(cudaMemsetAsync(c->dev_status, 0, kStatusWords * sizeof(unsigned), s));
     c->tc.status = c->dev_status;
     c->tc.wait_ns = (unsigned long long)(c->opt.wait_limit_s * 1e9);
     if (c->opt.vmult_kernel != 2) return STOKES_OK;
@@ -1474,15 +1474,35 @@ stokes_status setup_device_status(stokes_ctx* c, cudaStream_t s) {
     return STOKES_OK;
 }
 
-// Read and clear the device status word (synchronises s): TIMEOUT if a bounded device wait gave up.
+// Read and clear the device status words (synchronises s): EMESH if a STOKES_DEBUG index check
+// met a bad table entry, TIMEOUT if a bounded device wait gave up.
 stokes_status take_device_status(stokes_ctx* c, cudaStream_t s) {
     if (!c->dev_status) return STOKES_OK;
-    unsigned w = 0;
-    CK(cudaMemcpyAsync(&w, c->dev_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemsetAsync(c->dev_status, 0, sizeof(unsigned), s));
+    unsigned w[kStatusWords] = {};
+    CK(cudaMemcpyAsync(w, c->dev_status, sizeof(w), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemsetAsync(c->dev_status, 0, sizeof(w), s));
     CK(cudaStreamSynchronize(s));
-    if (w != 0) return fail(STOKES_TIMEOUT, "a bounded wait inside a kernel gave up (wait_limit_s)");
+    if (w[0] & kStatusBadIndex) {
+        const unsigned long long at = (static_cast<unsigned long long>(w[3]) << 32) | w[2];
+        return fail(STOKES_EMESH, std::string("index map ") + oct_table_name(int(w[1]) - 1) + ": entry " +
+                                      std::to_string(at) + " out of range");
+    }
+    if (w[0] != 0) return fail(STOKES_TIMEOUT, "a bounded wait inside a kernel gave up (wait_limit_s)");
     return STOKES_OK;
+}
+
+#ifdef STOKES_DEBUG
+constexpr bool kDebugBuild = true;
+#else
+constexpr bool kDebugBuild = false;
+#endif
+
+// STOKES_DEBUG builds read the status words at the end of every call that ran index-map kernels
+// (synchronising its stream), so the call that met a bad entry returns EMESH; release builds pass
+// st through.
+stokes_status debug_status(stokes_ctx* c, cudaStream_t s, stokes_status st) {
+    if (!kDebugBuild || st != STOKES_OK || !c) return st;
+    return take_device_status(c, s);
 }
 
 stokes_status validate_options(const stokes_options& o) {
@@ -1761,12 +1781,16 @@ stokes_status oct_setup_impl(const stokes_octree* mesh, const stokes_mu* mu, con
     if (!err.empty()) return fail(STOKES_EMESH, "octree: " + err);
     CK(brick_configure());
     CK(gs_configure());
+    CKS(setup_device_status(c, s));
     const OctHost& H = oc.host;
     // ---- active space
     OctActiveDev& a = oc.act;
     a.n_leaves = int(H.leaves.size());
     a.nu_nodes = H.unodes.size();
     a.np = H.pverts.size();
+    a.n_ucon = H.ucon_node.size() / kOctUCon;
+    a.n_pcon = H.pcon_node.size() / kOctPCon;
+    a.dbg.status = c->dev_status;
     // The active-space kernels visit leaves in Morton (z-curve) order of their lower corner on the
     // finest lattice, so that neighbouring threads share nodes in cache (the key order keeps the
     // leaves of different levels apart); numbering (key order) and results are unchanged up to the
@@ -1876,6 +1900,7 @@ stokes_status oct_setup_impl(const stokes_octree* mesh, const stokes_mu* mu, con
         L.g.h = std::ldexp(1.0, -LH.l);
         L.g.cell_nodes = cn;
         L.g.flags = fl;
+        L.g.dbg.status = c->dev_status;
         if (li > 0) {
             uint32_t* pa;
             uint16_t* po;
@@ -1978,7 +2003,7 @@ stokes_status oct_setup_impl(const stokes_octree* mesh, const stokes_mu* mu, con
         }
     }
     CK(cudaStreamSynchronize(s));
-    return STOKES_OK;
+    return debug_status(c, s, STOKES_OK);
 }
 
 }  // namespace
@@ -2258,7 +2283,8 @@ stokes_status stokes_vmult(stokes_ctx* c, int level, int block, int prec, const 
                            void* stream) {
     if (c && c->oct) {
         if (!src || !dst) return fail(STOKES_EINVAL, "null vector");
-        return oct_vmult(c, level, block, prec, src, dst, static_cast<cudaStream_t>(stream));
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        return debug_status(c, s, oct_vmult(c, level, block, prec, src, dst, s));
     }
     CKS(check_level(c, level));
     if (!src || !dst) return fail(STOKES_EINVAL, "null vector");
@@ -2298,8 +2324,10 @@ stokes_status gmg_vcycle(stokes_ctx* c, int prec, const void* rhs, void* x, void
     if (!c || !rhs || !x) return fail(STOKES_EINVAL, "null argument");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (c->oct) {
-        if (prec == STOKES_FP32) return oct_vcycle<float>(c, static_cast<const double*>(rhs), static_cast<double*>(x), s);
-        if (prec == STOKES_FP64) return oct_vcycle<double>(c, static_cast<const double*>(rhs), static_cast<double*>(x), s);
+        if (prec == STOKES_FP32)
+            return debug_status(c, s, oct_vcycle<float>(c, static_cast<const double*>(rhs), static_cast<double*>(x), s));
+        if (prec == STOKES_FP64)
+            return debug_status(c, s, oct_vcycle<double>(c, static_cast<const double*>(rhs), static_cast<double*>(x), s));
         return fail(STOKES_EINVAL, "bad precision");
     }
     if (prec == STOKES_FP32) return vcycle<float>(c, static_cast<const float*>(rhs), static_cast<float*>(x), s);
@@ -2367,6 +2395,18 @@ static stokes_status drop_graphs(stokes_ctx* c) {
             cudaGraphExecDestroy(ge);
             ge = nullptr;
         }
+    return STOKES_OK;
+}
+
+int stokes_debug_build(void) { return kDebugBuild ? 1 : 0; }
+
+stokes_status stokes_debug_index_cut(stokes_ctx* c, int table, long long cut) {
+    if (!kDebugBuild) return fail(STOKES_EINVAL, "index-map checks exist in STOKES_DEBUG builds only");
+    if (!c || !c->oct) return fail(STOKES_EINVAL, "an octree context is required");
+    if (table < 0 || table >= OCT_NTABLES || cut < 0) return fail(STOKES_EINVAL, "bad table or cut");
+    CKS(drop_graphs(c));   // captured launches hold the old bounds
+    c->oct->act.dbg.cut[table] = cut;
+    for (OctLevel& L : c->oct->lev) L.g.dbg.cut[table] = cut;
     return STOKES_OK;
 }
 
@@ -2653,13 +2693,15 @@ stokes_status stokes_coarse_solve(stokes_ctx* c, int prec, const void* b, void* 
 
 stokes_status stokes_schur_inverse(stokes_ctx* c, const double* rp, double* zp, void* stream) {
     if (!c || !rp || !zp) return fail(STOKES_EINVAL, "null argument");
-    return schur_inverse(c, rp, zp, static_cast<cudaStream_t>(stream));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return debug_status(c, s, schur_inverse(c, rp, zp, s));
 }
 
 stokes_status stokes_precondition(stokes_ctx* c, int vcycle_prec, const double* r, double* z, void* stream) {
     if (!c || !r || !z) return fail(STOKES_EINVAL, "null argument");
     if (vcycle_prec != STOKES_FP32 && vcycle_prec != STOKES_FP64) return fail(STOKES_EINVAL, "bad precision");
-    return precondition(c, vcycle_prec, r, z, static_cast<cudaStream_t>(stream));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return debug_status(c, s, precondition(c, vcycle_prec, r, z, s));
 }
 
 }  // extern "C"

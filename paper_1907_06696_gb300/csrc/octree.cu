@@ -31,6 +31,25 @@ inline unsigned blocks_for(size_t n, int t) {
 __constant__ double c_q2_at[5][3] = {{1, 0, 0}, {0.375, 0.75, -0.125}, {0, 1, 0}, {-0.125, 0.75, 0.375}, {0, 0, 1}};
 __device__ __forceinline__ double q2_at(int p, int m) { return c_q2_at[p][m]; }
 
+// Is entry v, read at position `at` of table t, below `bound`? STOKES_DEBUG builds check and record
+// the first failure (flag, table + 1, position); release builds return true without a test.
+__device__ __forceinline__ bool idx_ok(const OctDebug& d, int t, long long v, long long bound, size_t at) {
+#ifdef STOKES_DEBUG
+    if (v >= 0 && v < bound - d.cut[t]) return true;
+    if (d.status) {
+        atomicOr(d.status, kStatusBadIndex);
+        if (atomicCAS(d.status + 1, 0u, unsigned(t + 1)) == 0u) {
+            d.status[2] = unsigned(uint64_t(at) & 0xffffffffu);
+            d.status[3] = unsigned(uint64_t(at) >> 32);
+        }
+    }
+    return false;
+#else
+    (void)d; (void)t; (void)v; (void)bound; (void)at;
+    return true;
+#endif
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128) k_oct_cells(OctLevelDev L, const T* __restrict__ mu, const T* __restrict__ src,
                                                    T* __restrict__ acc) {
@@ -38,10 +57,13 @@ __global__ void __launch_bounds__(128) k_oct_cells(OctLevelDev L, const T* __res
     if (cell >= L.n_cells) return;
     const int32_t* cn = L.cell_nodes + size_t(cell) * 27;
     T u[3][27], w[3][27];
+    unsigned skip = 0;   // bit a: node a is a boundary node (or a bad table entry)
 #pragma unroll
     for (int a = 0; a < 27; ++a) {
         const int32_t node = cn[a];
-        const bool b = (L.flags[node] & 1) != 0;
+        const bool b = !idx_ok(L.dbg, OCT_CELL_NODES, node, (long long)L.nn, size_t(cell) * 27 + a) ||
+                       (L.flags[node] & 1) != 0;
+        skip |= unsigned(b) << a;
 #pragma unroll
         for (int c = 0; c < 3; ++c) u[c][a] = b ? T(0) : src[c * L.nn + node];
     }
@@ -49,8 +71,8 @@ __global__ void __launch_bounds__(128) k_oct_cells(OctLevelDev L, const T* __res
     const T s = mu[cell] * T(L.h);
 #pragma unroll
     for (int a = 0; a < 27; ++a) {
+        if ((skip >> a) & 1u) continue;
         const int32_t node = cn[a];
-        if (L.flags[node] & 1) continue;
 #pragma unroll
         for (int c = 0; c < 3; ++c) atomicAdd(acc + c * L.nn + node, w[c][a] * s);
     }
@@ -70,6 +92,7 @@ __global__ void k_oct_diag(OctLevelDev L, const double* __restrict__ mu, const d
     const double s = mu[cell] * L.h;
     for (int a = 0; a < 27; ++a) {
         const int32_t node = L.cell_nodes[size_t(cell) * 27 + a];
+        if (!idx_ok(L.dbg, OCT_CELL_NODES, node, (long long)L.nn, size_t(cell) * 27 + a)) continue;
         for (int c = 0; c < 3; ++c) atomicAdd(diag + c * L.nn + node, s * ref[c * 27 + a]);
     }
 }
@@ -91,14 +114,18 @@ __global__ void k_oct_prolongate(OctLevelDev F, OctLevelDev C, const T* __restri
             for (int c = 0; c < 3; ++c) fine[c * F.nn + n] = T(0);
         return;
     }
-    const int32_t* cn = C.cell_nodes + size_t(F.parent[n]) * 27;
+    const uint32_t par = F.parent[n];
     const int p = F.pos[n], px = p % 5, py = (p / 5) % 5, pz = p / 25;
     T v[3] = {T(0), T(0), T(0)};
-    for (int b = 0; b < 27; ++b) {
-        const double w = q2_at(px, b % 3) * q2_at(py, (b / 3) % 3) * q2_at(pz, b / 9);
-        if (w == 0.0) continue;
-        const int32_t node = cn[b];
-        for (int c = 0; c < 3; ++c) v[c] += T(w) * coarse[c * C.nn + node];
+    if (idx_ok(F.dbg, OCT_PARENT, par, C.n_cells, n) && idx_ok(F.dbg, OCT_POS, p, 125, n)) {
+        const int32_t* cn = C.cell_nodes + size_t(par) * 27;
+        for (int b = 0; b < 27; ++b) {
+            const double w = q2_at(px, b % 3) * q2_at(py, (b / 3) % 3) * q2_at(pz, b / 9);
+            if (w == 0.0) continue;
+            const int32_t node = cn[b];
+            if (!idx_ok(C.dbg, OCT_CELL_NODES, node, (long long)C.nn, size_t(par) * 27 + b)) continue;
+            for (int c = 0; c < 3; ++c) v[c] += T(w) * coarse[c * C.nn + node];
+        }
     }
     for (int c = 0; c < 3; ++c) fine[c * F.nn + n] = (add ? fine[c * F.nn + n] : T(0)) + v[c];
 }
@@ -107,13 +134,16 @@ template <typename T>
 __global__ void k_oct_restrict_add(OctLevelDev F, OctLevelDev C, const T* __restrict__ fine, T* __restrict__ coarse) {
     const size_t n = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (n >= F.nn || (F.flags[n] & 1)) return;
-    const int32_t* cn = C.cell_nodes + size_t(F.parent[n]) * 27;
+    const uint32_t par = F.parent[n];
     const int p = F.pos[n], px = p % 5, py = (p / 5) % 5, pz = p / 25;
+    if (!idx_ok(F.dbg, OCT_PARENT, par, C.n_cells, n) || !idx_ok(F.dbg, OCT_POS, p, 125, n)) return;
+    const int32_t* cn = C.cell_nodes + size_t(par) * 27;
     const T f[3] = {fine[n], fine[F.nn + n], fine[2 * F.nn + n]};
     for (int b = 0; b < 27; ++b) {
         const double w = q2_at(px, b % 3) * q2_at(py, (b / 3) % 3) * q2_at(pz, b / 9);
         if (w == 0.0) continue;
         const int32_t node = cn[b];
+        if (!idx_ok(C.dbg, OCT_CELL_NODES, node, (long long)C.nn, size_t(par) * 27 + b)) continue;
         if (C.flags[node] & 1) continue;
         for (int c = 0; c < 3; ++c) atomicAdd(coarse + c * C.nn + node, T(w) * f[c]);
     }
@@ -121,70 +151,93 @@ __global__ void k_oct_restrict_add(OctLevelDev F, OctLevelDev C, const T* __rest
 
 template <typename T>
 __global__ void k_oct_copy_to_level(size_t n, const int32_t* __restrict__ ai, const int32_t* __restrict__ li,
-                                    size_t nu, size_t nn, const double* __restrict__ active, T* __restrict__ level) {
+                                    size_t nu, size_t nn, const double* __restrict__ active, T* __restrict__ level,
+                                    OctDebug dbg) {
     const size_t t = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (t >= n) return;
+    if (!idx_ok(dbg, OCT_COPY_ACTIVE, ai[t], (long long)nu, t) || !idx_ok(dbg, OCT_COPY_LEVEL, li[t], (long long)nn, t))
+        return;
     for (int c = 0; c < 3; ++c) level[c * nn + li[t]] = T(active[c * nu + ai[t]]);
 }
 
 template <typename T>
 __global__ void k_oct_copy_from_level(size_t n, const int32_t* __restrict__ ai, const int32_t* __restrict__ li,
-                                      size_t nu, size_t nn, const T* __restrict__ level, double* __restrict__ active) {
+                                      size_t nu, size_t nn, const T* __restrict__ level, double* __restrict__ active,
+                                      OctDebug dbg) {
     const size_t t = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (t >= n) return;
+    if (!idx_ok(dbg, OCT_COPY_ACTIVE, ai[t], (long long)nu, t) || !idx_ok(dbg, OCT_COPY_LEVEL, li[t], (long long)nn, t))
+        return;
     for (int c = 0; c < 3; ++c) active[c * nu + ai[t]] = double(level[c * nn + li[t]]);
 }
 
 // ---- active blocks with hanging-node constraints
-__device__ __forceinline__ double gather_u(const OctActiveDev& a, const double* src, int c, int32_t r) {
-    if (r >= 0) return a.ubnd[r] ? 0.0 : src[c * a.nu_nodes + r];
-    const int32_t* nd = a.ucon_node + size_t(-r - 1) * kOctUCon;
-    const double* wt = a.ucon_w + size_t(-r - 1) * kOctUCon;
+// A reference r read at position `at` of leaf_u / leaf_p is a node (r >= 0) or constraint -r-1.
+__device__ __forceinline__ double gather_u(const OctActiveDev& a, const double* src, int c, int32_t r, size_t at) {
+    if (r >= 0) {
+        if (!idx_ok(a.dbg, OCT_LEAF_U, r, (long long)a.nu_nodes, at)) return 0.0;
+        return a.ubnd[r] ? 0.0 : src[c * a.nu_nodes + r];
+    }
+    const long long k = -(long long)r - 1;
+    if (!idx_ok(a.dbg, OCT_LEAF_U, k, (long long)a.n_ucon, at)) return 0.0;
+    const int32_t* nd = a.ucon_node + size_t(k) * kOctUCon;
+    const double* wt = a.ucon_w + size_t(k) * kOctUCon;
     double v = 0.0;
 #pragma unroll 1
     for (int t = 0; t < kOctUCon; ++t) {
         const int32_t node = nd[t];
         if (node < 0) break;
+        if (!idx_ok(a.dbg, OCT_UCON_NODE, node, (long long)a.nu_nodes, size_t(k) * kOctUCon + t)) continue;
         if (!a.ubnd[node]) v += wt[t] * src[c * a.nu_nodes + node];
     }
     return v;
 }
-__device__ __forceinline__ void scatter_u(const OctActiveDev& a, double* dst, int c, int32_t r, double v) {
+__device__ __forceinline__ void scatter_u(const OctActiveDev& a, double* dst, int c, int32_t r, double v, size_t at) {
     if (r >= 0) {
+        if (!idx_ok(a.dbg, OCT_LEAF_U, r, (long long)a.nu_nodes, at)) return;
         if (!a.ubnd[r]) atomicAdd(dst + c * a.nu_nodes + r, v);
         return;
     }
-    const int32_t* nd = a.ucon_node + size_t(-r - 1) * kOctUCon;
-    const double* wt = a.ucon_w + size_t(-r - 1) * kOctUCon;
+    const long long k = -(long long)r - 1;
+    if (!idx_ok(a.dbg, OCT_LEAF_U, k, (long long)a.n_ucon, at)) return;
+    const int32_t* nd = a.ucon_node + size_t(k) * kOctUCon;
+    const double* wt = a.ucon_w + size_t(k) * kOctUCon;
 #pragma unroll 1
     for (int t = 0; t < kOctUCon; ++t) {
         const int32_t node = nd[t];
         if (node < 0) break;
+        if (!idx_ok(a.dbg, OCT_UCON_NODE, node, (long long)a.nu_nodes, size_t(k) * kOctUCon + t)) continue;
         if (!a.ubnd[node]) atomicAdd(dst + c * a.nu_nodes + node, wt[t] * v);
     }
 }
-__device__ __forceinline__ double gather_p(const OctActiveDev& a, const double* src, int32_t r) {
-    if (r >= 0) return src[r];
-    const int32_t* nd = a.pcon_node + size_t(-r - 1) * kOctPCon;
-    const double* wt = a.pcon_w + size_t(-r - 1) * kOctPCon;
+__device__ __forceinline__ double gather_p(const OctActiveDev& a, const double* src, int32_t r, size_t at) {
+    if (r >= 0) return idx_ok(a.dbg, OCT_LEAF_P, r, (long long)a.np, at) ? src[r] : 0.0;
+    const long long k = -(long long)r - 1;
+    if (!idx_ok(a.dbg, OCT_LEAF_P, k, (long long)a.n_pcon, at)) return 0.0;
+    const int32_t* nd = a.pcon_node + size_t(k) * kOctPCon;
+    const double* wt = a.pcon_w + size_t(k) * kOctPCon;
     double v = 0.0;
 #pragma unroll 1
     for (int t = 0; t < kOctPCon; ++t) {
         if (nd[t] < 0) break;
+        if (!idx_ok(a.dbg, OCT_PCON_NODE, nd[t], (long long)a.np, size_t(k) * kOctPCon + t)) continue;
         v += wt[t] * src[nd[t]];
     }
     return v;
 }
-__device__ __forceinline__ void scatter_p(const OctActiveDev& a, double* dst, int32_t r, double v) {
+__device__ __forceinline__ void scatter_p(const OctActiveDev& a, double* dst, int32_t r, double v, size_t at) {
     if (r >= 0) {
-        atomicAdd(dst + r, v);
+        if (idx_ok(a.dbg, OCT_LEAF_P, r, (long long)a.np, at)) atomicAdd(dst + r, v);
         return;
     }
-    const int32_t* nd = a.pcon_node + size_t(-r - 1) * kOctPCon;
-    const double* wt = a.pcon_w + size_t(-r - 1) * kOctPCon;
+    const long long k = -(long long)r - 1;
+    if (!idx_ok(a.dbg, OCT_LEAF_P, k, (long long)a.n_pcon, at)) return;
+    const int32_t* nd = a.pcon_node + size_t(k) * kOctPCon;
+    const double* wt = a.pcon_w + size_t(k) * kOctPCon;
 #pragma unroll 1
     for (int t = 0; t < kOctPCon; ++t) {
         if (nd[t] < 0) break;
+        if (!idx_ok(a.dbg, OCT_PCON_NODE, nd[t], (long long)a.np, size_t(k) * kOctPCon + t)) continue;
         atomicAdd(dst + nd[t], wt[t] * v);
     }
 }
@@ -210,7 +263,7 @@ __global__ void __launch_bounds__(128) k_oct_active(OctActiveDev a, const double
         for (int m = 0; m < 27; ++m) {
             const int32_t r = ru[m];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) u[c][m] = gather_u(a, src_u, c, r);
+            for (int c = 0; c < 3; ++c) u[c][m] = gather_u(a, src_u, c, r, size_t(leaf) * 27 + m);
         }
         if (DO_B) {
             double pb[8];
@@ -220,7 +273,7 @@ __global__ void __launch_bounds__(128) k_oct_active(OctActiveDev a, const double
             q2::b_component<1>(u[1], pb);
             q2::b_component<2>(u[2], pb);
 #pragma unroll
-            for (int v = 0; v < 8; ++v) scatter_p(a, dst_p, rp[v], s * pb[v]);
+            for (int v = 0; v < 8; ++v) scatter_p(a, dst_p, rp[v], s * pb[v], size_t(leaf) * 8 + v);
         }
         if (DO_A) {
             q2::cell_A(u, w);
@@ -234,7 +287,7 @@ __global__ void __launch_bounds__(128) k_oct_active(OctActiveDev a, const double
     if (DO_BT) {
         double p8[8];
 #pragma unroll
-        for (int v = 0; v < 8; ++v) p8[v] = s * gather_p(a, src_p, rp[v]);
+        for (int v = 0; v < 8; ++v) p8[v] = s * gather_p(a, src_p, rp[v], size_t(leaf) * 8 + v);
         q2::bt_component<0>(p8, w[0]);
         q2::bt_component<1>(p8, w[1]);
         q2::bt_component<2>(p8, w[2]);
@@ -244,7 +297,7 @@ __global__ void __launch_bounds__(128) k_oct_active(OctActiveDev a, const double
         for (int m = 0; m < 27; ++m) {
             const int32_t r = ru[m];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) scatter_u(a, dst_u, c, r, w[c][m]);
+            for (int c = 0; c < 3; ++c) scatter_u(a, dst_u, c, r, w[c][m], size_t(leaf) * 27 + m);
         }
     }
 }
@@ -262,7 +315,7 @@ __global__ void k_oct_mass_p(OctActiveDev a, const double* __restrict__ src, dou
     const double h = ldexp(1.0, -int(a.level[leaf]));
     const double sc = h * h * h / a.mu[leaf];
     double p[8];
-    for (int v = 0; v < 8; ++v) p[v] = gather_p(a, src, rp[v]);
+    for (int v = 0; v < 8; ++v) p[v] = gather_p(a, src, rp[v], size_t(leaf) * 8 + v);
     for (int v = 0; v < 8; ++v) {
         double o = 0.0;
         for (int q = 0; q < 8; ++q) {
@@ -270,11 +323,17 @@ __global__ void k_oct_mass_p(OctActiveDev a, const double* __restrict__ src, dou
             for (int d = 0; d < 3; ++d) m *= (((v >> d) & 1) == ((q >> d) & 1)) ? (1.0 / 3.0) : (1.0 / 6.0);
             o += m * p[q];
         }
-        scatter_p(a, dst, rp[v], sc * o);
+        scatter_p(a, dst, rp[v], sc * o, size_t(leaf) * 8 + v);
     }
 }
 
 }  // namespace
+
+const char* oct_table_name(int table) {
+    static const char* names[OCT_NTABLES] = {"cell_nodes", "parent", "pos", "leaf_u", "ucon_node",
+                                             "leaf_p", "pcon_node", "copy_active", "copy_level"};
+    return table >= 0 && table < OCT_NTABLES ? names[table] : "?";
+}
 
 template <typename T>
 cudaError_t launch_oct_level_cells(const OctLevelDev& L, const T* mu, const T* src, T* acc, cudaStream_t s) {
@@ -316,20 +375,20 @@ cudaError_t launch_oct_restrict_add(const OctLevelDev& F, const OctLevelDev& C, 
 template <typename T>
 cudaError_t launch_oct_copy_to_level(size_t n_copy, const int32_t* active_idx, const int32_t* level_idx,
                                      size_t nu_nodes, size_t level_nn, const double* active, T* level,
-                                     cudaStream_t s) {
+                                     const OctDebug& dbg, cudaStream_t s) {
     if (n_copy == 0) return cudaSuccess;
     LAUNCH(PROF_CAST, s, (k_oct_copy_to_level<T><<<blocks_for(n_copy, 256), 256, 0, s>>>(
-                             n_copy, active_idx, level_idx, nu_nodes, level_nn, active, level)));
+                             n_copy, active_idx, level_idx, nu_nodes, level_nn, active, level, dbg)));
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_oct_copy_from_level(size_t n_copy, const int32_t* active_idx, const int32_t* level_idx,
                                        size_t nu_nodes, size_t level_nn, const T* level, double* active,
-                                       cudaStream_t s) {
+                                       const OctDebug& dbg, cudaStream_t s) {
     if (n_copy == 0) return cudaSuccess;
     LAUNCH(PROF_CAST, s, (k_oct_copy_from_level<T><<<blocks_for(n_copy, 256), 256, 0, s>>>(
-                             n_copy, active_idx, level_idx, nu_nodes, level_nn, level, active)));
+                             n_copy, active_idx, level_idx, nu_nodes, level_nn, level, active, dbg)));
     return cudaGetLastError();
 }
 
@@ -369,9 +428,9 @@ cudaError_t launch_oct_mass_p(const OctActiveDev& a, const double* src, double* 
     template cudaError_t launch_oct_restrict_add<T>(const OctLevelDev&, const OctLevelDev&, const T*, T*,          \
                                                     cudaStream_t);                                                \
     template cudaError_t launch_oct_copy_to_level<T>(size_t, const int32_t*, const int32_t*, size_t, size_t,       \
-                                                     const double*, T*, cudaStream_t);                            \
+                                                     const double*, T*, const OctDebug&, cudaStream_t);           \
     template cudaError_t launch_oct_copy_from_level<T>(size_t, const int32_t*, const int32_t*, size_t, size_t,     \
-                                                       const T*, double*, cudaStream_t);
+                                                       const T*, double*, const OctDebug&, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

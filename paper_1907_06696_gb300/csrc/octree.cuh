@@ -91,6 +91,35 @@ std::vector<uint64_t> oct_refine_by_indicator(const std::vector<uint64_t>& leave
 
 // ---- device side (octree.cu) ----
 
+// Index-map checks of STOKES_DEBUG builds. Every entry a kernel reads from one of these host-built
+// tables is compared with the size of what it indexes; a bad entry is skipped (its gather reads 0,
+// its scatter is dropped) and recorded in the context's status word (kStatusBadIndex, then the
+// table and the entry's position in it, first one wins), which the next read of the status word
+// turns into STOKES_EMESH. Nothing traps. Release builds compile the checks away.
+enum OctTable {
+    OCT_CELL_NODES = 0,   // level cell -> 27 level nodes
+    OCT_PARENT,           // level node -> parent cell on the next coarser level
+    OCT_POS,              // level node -> position in its parent (< 125)
+    OCT_LEAF_U,           // leaf -> 27 active velocity nodes or constraints
+    OCT_UCON_NODE,        // velocity constraint -> its terms' nodes
+    OCT_LEAF_P,           // leaf -> 8 active pressure vertices or constraints
+    OCT_PCON_NODE,        // pressure constraint -> its terms' vertices
+    OCT_COPY_ACTIVE,      // copy list -> active velocity node
+    OCT_COPY_LEVEL,       // copy list -> level node
+    OCT_NTABLES
+};
+const char* oct_table_name(int table);
+
+// Status word bits and layout (4 unsigned: flags, table + 1 of the first bad entry, its position
+// low and high word); bits 1 and 2 are the bounded waits' time-outs.
+constexpr unsigned kStatusBadIndex = 4u;
+constexpr int kStatusWords = 4;
+
+struct OctDebug {
+    unsigned* status = nullptr;          // the context's status words
+    long long cut[OCT_NTABLES] = {};     // test hook: bound lowered by cut[t] for table t
+};
+
 struct OctLevelDev {
     int n_cells = 0;
     size_t nn = 0;                      // level nodes; vectors hold 3 nn entries
@@ -99,6 +128,7 @@ struct OctLevelDev {
     const uint8_t* flags = nullptr;
     const uint32_t* parent = nullptr;
     const uint16_t* pos = nullptr;
+    OctDebug dbg;
 };
 
 struct OctActiveDev {
@@ -113,6 +143,8 @@ struct OctActiveDev {
     const uint8_t* ubnd = nullptr;
     const double* mu = nullptr;         // per leaf
     const uint8_t* level = nullptr;     // per leaf
+    size_t n_ucon = 0, n_pcon = 0;      // constraint records
+    OctDebug dbg;
 };
 
 // acc (+)= A_l src over the level's cells (src boundary entries read as 0, boundary rows of acc
@@ -137,11 +169,11 @@ cudaError_t launch_oct_restrict_add(const OctLevelDev& F, const OctLevelDev& C, 
 template <typename T>
 cudaError_t launch_oct_copy_to_level(size_t n_copy, const int32_t* active_idx, const int32_t* level_idx,
                                      size_t nu_nodes, size_t level_nn, const double* active, T* level,
-                                     cudaStream_t s);
+                                     const OctDebug& dbg, cudaStream_t s);
 template <typename T>
 cudaError_t launch_oct_copy_from_level(size_t n_copy, const int32_t* active_idx, const int32_t* level_idx,
                                        size_t nu_nodes, size_t level_nn, const T* level, double* active,
-                                       cudaStream_t s);
+                                       const OctDebug& dbg, cudaStream_t s);
 // Active blocks with hanging-node constraints (FP64): dst_u = A u + B^T p, dst_p = B u by flags;
 // dst parts are overwritten; Dirichlet rows of dst_u hold src_u (DO_A) or 0 (B^T only).
 cudaError_t launch_oct_active(const OctActiveDev& a, const double* src_u, const double* src_p, double* dst_u,

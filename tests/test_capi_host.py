@@ -155,3 +155,16 @@ def test_malformed_leaves_refused_on_host(lib):
     full = [key(1, i, j, k) for k in range(2) for j in range(2) for i in range(2)]
     assert octree_status(lib, full[:-1], 1) == capi.STOKES_EMESH                  # a hole
     assert octree_status(lib, full + [key(2, 0, 0, 0)], 1) == capi.STOKES_EMESH   # an overlap
+
+
+def test_debug_build_exports_and_reports_itself(lib):
+    """The STOKES_DEBUG build links, exports the same functions, and says which build it is; the
+    index-cut hook validates its arguments on the host in both builds."""
+    dbg = capi.open_library(B.build(debug=True))
+    missing = [n for n in capi.header_functions() if not hasattr(dbg, n)]
+    assert not missing, missing
+    assert lib.stokes_debug_build() == 0 and dbg.stokes_debug_build() == 1
+    assert lib.stokes_debug_index_cut(None, 0, 1) == capi.STOKES_EINVAL
+    assert b"STOKES_DEBUG builds only" in lib.stokes_last_error()
+    assert dbg.stokes_debug_index_cut(None, 0, 1) == capi.STOKES_EINVAL
+    assert b"octree context" in dbg.stokes_last_error()
