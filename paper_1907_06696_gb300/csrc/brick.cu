@@ -64,12 +64,23 @@ __global__ void __launch_bounds__(BS, sizeof(T) == 4 ? 384 / BS : 1) k_cell_atom
 
 // Consume the accumulated product and clear it. Constrained entries need no special
 // case: acc, b, dinv and d are 0 there. 128-bit accesses on the aligned bulk, scalar tail.
+// Each thread loads two 128-bit items of every operand before it stores anything, and clears
+// acc after its data-dependent stores: clearing acc first (right behind its load) measured
+// 2.8 TB/s for the Chebyshev consumer and 1.4 TB/s for the residual one at 128^3, against
+// 6.9 and 6.7 TB/s in this order.
 template <typename T> struct Vec4;
 template <> struct Vec4<float> { using type = float4; };
 template <> struct Vec4<double> { using type = double2; };
 
 __device__ __forceinline__ float4 vzero(float4) { return make_float4(0.f, 0.f, 0.f, 0.f); }
 __device__ __forceinline__ double2 vzero(double2) { return make_double2(0.0, 0.0); }
+
+constexpr int kConsumeItems = 2;   // 128-bit items per thread and iteration
+
+inline unsigned consume_blocks(size_t n, size_t per) {
+    const size_t nb = (n / per + 256 * kConsumeItems - 1) / (256 * kConsumeItems);
+    return unsigned(nb < 1 ? 1 : (nb < 4864 ? nb : 4864));
+}
 
 // d = c1 d + c2 dinv (b - acc); x += d; acc = 0
 template <typename T>
@@ -78,32 +89,48 @@ __global__ void __launch_bounds__(256) k_consume_cheb(size_t n, T* __restrict__ 
                                                      T c1, T c2, bool vec) {
     using V = typename Vec4<T>::type;
     constexpr int W = sizeof(V) / sizeof(T);
+    constexpr int U = kConsumeItems;
     const size_t nv = vec ? n / W : 0;
-    const size_t stride = size_t(gridDim.x) * blockDim.x;
-    for (size_t v = size_t(blockIdx.x) * blockDim.x + threadIdx.x; v < nv; v += stride) {
-        V A = reinterpret_cast<V*>(acc)[v];
-        const V B = reinterpret_cast<const V*>(b)[v], Di = reinterpret_cast<const V*>(dinv)[v];
-        V Dd = reinterpret_cast<V*>(d)[v], X = reinterpret_cast<V*>(x)[v];
-        T* a_ = reinterpret_cast<T*>(&A);
-        const T* b_ = reinterpret_cast<const T*>(&B);
-        const T* di_ = reinterpret_cast<const T*>(&Di);
-        T* d_ = reinterpret_cast<T*>(&Dd);
-        T* x_ = reinterpret_cast<T*>(&X);
+    const size_t stride = size_t(gridDim.x) * blockDim.x * U;
+    for (size_t v0 = size_t(blockIdx.x) * blockDim.x * U + threadIdx.x; v0 < nv; v0 += stride) {
+        V A[U], B[U], Di[U], Dd[U], X[U];
 #pragma unroll
-        for (int q = 0; q < W; ++q) {
-            const T dn = (c1 != T(0) ? c1 * d_[q] : T(0)) + c2 * (di_[q] * (b_[q] - a_[q]));
-            d_[q] = dn;
-            x_[q] += dn;
+        for (int u = 0; u < U; ++u) {
+            const size_t v = v0 + size_t(u) * blockDim.x;
+            if (v < nv) {
+                A[u] = reinterpret_cast<const V*>(acc)[v];
+                B[u] = reinterpret_cast<const V*>(b)[v];
+                Di[u] = reinterpret_cast<const V*>(dinv)[v];
+                Dd[u] = reinterpret_cast<const V*>(d)[v];
+                X[u] = reinterpret_cast<const V*>(x)[v];
+            }
         }
-        reinterpret_cast<V*>(acc)[v] = vzero(A);
-        reinterpret_cast<V*>(d)[v] = Dd;
-        reinterpret_cast<V*>(x)[v] = X;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const size_t v = v0 + size_t(u) * blockDim.x;
+            if (v >= nv) continue;
+            const T* a_ = reinterpret_cast<const T*>(&A[u]);
+            const T* b_ = reinterpret_cast<const T*>(&B[u]);
+            const T* di_ = reinterpret_cast<const T*>(&Di[u]);
+            T* d_ = reinterpret_cast<T*>(&Dd[u]);
+            T* x_ = reinterpret_cast<T*>(&X[u]);
+#pragma unroll
+            for (int q = 0; q < W; ++q) {
+                const T dn = (c1 != T(0) ? c1 * d_[q] : T(0)) + c2 * (di_[q] * (b_[q] - a_[q]));
+                d_[q] = dn;
+                x_[q] += dn;
+            }
+            reinterpret_cast<V*>(d)[v] = Dd[u];
+            reinterpret_cast<V*>(x)[v] = X[u];
+            reinterpret_cast<V*>(acc)[v] = vzero(A[u]);
+        }
     }
-    for (size_t i = nv * W + size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const size_t tail_stride = size_t(gridDim.x) * blockDim.x;
+    for (size_t i = nv * W + size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += tail_stride) {
         const T dn = (c1 != T(0) ? c1 * d[i] : T(0)) + c2 * (dinv[i] * (b[i] - acc[i]));
-        acc[i] = T(0);
         d[i] = dn;
         x[i] += dn;
+        acc[i] = T(0);
     }
 }
 
@@ -113,21 +140,35 @@ __global__ void __launch_bounds__(256) k_consume_resid(size_t n, T* __restrict__
                                                       T* __restrict__ r, bool vec) {
     using V = typename Vec4<T>::type;
     constexpr int W = sizeof(V) / sizeof(T);
+    constexpr int U = kConsumeItems;
     const size_t nv = vec ? n / W : 0;
-    const size_t stride = size_t(gridDim.x) * blockDim.x;
-    for (size_t v = size_t(blockIdx.x) * blockDim.x + threadIdx.x; v < nv; v += stride) {
-        V A = reinterpret_cast<V*>(acc)[v];
-        const V B = reinterpret_cast<const V*>(b)[v];
-        V R;
-        const T* a_ = reinterpret_cast<const T*>(&A);
-        const T* b_ = reinterpret_cast<const T*>(&B);
-        T* r_ = reinterpret_cast<T*>(&R);
+    const size_t stride = size_t(gridDim.x) * blockDim.x * U;
+    for (size_t v0 = size_t(blockIdx.x) * blockDim.x * U + threadIdx.x; v0 < nv; v0 += stride) {
+        V A[U], B[U];
 #pragma unroll
-        for (int q = 0; q < W; ++q) r_[q] = b_[q] - a_[q];
-        reinterpret_cast<V*>(acc)[v] = vzero(A);
-        reinterpret_cast<V*>(r)[v] = R;
+        for (int u = 0; u < U; ++u) {
+            const size_t v = v0 + size_t(u) * blockDim.x;
+            if (v < nv) {
+                A[u] = reinterpret_cast<const V*>(acc)[v];
+                B[u] = reinterpret_cast<const V*>(b)[v];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const size_t v = v0 + size_t(u) * blockDim.x;
+            if (v >= nv) continue;
+            V R;
+            const T* a_ = reinterpret_cast<const T*>(&A[u]);
+            const T* b_ = reinterpret_cast<const T*>(&B[u]);
+            T* r_ = reinterpret_cast<T*>(&R);
+#pragma unroll
+            for (int q = 0; q < W; ++q) r_[q] = b_[q] - a_[q];
+            reinterpret_cast<V*>(r)[v] = R;
+            reinterpret_cast<V*>(acc)[v] = vzero(A[u]);
+        }
     }
-    for (size_t i = nv * W + size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const size_t tail_stride = size_t(gridDim.x) * blockDim.x;
+    for (size_t i = nv * W + size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += tail_stride) {
         r[i] = b[i] - acc[i];
         acc[i] = T(0);
     }
@@ -195,9 +236,7 @@ cudaError_t launch_cell_epi(const BrickArgs<T>& a, int epi, T* acc, size_t n_u, 
     }
     cudaError_t e = accumulate<T>(a, acc, bs, tc, s);
     if (e != cudaSuccess) return e;
-    const size_t per = sizeof(T) == 4 ? 4 : 2;
-    const size_t b = (n_u / per + 255) / 256;
-    const unsigned blocks = unsigned(b < 1 ? 1 : (b < 4864 ? b : 4864));
+    const unsigned blocks = consume_blocks(n_u, sizeof(T) == 4 ? 4 : 2);
     // 128-bit accesses only when every operand is 16-byte aligned (callers may pass offset views)
     auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
     if (epi == EPI_RESID) {
@@ -218,9 +257,7 @@ PlaneLayout brick_layout(int n) { return make_plane_layout(n, kBrickX, kBrickY, 
 template <typename T>
 cudaError_t launch_consume(int epi, size_t n, T* acc, const T* b, const T* dinv, T* d, T* x_or_r, double c1,
                            double c2, cudaStream_t s) {
-    const size_t per = sizeof(T) == 4 ? 4 : 2;
-    const size_t nb = (n / per + 255) / 256;
-    const unsigned blocks = unsigned(nb < 1 ? 1 : (nb < 4864 ? nb : 4864));
+    const unsigned blocks = consume_blocks(n, sizeof(T) == 4 ? 4 : 2);
     auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
     if (epi == EPI_RESID) {
         const bool vec = al(acc) && al(b) && al(x_or_r);
