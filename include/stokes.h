@@ -117,7 +117,11 @@ typedef struct {
                                    scatter of 1 with the cell products on the tensor cores (A_cell =
                                    mu_c h A_hat with 5400 A_hat exact in f16; each cell's values scaled
                                    by a power of two and split into two f16 terms, 22 significant bits;
-                                   f32 accumulation), FP64 levels as 0 */
+                                   f32 accumulation), FP64 levels as 0; 3 = FP32 levels: three
+                                   threads per cell, one per output component, cross derivatives
+                                   exchanged in shared memory (by default 0 uses it on the FP32
+                                   levels of at most 16^3 cells, where a level operator's time is
+                                   one thread's serial work), FP64 levels as 0 */
     int graphs;                 /* 1 = capture the V-cycle's level recursion once per precision as a CUDA
                                    graph and replay it on a library stream ordered with the caller's
                                    stream by events (default); 0 = launch kernel by kernel. The first

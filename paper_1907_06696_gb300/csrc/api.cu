@@ -285,14 +285,24 @@ double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& 
     return 0.5 * (lo + hi);
 }
 
-// Level-operator selector for launch_level_op: 1 = brick kernel, 2 = tensor-core brick kernel
-// (FP32 levels), else the cell kernel's block size.
-int level_kernel(const stokes_ctx* c) { return c->opt.vmult_kernel == 1 || c->opt.vmult_kernel == 2 ? c->opt.vmult_kernel : c->cell_block; }
+// Level-operator selector for launch_level_op: 1 = brick kernel, 2 = tensor-core brick kernel,
+// 3 = component-split kernel (FP32 levels), else the cell kernel's block size. By default the
+// FP32 levels of at most kSplitMaxN^3 cells take the component-split kernel: there a level
+// operator is one short wave and its time one thread's serial work, which the split divides by 3.
+constexpr int kSplitMaxN = 16;
+
+template <typename T>
+int level_kernel(const stokes_ctx* c, int l) {
+    const int k = c->opt.vmult_kernel;
+    if (k == 1 || k == 2 || k == 3) return k;
+    if (sizeof(T) == 4 && c->lev[l].g.n <= kSplitMaxN) return 3;
+    return c->cell_block;
+}
 
 template <typename T>
 stokes_status vmult_level(stokes_ctx* c, int l, const T* src, T* dst, cudaStream_t s) {
     Level& L = c->lev[l];
-    CK(launch_level_op<T>(level_kernel(c), L.g, L.planes, EPI_PLAIN, vecs<T>(L).mu, src, dst, nullptr, nullptr,
+    CK(launch_level_op<T>(level_kernel<T>(c, l), L.g, L.planes, EPI_PLAIN, vecs<T>(L).mu, src, dst, nullptr, nullptr,
                           nullptr, 0.0, 0.0, slots<T>(L), vecs<T>(L).acc, s, &c->tc));
     return STOKES_OK;
 }
@@ -302,7 +312,7 @@ template <typename T>
 stokes_status cheb_step(stokes_ctx* c, int l, const T* b, T* x, double c1, double c2, cudaStream_t s) {
     Level& L = c->lev[l];
     LevelVecs<T>& v = vecs<T>(L);
-    CK(launch_level_op<T>(level_kernel(c), L.g, L.planes, EPI_CHEB, v.mu, x, nullptr, b, v.dinv, v.d, c1, c2,
+    CK(launch_level_op<T>(level_kernel<T>(c, l), L.g, L.planes, EPI_CHEB, v.mu, x, nullptr, b, v.dinv, v.d, c1, c2,
                           slots<T>(L), v.acc, s, &c->tc));
     return STOKES_OK;
 }
@@ -345,7 +355,7 @@ stokes_status vcycle_level(stokes_ctx* c, int l, cudaStream_t s) {
     if (l == 0) return coarse_solve<T>(c, v.b, v.x, s);
     LevelVecs<T>& vc = vecs<T>(c->lev[l - 1]);
     CKS(smooth<T>(c, l, v.b, v.x, true, s));
-    CK(launch_level_op<T>(level_kernel(c), L.g, L.planes, EPI_RESID, v.mu, v.x, v.r, v.b, nullptr, nullptr, 0.0,
+    CK(launch_level_op<T>(level_kernel<T>(c, l), L.g, L.planes, EPI_RESID, v.mu, v.x, v.r, v.b, nullptr, nullptr, 0.0,
                           0.0, slots<T>(L), v.acc, s, &c->tc));
     CK(launch_restrict<T>(L.g, v.r, vc.b, s));
     CKS(vcycle_level<T>(c, l - 1, s));
@@ -1508,7 +1518,7 @@ stokes_status debug_status(stokes_ctx* c, cudaStream_t s, stokes_status st) {
 stokes_status validate_options(const stokes_options& o) {
     if (o.cheb_degree < 1 || o.smoothing_range <= 1.0 || o.eig_safety <= 0.0 || o.lanczos_steps < 1 ||
         o.schur_degree < 0 || o.restart < 1 || o.restart > 500 || (o.outer_arith != 0 && o.outer_arith != 1) ||
-        o.vmult_kernel < 0 || o.vmult_kernel > 2 || (o.graphs != 0 && o.graphs != 1) || !(o.wait_limit_s >= 0.0) ||
+        o.vmult_kernel < 0 || o.vmult_kernel > 3 || (o.graphs != 0 && o.graphs != 1) || !(o.wait_limit_s >= 0.0) ||
         (o.batch_vcycle != 0 && o.batch_vcycle != 1) ||
         o.wait_limit_s > 1e6 ||
         (o.precond_kind != 0 && o.precond_kind != 1) || o.outer_solver < 0 || o.outer_solver > 3 || (o.gram_schmidt != 0 && o.gram_schmidt != 1) ||

@@ -62,6 +62,92 @@ __global__ void __launch_bounds__(BS, sizeof(T) == 4 ? 384 / BS : 1) k_cell_atom
     }
 }
 
+// ---- component-split variant: three threads per cell, warp c of each group of three computes
+// output component c. A cell's output row c is
+//   w_c = 2 D_c^T W (d_c U_c) + sum_{d != c} D_d^T W (d_d U_c + d_c U_d),
+// so the thread of component c interpolates only its own component U_c, forms its three
+// derivatives d_e U_c, and takes the cross terms d_c U_d from the other two threads through
+// shared memory. The arithmetic per cell is that of the one-thread kernel (the same sweeps), the
+// serial work per thread a third of it: the small levels, where a level operator is one wave of
+// a few warps and its time is one thread's latency, get faster; the product is the same up to
+// the order of the sums.
+constexpr int kSplitCells = 32;   // cells per block; block = 3 warps
+
+__global__ void __launch_bounds__(3 * kSplitCells) k_cell_split(BrickArgs<float> a, float* acc) {
+    __shared__ float D[3][3][27][kSplitCells];   // D[c][e][q][cell] = d_e U_c at Gauss point q
+    const int c = threadIdx.x / kSplitCells;     // warp-uniform
+    const int lc = threadIdx.x % kSplitCells;
+    const size_t cells = size_t(a.n) * a.n * a.n;
+    const size_t cell = size_t(blockIdx.x) * kSplitCells + lc;
+    const bool valid = cell < cells;
+    const int ci = valid ? int(cell % a.n) : 0;
+    const int cj = valid ? int((cell / a.n) % a.n) : 0;
+    const int ck = valid ? int(cell / (size_t(a.n) * a.n)) : 0;
+    const int M = a.M;
+    const size_t base = size_t(2 * ci) + size_t(M) * (size_t(2 * cj) + size_t(M) * size_t(2 * ck));
+    const float* src = a.src + size_t(c) * a.nodes + base;
+    float u[27];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const bool bk = (2 * ck + k == 0) || (2 * ck + k == M - 1);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const bool bj = bk || (2 * cj + j == 0) || (2 * cj + j == M - 1);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const bool bnd = !valid || bj || (2 * ci + i == 0) || (2 * ci + i == M - 1);
+                u[i + 3 * j + 9 * k] = bnd ? 0.0f : src[i + M * (j + M * k)];
+            }
+        }
+    }
+    q2::interp<0>(u);
+    q2::interp<1>(u);
+    q2::interp<2>(u);
+    float g[27];
+    q2::deriv<0, false>(u, g);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) D[c][0][q][lc] = g[q];
+    q2::deriv<1, false>(u, g);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) D[c][1][q][lc] = g[q];
+    q2::deriv<2, false>(u, g);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) D[c][2][q][lc] = g[q];
+    __syncthreads();
+    float w[27];
+#pragma unroll
+    for (int q = 0; q < 27; ++q) w[q] = 0.0f;
+    // d = 0, 1, 2 at compile time; the diagonal term (d == c) carries the factor 2
+#pragma unroll
+    for (int q = 0; q < 27; ++q) g[q] = c == 0 ? D[0][0][q][lc] : D[c][0][q][lc] + D[0][c][q][lc];
+    if (c == 0) q2::derivT_w<0, 2>(g, w); else q2::derivT_w<0, 1>(g, w);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) g[q] = c == 1 ? D[1][1][q][lc] : D[c][1][q][lc] + D[1][c][q][lc];
+    if (c == 1) q2::derivT_w<1, 2>(g, w); else q2::derivT_w<1, 1>(g, w);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) g[q] = c == 2 ? D[2][2][q][lc] : D[c][2][q][lc] + D[2][c][q][lc];
+    if (c == 2) q2::derivT_w<2, 2>(g, w); else q2::derivT_w<2, 1>(g, w);
+    q2::interpT<0>(w);
+    q2::interpT<1>(w);
+    q2::interpT<2>(w);
+    if (!valid) return;
+    const float sc = a.mu[cell] * a.h;
+    float* out = acc + size_t(c) * a.nodes + base;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const bool bk = (2 * ck + k == 0) || (2 * ck + k == M - 1);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const bool bj = bk || (2 * cj + j == 0) || (2 * cj + j == M - 1);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                if (bj || (2 * ci + i == 0) || (2 * ci + i == M - 1)) continue;
+                atomicAdd(out + i + M * (j + M * k), w[i + 3 * j + 9 * k] * sc);
+            }
+        }
+    }
+}
+
 // Consume the accumulated product and clear it. Constrained entries need no special
 // case: acc, b, dinv and d are 0 there. 128-bit accesses on the aligned bulk, scalar tail.
 // Each thread loads two 128-bit items of every operand before it stores anything, and clears
@@ -213,13 +299,22 @@ cudaError_t launch_cell(const BrickArgs<T>& a, T* acc, int bs, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Accumulate A src into acc: the cell kernel, or (FP32 with tc given) the tensor-core kernel.
+// Accumulate A src into acc: the cell kernel with bs threads per block, or for FP32 levels the
+// component-split kernel (bs = kSplitKernel) or (tc given) the tensor-core kernel.
+constexpr int kSplitKernel = 3;
+
 template <typename T>
 cudaError_t accumulate(const BrickArgs<T>& a, T* acc, int bs, const TcArgs* tc, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
         if (tc) return launch_cell_tc(a, acc, *tc, s);
+        if (bs == kSplitKernel) {
+            const size_t cells = size_t(a.n) * a.n * a.n;
+            LAUNCH(PROF_VMULT_F32, s, (k_cell_split<<<unsigned((cells + kSplitCells - 1) / kSplitCells),
+                                                      3 * kSplitCells, 0, s>>>(a, acc)));
+            return cudaGetLastError();
+        }
     }
-    return launch_cell<T>(a, acc, bs, s);
+    return launch_cell<T>(a, acc, bs == kSplitKernel ? 128 : bs, s);
 }
 
 template <typename T>
@@ -310,7 +405,7 @@ cudaError_t launch_level_op(int kernel, const LevelGeom& g, const PlaneLayout& L
             kernel = 128;   // no FP64 tensor-core path
         }
     }
-    if (kernel == 0 || kernel == 64 || kernel == 128 || kernel == 256)
+    if (kernel == 0 || kernel == kSplitKernel || kernel == 64 || kernel == 128 || kernel == 256)
         return launch_cell_epi<T>(a, epi, acc, g.n_u, kernel == 0 ? 128 : kernel, s);
     switch (epi) {
         case EPI_PLAIN: return launch_epi<T, EPI_PLAIN>(a, s);

@@ -366,6 +366,8 @@ cudaError_t launch_cell_tc(const BrickArgs<float>& a, float* acc, const TcArgs& 
 // kernel 0, 64, 128, 256: one thread per cell (blocks of 128, 64, 128, 256 threads) with atomic
 //           adds into acc (n_u entries, zero on entry and on return) and a consumer kernel for the
 //           epilogue;
+// kernel 3: FP32: the cell kernel's accumulation with three threads per cell (one per output
+//           component), the same consumer kernels; FP64: kernel 128;
 // kernel 1: the brick-tiled kernel with the epilogue fused (slots: brick_layout(n).total entries);
 // kernel 2: FP32: the cell products on the tensor cores, accumulated like kernel 0 (tc must be
 //           given); FP64: kernel 128.

@@ -73,8 +73,9 @@ _ctx_cache = {}
 
 def gpu_ctx(capi, name, kernel=0):
     """Context of a named problem; kernel selects the V-cycle level operator
-    (0 = cell-parallel with atomic adds, 1 = brick-tiled deterministic, 2 = brick-tiled with the
-    FP32 cell products on the tensor cores)."""
+    (0 = cell-parallel with atomic adds, component-split on the FP32 levels up to 16^3, 1 =
+    brick-tiled deterministic, 2 = brick-tiled with the FP32 cell products on the tensor cores, 3 =
+    component-split on every FP32 level)."""
     key = (name, kernel)
     if key not in _ctx_cache:
         p = oracle_problem(name)[0]
@@ -130,7 +131,7 @@ def test_inverse_diagonal_and_lambda(capi, name):
 
 
 # ----------------------------------------------------------------- operators
-@pytest.mark.parametrize("kernel", [0, 1, 2])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3])
 @pytest.mark.parametrize("name", ["cube8", "n12", "cube16", "n24"])
 def test_vmult_A_all_levels(capi, name, kernel):
     p, m, mus, G, ops, F = oracle_problem(name)
@@ -195,7 +196,7 @@ def test_transfers(capi, name):
             assert_close(host(outc), ref_r, tol)
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3])
 @pytest.mark.parametrize("name", ["cube8", "n12"])
 def test_chebyshev_smoother(capi, name, kernel):
     p, m, mus, G, ops, F = oracle_problem(name)
@@ -226,7 +227,7 @@ def test_coarse_solve(capi, name):
         assert_close(host(x), ref, tol)
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3])
 @pytest.mark.parametrize("name", ["cube8", "n12", "cube16", "n24", "n10c5", "n12c6"])
 def test_vcycle(capi, name, kernel):
     p, m, mus, G, ops, F = oracle_problem(name)
@@ -258,7 +259,7 @@ def test_schur_and_block_preconditioner(capi, name):
     assert_close(host(z), ref, F32_CYCLE_TOL)
 
 
-@pytest.mark.parametrize("kernel", [0, 2])
+@pytest.mark.parametrize("kernel", [0, 2, 3])
 @pytest.mark.parametrize("name", ["cube8", "n12", "n10c5"])
 def test_solve_fp64_and_fp32_vcycle(capi, name, kernel):
     p, m, mus, G, ops, F = oracle_problem(name)
@@ -420,12 +421,12 @@ def test_tensor_core_operator_wait_timeout(capi):
     assert_close(host(dst), G.levels[-1].ops.apply_A(x), F32_TOL)
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3])
 @pytest.mark.parametrize("prec", [0, 1])
 def test_graph_replay_matches_kernel_launches(capi, prec, kernel):
     """The captured V-cycle graph runs the same kernels in the same order, over two replays with
     different right-hand sides: bitwise equal output with the deterministic brick operator (1); with
-    the atomic operators (0; 2, whose shared and global atomic adds vary their order from run to
+    the atomic operators (0, 3; 2, whose shared and global atomic adds vary their order from run to
     run) equal to rounding."""
     p = oracle_problem("n12")[0]
     outs = []
