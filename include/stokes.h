@@ -166,6 +166,18 @@ typedef struct {
                                    per phase, grid barriers bounded by wait_limit_s, the other problems
                                    masked out), other rounds as 0. Read from the first context of the
                                    batch. */
+    int fused_smoother;         /* 1 = each Jacobi-Chebyshev step's vector update is carried by the
+                                   next product on the level (the cell and component-split operators,
+                                   vmult_kernel 0 and 3): each node's operand x' = x + c1 d + c2
+                                   D^-1 (b - A x) is formed where the product gathers it, the owner
+                                   cell stores the new (d, x), and the pre-smoothing's last update
+                                   rides on its residual's product, so a degree-k smoothing takes k
+                                   products and one vector pass instead of k of each; 0 = a separate
+                                   vector pass after every product (default: on GB300 the products
+                                   are bound by issue and latency, and gathering five vectors at every
+                                   node of every cell costs them more than the streaming pass saves:
+                                   a degree-4 smoothing at 64^3 takes 374 us fused, 268 us separate).
+                                   Same arithmetic. */
 } stokes_options;
 
 typedef struct {

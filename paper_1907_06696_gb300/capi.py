@@ -50,7 +50,7 @@ class stokes_options(C.Structure):
                 ("lanczos_steps", C.c_int), ("schur_degree", C.c_int), ("restart", C.c_int),
                 ("outer_arith", C.c_int), ("vmult_kernel", C.c_int), ("graphs", C.c_int), ("precond_kind", C.c_int),
                 ("outer_solver", C.c_int), ("idr_s", C.c_int), ("gram_schmidt", C.c_int),
-                ("wait_limit_s", C.c_double), ("batch_vcycle", C.c_int)]
+                ("wait_limit_s", C.c_double), ("batch_vcycle", C.c_int), ("fused_smoother", C.c_int)]
 
 
 class stokes_solve_info(C.Structure):

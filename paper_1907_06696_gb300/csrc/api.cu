@@ -125,6 +125,11 @@ struct LevelVecs {
     T* mu = nullptr;  // cell viscosity
     T* dinv = nullptr;
     T* acc = nullptr; // operator accumulator of the cell-parallel kernel (kept at zero between uses)
+    // the fused smoother's second (d, x) pair and its two further accumulators (zero between uses)
+    T* x2 = nullptr;
+    T* d2 = nullptr;
+    T* acc2 = nullptr;
+    T* acc3 = nullptr;
 };
 
 struct Level {
@@ -339,6 +344,82 @@ stokes_status smooth(stokes_ctx* c, int l, const T* b, T* x, bool zero_guess, cu
     return STOKES_OK;
 }
 
+// Whether level l smooths with each Chebyshev step carried by the next product (the cell and
+// component-split operators; the level has the second (d, x) pair and the extra accumulators).
+template <typename T>
+bool fused_level(const stokes_ctx* c, int l) {
+    const int k = level_kernel<T>(c, l);
+    return c->opt.fused_smoother == 1 && k != 1 && k != 2 && vecs<T>(const_cast<Level&>(c->lev[l])).x2 != nullptr;
+}
+
+// Degree-k smoothing with each step's update carried by the next product (ChebGather); with r
+// given also r = b - A x_k, whose product then carries the last update. The iterates alternate
+// between (x, d) and the level's (x2, d2); the accumulators rotate over acc, acc2, acc3 (all zero
+// again on return). x receives the result.
+template <typename T>
+stokes_status smooth_fused(stokes_ctx* c, int l, const T* b, T* x, bool zero_guess, T* r, cudaStream_t s) {
+    Level& L = c->lev[l];
+    LevelVecs<T>& v = vecs<T>(L);
+    const int kern = level_kernel<T>(c, l);
+    const int deg = c->opt.cheb_degree;
+    const double theta = 0.5 * (L.hi + L.lo), delta = 0.5 * (L.hi - L.lo);
+    const double sigma = theta / delta;
+    // coefficients of step j: d <- c1[j] d + c2[j] D^-1 (b - A x), x <- x + d (as smooth())
+    std::vector<double> c1(deg), c2(deg);
+    double rho = 1.0 / sigma;
+    c1[0] = 0.0;
+    c2[0] = 1.0 / theta;
+    for (int j = 1; j < deg; ++j) {
+        const double rho_new = 1.0 / (2.0 * sigma - rho);
+        c1[j] = rho_new * rho;
+        c2[j] = 2.0 * rho_new / delta;
+        rho = rho_new;
+    }
+    T* X[2] = {x, v.x2};
+    T* Dv[2] = {v.d, v.d2};
+    T* A[3] = {v.acc, v.acc2, v.acc3};
+    const size_t n = L.g.n_u;
+    // products of the iterates first .. last: the first plain, the others carrying a step
+    const int first = zero_guess ? 1 : 0;
+    const int last = r ? deg : deg - 1;
+    const int m = last - first + 1;
+    const int fused = m > 1 ? m - 1 : 0;
+    // with r the last carried step writes x_k, which must land in x: start in pair (fused mod 2)
+    const int p0 = (r && (fused & 1)) ? 1 : 0;
+    if (zero_guess) {
+        CK(launch_cheb_update<T>(n, b, nullptr, v.dinv, Dv[p0], X[p0], 0.0, c2[0], false, s));
+    } else if (p0 == 1) {
+        CK(cudaMemcpyAsync(X[1], x, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    }
+    if (m <= 0) return STOKES_OK;
+    int cur = p0;
+    CK(launch_accumulate<T>(kern, L.g, v.mu, X[cur], A[0], s));
+    for (int j = 2; j <= m; ++j) {
+        const int step = first + j - 2;   // the update from iterate `step` to `step + 1`
+        ChebGather<T> g;
+        g.acc_prev = A[(j - 2) % 3];
+        g.b = b;
+        g.dinv = v.dinv;
+        g.d_old = Dv[cur];
+        g.x_old = X[cur];
+        g.d_new = Dv[cur ^ 1];
+        g.x_new = X[cur ^ 1];
+        g.acc_zero = j == 2 ? nullptr : A[j % 3];
+        g.c1 = T(c1[step]);
+        g.c2 = T(c2[step]);
+        CK(launch_cell_cheb<T>(kern, L.g, v.mu, g, A[(j - 1) % 3], s));
+        cur ^= 1;
+    }
+    T* zero2 = m >= 2 ? A[(m - 2) % 3] : nullptr;
+    if (r) {
+        CK(launch_consume2<T>(EPI_RESID, n, A[(m - 1) % 3], b, nullptr, nullptr, nullptr, nullptr, r, zero2, 0.0, 0.0, s));
+    } else {
+        CK(launch_consume2<T>(EPI_CHEB, n, A[(m - 1) % 3], b, v.dinv, Dv[cur], X[cur], Dv[0], X[0], zero2, c1[deg - 1],
+                              c2[deg - 1], s));
+    }
+    return STOKES_OK;
+}
+
 template <typename T>
 stokes_status coarse_solve(stokes_ctx* c, const T* b, T* x, cudaStream_t s) {
     Level& L0 = c->lev[0];
@@ -354,13 +435,19 @@ stokes_status vcycle_level(stokes_ctx* c, int l, cudaStream_t s) {
     LevelVecs<T>& v = vecs<T>(L);
     if (l == 0) return coarse_solve<T>(c, v.b, v.x, s);
     LevelVecs<T>& vc = vecs<T>(c->lev[l - 1]);
-    CKS(smooth<T>(c, l, v.b, v.x, true, s));
-    CK(launch_level_op<T>(level_kernel<T>(c, l), L.g, L.planes, EPI_RESID, v.mu, v.x, v.r, v.b, nullptr, nullptr, 0.0,
-                          0.0, slots<T>(L), v.acc, s, &c->tc));
+    const bool fused = fused_level<T>(c, l);
+    if (fused) {
+        CKS(smooth_fused<T>(c, l, v.b, v.x, true, v.r, s));   // pre-smoothing and its residual
+    } else {
+        CKS(smooth<T>(c, l, v.b, v.x, true, s));
+        CK(launch_level_op<T>(level_kernel<T>(c, l), L.g, L.planes, EPI_RESID, v.mu, v.x, v.r, v.b, nullptr, nullptr,
+                              0.0, 0.0, slots<T>(L), v.acc, s, &c->tc));
+    }
     CK(launch_restrict<T>(L.g, v.r, vc.b, s));
     CKS(vcycle_level<T>(c, l - 1, s));
     CK(launch_prolongate<T>(L.g, vc.x, v.x, true, s));
-    CKS(smooth<T>(c, l, v.b, v.x, false, s));
+    if (fused) CKS(smooth_fused<T>(c, l, v.b, v.x, false, nullptr, s));
+    else CKS(smooth<T>(c, l, v.b, v.x, false, s));
     return STOKES_OK;
 }
 
@@ -1519,7 +1606,7 @@ stokes_status validate_options(const stokes_options& o) {
     if (o.cheb_degree < 1 || o.smoothing_range <= 1.0 || o.eig_safety <= 0.0 || o.lanczos_steps < 1 ||
         o.schur_degree < 0 || o.restart < 1 || o.restart > 500 || (o.outer_arith != 0 && o.outer_arith != 1) ||
         o.vmult_kernel < 0 || o.vmult_kernel > 3 || (o.graphs != 0 && o.graphs != 1) || !(o.wait_limit_s >= 0.0) ||
-        (o.batch_vcycle != 0 && o.batch_vcycle != 1) ||
+        (o.batch_vcycle != 0 && o.batch_vcycle != 1) || (o.fused_smoother != 0 && o.fused_smoother != 1) ||
         o.wait_limit_s > 1e6 ||
         (o.precond_kind != 0 && o.precond_kind != 1) || o.outer_solver < 0 || o.outer_solver > 3 || (o.gram_schmidt != 0 && o.gram_schmidt != 1) ||
         (o.outer_solver == 3 && o.precond_kind != 1) ||
@@ -1630,6 +1717,16 @@ stokes_status setup_impl(const stokes_mesh* mesh, const stokes_mu* mu, const sto
             CKS(dalloc(c, p, nu));
         CK(cudaMemsetAsync(Lv.v64.acc, 0, nu * sizeof(double), s));
         CK(cudaMemsetAsync(Lv.v32.acc, 0, nu * sizeof(float), s));
+        if (o.fused_smoother == 1 && l > 0) {
+            for (auto* p : {&Lv.v64.x2, &Lv.v64.d2, &Lv.v64.acc2, &Lv.v64.acc3}) {
+                CKS(dalloc(c, p, nu));
+                CK(cudaMemsetAsync(*p, 0, nu * sizeof(double), s));
+            }
+            for (auto* p : {&Lv.v32.x2, &Lv.v32.d2, &Lv.v32.acc2, &Lv.v32.acc3}) {
+                CKS(dalloc(c, p, nu));
+                CK(cudaMemsetAsync(*p, 0, nu * sizeof(float), s));
+            }
+        }
         CK(cudaMemsetAsync(Lv.v64.d, 0, nu * sizeof(double), s));
         CK(cudaMemsetAsync(Lv.v32.d, 0, nu * sizeof(float), s));
         CKS(dalloc(c, &Lv.v64.mu, nc));
@@ -2037,6 +2134,7 @@ void stokes_default_options(stokes_options* opt) {
     opt->gram_schmidt = 1;
     opt->wait_limit_s = 1.0;
     opt->batch_vcycle = 0;
+    opt->fused_smoother = 0;
 }
 
 const char* stokes_strerror(stokes_status s) {
@@ -2685,10 +2783,18 @@ stokes_status stokes_smooth(stokes_ctx* c, int level, int prec, const void* b, v
     if (level < 1) return fail(STOKES_EINVAL, "smoothing needs level >= 1");
     if (!b || !x) return fail(STOKES_EINVAL, "null vector");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (prec == STOKES_FP32)
-        return smooth<float>(c, level, static_cast<const float*>(b), static_cast<float*>(x), zero_guess != 0, s);
-    if (prec == STOKES_FP64)
-        return smooth<double>(c, level, static_cast<const double*>(b), static_cast<double*>(x), zero_guess != 0, s);
+    if (prec == STOKES_FP32) {
+        const float* bf = static_cast<const float*>(b);
+        float* xf = static_cast<float*>(x);
+        return fused_level<float>(c, level) ? smooth_fused<float>(c, level, bf, xf, zero_guess != 0, nullptr, s)
+                                            : smooth<float>(c, level, bf, xf, zero_guess != 0, s);
+    }
+    if (prec == STOKES_FP64) {
+        const double* bd = static_cast<const double*>(b);
+        double* xd = static_cast<double*>(x);
+        return fused_level<double>(c, level) ? smooth_fused<double>(c, level, bd, xd, zero_guess != 0, nullptr, s)
+                                             : smooth<double>(c, level, bd, xd, zero_guess != 0, s);
+    }
     return fail(STOKES_EINVAL, "bad precision");
 }
 

@@ -73,6 +73,41 @@ __global__ void __launch_bounds__(BS, sizeof(T) == 4 ? 384 / BS : 1) k_cell_atom
 // the order of the sums.
 constexpr int kSplitCells = 32;   // cells per block; block = 3 warps
 
+// The cell product of the component-split kernels: u holds the nodal values of this thread's
+// component on entry and the cell's output row c (without mu h) on return; all threads of the
+// block take part (the exchange has a barrier).
+__device__ __forceinline__ void split_apply(float (&u)[27], float (&D)[3][3][27][kSplitCells], int c, int lc) {
+    q2::interp<0>(u);
+    q2::interp<1>(u);
+    q2::interp<2>(u);
+    float g[27];
+    q2::deriv<0, false>(u, g);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) D[c][0][q][lc] = g[q];
+    q2::deriv<1, false>(u, g);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) D[c][1][q][lc] = g[q];
+    q2::deriv<2, false>(u, g);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) D[c][2][q][lc] = g[q];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 27; ++q) u[q] = 0.0f;
+    // d = 0, 1, 2 at compile time; the diagonal term (d == c) carries the factor 2
+#pragma unroll
+    for (int q = 0; q < 27; ++q) g[q] = c == 0 ? D[0][0][q][lc] : D[c][0][q][lc] + D[0][c][q][lc];
+    if (c == 0) q2::derivT_w<0, 2>(g, u); else q2::derivT_w<0, 1>(g, u);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) g[q] = c == 1 ? D[1][1][q][lc] : D[c][1][q][lc] + D[1][c][q][lc];
+    if (c == 1) q2::derivT_w<1, 2>(g, u); else q2::derivT_w<1, 1>(g, u);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) g[q] = c == 2 ? D[2][2][q][lc] : D[c][2][q][lc] + D[2][c][q][lc];
+    if (c == 2) q2::derivT_w<2, 2>(g, u); else q2::derivT_w<2, 1>(g, u);
+    q2::interpT<0>(u);
+    q2::interpT<1>(u);
+    q2::interpT<2>(u);
+}
+
 __global__ void __launch_bounds__(3 * kSplitCells) k_cell_split(BrickArgs<float> a, float* acc) {
     __shared__ float D[3][3][27][kSplitCells];   // D[c][e][q][cell] = d_e U_c at Gauss point q
     const int c = threadIdx.x / kSplitCells;     // warp-uniform
@@ -100,36 +135,7 @@ __global__ void __launch_bounds__(3 * kSplitCells) k_cell_split(BrickArgs<float>
             }
         }
     }
-    q2::interp<0>(u);
-    q2::interp<1>(u);
-    q2::interp<2>(u);
-    float g[27];
-    q2::deriv<0, false>(u, g);
-#pragma unroll
-    for (int q = 0; q < 27; ++q) D[c][0][q][lc] = g[q];
-    q2::deriv<1, false>(u, g);
-#pragma unroll
-    for (int q = 0; q < 27; ++q) D[c][1][q][lc] = g[q];
-    q2::deriv<2, false>(u, g);
-#pragma unroll
-    for (int q = 0; q < 27; ++q) D[c][2][q][lc] = g[q];
-    __syncthreads();
-    float w[27];
-#pragma unroll
-    for (int q = 0; q < 27; ++q) w[q] = 0.0f;
-    // d = 0, 1, 2 at compile time; the diagonal term (d == c) carries the factor 2
-#pragma unroll
-    for (int q = 0; q < 27; ++q) g[q] = c == 0 ? D[0][0][q][lc] : D[c][0][q][lc] + D[0][c][q][lc];
-    if (c == 0) q2::derivT_w<0, 2>(g, w); else q2::derivT_w<0, 1>(g, w);
-#pragma unroll
-    for (int q = 0; q < 27; ++q) g[q] = c == 1 ? D[1][1][q][lc] : D[c][1][q][lc] + D[1][c][q][lc];
-    if (c == 1) q2::derivT_w<1, 2>(g, w); else q2::derivT_w<1, 1>(g, w);
-#pragma unroll
-    for (int q = 0; q < 27; ++q) g[q] = c == 2 ? D[2][2][q][lc] : D[c][2][q][lc] + D[2][c][q][lc];
-    if (c == 2) q2::derivT_w<2, 2>(g, w); else q2::derivT_w<2, 1>(g, w);
-    q2::interpT<0>(w);
-    q2::interpT<1>(w);
-    q2::interpT<2>(w);
+    split_apply(u, D, c, lc);
     if (!valid) return;
     const float sc = a.mu[cell] * a.h;
     float* out = acc + size_t(c) * a.nodes + base;
@@ -142,7 +148,137 @@ __global__ void __launch_bounds__(3 * kSplitCells) k_cell_split(BrickArgs<float>
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 if (bj || (2 * ci + i == 0) || (2 * ci + i == M - 1)) continue;
-                atomicAdd(out + i + M * (j + M * k), w[i + 3 * j + 9 * k] * sc);
+                atomicAdd(out + i + M * (j + M * k), u[i + 3 * j + 9 * k] * sc);
+            }
+        }
+    }
+}
+
+// ---- the two operators with the pending Chebyshev step applied at the gather (ChebGather)
+// The step's buffers are passed as separate restrict-qualified parameters: the owners' stores
+// cannot alias the gathered loads, so the loads of all 27 nodes may be issued before any store
+// (through the struct the compiler has to keep each node's loads behind the previous node's
+// stores, one memory latency per node).
+template <typename T>
+__device__ __forceinline__ T cheb_node(const T* __restrict__ acc_prev, const T* __restrict__ b,
+                                       const T* __restrict__ dinv, const T* __restrict__ d_old,
+                                       const T* __restrict__ x_old, T* __restrict__ d_new, T* __restrict__ x_new,
+                                       T* __restrict__ acc_zero, T c1, T c2, size_t i, bool own) {
+    const T dn = (c1 != T(0) ? c1 * d_old[i] : T(0)) + c2 * (dinv[i] * (b[i] - acc_prev[i]));
+    const T xn = x_old[i] + dn;
+    if (own) {
+        d_new[i] = dn;
+        x_new[i] = xn;
+        if (acc_zero) acc_zero[i] = T(0);
+    }
+    return xn;
+}
+
+template <typename T, int BS>
+__global__ void __launch_bounds__(BS, sizeof(T) == 4 ? 384 / BS : 1)
+    k_cell_cheb(BrickArgs<T> a, const T* __restrict__ acc_prev, const T* __restrict__ b, const T* __restrict__ dinv,
+                const T* __restrict__ d_old, const T* __restrict__ x_old, T* __restrict__ d_new,
+                T* __restrict__ x_new, T* __restrict__ acc_zero, T c1, T c2, T* __restrict__ acc) {
+    const size_t cell = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (cell >= size_t(a.n) * a.n * a.n) return;
+    const int ci = int(cell % a.n), cj = int((cell / a.n) % a.n), ck = int(cell / (size_t(a.n) * a.n));
+    const int M = a.M;
+    const size_t base = size_t(2 * ci) + size_t(M) * (size_t(2 * cj) + size_t(M) * size_t(2 * ck));
+    T u[3][27], w[3][27];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const bool bk = (2 * ck + k == 0) || (2 * ck + k == M - 1);
+        const bool ok = k < 2 || ck == a.n - 1;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const bool bj = bk || (2 * cj + j == 0) || (2 * cj + j == M - 1);
+            const bool oj = ok && (j < 2 || cj == a.n - 1);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const bool bnd = bj || (2 * ci + i == 0) || (2 * ci + i == M - 1);
+                const bool own = oj && (i < 2 || ci == a.n - 1);
+                const size_t off = base + size_t(i + M * (j + M * k));
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const T xn = cheb_node(acc_prev, b, dinv, d_old, x_old, d_new, x_new, acc_zero, c1, c2,
+                                           size_t(c) * a.nodes + off, own);
+                    u[c][i + 3 * j + 9 * k] = bnd ? T(0) : xn;
+                }
+            }
+        }
+    }
+    q2::cell_A(u, w);
+    const T sc = a.mu[cell] * a.h;
+    T* out = acc + base;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const bool bk = (2 * ck + k == 0) || (2 * ck + k == M - 1);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const bool bj = bk || (2 * cj + j == 0) || (2 * cj + j == M - 1);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                if (bj || (2 * ci + i == 0) || (2 * ci + i == M - 1)) continue;
+                const int off = i + M * (j + M * k);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) atomicAdd(out + c * a.nodes + off, w[c][i + 3 * j + 9 * k] * sc);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(3 * kSplitCells)
+    k_cell_split_cheb(BrickArgs<float> a, const float* __restrict__ acc_prev, const float* __restrict__ b,
+                      const float* __restrict__ dinv, const float* __restrict__ d_old, const float* __restrict__ x_old,
+                      float* __restrict__ d_new, float* __restrict__ x_new, float* __restrict__ acc_zero, float c1,
+                      float c2, float* __restrict__ acc) {
+    __shared__ float D[3][3][27][kSplitCells];
+    const int c = threadIdx.x / kSplitCells;
+    const int lc = threadIdx.x % kSplitCells;
+    const size_t cells = size_t(a.n) * a.n * a.n;
+    const size_t cell = size_t(blockIdx.x) * kSplitCells + lc;
+    const bool valid = cell < cells;
+    const int ci = valid ? int(cell % a.n) : 0;
+    const int cj = valid ? int((cell / a.n) % a.n) : 0;
+    const int ck = valid ? int(cell / (size_t(a.n) * a.n)) : 0;
+    const int M = a.M;
+    const size_t base = size_t(2 * ci) + size_t(M) * (size_t(2 * cj) + size_t(M) * size_t(2 * ck));
+    const size_t cbase = size_t(c) * a.nodes + base;
+    float u[27];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const bool bk = (2 * ck + k == 0) || (2 * ck + k == M - 1);
+        const bool ok = k < 2 || ck == a.n - 1;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const bool bj = bk || (2 * cj + j == 0) || (2 * cj + j == M - 1);
+            const bool oj = ok && (j < 2 || cj == a.n - 1);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const bool bnd = bj || (2 * ci + i == 0) || (2 * ci + i == M - 1);
+                const bool own = oj && (i < 2 || ci == a.n - 1);
+                float xn = 0.0f;
+                if (valid)
+                    xn = cheb_node(acc_prev, b, dinv, d_old, x_old, d_new, x_new, acc_zero, c1, c2,
+                                   cbase + size_t(i + M * (j + M * k)), own);
+                u[i + 3 * j + 9 * k] = (!valid || bnd) ? 0.0f : xn;
+            }
+        }
+    }
+    split_apply(u, D, c, lc);
+    if (!valid) return;
+    const float sc = a.mu[cell] * a.h;
+    float* out = acc + cbase;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const bool bk = (2 * ck + k == 0) || (2 * ck + k == M - 1);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const bool bj = bk || (2 * cj + j == 0) || (2 * cj + j == M - 1);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                if (bj || (2 * ci + i == 0) || (2 * ci + i == M - 1)) continue;
+                atomicAdd(out + i + M * (j + M * k), u[i + 3 * j + 9 * k] * sc);
             }
         }
     }
@@ -168,11 +304,12 @@ inline unsigned consume_blocks(size_t n, size_t per) {
     return unsigned(nb < 1 ? 1 : (nb < 4864 ? nb : 4864));
 }
 
-// d = c1 d + c2 dinv (b - acc); x += d; acc = 0
+// d_dst = c1 d_src + c2 dinv (b - acc); x_dst = x_src + d_dst; acc = 0 (and zero2 = 0 when given).
+// The (d, x) outputs may be the inputs (in place): each entry is read before it is written.
 template <typename T>
 __global__ void __launch_bounds__(256) k_consume_cheb(size_t n, T* __restrict__ acc, const T* __restrict__ b,
-                                                     const T* __restrict__ dinv, T* __restrict__ d, T* __restrict__ x,
-                                                     T c1, T c2, bool vec) {
+                                                     const T* __restrict__ dinv, const T* d_src, const T* x_src,
+                                                     T* d, T* x, T* __restrict__ zero2, T c1, T c2, bool vec) {
     using V = typename Vec4<T>::type;
     constexpr int W = sizeof(V) / sizeof(T);
     constexpr int U = kConsumeItems;
@@ -187,8 +324,8 @@ __global__ void __launch_bounds__(256) k_consume_cheb(size_t n, T* __restrict__ 
                 A[u] = reinterpret_cast<const V*>(acc)[v];
                 B[u] = reinterpret_cast<const V*>(b)[v];
                 Di[u] = reinterpret_cast<const V*>(dinv)[v];
-                Dd[u] = reinterpret_cast<const V*>(d)[v];
-                X[u] = reinterpret_cast<const V*>(x)[v];
+                Dd[u] = reinterpret_cast<const V*>(d_src)[v];
+                X[u] = reinterpret_cast<const V*>(x_src)[v];
             }
         }
 #pragma unroll
@@ -209,21 +346,24 @@ __global__ void __launch_bounds__(256) k_consume_cheb(size_t n, T* __restrict__ 
             reinterpret_cast<V*>(d)[v] = Dd[u];
             reinterpret_cast<V*>(x)[v] = X[u];
             reinterpret_cast<V*>(acc)[v] = vzero(A[u]);
+            if (zero2) reinterpret_cast<V*>(zero2)[v] = vzero(A[u]);
         }
     }
     const size_t tail_stride = size_t(gridDim.x) * blockDim.x;
     for (size_t i = nv * W + size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += tail_stride) {
-        const T dn = (c1 != T(0) ? c1 * d[i] : T(0)) + c2 * (dinv[i] * (b[i] - acc[i]));
+        const T dn = (c1 != T(0) ? c1 * d_src[i] : T(0)) + c2 * (dinv[i] * (b[i] - acc[i]));
+        const T xn = x_src[i] + dn;
         d[i] = dn;
-        x[i] += dn;
+        x[i] = xn;
         acc[i] = T(0);
+        if (zero2) zero2[i] = T(0);
     }
 }
 
-// r = b - acc; acc = 0
+// r = b - acc; acc = 0 (and zero2 = 0 when given)
 template <typename T>
 __global__ void __launch_bounds__(256) k_consume_resid(size_t n, T* __restrict__ acc, const T* __restrict__ b,
-                                                      T* __restrict__ r, bool vec) {
+                                                      T* __restrict__ r, T* __restrict__ zero2, bool vec) {
     using V = typename Vec4<T>::type;
     constexpr int W = sizeof(V) / sizeof(T);
     constexpr int U = kConsumeItems;
@@ -251,12 +391,14 @@ __global__ void __launch_bounds__(256) k_consume_resid(size_t n, T* __restrict__
             for (int q = 0; q < W; ++q) r_[q] = b_[q] - a_[q];
             reinterpret_cast<V*>(r)[v] = R;
             reinterpret_cast<V*>(acc)[v] = vzero(A[u]);
+            if (zero2) reinterpret_cast<V*>(zero2)[v] = vzero(A[u]);
         }
     }
     const size_t tail_stride = size_t(gridDim.x) * blockDim.x;
     for (size_t i = nv * W + size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += tail_stride) {
         r[i] = b[i] - acc[i];
         acc[i] = T(0);
+        if (zero2) zero2[i] = T(0);
     }
 }
 
@@ -336,11 +478,12 @@ cudaError_t launch_cell_epi(const BrickArgs<T>& a, int epi, T* acc, size_t n_u, 
     auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
     if (epi == EPI_RESID) {
         const bool vec = al(acc) && al(a.b) && al(a.dst);
-        LAUNCH(PROF_SMOOTH_VEC, s, (k_consume_resid<T><<<blocks, 256, 0, s>>>(n_u, acc, a.b, a.dst, vec)));
+        LAUNCH(PROF_SMOOTH_VEC, s, (k_consume_resid<T><<<blocks, 256, 0, s>>>(n_u, acc, a.b, a.dst, nullptr, vec)));
     } else {
         const bool vec = al(acc) && al(a.b) && al(a.dinv) && al(a.d) && al(a.src);
-        LAUNCH(PROF_SMOOTH_VEC, s, (k_consume_cheb<T><<<blocks, 256, 0, s>>>(n_u, acc, a.b, a.dinv, a.d,
-                                                                            const_cast<T*>(a.src), a.c1, a.c2, vec)));
+        LAUNCH(PROF_SMOOTH_VEC, s, (k_consume_cheb<T><<<blocks, 256, 0, s>>>(n_u, acc, a.b, a.dinv, a.d, a.src, a.d,
+                                                                            const_cast<T*>(a.src), nullptr, a.c1,
+                                                                            a.c2, vec)));
     }
     return cudaGetLastError();
 }
@@ -356,13 +499,83 @@ cudaError_t launch_consume(int epi, size_t n, T* acc, const T* b, const T* dinv,
     auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
     if (epi == EPI_RESID) {
         const bool vec = al(acc) && al(b) && al(x_or_r);
-        LAUNCH(PROF_SMOOTH_VEC, s, (k_consume_resid<T><<<blocks, 256, 0, s>>>(n, acc, b, x_or_r, vec)));
+        LAUNCH(PROF_SMOOTH_VEC, s, (k_consume_resid<T><<<blocks, 256, 0, s>>>(n, acc, b, x_or_r, nullptr, vec)));
     } else {
         const bool vec = al(acc) && al(b) && al(dinv) && al(d) && al(x_or_r);
-        LAUNCH(PROF_SMOOTH_VEC, s, (k_consume_cheb<T><<<blocks, 256, 0, s>>>(n, acc, b, dinv, d, x_or_r, T(c1), T(c2), vec)));
+        LAUNCH(PROF_SMOOTH_VEC, s, (k_consume_cheb<T><<<blocks, 256, 0, s>>>(n, acc, b, dinv, d, x_or_r, d, x_or_r,
+                                                                            nullptr, T(c1), T(c2), vec)));
     }
     return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_cell_cheb(int kernel, const LevelGeom& geo, const T* mu, const ChebGather<T>& g, T* acc,
+                             cudaStream_t s) {
+    BrickArgs<T> a{};
+    a.n = geo.n;
+    a.M = geo.M;
+    a.nodes = geo.nodes;
+    a.h = T(geo.h);
+    a.mu = mu;
+    const size_t cells = size_t(a.n) * a.n * a.n;
+    const int cls = sizeof(T) == 4 ? PROF_VMULT_F32 : PROF_VMULT_F64;
+    if constexpr (sizeof(T) == 4) {
+        if (kernel == kSplitKernel) {
+            LAUNCH(cls, s, (k_cell_split_cheb<<<unsigned((cells + kSplitCells - 1) / kSplitCells), 3 * kSplitCells, 0,
+                                                s>>>(a, g.acc_prev, g.b, g.dinv, g.d_old, g.x_old, g.d_new, g.x_new,
+                                                     g.acc_zero, g.c1, g.c2, acc)));
+            return cudaGetLastError();
+        }
+    }
+#define STK_CHEB_ARGS a, g.acc_prev, g.b, g.dinv, g.d_old, g.x_old, g.d_new, g.x_new, g.acc_zero, g.c1, g.c2, acc
+    if (kernel == 64)
+        LAUNCH(cls, s, (k_cell_cheb<T, 64><<<unsigned((cells + 63) / 64), 64, 0, s>>>(STK_CHEB_ARGS)));
+    else if (kernel == 256)
+        LAUNCH(cls, s, (k_cell_cheb<T, 256><<<unsigned((cells + 255) / 256), 256, 0, s>>>(STK_CHEB_ARGS)));
+    else
+        LAUNCH(cls, s, (k_cell_cheb<T, 128><<<unsigned((cells + 127) / 128), 128, 0, s>>>(STK_CHEB_ARGS)));
+#undef STK_CHEB_ARGS
+    return cudaGetLastError();
+}
+template cudaError_t launch_cell_cheb<float>(int, const LevelGeom&, const float*, const ChebGather<float>&, float*,
+                                             cudaStream_t);
+template cudaError_t launch_cell_cheb<double>(int, const LevelGeom&, const double*, const ChebGather<double>&, double*,
+                                              cudaStream_t);
+
+template <typename T>
+cudaError_t launch_accumulate(int kernel, const LevelGeom& geo, const T* mu, const T* src, T* acc, cudaStream_t s) {
+    BrickArgs<T> a{};
+    a.n = geo.n;
+    a.M = geo.M;
+    a.nodes = geo.nodes;
+    a.h = T(geo.h);
+    a.mu = mu;
+    a.src = src;
+    return accumulate<T>(a, acc, kernel == 0 ? 128 : kernel, nullptr, s);
+}
+template cudaError_t launch_accumulate<float>(int, const LevelGeom&, const float*, const float*, float*, cudaStream_t);
+template cudaError_t launch_accumulate<double>(int, const LevelGeom&, const double*, const double*, double*,
+                                               cudaStream_t);
+
+template <typename T>
+cudaError_t launch_consume2(int epi, size_t n, T* acc, const T* b, const T* dinv, const T* d_src, const T* x_src,
+                            T* d_dst, T* x_dst, T* zero2, double c1, double c2, cudaStream_t s) {
+    const unsigned blocks = consume_blocks(n, sizeof(T) == 4 ? 4 : 2);
+    auto al = [](const void* p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+    if (epi == EPI_RESID) {
+        const bool vec = al(acc) && al(b) && al(x_dst) && al(zero2);
+        LAUNCH(PROF_SMOOTH_VEC, s, (k_consume_resid<T><<<blocks, 256, 0, s>>>(n, acc, b, x_dst, zero2, vec)));
+    } else {
+        const bool vec = al(acc) && al(b) && al(dinv) && al(d_src) && al(x_src) && al(d_dst) && al(x_dst) && al(zero2);
+        LAUNCH(PROF_SMOOTH_VEC, s, (k_consume_cheb<T><<<blocks, 256, 0, s>>>(n, acc, b, dinv, d_src, x_src, d_dst, x_dst,
+                                                                            zero2, T(c1), T(c2), vec)));
+    }
+    return cudaGetLastError();
+}
+template cudaError_t launch_consume2<float>(int, size_t, float*, const float*, const float*, const float*, const float*,
+                                            float*, float*, float*, double, double, cudaStream_t);
+template cudaError_t launch_consume2<double>(int, size_t, double*, const double*, const double*, const double*,
+                                             const double*, double*, double*, double*, double, double, cudaStream_t);
 template cudaError_t launch_consume<float>(int, size_t, float*, const float*, const float*, float*, float*, double,
                                            double, cudaStream_t);
 template cudaError_t launch_consume<double>(int, size_t, double*, const double*, const double*, double*, double*,

@@ -345,6 +345,42 @@ inline size_t plane_threads(const PlaneLayout& L) {
 PlaneLayout brick_layout(int n);
 // Shared-memory opt-in of every brick kernel instantiation (call once before any launch or capture).
 cudaError_t brick_configure();
+// One Chebyshev step carried by the next product (the cell and component-split operators).
+// Chebyshev step k ends with d' = c1 d + c2 dinv (b - A x), x' = x + d'; instead of a separate
+// consumer pass, the kernel forming A x' computes d', x' at every node it gathers (the same
+// arithmetic in the same order), uses x' as its operand, and the node's owner cell (local index 0
+// or 1 along each axis, or 2 in the last cell of the level) stores d', x' into the other buffers of
+// the (d, x) pairs and clears acc_zero there. The pairs alternate, so no kernel reads a value that
+// another cell of the same launch writes; the accumulators rotate over three buffers: one holds
+// A x (read), one receives A x' (atomic adds), one is cleared for the launch after next.
+template <typename T>
+struct ChebGather {
+    const T* acc_prev;   // A x, complete
+    const T* b;
+    const T* dinv;
+    const T* d_old;
+    const T* x_old;
+    T* d_new;            // written at owned nodes (all nodes, boundary ones included, across the launch)
+    T* x_new;
+    T* acc_zero;         // cleared at owned nodes (null: nothing to clear)
+    T c1, c2;
+};
+
+// acc += A x' with x' from the pending step g (kernel: 0, 64, 128, 256 the cell kernel's block
+// size, 3 the component-split kernel on FP32 levels).
+template <typename T>
+cudaError_t launch_cell_cheb(int kernel, const LevelGeom& geo, const T* mu, const ChebGather<T>& g, T* acc,
+                             cudaStream_t s);
+// acc += A src with the cell (kernel 0, 64, 128, 256) or component-split (3, FP32) operator.
+template <typename T>
+cudaError_t launch_accumulate(int kernel, const LevelGeom& geo, const T* mu, const T* src, T* acc, cudaStream_t s);
+// The consumers with separate input and output (d, x) buffers (equal pointers: in place) and a
+// second accumulator to clear (zero2, may be null). epi 1: r = b - acc (r in x_dst); epi 2: the
+// Chebyshev update.
+template <typename T>
+cudaError_t launch_consume2(int epi, size_t n, T* acc, const T* b, const T* dinv, const T* d_src, const T* x_src,
+                            T* d_dst, T* x_dst, T* zero2, double c1, double c2, cudaStream_t s);
+
 // Tensor-core level operator (brick_tc.cu): the f16 table of 5400 A_hat in the layout its
 // kernel reads (tc_table_bytes() bytes, built once by tc_build_table), a device status word
 // (bit 0: a bounded wait for the MMAs gave up) and that wait's limit in nanoseconds.

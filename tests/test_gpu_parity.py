@@ -451,6 +451,39 @@ def test_graph_replay_matches_kernel_launches(capi, prec, kernel):
             assert rel(a, b) <= (1e-13 if prec == 0 else 1e-6)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 3])
+def test_fused_smoother_matches_separate_passes(capi, prec, kernel):
+    """The smoother with each Chebyshev step carried by the next product (fused_smoother 1)
+    computes what the separate vector passes (0, the default) compute: the same per-node arithmetic,
+    so smoothing steps of every level (zero and non-zero initial guess) and whole V-cycles agree to
+    the rounding of the atomic sums' order."""
+    p, m, mus, G, ops, F = oracle_problem("n12")
+    dt = torch.float64 if prec == 0 else torch.float32
+    out = []
+    for fused in (0, 1):
+        opt = capi.stokes_default_options()
+        opt.vmult_kernel = kernel
+        opt.fused_smoother = fused
+        ctx = capi.stokes_setup_problem(p, options=opt)
+        res = []
+        for l in range(1, p.n_levels):
+            lev = G.levels[l]
+            b = dev(si.uniform(5100 + l, lev.mesh.n_u) * lev.free, dt)
+            for zero in (True, False):
+                x = dev(si.uniform(5200 + l, lev.mesh.n_u) * lev.free, dt)
+                capi.stokes_smooth(ctx, l, prec, b, x, zero)
+                res.append(host(x))
+        rhs = dev(si.uniform(5300, ctx.n_u), dt)
+        x = torch.empty_like(rhs)
+        capi.gmg_vcycle(ctx, prec, rhs, x)
+        res.append(host(x))
+        out.append(res)
+        ctx.close()
+    for a, b in zip(out[0], out[1]):
+        assert rel(b, a) <= (1e-13 if prec == 0 else 1e-6)
+
+
 def test_batch_solve_matches_individual_solves(capi):
     """stokes_batch_solve over problems of different sizes and level counts runs the same FGMRES as
     stokes_solve: iteration counts within 1 (the batched V-cycle and the single-problem graph sum
