@@ -35,7 +35,62 @@ __global__ void __launch_bounds__(BX * BY * BZ, sizeof(T) == 4 ? 3 : 1) k_brick(
 // ---- cell-parallel variant: one thread per cell, atomic adds into a zeroed accumulator;
 // the consumer kernels below run the epilogue and clear the accumulator again.
 // Threads per block BS: 64, 128 or 256 (the register budget per thread is the same, 170 for FP32).
-template <typename T, int BS>
+// FP32 scatter of one x-row of a cell (the values of local nodes (0..2, j, k)) with one 8-byte
+// and one 4-byte atomic add instead of three 4-byte ones. The row's first node lies at element
+// offset c nodes + 2ci + M (2cj + j) + M^2 (2ck + k), whose parity is (c + j + k) mod 2 (nodes =
+// M^3 and M are odd), so the pair (0,1) or (1,2) is 8-byte aligned when the accumulator is; the
+// parity is a compile-time constant in the cell kernel and warp-uniform in the split kernel.
+// Measured on the operator's gather-and-scatter alone at 128^3: 0.229 ms with 81 single adds per
+// cell, 0.180 ms with 27 pairs and 27 singles.
+__device__ __forceinline__ void add_row3(float* row, int parity, float v0, float v1, float v2) {
+    if (parity == 0) {
+        atomicAdd(reinterpret_cast<float2*>(row), make_float2(v0, v1));
+        atomicAdd(row + 2, v2);
+    } else {
+        atomicAdd(row, v0);
+        atomicAdd(reinterpret_cast<float2*>(row + 1), make_float2(v1, v2));
+    }
+}
+
+// Scatter of a cell's scaled output w into acc (boundary nodes untouched: rows on the boundary
+// are skipped, boundary nodes inside a row get 0 added, so acc stays 0 there).
+template <typename T, bool PAIRS>
+__device__ __forceinline__ void scatter_cell(T* out, size_t nodes, int M, int ci, int cj, int ck, const T (&w)[3][27]) {
+    if constexpr (PAIRS && sizeof(T) == 4) {
+        const bool b0 = ci == 0, b2 = 2 * ci + 2 == M - 1;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const bool bk = (2 * ck + k == 0) || (2 * ck + k == M - 1);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                if (bk || (2 * cj + j == 0) || (2 * cj + j == M - 1)) continue;
+                const int off = M * (j + M * k);
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    add_row3(out + c * nodes + off, (c + j + k) & 1, b0 ? 0.0f : w[c][3 * j + 9 * k],
+                             w[c][1 + 3 * j + 9 * k], b2 ? 0.0f : w[c][2 + 3 * j + 9 * k]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const bool bk = (2 * ck + k == 0) || (2 * ck + k == M - 1);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const bool bj = bk || (2 * cj + j == 0) || (2 * cj + j == M - 1);
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    if (bj || (2 * ci + i == 0) || (2 * ci + i == M - 1)) continue;
+                    const int off = i + M * (j + M * k);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) atomicAdd(out + c * nodes + off, w[c][i + 3 * j + 9 * k]);
+                }
+            }
+        }
+    }
+}
+
+template <typename T, int BS, bool PAIRS>
 __global__ void __launch_bounds__(BS, sizeof(T) == 4 ? 384 / BS : 1) k_cell_atomic(BrickArgs<T> a, T* acc) {
     const size_t cell = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (cell >= size_t(a.n) * a.n * a.n) return;
@@ -45,21 +100,7 @@ __global__ void __launch_bounds__(BS, sizeof(T) == 4 ? 384 / BS : 1) k_cell_atom
     if (!brick_compute<T, 1, 1, 1>(a, ci, cj, ck, 0, w)) return;
     const int M = a.M;
     T* out = acc + (size_t(2 * ci) + size_t(M) * (size_t(2 * cj) + size_t(M) * size_t(2 * ck)));
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const bool bk = (2 * ck + k == 0) || (2 * ck + k == M - 1);
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const bool bj = bk || (2 * cj + j == 0) || (2 * cj + j == M - 1);
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                if (bj || (2 * ci + i == 0) || (2 * ci + i == M - 1)) continue;
-                const int off = i + M * (j + M * k);
-#pragma unroll
-                for (int c = 0; c < 3; ++c) atomicAdd(out + c * a.nodes + off, w[c][i + 3 * j + 9 * k]);
-            }
-        }
-    }
+    scatter_cell<T, PAIRS>(out, a.nodes, M, ci, cj, ck, w);
 }
 
 // ---- component-split variant: three threads per cell, warp c of each group of three computes
@@ -108,6 +149,35 @@ __device__ __forceinline__ void split_apply(float (&u)[27], float (&D)[3][3][27]
     q2::interpT<2>(u);
 }
 
+// Scatter of component c of a cell's output row (times sc) into acc at out = acc + c nodes +
+// the cell's first node; with PAIRS the rows go as pairs (parity (c + j + k) mod 2, uniform over
+// the warp of component c).
+template <bool PAIRS>
+__device__ __forceinline__ void split_scatter(float* out, int c, int M, int ci, int cj, int ck, float sc,
+                                              const float (&u)[27]) {
+    const bool b0 = ci == 0, b2 = 2 * ci + 2 == M - 1;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const bool bk = (2 * ck + k == 0) || (2 * ck + k == M - 1);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            if (bk || (2 * cj + j == 0) || (2 * cj + j == M - 1)) continue;
+            float* row = out + M * (j + M * k);
+            if (PAIRS) {
+                add_row3(row, (c + j + k) & 1, b0 ? 0.0f : u[3 * j + 9 * k] * sc, u[1 + 3 * j + 9 * k] * sc,
+                         b2 ? 0.0f : u[2 + 3 * j + 9 * k] * sc);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    if ((i == 0 && b0) || (i == 2 && b2)) continue;
+                    atomicAdd(row + i, u[i + 3 * j + 9 * k] * sc);
+                }
+            }
+        }
+    }
+}
+
+template <bool PAIRS>
 __global__ void __launch_bounds__(3 * kSplitCells) k_cell_split(BrickArgs<float> a, float* acc) {
     __shared__ float D[3][3][27][kSplitCells];   // D[c][e][q][cell] = d_e U_c at Gauss point q
     const int c = threadIdx.x / kSplitCells;     // warp-uniform
@@ -137,21 +207,7 @@ __global__ void __launch_bounds__(3 * kSplitCells) k_cell_split(BrickArgs<float>
     }
     split_apply(u, D, c, lc);
     if (!valid) return;
-    const float sc = a.mu[cell] * a.h;
-    float* out = acc + size_t(c) * a.nodes + base;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const bool bk = (2 * ck + k == 0) || (2 * ck + k == M - 1);
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const bool bj = bk || (2 * cj + j == 0) || (2 * cj + j == M - 1);
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                if (bj || (2 * ci + i == 0) || (2 * ci + i == M - 1)) continue;
-                atomicAdd(out + i + M * (j + M * k), u[i + 3 * j + 9 * k] * sc);
-            }
-        }
-    }
+    split_scatter<PAIRS>(acc + size_t(c) * a.nodes + base, c, M, ci, cj, ck, a.mu[cell] * a.h, u);
 }
 
 // ---- the two operators with the pending Chebyshev step applied at the gather (ChebGather)
@@ -227,6 +283,7 @@ __global__ void __launch_bounds__(BS, sizeof(T) == 4 ? 384 / BS : 1)
     }
 }
 
+template <bool PAIRS>
 __global__ void __launch_bounds__(3 * kSplitCells)
     k_cell_split_cheb(BrickArgs<float> a, const float* __restrict__ acc_prev, const float* __restrict__ b,
                       const float* __restrict__ dinv, const float* __restrict__ d_old, const float* __restrict__ x_old,
@@ -267,21 +324,7 @@ __global__ void __launch_bounds__(3 * kSplitCells)
     }
     split_apply(u, D, c, lc);
     if (!valid) return;
-    const float sc = a.mu[cell] * a.h;
-    float* out = acc + cbase;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const bool bk = (2 * ck + k == 0) || (2 * ck + k == M - 1);
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const bool bj = bk || (2 * cj + j == 0) || (2 * cj + j == M - 1);
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                if (bj || (2 * ci + i == 0) || (2 * ci + i == M - 1)) continue;
-                atomicAdd(out + i + M * (j + M * k), u[i + 3 * j + 9 * k] * sc);
-            }
-        }
-    }
+    split_scatter<PAIRS>(acc + cbase, c, M, ci, cj, ck, a.mu[cell] * a.h, u);
 }
 
 // Consume the accumulated product and clear it. Constrained entries need no special
@@ -432,12 +475,18 @@ template <typename T>
 cudaError_t launch_cell(const BrickArgs<T>& a, T* acc, int bs, cudaStream_t s) {
     const size_t cells = size_t(a.n) * a.n * a.n;
     const int cls = sizeof(T) == 4 ? PROF_VMULT_F32 : PROF_VMULT_F64;
-    if (bs == 64)
-        LAUNCH(cls, s, (k_cell_atomic<T, 64><<<unsigned((cells + 63) / 64), 64, 0, s>>>(a, acc)));
-    else if (bs == 256)
-        LAUNCH(cls, s, (k_cell_atomic<T, 256><<<unsigned((cells + 255) / 256), 256, 0, s>>>(a, acc)));
-    else
-        LAUNCH(cls, s, (k_cell_atomic<T, 128><<<unsigned((cells + 127) / 128), 128, 0, s>>>(a, acc)));
+    // pair atomics need an 8-byte aligned accumulator (callers may pass offset views)
+    const bool pairs = (reinterpret_cast<uintptr_t>(acc) & 7u) == 0;
+    if (bs == 64) {
+        if (pairs) LAUNCH(cls, s, (k_cell_atomic<T, 64, true><<<unsigned((cells + 63) / 64), 64, 0, s>>>(a, acc)));
+        else LAUNCH(cls, s, (k_cell_atomic<T, 64, false><<<unsigned((cells + 63) / 64), 64, 0, s>>>(a, acc)));
+    } else if (bs == 256) {
+        if (pairs) LAUNCH(cls, s, (k_cell_atomic<T, 256, true><<<unsigned((cells + 255) / 256), 256, 0, s>>>(a, acc)));
+        else LAUNCH(cls, s, (k_cell_atomic<T, 256, false><<<unsigned((cells + 255) / 256), 256, 0, s>>>(a, acc)));
+    } else {
+        if (pairs) LAUNCH(cls, s, (k_cell_atomic<T, 128, true><<<unsigned((cells + 127) / 128), 128, 0, s>>>(a, acc)));
+        else LAUNCH(cls, s, (k_cell_atomic<T, 128, false><<<unsigned((cells + 127) / 128), 128, 0, s>>>(a, acc)));
+    }
     return cudaGetLastError();
 }
 
@@ -451,8 +500,11 @@ cudaError_t accumulate(const BrickArgs<T>& a, T* acc, int bs, const TcArgs* tc, 
         if (tc) return launch_cell_tc(a, acc, *tc, s);
         if (bs == kSplitKernel) {
             const size_t cells = size_t(a.n) * a.n * a.n;
-            LAUNCH(PROF_VMULT_F32, s, (k_cell_split<<<unsigned((cells + kSplitCells - 1) / kSplitCells),
-                                                      3 * kSplitCells, 0, s>>>(a, acc)));
+            const unsigned blocks = unsigned((cells + kSplitCells - 1) / kSplitCells);
+            if ((reinterpret_cast<uintptr_t>(acc) & 7u) == 0)
+                LAUNCH(PROF_VMULT_F32, s, (k_cell_split<true><<<blocks, 3 * kSplitCells, 0, s>>>(a, acc)));
+            else
+                LAUNCH(PROF_VMULT_F32, s, (k_cell_split<false><<<blocks, 3 * kSplitCells, 0, s>>>(a, acc)));
             return cudaGetLastError();
         }
     }
@@ -521,9 +573,15 @@ cudaError_t launch_cell_cheb(int kernel, const LevelGeom& geo, const T* mu, cons
     const int cls = sizeof(T) == 4 ? PROF_VMULT_F32 : PROF_VMULT_F64;
     if constexpr (sizeof(T) == 4) {
         if (kernel == kSplitKernel) {
-            LAUNCH(cls, s, (k_cell_split_cheb<<<unsigned((cells + kSplitCells - 1) / kSplitCells), 3 * kSplitCells, 0,
-                                                s>>>(a, g.acc_prev, g.b, g.dinv, g.d_old, g.x_old, g.d_new, g.x_new,
-                                                     g.acc_zero, g.c1, g.c2, acc)));
+            const unsigned blocks = unsigned((cells + kSplitCells - 1) / kSplitCells);
+            if ((reinterpret_cast<uintptr_t>(acc) & 7u) == 0)
+                LAUNCH(cls, s, (k_cell_split_cheb<true><<<blocks, 3 * kSplitCells, 0, s>>>(
+                                   a, g.acc_prev, g.b, g.dinv, g.d_old, g.x_old, g.d_new, g.x_new, g.acc_zero, g.c1,
+                                   g.c2, acc)));
+            else
+                LAUNCH(cls, s, (k_cell_split_cheb<false><<<blocks, 3 * kSplitCells, 0, s>>>(
+                                   a, g.acc_prev, g.b, g.dinv, g.d_old, g.x_old, g.d_new, g.x_new, g.acc_zero, g.c1,
+                                   g.c2, acc)));
             return cudaGetLastError();
         }
     }

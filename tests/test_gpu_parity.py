@@ -451,6 +451,23 @@ def test_graph_replay_matches_kernel_launches(capi, prec, kernel):
             assert rel(a, b) <= (1e-13 if prec == 0 else 1e-6)
 
 
+@pytest.mark.parametrize("kernel", [0, 3])
+def test_vmult_into_unaligned_views(capi, kernel):
+    """The FP32 cell kernels add a row's node pairs with 8-byte atomics when the output is 8-byte
+    aligned; a caller's output view at an odd element offset takes the single-add scatter. Both
+    give the same product (to the rounding of the atomic sums' order) on every level."""
+    p, m, mus, G, ops, F = oracle_problem("n12")
+    ctx = gpu_ctx(capi, "n12", kernel)
+    for l in range(p.n_levels):
+        nu = ctx.size(l, 0)
+        x = dev(si.uniform(5400 + l, nu), torch.float32)
+        y = torch.empty(nu, dtype=torch.float32, device="cuda")
+        buf = torch.empty(nu + 1, dtype=torch.float32, device="cuda")
+        capi.stokes_vmult(ctx, l, capi.BLOCK_A, capi.STOKES_FP32, x, y)
+        capi.stokes_vmult(ctx, l, capi.BLOCK_A, capi.STOKES_FP32, x, buf[1:])
+        assert rel(host(buf[1:]), host(y)) <= 1e-6
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("kernel", [0, 3])
 def test_fused_smoother_matches_separate_passes(capi, prec, kernel):
