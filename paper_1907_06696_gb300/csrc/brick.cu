@@ -35,23 +35,6 @@ __global__ void __launch_bounds__(BX * BY * BZ, sizeof(T) == 4 ? 3 : 1) k_brick(
 // ---- cell-parallel variant: one thread per cell, atomic adds into a zeroed accumulator;
 // the consumer kernels below run the epilogue and clear the accumulator again.
 // Threads per block BS: 64, 128 or 256 (the register budget per thread is the same, 170 for FP32).
-// FP32 scatter of one x-row of a cell (the values of local nodes (0..2, j, k)) with one 8-byte
-// and one 4-byte atomic add instead of three 4-byte ones. The row's first node lies at element
-// offset c nodes + 2ci + M (2cj + j) + M^2 (2ck + k), whose parity is (c + j + k) mod 2 (nodes =
-// M^3 and M are odd), so the pair (0,1) or (1,2) is 8-byte aligned when the accumulator is; the
-// parity is a compile-time constant in the cell kernel and warp-uniform in the split kernel.
-// Measured on the operator's gather-and-scatter alone at 128^3: 0.229 ms with 81 single adds per
-// cell, 0.180 ms with 27 pairs and 27 singles.
-__device__ __forceinline__ void add_row3(float* row, int parity, float v0, float v1, float v2) {
-    if (parity == 0) {
-        atomicAdd(reinterpret_cast<float2*>(row), make_float2(v0, v1));
-        atomicAdd(row + 2, v2);
-    } else {
-        atomicAdd(row, v0);
-        atomicAdd(reinterpret_cast<float2*>(row + 1), make_float2(v1, v2));
-    }
-}
-
 // Scatter of a cell's scaled output w into acc (boundary nodes untouched: rows on the boundary
 // are skipped, boundary nodes inside a row get 0 added, so acc stays 0 there).
 template <typename T, bool PAIRS>

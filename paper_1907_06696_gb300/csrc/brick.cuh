@@ -345,6 +345,25 @@ inline size_t plane_threads(const PlaneLayout& L) {
 PlaneLayout brick_layout(int n);
 // Shared-memory opt-in of every brick kernel instantiation (call once before any launch or capture).
 cudaError_t brick_configure();
+// FP32 scatter of one x-row of a cell (the values of local nodes (0..2, j, k)) with one 8-byte
+// and one 4-byte atomic add instead of three 4-byte ones. The row's first node lies at element
+// offset c nodes + 2ci + M (2cj + j) + M^2 (2ck + k), whose parity is (c + j + k) mod 2 (nodes =
+// M^3 and M are odd), so the pair (0,1) or (1,2) is 8-byte aligned when the accumulator is; the
+// parity is a compile-time constant in the cell kernel and warp-uniform in the split kernel.
+// Measured on the operator's gather-and-scatter alone at 128^3: 0.229 ms with 81 single adds per
+// cell, 0.180 ms with 27 pairs and 27 singles.
+#ifdef __CUDACC__
+__device__ __forceinline__ void add_row3(float* row, int parity, float v0, float v1, float v2) {
+    if (parity == 0) {
+        atomicAdd(reinterpret_cast<float2*>(row), make_float2(v0, v1));
+        atomicAdd(row + 2, v2);
+    } else {
+        atomicAdd(row, v0);
+        atomicAdd(reinterpret_cast<float2*>(row + 1), make_float2(v1, v2));
+    }
+}
+#endif
+
 // One Chebyshev step carried by the next product (the cell and component-split operators).
 // Chebyshev step k ends with d' = c1 d + c2 dinv (b - A x), x' = x + d'; instead of a separate
 // consumer pass, the kernel forming A x' computes d', x' at every node it gathers (the same

@@ -210,6 +210,32 @@ __device__ __forceinline__ void scatter_part(uint32_t tmem_lane, float f, int ba
         }
 }
 
+// DIRECT variant of phases 3-4: this thread's half of the D row, times f, added straight into the
+// accumulator row by row (row r = component r / 9, local (j, k) = ((r % 9) % 3, (r % 9) / 3), the
+// three nodes n = 3r .. 3r + 2) with one 8-byte and one 4-byte atomic (add_row3's parity rule);
+// rows on the domain boundary are skipped, boundary nodes inside a row get 0. Warp-collective
+// like scatter_part.
+template <int N0>
+__device__ __forceinline__ void scatter_direct(uint32_t tmem_lane, float f, float* cell_out, size_t nodes,
+                                               const int (&roff)[9], const CellFlags& fl) {
+    uint32_t r[3][16];
+#pragma unroll
+    for (int chunk = 0; chunk < 3; ++chunk) tc::tmem_ld16(tmem_lane + uint32_t(kDcol + N0 + 16 * chunk), r[chunk]);
+    tc::tmem_ld_wait();
+    constexpr int R0 = N0 / 3, R1 = (N0 + 48 < 81 ? N0 + 48 : 81) / 3;
+#pragma unroll
+    for (int rr = R0; rr < R1; ++rr) {
+        const int c = rr / 9, j = (rr % 9) % 3, k = (rr % 9) / 3;
+        if (!fl.valid || (j == 0 && fl.ylo) || (j == 2 && fl.yhi) || (k == 0 && fl.zlo) || (k == 2 && fl.zhi)) continue;
+        const int q = 3 * rr - N0;
+        const float v0 = fl.xlo ? 0.0f : __uint_as_float(r[q / 16][q % 16]) * f;
+        const float v1 = __uint_as_float(r[(q + 1) / 16][(q + 1) % 16]) * f;
+        const float v2 = fl.xhi ? 0.0f : __uint_as_float(r[(q + 2) / 16][(q + 2) % 16]) * f;
+        add_row3(cell_out + size_t(c) * nodes + roff[j + 3 * k], (c + j + k) & 1, v0, v1, v2);
+    }
+}
+
+template <bool DIRECT>
 __global__ void __launch_bounds__(512, 1)
     k_cell_tc(BrickArgs<float> a, float* __restrict__ acc, const __half* __restrict__ table, unsigned* status,
               unsigned long long wait_ns, int nbx, int nby, int nbricks) {
@@ -311,6 +337,17 @@ __global__ void __launch_bounds__(512, 1)
         }
         phase ^= 1u;
         tc::fence_after_sync();
+        if constexpr (DIRECT) {
+            const float f = valid ? a.mu[size_t(ci) + size_t(a.n) * (cj + size_t(a.n) * ck)] * a.h * inv_s *
+                                        float(1.0 / kTableScale)
+                                  : 0.0f;
+            float* cell_out = acc + (valid ? size_t(2 * ci) + size_t(M) * (size_t(2 * cj) + size_t(M) * size_t(2 * ck))
+                                           : size_t(0));
+            if (half == 0) scatter_direct<0>(tmem_lane, f, cell_out, a.nodes, roff, fl);
+            else scatter_direct<48>(tmem_lane, f, cell_out, a.nodes, roff, fl);
+            tc::fence_before_sync();
+            continue;   // the next brick's first group barrier orders these TMEM loads before its MMAs
+        }
         {
             const float f = valid ? a.mu[size_t(ci) + size_t(a.n) * (cj + size_t(a.n) * ck)] * a.h * inv_s *
                                         float(1.0 / kTableScale)
@@ -356,7 +393,9 @@ int sm_count() {
 }  // namespace
 
 cudaError_t tc_configure() {
-    return cudaFuncSetAttribute(k_cell_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemAsk));
+    cudaError_t e = cudaFuncSetAttribute(k_cell_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemAsk));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_cell_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemAsk));
 }
 
 size_t tc_table_bytes() { return size_t(kTableBytes); }
@@ -375,8 +414,13 @@ cudaError_t launch_cell_tc(const BrickArgs<float>& a, float* acc, const TcArgs& 
     int grid = (nbricks + 1) / 2;
     if (grid > sm_count()) grid = sm_count();
     prof_begin(PROF_VMULT_F32, s);
-    k_cell_tc<<<grid, 512, kSmemAsk, s>>>(a, acc, static_cast<const __half*>(t.table), t.status, t.wait_ns, nbx,
-                                          nby, nbricks);
+    // direct pair atomics need an 8-byte aligned accumulator; otherwise the node-tile scatter
+    if ((reinterpret_cast<uintptr_t>(acc) & 7u) == 0)
+        k_cell_tc<true><<<grid, 512, kSmemAsk, s>>>(a, acc, static_cast<const __half*>(t.table), t.status, t.wait_ns,
+                                                    nbx, nby, nbricks);
+    else
+        k_cell_tc<false><<<grid, 512, kSmemAsk, s>>>(a, acc, static_cast<const __half*>(t.table), t.status, t.wait_ns,
+                                                     nbx, nby, nbricks);
     prof_end(PROF_VMULT_F32, s);
     prof_count(1);
     return cudaGetLastError();
