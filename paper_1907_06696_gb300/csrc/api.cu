@@ -438,12 +438,20 @@ stokes_status vcycle_level(stokes_ctx* c, int l, cudaStream_t s) {
     const bool fused = fused_level<T>(c, l);
     if (fused) {
         CKS(smooth_fused<T>(c, l, v.b, v.x, true, v.r, s));   // pre-smoothing and its residual
+        CK(launch_restrict<T>(L.g, v.r, vc.b, s));
     } else {
         CKS(smooth<T>(c, l, v.b, v.x, true, s));
-        CK(launch_level_op<T>(level_kernel<T>(c, l), L.g, L.planes, EPI_RESID, v.mu, v.x, v.r, v.b, nullptr, nullptr,
-                              0.0, 0.0, slots<T>(L), v.acc, s, &c->tc));
+        const int kern = level_kernel<T>(c, l);
+        if (kern != 1 && kern != 2) {
+            // the residual b - A x is formed inside the restriction, which clears the accumulator
+            CK(launch_accumulate<T>(kern, L.g, v.mu, v.x, v.acc, s));
+            CK(launch_restrict_resid<T>(L.g, nullptr, v.b, v.acc, vc.b, s));
+        } else {
+            CK(launch_level_op<T>(kern, L.g, L.planes, EPI_RESID, v.mu, v.x, v.r, v.b, nullptr, nullptr, 0.0, 0.0,
+                                  slots<T>(L), v.acc, s, &c->tc));
+            CK(launch_restrict<T>(L.g, v.r, vc.b, s, kern == 1));   // the brick operator's cycle stays deterministic
+        }
     }
-    CK(launch_restrict<T>(L.g, v.r, vc.b, s));
     CKS(vcycle_level<T>(c, l - 1, s));
     CK(launch_prolongate<T>(L.g, vc.x, v.x, true, s));
     if (fused) CKS(smooth_fused<T>(c, l, v.b, v.x, false, nullptr, s));

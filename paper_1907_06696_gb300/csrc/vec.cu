@@ -7,8 +7,10 @@
 // when i_f is even; when odd it sits at 1/4 or 3/4 of coarse cell m = i_f/4
 // and takes l_0, l_1, l_2 of the coarse cell at that point:
 // (3/8, 3/4, -1/8) at 1/4 and (-1/8, 3/4, 3/8) at 3/4. The 3D weights are the
-// products over the axes. Restriction is the exact transpose, evaluated as a
-// gather per coarse node (no atomics).
+// products over the axes. Restriction is the exact transpose. Both run per
+// coarse cell as three 1D sweeps (k_prolong_cells, k_restrict_cells); the
+// per-node forms of transfer.cuh serve the batched V-cycle and the deterministic
+// restriction of the brick-operator V-cycle.
 #include "internal.cuh"
 #include "prof.cuh"
 #include "transfer.cuh"
@@ -27,21 +29,191 @@ namespace {
 
 inline unsigned blocks_for(size_t n, int t) { return unsigned((n + t - 1) / t); }
 
-template <typename T>
-__global__ void k_prolongate(int nf, const T* __restrict__ coarse, T* __restrict__ fine, bool add) {
-    const size_t node = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const int Mf = 2 * nf + 1;
-    if (node >= size_t(Mf) * Mf * Mf) return;
-    prolongate_node<T, false>(nf, coarse, fine, add, node);
-}
 
+// Restriction as a gather per coarse node (no atomics, the same sums in the same order on every
+// run): the form of the deterministic brick-operator V-cycle.
 template <typename T>
-__global__ void k_restrict(int nf, const T* __restrict__ fine, T* __restrict__ coarse) {
+__global__ void k_restrict_nodes(int nf, const T* __restrict__ fine, T* __restrict__ coarse) {
     const size_t node = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int Mc = nf + 1;
     if (node >= size_t(Mc) * Mc * Mc) return;
     restrict_node<T, false>(nf, fine, coarse, node);
 }
+
+// ---- transfers by coarse cells (sum-factorised): thread (component c, coarse cell C) works on the
+// 3 x 3 x 3 coarse nodes 2C + {0,1,2} and the 5 x 5 x 5 fine nodes 4C + {0..4} of the cell. Along
+// one axis the fine values at 0, 1/4, 1/2, 3/4, 1 of the coarse cell are
+//   p0 = a0, p1 = 3/8 a0 + 3/4 a1 - 1/8 a2, p2 = a1, p3 = -1/8 a0 + 3/4 a1 + 3/8 a2, p4 = a2,
+// and restriction applies the transpose. A fine node shared by neighbouring coarse cells belongs to
+// the cell in which its local index is 0..3 along each axis (4 in the last cell along that axis), so
+// each is written (prolongation) or counted (restriction) once; the Q2 field is continuous, so the
+// owner's values are everyone's.
+template <typename T>
+__device__ __forceinline__ void pro5(T a0, T a1, T a2, T (&p)[5]) {
+    p[0] = a0;
+    p[1] = T(0.375) * a0 + T(0.75) * a1 - T(0.125) * a2;
+    p[2] = a1;
+    p[3] = T(-0.125) * a0 + T(0.75) * a1 + T(0.375) * a2;
+    p[4] = a2;
+}
+template <typename T>
+__device__ __forceinline__ void res3(const T (&v)[5], T& o0, T& o1, T& o2) {
+    o0 = v[0] + T(0.375) * v[1] - T(0.125) * v[3];
+    o1 = T(0.75) * v[1] + v[2] + T(0.75) * v[3];
+    o2 = T(-0.125) * v[1] + T(0.375) * v[3] + v[4];
+}
+
+// fine (+)= P coarse (fine boundary nodes: 0, or left unchanged with add). Thread (component c,
+// fine plane z of the coarse cell, coarse cell) runs the x and y sweeps of the cell's 27 values and
+// the z interpolation for its plane; it loads the 25 old values of its plane before it stores any,
+// so that its memory round trips do not line up one behind the other.
+template <typename T>
+__global__ void __launch_bounds__(128) k_prolong_cells(int nc, const T* __restrict__ coarse, T* __restrict__ fine,
+                                                       bool add) {
+    const size_t ncell = size_t(nc) * nc * nc;
+    const size_t t = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= 15 * ncell) return;
+    const size_t cell = t % ncell;
+    const int z = int((t / ncell) % 5), c = int(t / (5 * ncell));
+    const int ci = int(cell % nc), cj = int((cell / nc) % nc), ck = int(cell / (size_t(nc) * nc));
+    if (z == 4 && ck != nc - 1) return;   // that plane belongs to the next cell along z
+    const int Mc = 2 * nc + 1, Mf = 4 * nc + 1;
+    const size_t nodes_c = size_t(Mc) * Mc * Mc, nodes_f = size_t(Mf) * Mf * Mf;
+    const T* cp = coarse + size_t(c) * nodes_c + (size_t(2 * ci) + size_t(Mc) * (size_t(2 * cj) + size_t(Mc) * 2 * ck));
+    T t1[5][3][3];   // [x][b][d] after the x sweep
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const T* r = cp + size_t(Mc) * (b + size_t(Mc) * d);
+            T p[5];
+            pro5(r[0], r[1], r[2], p);
+#pragma unroll
+            for (int x = 0; x < 5; ++x) t1[x][b][d] = p[x];
+        }
+    // the z weights of this plane (row z of the 5 x 3 interpolation)
+    const T wz0 = z == 0 ? T(1) : z == 1 ? T(0.375) : z == 3 ? T(-0.125) : T(0);
+    const T wz1 = z == 1 || z == 3 ? T(0.75) : z == 2 ? T(1) : T(0);
+    const T wz2 = z == 4 ? T(1) : z == 1 ? T(-0.125) : z == 3 ? T(0.375) : T(0);
+    const bool lx = ci == nc - 1, ly = cj == nc - 1;
+    const bool bz = (4 * ck + z == 0) || (4 * ck + z == Mf - 1);
+    T* fp = fine + size_t(c) * nodes_f + (size_t(4 * ci) + size_t(Mf) * (size_t(4 * cj) + size_t(Mf) * (4 * ck + z)));
+    T out[5][5];
+#pragma unroll
+    for (int x = 0; x < 5; ++x) {
+        T p[5];
+#pragma unroll
+        for (int y = 0; y < 5; ++y) p[y] = T(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const T w = d == 0 ? wz0 : d == 1 ? wz1 : wz2;
+            T q[5];
+            pro5(t1[x][0][d], t1[x][1][d], t1[x][2][d], q);
+#pragma unroll
+            for (int y = 0; y < 5; ++y) p[y] += w * q[y];
+        }
+#pragma unroll
+        for (int y = 0; y < 5; ++y) out[x][y] = p[y];
+    }
+    // owned nodes of the plane: x, y in 0..3 (4 in the last cell along the axis)
+    auto owned = [&](int x, int y) { return (x < 4 || lx) && (y < 4 || ly); };
+    auto bnd = [&](int x, int y) {
+        return bz || (4 * ci + x == 0) || (4 * ci + x == Mf - 1) || (4 * cj + y == 0) || (4 * cj + y == Mf - 1);
+    };
+    if (add) {
+        T old[5][5];
+#pragma unroll
+        for (int y = 0; y < 5; ++y)
+#pragma unroll
+            for (int x = 0; x < 5; ++x) old[x][y] = owned(x, y) && !bnd(x, y) ? fp[x + size_t(Mf) * y] : T(0);
+#pragma unroll
+        for (int y = 0; y < 5; ++y)
+#pragma unroll
+            for (int x = 0; x < 5; ++x)
+                if (owned(x, y) && !bnd(x, y)) fp[x + size_t(Mf) * y] = old[x][y] + out[x][y];
+    } else {
+#pragma unroll
+        for (int y = 0; y < 5; ++y)
+#pragma unroll
+            for (int x = 0; x < 5; ++x)
+                if (owned(x, y)) fp[x + size_t(Mf) * y] = bnd(x, y) ? T(0) : out[x][y];
+    }
+}
+
+// coarse += P^T r on the free coarse nodes (coarse zero on entry), r = fine_r, or r = b - acc with
+// acc cleared at the nodes read (the V-cycle residual, formed here instead of in a pass of its own)
+template <typename T>
+__global__ void __launch_bounds__(128) k_restrict_cells(int nc, const T* __restrict__ fine_r, const T* __restrict__ b,
+                                                        T* __restrict__ acc, T* __restrict__ coarse) {
+    const size_t ncell = size_t(nc) * nc * nc;
+    const size_t t = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= 3 * ncell) return;
+    const int c = int(t / ncell);
+    const size_t cell = t % ncell;
+    const int ci = int(cell % nc), cj = int((cell / nc) % nc), ck = int(cell / (size_t(nc) * nc));
+    const int Mc = 2 * nc + 1, Mf = 4 * nc + 1;
+    const size_t nodes_c = size_t(Mc) * Mc * Mc, nodes_f = size_t(Mf) * Mf * Mf;
+    const bool lx = ci == nc - 1, ly = cj == nc - 1, lz = ck == nc - 1;
+    const size_t fbase = size_t(c) * nodes_f + (size_t(4 * ci) + size_t(Mf) * (size_t(4 * cj) + size_t(Mf) * 4 * ck));
+    T t2[5][5][3];   // [x][y][d] after the z sweep
+#pragma unroll
+    for (int y = 0; y < 5; ++y)
+#pragma unroll
+        for (int x = 0; x < 5; ++x) {
+            T v[5];
+#pragma unroll
+            for (int z = 0; z < 5; ++z) {
+                const bool own = (x < 4 || lx) && (y < 4 || ly) && (z < 4 || lz);
+                const size_t f = fbase + x + size_t(Mf) * (y + size_t(Mf) * z);
+                T r = T(0);
+                if (own) r = fine_r ? fine_r[f] : b[f] - acc[f];
+                v[z] = r;
+            }
+            res3(v, t2[x][y][0], t2[x][y][1], t2[x][y][2]);
+        }
+    // clear the accumulator only after every load: a store between them would keep each later load
+    // of acc behind it (one memory latency per line)
+    if (!fine_r) {
+#pragma unroll
+        for (int y = 0; y < 5; ++y)
+#pragma unroll
+            for (int x = 0; x < 5; ++x)
+#pragma unroll
+                for (int z = 0; z < 5; ++z)
+                    if ((x < 4 || lx) && (y < 4 || ly) && (z < 4 || lz))
+                        acc[fbase + x + size_t(Mf) * (y + size_t(Mf) * z)] = T(0);
+    }
+    T t1[5][3][3];   // [x][b][d]
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int x = 0; x < 5; ++x) {
+            T v[5];
+#pragma unroll
+            for (int y = 0; y < 5; ++y) v[y] = t2[x][y][d];
+            res3(v, t1[x][0][d], t1[x][1][d], t1[x][2][d]);
+        }
+    T* cp = coarse + size_t(c) * nodes_c + (size_t(2 * ci) + size_t(Mc) * (size_t(2 * cj) + size_t(Mc) * 2 * ck));
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const bool bd = (2 * ck + d == 0) || (2 * ck + d == Mc - 1);
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb) {
+            const bool bb_ = bd || (2 * cj + bb == 0) || (2 * cj + bb == Mc - 1);
+            T v[5];
+#pragma unroll
+            for (int x = 0; x < 5; ++x) v[x] = t1[x][bb][d];
+            T o[3];
+            res3(v, o[0], o[1], o[2]);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (bb_ || (2 * ci + a == 0) || (2 * ci + a == Mc - 1)) continue;
+                atomicAdd(cp + a + size_t(Mc) * (bb + size_t(Mc) * d), o[a]);
+            }
+        }
+    }
+}
+
 
 template <typename T>
 __global__ void k_cheb_update(size_t n, const T* __restrict__ b, const T* __restrict__ Ax,
@@ -201,20 +373,38 @@ int multidot_blocks() { return kDotBlocks; }
 
 template <typename T>
 cudaError_t launch_prolongate(const LevelGeom& fine, const T* coarse, T* finev, bool add, cudaStream_t s) {
-    LAUNCH(PROF_TRANSFER, s, k_prolongate<T><<<blocks_for(fine.nodes, 256), 256, 0, s>>>(fine.n, coarse, finev, add));
+    const int nc = fine.n / 2;
+    const size_t threads = 15 * size_t(nc) * nc * nc;
+    LAUNCH(PROF_TRANSFER, s, k_prolong_cells<T><<<blocks_for(threads, 128), 128, 0, s>>>(nc, coarse, finev, add));
     return cudaGetLastError();
 }
 template cudaError_t launch_prolongate<float>(const LevelGeom&, const float*, float*, bool, cudaStream_t);
 template cudaError_t launch_prolongate<double>(const LevelGeom&, const double*, double*, bool, cudaStream_t);
 
 template <typename T>
-cudaError_t launch_restrict(const LevelGeom& fine, const T* finev, T* coarse, cudaStream_t s) {
+cudaError_t launch_restrict(const LevelGeom& fine, const T* finev, T* coarse, cudaStream_t s, bool deterministic) {
+    if (!deterministic) return launch_restrict_resid<T>(fine, finev, nullptr, nullptr, coarse, s);
     const size_t Mc = size_t(fine.n) + 1;
-    LAUNCH(PROF_TRANSFER, s, k_restrict<T><<<blocks_for(Mc * Mc * Mc, 256), 256, 0, s>>>(fine.n, finev, coarse));
+    LAUNCH(PROF_TRANSFER, s, k_restrict_nodes<T><<<blocks_for(Mc * Mc * Mc, 256), 256, 0, s>>>(fine.n, finev, coarse));
     return cudaGetLastError();
 }
-template cudaError_t launch_restrict<float>(const LevelGeom&, const float*, float*, cudaStream_t);
-template cudaError_t launch_restrict<double>(const LevelGeom&, const double*, double*, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_restrict_resid(const LevelGeom& fine, const T* r, const T* b, T* acc, T* coarse, cudaStream_t s) {
+    const int nc = fine.n / 2;
+    const size_t Mc = size_t(2 * nc) + 1;
+    cudaError_t e = cudaMemsetAsync(coarse, 0, 3 * Mc * Mc * Mc * sizeof(T), s);
+    if (e != cudaSuccess) return e;
+    const size_t threads = 3 * size_t(nc) * nc * nc;
+    LAUNCH(PROF_TRANSFER, s, k_restrict_cells<T><<<blocks_for(threads, 128), 128, 0, s>>>(nc, r, b, acc, coarse));
+    return cudaGetLastError();
+}
+template cudaError_t launch_restrict_resid<float>(const LevelGeom&, const float*, const float*, float*, float*,
+                                                  cudaStream_t);
+template cudaError_t launch_restrict_resid<double>(const LevelGeom&, const double*, const double*, double*, double*,
+                                                   cudaStream_t);
+template cudaError_t launch_restrict<float>(const LevelGeom&, const float*, float*, cudaStream_t, bool);
+template cudaError_t launch_restrict<double>(const LevelGeom&, const double*, double*, cudaStream_t, bool);
 
 template <typename T>
 cudaError_t launch_cheb_update(size_t n, const T* b, const T* Ax, const T* dinv, T* d, T* x, double c1, double c2,
