@@ -107,10 +107,9 @@ typedef struct {
     int restart;                /* FGMRES restart length (50, Section 3.4) */
     int outer_arith;            /* arithmetic of the FP64-interface outer operator: 0 = native FP64;
                                    1 = double-float (pairs of floats, ~48-bit significand) on the FP32
-                                   units for every block that contains A (default: 1.6 ms vs 1.95 ms at
-                                   64^3 on GB300, whose FP64 rate is 1/72 of FP32); B^T or B alone always
-                                   run in native FP64, which is faster for them. Both match the FP64
-                                   oracle to 1e-12. */
+                                   units for every block (default; GB300's FP64 rate is 1/72 of FP32: the
+                                   Stokes block takes 0.83 vs 1.95 ms, B^T alone 0.15 vs 0.22 ms at
+                                   64^3). Both match the FP64 oracle to 1e-12. */
     int vmult_kernel;           /* level operator of the V-cycle: 0 = one thread per cell with atomic adds
                                    and a separate epilogue pass (default); 1 = brick-tiled, atomic-free
                                    and deterministic, epilogue fused; 2 = FP32 levels: the brick-tiled

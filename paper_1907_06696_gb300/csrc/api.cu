@@ -186,6 +186,8 @@ struct stokes_ctx {
     double p_wsum = 1.0;
     // Schur Chebyshev work (N_p each)
     double *sp_d = nullptr, *sp_t = nullptr;
+    double *sp_z2 = nullptr, *sp_d2 = nullptr;   // second (z, d) pair of the gathered S_hat^-1 steps
+    double* mp_scale = nullptr;                 // h^3 / mu per finest cell
     // preconditioner / operator work (N_u)
     double* tu = nullptr;
     float *stage_in = nullptr, *stage_out = nullptr;   // FP32 V-cycle input / output
@@ -629,15 +631,20 @@ stokes_status schur_inverse(stokes_ctx* c, const double* rp, double* zp, cudaStr
     const double lo = 1.0 / 8.0, hi = 27.0 / 8.0;
     const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
     double rho = 1.0 / sigma;
-    const double* mu = c->lev[c->L - 1].v64.mu;
     // degree 0: S_hat = diag(M_p) itself (Section 3.4); otherwise the first Chebyshev step
-    const double c0 = c->opt.schur_degree == 0 ? 1.0 : 1.0 / theta;
-    CK(launch_cheb_update<double>(g.n_p, rp, nullptr, c->mp_dinv, c->sp_d, zp, 0.0, c0, false, s));
-    for (int it = 1; it < c->opt.schur_degree; ++it) {
-        CK(launch_mass_p(g, mu, zp, c->sp_t, s));
+    const int deg = c->opt.schur_degree;
+    const double c0 = deg == 0 ? 1.0 : 1.0 / theta;
+    // the later steps form M_p z per vertex and update in the same kernel, alternating between
+    // (zp, sp_d) and (sp_z2, sp_d2); the first step starts in the pair the last one ends in zp
+    double* Z[2] = {zp, c->sp_z2};
+    double* D[2] = {c->sp_d, c->sp_d2};
+    int cur = deg > 1 ? (deg - 1) & 1 : 0;
+    CK(launch_cheb_update<double>(g.n_p, rp, nullptr, c->mp_dinv, D[cur], Z[cur], 0.0, c0, false, s));
+    for (int it = 1; it < deg; ++it) {
         const double rho_new = 1.0 / (2.0 * sigma - rho);
-        CK(launch_cheb_update<double>(g.n_p, rp, c->sp_t, c->mp_dinv, c->sp_d, zp, rho_new * rho,
-                                      2.0 * rho_new / delta, true, s));
+        CK(launch_schur_cheb(g, c->mp_scale, rp, c->mp_dinv, Z[cur], D[cur], Z[cur ^ 1], D[cur ^ 1], rho_new * rho,
+                             2.0 * rho_new / delta, s));
+        cur ^= 1;
         rho = rho_new;
     }
     return STOKES_OK;
@@ -1749,6 +1756,9 @@ stokes_status setup_impl(const stokes_mesh* mesh, const stokes_mu* mu, const sto
     CKS(dalloc(c, &c->p_weights, gf.n_p));
     CKS(dalloc(c, &c->sp_d, gf.n_p));
     CKS(dalloc(c, &c->sp_t, gf.n_p));
+    CKS(dalloc(c, &c->sp_z2, gf.n_p));
+    CKS(dalloc(c, &c->sp_d2, gf.n_p));
+    CKS(dalloc(c, &c->mp_scale, gf.cells));
     CKS(dalloc(c, &c->tu, gf.n_u));
     CKS(dalloc(c, &c->stage_in, gf.n_u));
     CKS(dalloc(c, &c->stage_out, gf.n_u));
@@ -1785,6 +1795,7 @@ stokes_status setup_impl(const stokes_mesh* mesh, const stokes_mu* mu, const sto
     }
     // ---- pressure mass diagonal and weights (Section 2.2.2)
     CK(launch_mass_p_diag(gf, c->lev[L - 1].v64.mu, c->sp_t, c->p_weights, s));
+    CK(launch_mass_scale(gf, c->lev[L - 1].v64.mu, c->mp_scale, s));
     CK(launch_recip(gf.n_p, c->sp_t, c->mp_dinv, s));
     {
         double* ones = c->sp_d;

@@ -44,6 +44,13 @@ cudaError_t launch_outer_df64(const LevelGeom& g, const double* mu, const double
                               double* dst_u, double* dst_p, bool do_a, bool do_bt, bool do_b, cudaStream_t s);
 // dst = M_p src (weighted pressure mass, FP64).
 cudaError_t launch_mass_p(const LevelGeom& g, const double* mu, const double* src, double* dst, cudaStream_t s);
+// scale[cell] = h^3 / mu[cell]
+cudaError_t launch_mass_scale(const LevelGeom& g, const double* mu, double* scale, cudaStream_t s);
+// One Chebyshev step of S_hat^-1 with M_p gathered per vertex (double-float products):
+// d_new = c1 d + c2 dinv (r - M_p z), z_new = z + d_new; z_new, d_new must not alias z, d.
+cudaError_t launch_schur_cheb(const LevelGeom& g, const double* scale, const double* r, const double* dinv,
+                              const double* z, const double* d, double* z_new, double* d_new, double c1, double c2,
+                              cudaStream_t s);
 // diag(M_p) and int psi_l (pressure weights), FP64.
 cudaError_t launch_mass_p_diag(const LevelGeom& g, const double* mu, double* diag, double* weights,
                                cudaStream_t s);

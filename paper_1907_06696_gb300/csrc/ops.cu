@@ -215,6 +215,68 @@ __global__ void k_mass_p(int n, double h, const double* __restrict__ mu, const d
     }
 }
 
+// s_K = h^3 / mu_K per cell: the factor of the cell's pressure mass matrix (Section 2.2.2, the
+// 1/mu-weighted mass matrix), as k_mass_p forms it.
+__global__ void k_mass_scale(size_t cells, double h, const double* __restrict__ mu, double* __restrict__ scale) {
+    const size_t cell = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (cell < cells) scale[cell] = h * h * h / mu[cell];
+}
+
+// One Jacobi-Chebyshev step of S_hat^-1 with the M_p product gathered per pressure vertex:
+//   d' = c1 d + c2 D^-1 (r - M_p z),  z' = z + d'   (into the other buffers of the pairs).
+// (M_p z)_v sums the element products of the up to 8 cells around v, s_K sum_w m(v, w) z_w with
+// m = M1 x M1 x M1 (M1 the 1D Q1 mass matrix on [0,1]); no atomics, one thread per vertex. The
+// products run in double-float on the FP32 pipes (the 27 neighbouring values split once): in FP64
+// the 64 multiply-adds per vertex would bind the kernel to the FP64 pipe (1/72 of the FP32 rate).
+__global__ void __launch_bounds__(128) k_schur_cheb(int n, const double* __restrict__ scale, const double* __restrict__ r,
+                                                    const double* __restrict__ dinv, const double* __restrict__ z,
+                                                    const double* __restrict__ d, double* __restrict__ z_new,
+                                                    double* __restrict__ d_new, double c1, double c2) {
+    using q2::df64;
+    const int P = n + 1;
+    const size_t vtx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (vtx >= size_t(P) * P * P) return;
+    const int vi = int(vtx % P), vj = int((vtx / P) % P), vk = int(vtx / (size_t(P) * P));
+    df64 zz[3][3][3];   // [k][j][i], the vertex (vi + i - 1, vj + j - 1, vk + k - 1)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const int wi = vi + i - 1, wj = vj + j - 1, wk = vk + k - 1;
+                const bool in = wi >= 0 && wj >= 0 && wk >= 0 && wi < P && wj < P && wk < P;
+                zz[k][j][i] = in ? q2::split_double(z[size_t(wi) + size_t(P) * (wj + size_t(P) * wk)]) : df64();
+            }
+    df64 acc;
+#pragma unroll
+    for (int ck = 0; ck < 2; ++ck)
+#pragma unroll
+        for (int cj = 0; cj < 2; ++cj)
+#pragma unroll
+            for (int ci = 0; ci < 2; ++ci) {
+                // cell (vi - 1 + ci, ...): v is its local corner (1 - ci, 1 - cj, 1 - ck)
+                const int gi = vi - 1 + ci, gj = vj - 1 + cj, gk = vk - 1 + ck;
+                if (gi < 0 || gj < 0 || gk < 0 || gi >= n || gj >= n || gk >= n) continue;
+                df64 inner;
+#pragma unroll
+                for (int wk = 0; wk < 2; ++wk)
+#pragma unroll
+                    for (int wj = 0; wj < 2; ++wj)
+#pragma unroll
+                        for (int wi = 0; wi < 2; ++wi) {
+                            const double m = q2::M1(1 - ci, wi) * q2::M1(1 - cj, wj) * q2::M1(1 - ck, wk);
+                            q2::mac(inner, df64(m), zz[ck + wk][cj + wj][ci + wi]);
+                        }
+                q2::renorm(inner);
+                acc = acc + q2::split_double(scale[size_t(gi) + size_t(n) * (gj + size_t(n) * gk)]) * inner;
+            }
+    const double mz = acc.to_double();
+    const double dn = (c1 != 0.0 ? c1 * d[vtx] : 0.0) + c2 * (dinv[vtx] * (r[vtx] - mz));
+    d_new[vtx] = dn;
+    z_new[vtx] = z[vtx] + dn;
+}
+
 __global__ void k_mass_p_diag(int n, double h, const double* __restrict__ mu, double* __restrict__ diag,
                               double* __restrict__ weights) {
     const size_t vtx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -423,8 +485,9 @@ cudaError_t launch_stokes_blocks(const LevelGeom& g, const double* mu, const dou
         e = cudaMemsetAsync(dst_p, 0, g.n_p * sizeof(double), s);
         if (e != cudaSuccess) return e;
     }
-    // double-float pays off where the A part is present; B^T or B alone are cheaper in native FP64
-    e = (df64 && do_a) ? launch_outer_df64(g, mu, src_u, src_p, dst_u, dst_p, do_a, do_bt, do_b, s)
+    // double-float on the FP32 pipes for every block (GB300's FP64 pipe retires 1/72 of the FP32
+    // rate): B^T alone, the preconditioner's, takes 148 us at 64^3 against 221 us in native FP64
+    e = df64 ? launch_outer_df64(g, mu, src_u, src_p, dst_u, dst_p, do_a, do_bt, do_b, s)
                        : stokes_blocks_ct<double>(g, mu, src_u, src_p, dst_u, dst_p, do_a, do_bt, do_b, s);
     if (e != cudaSuccess) return e;
     if (do_a) {
@@ -438,6 +501,19 @@ cudaError_t launch_mass_p(const LevelGeom& g, const double* mu, const double* sr
     cudaError_t e = cudaMemsetAsync(dst, 0, g.n_p * sizeof(double), s);
     if (e != cudaSuccess) return e;
     LAUNCH(PROF_MASS_P, s, k_mass_p<<<blocks_for(g.cells, 128), 128, 0, s>>>(g.n, g.h, mu, src, dst));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mass_scale(const LevelGeom& g, const double* mu, double* scale, cudaStream_t s) {
+    LAUNCH(PROF_MASS_P, s, k_mass_scale<<<blocks_for(g.cells, 256), 256, 0, s>>>(g.cells, g.h, mu, scale));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_schur_cheb(const LevelGeom& g, const double* scale, const double* r, const double* dinv,
+                              const double* z, const double* d, double* z_new, double* d_new, double c1, double c2,
+                              cudaStream_t s) {
+    LAUNCH(PROF_MASS_P, s, k_schur_cheb<<<blocks_for(g.n_p, 128), 128, 0, s>>>(g.n, scale, r, dinv, z, d, z_new, d_new,
+                                                                             c1, c2));
     return cudaGetLastError();
 }
 
