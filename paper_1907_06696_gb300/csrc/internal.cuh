@@ -44,6 +44,8 @@ cudaError_t launch_outer_df64(const LevelGeom& g, const double* mu, const double
                               double* dst_u, double* dst_p, bool do_a, bool do_bt, bool do_b, cudaStream_t s);
 // dst = M_p src (weighted pressure mass, FP64).
 cudaError_t launch_mass_p(const LevelGeom& g, const double* mu, const double* src, double* dst, cudaStream_t s);
+// out = B^T p on the uniform mesh (velocity boundary nodes 0), gathered per node pair; no atomics
+cudaError_t launch_bt_gather(const LevelGeom& g, const double* p, double* out, cudaStream_t s);
 // scale[cell] = h^3 / mu[cell]
 cudaError_t launch_mass_scale(const LevelGeom& g, const double* mu, double* scale, cudaStream_t s);
 // One Chebyshev step of S_hat^-1 with M_p gathered per vertex (double-float products):

@@ -215,6 +215,105 @@ __global__ void k_mass_p(int n, double h, const double* __restrict__ mu, const d
     }
 }
 
+// ---- B^T on the uniform mesh as a gather. B^T carries no viscosity, so component c of B^T p is
+// -h^2 (X_2 x X_1 x X_0) p with X_d the 1D moment operator assembled over the cells along axis d
+// (DP, the moments of the Q2 basis derivatives against the Q1 basis, along axis c; VP, those of
+// the basis itself, along the other two). An interior Q2 node 2e (a vertex) has the row
+// (XP(2,0), XP(2,1) + XP(0,0), XP(0,1)) at vertices e-1, e, e+1, an interior node 2e+1 the row
+// (XP(1,0), XP(1,1)) at e, e+1. Thread (c, e, J, K) forms t_a = sum X_1[J][b] X_2[K][k] p(a, b, k)
+// for a = e-1, e, e+1 and writes the x-nodes 2e and 2e+1 of the line (J, K); boundary nodes get 0,
+// as in the cell kernels. No atomics; double-float products on the FP32 pipes.
+template <int C>
+__device__ __forceinline__ double bt_x_row(int i, int a, int e) {
+    // entry of X_0 (axis 0) in row i at vertex a, for the rows this thread writes (i = 2e, 2e + 1)
+    constexpr bool D = C == 0;
+    auto xp = [](int m, int v) { return D ? q2::DP(m, v) : q2::VP(m, v); };
+    if (i & 1) return a == e ? xp(1, 0) : (a == e + 1 ? xp(1, 1) : 0.0);
+    return a == e - 1 ? xp(2, 0) : (a == e ? xp(2, 1) + xp(0, 0) : (a == e + 1 ? xp(0, 1) : 0.0));
+}
+
+template <int C, int AX>
+__device__ __forceinline__ void bt_row(int i, double (&w)[3]) {
+    // row i of X_AX (interior i) over the vertices i/2 - 1, i/2, i/2 + 1
+    constexpr bool D = C == AX;
+    auto xp = [](int m, int v) { return D ? q2::DP(m, v) : q2::VP(m, v); };
+    if (i & 1) {   // vertices i/2, i/2 + 1
+        w[0] = 0.0;
+        w[1] = xp(1, 0);
+        w[2] = xp(1, 1);
+    } else {
+        w[0] = xp(2, 0);
+        w[1] = xp(2, 1) + xp(0, 0);
+        w[2] = xp(0, 1);
+    }
+}
+
+// Block (line (J, K), component c): thread e forms t_e = sum_{b,k} X_1[J][b] X_2[K][k] p(e, b, k)
+// into shared memory, then writes the x-nodes 2e and 2e + 1 of the line from t_{e-1}, t_e, t_{e+1}.
+template <int C>
+__device__ __forceinline__ void bt_line(int n, double s, const double* __restrict__ p, double* __restrict__ out,
+                                        int J, int K, q2::df64* t, q2::df64* w) {
+    using q2::df64;
+    const int P = n + 1, M = 2 * n + 1;
+    const int e = int(threadIdx.x);
+    double* o = out + size_t(C) * size_t(M) * M * M + size_t(M) * (J + size_t(M) * K);
+    if (J == 0 || J == M - 1 || K == 0 || K == M - 1) {   // boundary rows
+        for (int i = e; i < M; i += int(blockDim.x)) o[i] = 0.0;
+        return;
+    }
+    if (e < 9) {   // the 9 (b, k) weights of the line
+        double wy[3], wz[3];
+        bt_row<C, 1>(J, wy);
+        bt_row<C, 2>(K, wz);
+        w[e] = q2::split_double(wy[e % 3] * wz[e / 3]);
+    }
+    __syncthreads();
+    const int by = J / 2 - 1, bz = K / 2 - 1;
+    if (e < P) {
+        df64 acc;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const int b = by + q % 3, k = bz + q / 3;
+            if (b < 0 || b >= P || k < 0 || k >= P) continue;   // zero weights only
+            q2::mac(acc, w[q], q2::split_double(p[size_t(e) + size_t(P) * (b + size_t(P) * k)]));
+        }
+        q2::renorm(acc);
+        t[e] = acc;
+    }
+    __syncthreads();
+    if (e >= P) return;
+    const int i0 = 2 * e;
+    if (i0 == 0 || i0 == M - 1) {
+        o[i0] = 0.0;
+    } else {
+        df64 v;
+        q2::mac(v, df64(bt_x_row<C>(i0, e - 1, e)), t[e - 1]);
+        q2::mac(v, df64(bt_x_row<C>(i0, e, e)), t[e]);
+        q2::mac(v, df64(bt_x_row<C>(i0, e + 1, e)), t[e + 1]);
+        q2::renorm(v);
+        o[i0] = s * v.to_double();
+    }
+    if (e < n) {
+        df64 v;
+        q2::mac(v, df64(bt_x_row<C>(i0 + 1, e, e)), t[e]);
+        q2::mac(v, df64(bt_x_row<C>(i0 + 1, e + 1, e)), t[e + 1]);
+        q2::renorm(v);
+        o[i0 + 1] = s * v.to_double();
+    }
+}
+
+__global__ void k_bt_gather(int n, double h, const double* __restrict__ p, double* __restrict__ out) {
+    extern __shared__ __align__(16) unsigned char bt_smem[];
+    q2::df64* t = reinterpret_cast<q2::df64*>(bt_smem);   // n + 1 entries
+    q2::df64* w = t + (n + 1);                             // 9 entries
+    const int M = 2 * n + 1;
+    const int J = int(blockIdx.x % unsigned(M)), K = int(blockIdx.x / unsigned(M)), c = int(blockIdx.y);
+    const double s = -h * h;
+    if (c == 0) bt_line<0>(n, s, p, out, J, K, t, w);
+    else if (c == 1) bt_line<1>(n, s, p, out, J, K, t, w);
+    else bt_line<2>(n, s, p, out, J, K, t, w);
+}
+
 // s_K = h^3 / mu_K per cell: the factor of the cell's pressure mass matrix (Section 2.2.2, the
 // 1/mu-weighted mass matrix), as k_mass_p forms it.
 __global__ void k_mass_scale(size_t cells, double h, const double* __restrict__ mu, double* __restrict__ scale) {
@@ -477,6 +576,8 @@ cudaError_t launch_stokes_blocks(const LevelGeom& g, const double* mu, const dou
                                  double* dst_u, double* dst_p, bool do_a, bool do_bt, bool do_b, bool df64,
                                  cudaStream_t s) {
     cudaError_t e;
+    // B^T alone (the preconditioner's): the gather writes every velocity entry, no clear needed
+    if (df64 && !do_a && do_bt && !do_b) return launch_bt_gather(g, src_p, dst_u, s);
     if (do_a || do_bt) {
         e = cudaMemsetAsync(dst_u, 0, g.n_u * sizeof(double), s);
         if (e != cudaSuccess) return e;
@@ -501,6 +602,15 @@ cudaError_t launch_mass_p(const LevelGeom& g, const double* mu, const double* sr
     cudaError_t e = cudaMemsetAsync(dst, 0, g.n_p * sizeof(double), s);
     if (e != cudaSuccess) return e;
     LAUNCH(PROF_MASS_P, s, k_mass_p<<<blocks_for(g.cells, 128), 128, 0, s>>>(g.n, g.h, mu, src, dst));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bt_gather(const LevelGeom& g, const double* p, double* out, cudaStream_t s) {
+    // one block per (line, component), one thread per vertex of the line (x-nodes 2e, 2e + 1)
+    const unsigned threads = unsigned((g.n + 1 + 31) / 32 * 32);
+    const size_t smem = size_t(g.n + 1 + 9) * sizeof(q2::df64);
+    const dim3 grid(unsigned(size_t(g.M) * g.M), 3);
+    LAUNCH(PROF_BT_F64, s, k_bt_gather<<<grid, threads, smem, s>>>(g.n, g.h, p, out));
     return cudaGetLastError();
 }
 
