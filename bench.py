@@ -75,7 +75,8 @@ def parse():
                          "(Table 1 comparison)")
     ap.add_argument("--kernels", action="store_true",
                     help="profiling case: set up the workload, run 3 FP32 vmults, 2 FP64 Stokes applies, "
-                         "1 FP32 V-cycle, print one line and exit (for ncu); no Krylov basis is allocated")
+                         "1 FP32 V-cycle and 1 preconditioner application, print one line and exit (for ncu); "
+                         "no Krylov basis is allocated")
     ap.add_argument("--kernels-gs", action="store_true",
                     help="with --kernels: also 40 FGMRES iterations (Gram-Schmidt passes up to a 40-vector basis)")
     ap.add_argument("--vmult-kernel", type=int, default=None,
@@ -704,6 +705,9 @@ def run_kernels(args):
     for _ in range(2):
         capi.stokes_vmult(ctx, -1, capi.BLOCK_STOKES, capi.STOKES_FP64, up, out)
     capi.gmg_vcycle(ctx, capi.STOKES_FP32, x, y)
+    # one preconditioner application: S_hat^-1 steps, B^T, the FP32 V-cycle
+    z = torch.empty_like(up)
+    capi.stokes_precondition(ctx, capi.STOKES_FP32, up, z)
     if args.kernels_gs:
         # 40 FGMRES iterations: Gram-Schmidt passes up to a 40-vector basis
         up.zero_()
