@@ -1360,29 +1360,27 @@ stokes_status idr_solve(stokes_ctx* c, int prec, const double* b, double* x, dou
                     cc[i - k] = acc / M(i, i);
                 }
                 CK(cudaMemcpyAsync(c->idr_c, cc.data(), sizeof(double) * (sd - k), cudaMemcpyHostToDevice, s));
-                CK(cudaMemcpyAsync(v, r, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
-                CK(launch_multiaxpy(N, sd - k, col(G, k), N, c->idr_c, v, -1.0, s));   // v = r - G c
-                CKS(precondition(c, prec, v, tmp, s));                               // tmp = P^-1 v
-                CK(cudaMemsetAsync(t, 0, N * sizeof(double), s));
-                CK(launch_multiaxpy(N, sd - k, col(U, k), N, c->idr_c, t, 1.0, s));   // t = U[:, k:] c
-                CK(launch_axpby(N, om, tmp, 1.0, t, s));                                // t += om P^-1 v
-                CK(cudaMemcpyAsync(col(U, k), t, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
-                CKS(apply_stokes(c, col(U, k), col(G, k), s));                          // G_k = K U_k
+                CK(launch_lincomb(N, sd - k, col(G, k), N, c->idr_c, 1.0, r, v, -1.0, s));   // v = r - G c
+                CKS(precondition(c, prec, v, tmp, s));                                     // tmp = P^-1 v
+                // U_k = U[:, k:] c + om P^-1 v, in place (each entry of U_k read before written)
+                CK(launch_lincomb(N, sd - k, col(U, k), N, c->idr_c, om, tmp, col(U, k), 1.0, s));
+                CKS(apply_stokes(c, col(U, k), col(G, k), s));                                // G_k = K U_k
                 ++its;
                 for (int i = 0; i < k; ++i) {
                     double pg = 0.0;
                     CKS(dot(c, N, col(P, i), col(G, k), s, &pg));
                     const double alpha = pg / M(i, i);
-                    CK(launch_axpby(N, -alpha, col(G, i), 1.0, col(G, k), s));
-                    CK(launch_axpby(N, -alpha, col(U, i), 1.0, col(U, k), s));
+                    // G_k -= alpha G_i and U_k -= alpha U_i in one pass
+                    CK(launch_axpy2(N, -alpha, col(G, i), col(G, k), -alpha, col(U, i), col(U, k), nullptr, nullptr,
+                                    s));
                 }
                 CKS(multidot(sd - k, col(P, k), col(G, k), dots.data()));              // M[k:, k] = P^T G_k
                 for (int i = k; i < sd; ++i) M(i, k) = dots[i - k];
                 if (!std::isfinite(M(k, k)) || M(k, k) == 0.0) { st = STOKES_BREAKDOWN; done = true; break; }
                 const double beta = f[k] / M(k, k);
-                CK(launch_axpby(N, -beta, col(G, k), 1.0, r, s));
-                CK(launch_axpby(N, beta, col(U, k), 1.0, x, s));
-                CKS(dot(c, N, r, r, s, &rr));
+                // r -= beta G_k, x += beta U_k and |r|^2 in one pass
+                CK(launch_axpy2(N, -beta, col(G, k), r, beta, col(U, k), x, c->partials, c->dots, s));
+                CKS(fetch(c, 1, s, &rr));
                 rnorm = std::sqrt(rr);
                 if (!std::isfinite(rnorm)) { st = STOKES_BREAKDOWN; done = true; break; }
                 if (rnorm <= tol) { st = STOKES_OK; done = true; break; }
@@ -1394,16 +1392,16 @@ stokes_status idr_solve(stokes_ctx* c, int prec, const double* b, double* x, dou
             CKS(precondition(c, prec, r, v, s));
             CKS(apply_stokes(c, v, t, s));
             ++its;
-            double tt = 0.0, tr = 0.0;
-            CKS(dot(c, N, t, t, s, &tt));
-            CKS(dot(c, N, t, r, s, &tr));
+            double t2[2] = {0.0, 0.0};
+            CK(launch_dot2(N, t, t, r, c->partials, c->dots, s));   // t . t and t . r in one pass
+            CKS(fetch(c, 2, s, t2));
+            const double tt = t2[0], tr = t2[1];
             if (!(tt > 0.0) || !std::isfinite(tt)) { st = STOKES_BREAKDOWN; break; }
             om = tr / tt;
             const double rho = std::fabs(tr) / (std::sqrt(tt) * rnorm);
             if (rho < 0.7) om = om * 0.7 / rho;
-            CK(launch_axpby(N, om, v, 1.0, x, s));
-            CK(launch_axpby(N, -om, t, 1.0, r, s));
-            CKS(dot(c, N, r, r, s, &rr));
+            CK(launch_axpy2(N, -om, t, r, om, v, x, c->partials, c->dots, s));   // r -= om t, x += om v, |r|^2
+            CKS(fetch(c, 1, s, &rr));
             rnorm = std::sqrt(rr);
             if (!std::isfinite(rnorm)) { st = STOKES_BREAKDOWN; break; }
             if (rnorm <= tol) { st = STOKES_OK; break; }
@@ -1485,12 +1483,9 @@ stokes_status minres_solve(stokes_ctx* c, int prec, const double* b, double* x, 
             const double a2 = sn * delta + c_old * cs * gamma;
             const double a3 = s_old * gamma;
             // next Lanczos vector (scaled by gamma_new) into v_old; unnormalised w and K w
-            CK(launch_axpby(N, 1.0, q, -gamma / gamma_old, v_old, s));
-            CK(launch_axpby(N, -delta / gamma, v, 1.0, v_old, s));
-            CK(launch_axpby(N, 1.0, q, -a3, Kw_old, s));
-            CK(launch_axpby(N, -a2, Kw, 1.0, Kw_old, s));
-            CK(launch_axpby(N, 1.0, z, -a3, w_old, s));
-            CK(launch_axpby(N, -a2, w, 1.0, w_old, s));
+            // the three recurrences in one pass (each the two axpby steps of the unfused form)
+            CK(launch_minres_dirs(N, q, z, v_old, v, -gamma / gamma_old, -delta / gamma, Kw_old, Kw, -a3, -a2, w_old,
+                                  w, -a3, -a2, s));
             CKS(precondition(c, prec, v_old, q, s));                             // z_new into q
             CKS(dot(c, N, v_old, q, s, &g2));
             if (!(g2 >= 0.0) || !std::isfinite(g2)) { st = STOKES_BREAKDOWN; done = true; break; }
@@ -1500,10 +1495,8 @@ stokes_status minres_solve(stokes_ctx* c, int prec, const double* b, double* x, 
             s_old = sn;
             cs = a0 / a1;
             sn = gamma_new / a1;
-            CK(launch_axpby(N, 0.0, w_old, 1.0 / a1, w_old, s));               // w_new
-            CK(launch_axpby(N, 0.0, Kw_old, 1.0 / a1, Kw_old, s));             // K w_new
-            CK(launch_axpby(N, cs * eta, w_old, 1.0, x, s));
-            CK(launch_axpby(N, -cs * eta, Kw_old, 1.0, r, s));
+            // w_new = w_old / a1, K w_new likewise, x += cs eta w_new, r -= cs eta K w_new, |r|^2
+            CK(launch_minres_update(N, 1.0 / a1, w_old, Kw_old, cs * eta, x, r, c->partials, c->dots, s));
             eta = -sn * eta;
             ++its;
             std::swap(v_old, v);      // v <- v_new, v_old <- v
@@ -1512,7 +1505,7 @@ stokes_status minres_solve(stokes_ctx* c, int prec, const double* b, double* x, 
             std::swap(Kw_old, Kw);
             gamma_old = gamma;
             gamma = gamma_new;
-            CKS(dot(c, N, r, r, s, &rr));
+            CKS(fetch(c, 1, s, &rr));
             rnorm = std::sqrt(rr);
             if (!std::isfinite(rnorm)) { st = STOKES_BREAKDOWN; done = true; break; }
             if (rnorm <= tol || gamma == 0.0) break;

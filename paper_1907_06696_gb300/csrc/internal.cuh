@@ -120,6 +120,24 @@ int multidot_blocks();
 // w -= sum_i h[i] V[i*ld + :], i < k (h on device); with sign = +1 adds instead.
 cudaError_t launch_multiaxpy(size_t n, int k, const double* V, size_t ld, const double* h, double* w, double sign,
                              cudaStream_t s);
+// Fused vector passes of IDR(s) and MINRES (FP64). out non-null: out[0] (out[0..1] for dot2) on the
+// device from the partials, as launch_multidot.
+// y1 += a1 x1, y2 += a2 x2 (x2 null: no second update); out: y1 . y1 of the updated y1
+cudaError_t launch_axpy2(size_t n, double a1, const double* x1, double* y1, double a2, const double* x2, double* y2,
+                         double* partials, double* out, cudaStream_t s);
+// out[0] = x . y1, out[1] = x . y2
+cudaError_t launch_dot2(size_t n, const double* x, const double* y1, const double* y2, double* partials, double* out,
+                        cudaStream_t s);
+// w = a src + sign sum_{i<k} h_i V_i (h on the device; w may alias src or a row of V)
+cudaError_t launch_lincomb(size_t n, int k, const double* V, size_t ld, const double* h, double a, const double* src,
+                           double* w, double sign, cudaStream_t s);
+// vo = q + bv vo + cv v, kwo = q + bk kwo + ck kw, wo = z + bw wo + cw w
+cudaError_t launch_minres_dirs(size_t n, const double* q, const double* z, double* vo, const double* v, double bv,
+                               double cv, double* kwo, const double* kw, double bk, double ck, double* wo,
+                               const double* w, double bw, double cw, cudaStream_t s);
+// w *= f, kw *= f, x += e w, r -= e kw; out[0] = r . r
+cudaError_t launch_minres_update(size_t n, double f, double* w, double* kw, double e, double* x, double* r,
+                                 double* partials, double* out, cudaStream_t s);
 
 // Fused Gram-Schmidt passes (krylov.cu), all results on the device; `partials` holds
 // gs_partials_blocks() * (k + 1) doubles at least. df = double-float arithmetic with V stored

@@ -362,6 +362,91 @@ __global__ void k_multiaxpy(size_t n, int k, const double* __restrict__ V, size_
     }
 }
 
+// ---- fused vector passes of the memory-light solvers (IDR(s), MINRES): several updates of the
+// same entries, and the norm of an updated vector, in one sweep. Grid kDotBlocks x kDotThreads so
+// that the per-block partial sums land where k_multidot_final reads them.
+
+// y1 += a1 x1, y2 += a2 x2 (x2 null: y2 untouched); partials non-null: row 0 = slices of y1 . y1
+__global__ void __launch_bounds__(kDotThreads) k_axpy2(size_t n, double a1, const double* __restrict__ x1,
+                                                       double* __restrict__ y1, double a2,
+                                                       const double* __restrict__ x2, double* __restrict__ y2,
+                                                       double* __restrict__ partials) {
+    double acc = 0.0;
+    for (size_t e = size_t(blockIdx.x) * kDotThreads + threadIdx.x; e < n; e += size_t(kDotBlocks) * kDotThreads) {
+        const double v = y1[e] + a1 * x1[e];
+        y1[e] = v;
+        acc += v * v;
+        if (x2) y2[e] += a2 * x2[e];
+    }
+    if (partials) {
+        const double sum = block_sum(acc);
+        if (threadIdx.x == 0) partials[blockIdx.x] = sum;
+    }
+}
+
+// rows 0, 1 = slices of x . y1 and x . y2
+__global__ void __launch_bounds__(kDotThreads) k_dot2_partial(size_t n, const double* __restrict__ x,
+                                                              const double* __restrict__ y1,
+                                                              const double* __restrict__ y2,
+                                                              double* __restrict__ partials) {
+    double a = 0.0, b = 0.0;
+    for (size_t e = size_t(blockIdx.x) * kDotThreads + threadIdx.x; e < n; e += size_t(kDotBlocks) * kDotThreads) {
+        const double xe = x[e];
+        a += xe * y1[e];
+        b += xe * y2[e];
+    }
+    const double sa = block_sum(a), sb = block_sum(b);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = sa;
+        partials[kDotBlocks + blockIdx.x] = sb;
+    }
+}
+
+// w = a src + sign sum_i h_i V_i; w may be src or one of the rows V_i (each entry is read before
+// it is written, by the same thread), so no restrict on them
+__global__ void k_lincomb(size_t n, int k, const double* V, size_t ld, const double* __restrict__ h, double a,
+                          const double* src, double* w, double sign) {
+    for (size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += size_t(gridDim.x) * blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < k; ++i) s += h[i] * V[size_t(i) * ld + e];
+        w[e] = a * src[e] + sign * s;
+    }
+}
+
+// MINRES: the next Lanczos vector and the two recurrences of the search directions,
+//   vo = q + bv vo + cv v,  kwo = q + bk kwo + ck kw,  wo = z + bw wo + cw w,
+// each as the two axpby steps of the unfused form in the same order
+__global__ void k_minres_dirs(size_t n, const double* __restrict__ q, const double* __restrict__ z,
+                              double* __restrict__ vo, const double* __restrict__ v, double bv, double cv,
+                              double* __restrict__ kwo, const double* __restrict__ kw, double bk, double ck,
+                              double* __restrict__ wo, const double* __restrict__ w, double bw, double cw) {
+    for (size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += size_t(gridDim.x) * blockDim.x) {
+        const double qe = q[e];
+        vo[e] = cv * v[e] + (qe + bv * vo[e]);
+        kwo[e] = ck * kw[e] + (qe + bk * kwo[e]);
+        wo[e] = cw * w[e] + (z[e] + bw * wo[e]);
+    }
+}
+
+// MINRES: scale the new directions by f, x += e w, r -= e K w; row 0 of partials = slices of r . r
+__global__ void __launch_bounds__(kDotThreads) k_minres_update(size_t n, double f, double* __restrict__ w,
+                                                               double* __restrict__ kw, double e_,
+                                                               double* __restrict__ x, double* __restrict__ r,
+                                                               double* __restrict__ partials) {
+    double acc = 0.0;
+    for (size_t e = size_t(blockIdx.x) * kDotThreads + threadIdx.x; e < n; e += size_t(kDotBlocks) * kDotThreads) {
+        const double we = f * w[e], kwe = f * kw[e];
+        w[e] = we;
+        kw[e] = kwe;
+        x[e] += e_ * we;
+        const double re = r[e] - e_ * kwe;
+        r[e] = re;
+        acc += re * re;
+    }
+    const double sum = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = sum;
+}
+
 inline unsigned grid_stride_blocks(size_t n) {
     const size_t b = (n + 255) / 256;
     return unsigned(b < 4864 ? (b == 0 ? 1 : b) : 4864);
@@ -484,6 +569,41 @@ cudaError_t launch_multidot(size_t n, int k, const double* V, size_t ld, const d
     dim3 grid(kDotBlocks, unsigned((kt + kDotBatch - 1) / kDotBatch));
     LAUNCH(PROF_KRYLOV, s, k_multidot_partial<<<grid, kDotThreads, 0, s>>>(n, k, self ? 1 : 0, V, ld, w, partials));
     LAUNCH(PROF_KRYLOV, s, k_multidot_final<<<unsigned(kt), kDotThreads, 0, s>>>(kt, partials, out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpy2(size_t n, double a1, const double* x1, double* y1, double a2, const double* x2, double* y2,
+                         double* partials, double* out, cudaStream_t s) {
+    LAUNCH(PROF_KRYLOV, s, k_axpy2<<<kDotBlocks, kDotThreads, 0, s>>>(n, a1, x1, y1, a2, x2, y2, out ? partials : nullptr));
+    if (out) LAUNCH(PROF_KRYLOV, s, k_multidot_final<<<1, kDotThreads, 0, s>>>(1, partials, out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dot2(size_t n, const double* x, const double* y1, const double* y2, double* partials, double* out,
+                        cudaStream_t s) {
+    LAUNCH(PROF_KRYLOV, s, k_dot2_partial<<<kDotBlocks, kDotThreads, 0, s>>>(n, x, y1, y2, partials));
+    LAUNCH(PROF_KRYLOV, s, k_multidot_final<<<2, kDotThreads, 0, s>>>(2, partials, out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lincomb(size_t n, int k, const double* V, size_t ld, const double* h, double a, const double* src,
+                           double* w, double sign, cudaStream_t s) {
+    LAUNCH(PROF_KRYLOV, s, k_lincomb<<<grid_stride_blocks(n), 256, 0, s>>>(n, k, V, ld, h, a, src, w, sign));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_minres_dirs(size_t n, const double* q, const double* z, double* vo, const double* v, double bv,
+                               double cv, double* kwo, const double* kw, double bk, double ck, double* wo,
+                               const double* w, double bw, double cw, cudaStream_t s) {
+    LAUNCH(PROF_KRYLOV, s, k_minres_dirs<<<grid_stride_blocks(n), 256, 0, s>>>(n, q, z, vo, v, bv, cv, kwo, kw, bk, ck,
+                                                                             wo, w, bw, cw));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_minres_update(size_t n, double f, double* w, double* kw, double e, double* x, double* r,
+                                 double* partials, double* out, cudaStream_t s) {
+    LAUNCH(PROF_KRYLOV, s, k_minres_update<<<kDotBlocks, kDotThreads, 0, s>>>(n, f, w, kw, e, x, r, partials));
+    LAUNCH(PROF_KRYLOV, s, k_multidot_final<<<1, kDotThreads, 0, s>>>(1, partials, out));
     return cudaGetLastError();
 }
 
