@@ -79,10 +79,7 @@ cudaError_t launch_prolongate(const LevelGeom& fine, const T* coarse, T* finev, 
 // coarse cell with atomic adds.
 template <typename T>
 cudaError_t launch_restrict(const LevelGeom& fine, const T* finev, T* coarse, cudaStream_t s, bool deterministic = false);
-// coarse = P^T r with r = b - acc formed on the fly and acc cleared (r null), or r given (b, acc
-// null); clears coarse first.
-template <typename T>
-cudaError_t launch_restrict_resid(const LevelGeom& fine, const T* r, const T* b, T* acc, T* coarse, cudaStream_t s);
+
 // Chebyshev update: r = Dinv (b - Ax) (Ax may be null = 0); d = c1 d + c2 r; x = (x_valid ? x : 0) + d.
 template <typename T>
 cudaError_t launch_cheb_update(size_t n, const T* b, const T* Ax, const T* dinv, T* d, T* x, double c1, double c2,

@@ -140,11 +140,9 @@ __global__ void __launch_bounds__(128) k_prolong_cells(int nc, const T* __restri
     }
 }
 
-// coarse += P^T r on the free coarse nodes (coarse zero on entry), r = fine_r, or r = b - acc with
-// acc cleared at the nodes read (the V-cycle residual, formed here instead of in a pass of its own)
+// coarse += P^T r on the free coarse nodes (coarse zero on entry)
 template <typename T>
-__global__ void __launch_bounds__(128) k_restrict_cells(int nc, const T* __restrict__ fine_r, const T* __restrict__ b,
-                                                        T* __restrict__ acc, T* __restrict__ coarse) {
+__global__ void __launch_bounds__(128) k_restrict_cells(int nc, const T* __restrict__ fine_r, T* __restrict__ coarse) {
     const size_t ncell = size_t(nc) * nc * nc;
     const size_t t = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (t >= 3 * ncell) return;
@@ -165,24 +163,10 @@ __global__ void __launch_bounds__(128) k_restrict_cells(int nc, const T* __restr
             for (int z = 0; z < 5; ++z) {
                 const bool own = (x < 4 || lx) && (y < 4 || ly) && (z < 4 || lz);
                 const size_t f = fbase + x + size_t(Mf) * (y + size_t(Mf) * z);
-                T r = T(0);
-                if (own) r = fine_r ? fine_r[f] : b[f] - acc[f];
-                v[z] = r;
+                v[z] = own ? fine_r[f] : T(0);
             }
             res3(v, t2[x][y][0], t2[x][y][1], t2[x][y][2]);
         }
-    // clear the accumulator only after every load: a store between them would keep each later load
-    // of acc behind it (one memory latency per line)
-    if (!fine_r) {
-#pragma unroll
-        for (int y = 0; y < 5; ++y)
-#pragma unroll
-            for (int x = 0; x < 5; ++x)
-#pragma unroll
-                for (int z = 0; z < 5; ++z)
-                    if ((x < 4 || lx) && (y < 4 || ly) && (z < 4 || lz))
-                        acc[fbase + x + size_t(Mf) * (y + size_t(Mf) * z)] = T(0);
-    }
     T t1[5][3][3];   // [x][b][d]
 #pragma unroll
     for (int d = 0; d < 3; ++d)
@@ -468,26 +452,19 @@ template cudaError_t launch_prolongate<double>(const LevelGeom&, const double*, 
 
 template <typename T>
 cudaError_t launch_restrict(const LevelGeom& fine, const T* finev, T* coarse, cudaStream_t s, bool deterministic) {
-    if (!deterministic) return launch_restrict_resid<T>(fine, finev, nullptr, nullptr, coarse, s);
-    const size_t Mc = size_t(fine.n) + 1;
-    LAUNCH(PROF_TRANSFER, s, k_restrict_nodes<T><<<blocks_for(Mc * Mc * Mc, 256), 256, 0, s>>>(fine.n, finev, coarse));
-    return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_restrict_resid(const LevelGeom& fine, const T* r, const T* b, T* acc, T* coarse, cudaStream_t s) {
+    if (deterministic) {
+        const size_t Mc = size_t(fine.n) + 1;
+        LAUNCH(PROF_TRANSFER, s, k_restrict_nodes<T><<<blocks_for(Mc * Mc * Mc, 256), 256, 0, s>>>(fine.n, finev, coarse));
+        return cudaGetLastError();
+    }
     const int nc = fine.n / 2;
     const size_t Mc = size_t(2 * nc) + 1;
     cudaError_t e = cudaMemsetAsync(coarse, 0, 3 * Mc * Mc * Mc * sizeof(T), s);
     if (e != cudaSuccess) return e;
     const size_t threads = 3 * size_t(nc) * nc * nc;
-    LAUNCH(PROF_TRANSFER, s, k_restrict_cells<T><<<blocks_for(threads, 128), 128, 0, s>>>(nc, r, b, acc, coarse));
+    LAUNCH(PROF_TRANSFER, s, k_restrict_cells<T><<<blocks_for(threads, 128), 128, 0, s>>>(nc, finev, coarse));
     return cudaGetLastError();
 }
-template cudaError_t launch_restrict_resid<float>(const LevelGeom&, const float*, const float*, float*, float*,
-                                                  cudaStream_t);
-template cudaError_t launch_restrict_resid<double>(const LevelGeom&, const double*, const double*, double*, double*,
-                                                   cudaStream_t);
 template cudaError_t launch_restrict<float>(const LevelGeom&, const float*, float*, cudaStream_t, bool);
 template cudaError_t launch_restrict<double>(const LevelGeom&, const double*, double*, cudaStream_t, bool);
 
