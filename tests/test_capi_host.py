@@ -26,6 +26,9 @@ def test_exports_every_header_function(lib):
 def test_defaults_and_strerror(lib):
     o = capi.stokes_default_options()
     assert (o.cheb_degree, o.lanczos_steps, o.schur_degree, o.restart) == (4, 12, 5, 50)
+    # the last fields of the struct: their defaults pin the ctypes layout against the header's
+    assert abs(o.wait_limit_s - 1.0) < 1e-15 and o.batch_vcycle == 0 and o.fused_smoother == 0
+    assert (o.vmult_kernel, o.outer_arith, o.graphs) == (0, 1, 1)
     assert abs(o.smoothing_range - 15.0) < 1e-15 and abs(o.eig_safety - 1.2) < 1e-15
     assert lib.stokes_strerror(capi.STOKES_EMESH) == b"unsupported mesh"
 
