@@ -205,6 +205,50 @@ def test_BT_of_linear_pressure_and_adjointness():
     assert abs(ops.apply_B(u) @ q - u @ ops.apply_BT(q)) < 1e-13
 
 
+def _moments_1d(n, deriv):
+    """Assembled 1D moments X[i, v] = int over [0, 1] of (l_i or l_i') psi_v for the Q2 nodes i
+    (2n + 1, on n cells of side 1/n) against the Q1 vertices v (n + 1): the exact integrals of
+    piecewise polynomials of degree <= 3, by 3-point Gauss-Legendre per cell (numpy's nodes),
+    in reference-cell units (no powers of h)."""
+    xg, wg = np.polynomial.legendre.leggauss(3)
+    xg, wg = (xg + 1) / 2, wg / 2
+    X = np.zeros((2 * n + 1, n + 1))
+    for e in range(n):
+        for x, w in zip(xg, wg):
+            # Q2 nodes at 0, 1/2, 1 of the cell and Q1 vertices at 0, 1, by Lagrange's formula
+            q2 = [2 * (x - 0.5) * (x - 1), -4 * x * (x - 1), 2 * x * (x - 0.5)]
+            dq2 = [4 * x - 3, -8 * x + 4, 4 * x - 1]
+            q1 = [1 - x, x]
+            for a in range(3):
+                for v in range(2):
+                    X[2 * e + a, e + v] += w * (dq2[a] if deriv else q2[a]) * q1[v]
+    return X
+
+
+@pytest.mark.parametrize("n", [2, 3, 5])
+def test_BT_is_a_tensor_product_of_assembled_1d_moments(n):
+    """B^T carries no viscosity: component c of B^T p is -h^2 (X_z x X_y x X_x) p with the 1D
+    moments X assembled along each axis (derivative moments along axis c, plain moments along the
+    other two), on every free row; the rows of constrained velocity nodes are 0. Computed here from
+    1D Gauss quadrature of the Lagrange bases, independent of the element matrices (the form the
+    uniform-mesh B^T kernel evaluates)."""
+    m = mesh.Mesh(n)
+    mu = 0.5 + si.uniform01(31, m.n_cells) * 10     # any viscosity: B^T must not see it
+    ops = operators.Operators(m, mu)
+    p = si.uniform(32, m.n_p)
+    got = ops.apply_BT(p)
+    V, D = _moments_1d(n, False), _moments_1d(n, True)
+    P = n + 1
+    pg = p.reshape(P, P, P)   # [k][j][i], vertex = i + P j + P^2 k
+    for c in range(3):
+        X = [D if c == d else V for d in range(3)]
+        want = -m.h ** 2 * np.einsum("ia,jb,kc,cba->kji", X[0], X[1], X[2], pg).ravel()
+        rows = got[c * m.n_nodes:(c + 1) * m.n_nodes]
+        free = ~m.dirichlet[c * m.n_nodes:(c + 1) * m.n_nodes]
+        assert np.allclose(rows[free], want[free], rtol=1e-13, atol=1e-15 * np.abs(want).max())
+        assert np.all(rows[~free] == 0.0)
+
+
 def test_Mp_integrals_and_wathen_bound():
     n = 3
     m = mesh.Mesh(n)
