@@ -576,8 +576,9 @@ cudaError_t launch_stokes_blocks(const LevelGeom& g, const double* mu, const dou
                                  double* dst_u, double* dst_p, bool do_a, bool do_bt, bool do_b, bool df64,
                                  cudaStream_t s) {
     cudaError_t e;
-    // B^T alone (the preconditioner's): the gather writes every velocity entry, no clear needed
-    if (df64 && !do_a && do_bt && !do_b) return launch_bt_gather(g, src_p, dst_u, s);
+    // B^T alone (the preconditioner's): the gather writes every velocity entry, no clear needed;
+    // its blocks hold one thread per vertex of a line (n + 1 <= 1024)
+    if (df64 && !do_a && do_bt && !do_b && g.n + 1 <= 1024) return launch_bt_gather(g, src_p, dst_u, s);
     if (do_a || do_bt) {
         e = cudaMemsetAsync(dst_u, 0, g.n_u * sizeof(double), s);
         if (e != cudaSuccess) return e;
