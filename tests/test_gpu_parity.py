@@ -6,7 +6,7 @@ Tolerances (derived from the arithmetic):
   order (sum factorisation vs element matrices, atomics vs bincount). Each
   output is a sum of <= 8 cells x 81 terms of similar magnitude, so the
   rounding difference is a few hundred ulp at most: relative 2-norm error
-  <= 1e-12 (the benchmark spec's bound) and max-norm error <= 1e-12 ||ref||_inf.
+  <= 1e-12 (the required FP64 bound) and max-norm error <= 1e-12 ||ref||_inf.
 * FP32 operator / transfer kernels: inputs rounded to FP32 (2^-24 relative)
   and ~100 FP32 operations per output: relative error <= 2e-6.
 * FP32 smoothing and V-cycle: the same per-kernel error, propagated through
