@@ -13,6 +13,7 @@
 #include "q2_basis.cuh"
 #include "df64.cuh"
 #include "prof.cuh"
+#include "pressure.cuh"
 
 #define LAUNCH(cls, s, ...)              \
     do {                                \
@@ -215,45 +216,12 @@ __global__ void k_mass_p(int n, double h, const double* __restrict__ mu, const d
     }
 }
 
-// ---- B^T on the uniform mesh as a gather. B^T carries no viscosity, so component c of B^T p is
-// -h^2 (X_2 x X_1 x X_0) p with X_d the 1D moment operator assembled over the cells along axis d
-// (DP, the moments of the Q2 basis derivatives against the Q1 basis, along axis c; VP, those of
-// the basis itself, along the other two). An interior Q2 node 2e (a vertex) has the row
-// (XP(2,0), XP(2,1) + XP(0,0), XP(0,1)) at vertices e-1, e, e+1, an interior node 2e+1 the row
-// (XP(1,0), XP(1,1)) at e, e+1. Thread (c, e, J, K) forms t_a = sum X_1[J][b] X_2[K][k] p(a, b, k)
-// for a = e-1, e, e+1 and writes the x-nodes 2e and 2e+1 of the line (J, K); boundary nodes get 0,
-// as in the cell kernels. No atomics; double-float products on the FP32 pipes.
-template <int C>
-__device__ __forceinline__ double bt_x_row(int i, int a, int e) {
-    // entry of X_0 (axis 0) in row i at vertex a, for the rows this thread writes (i = 2e, 2e + 1)
-    constexpr bool D = C == 0;
-    auto xp = [](int m, int v) { return D ? q2::DP(m, v) : q2::VP(m, v); };
-    if (i & 1) return a == e ? xp(1, 0) : (a == e + 1 ? xp(1, 1) : 0.0);
-    return a == e - 1 ? xp(2, 0) : (a == e ? xp(2, 1) + xp(0, 0) : (a == e + 1 ? xp(0, 1) : 0.0));
-}
-
-template <int C, int AX>
-__device__ __forceinline__ void bt_row(int i, double (&w)[3]) {
-    // row i of X_AX (interior i) over the vertices i/2 - 1, i/2, i/2 + 1
-    constexpr bool D = C == AX;
-    auto xp = [](int m, int v) { return D ? q2::DP(m, v) : q2::VP(m, v); };
-    if (i & 1) {   // vertices i/2, i/2 + 1
-        w[0] = 0.0;
-        w[1] = xp(1, 0);
-        w[2] = xp(1, 1);
-    } else {
-        w[0] = xp(2, 0);
-        w[1] = xp(2, 1) + xp(0, 0);
-        w[2] = xp(0, 1);
-    }
-}
-
-// Block (line (J, K), component c): thread e forms t_e = sum_{b,k} X_1[J][b] X_2[K][k] p(e, b, k)
-// into shared memory, then writes the x-nodes 2e and 2e + 1 of the line from t_{e-1}, t_e, t_{e+1}.
+// ---- B^T on the uniform mesh as a gather (pressure.cuh). Block (line (J, K), component c):
+// threads 0..8 put the line's weights, thread e then t_e into shared memory; thread e writes the
+// x-nodes 2e and 2e + 1. No atomics.
 template <int C>
 __device__ __forceinline__ void bt_line(int n, double s, const double* __restrict__ p, double* __restrict__ out,
                                         int J, int K, q2::df64* t, q2::df64* w) {
-    using q2::df64;
     const int P = n + 1, M = 2 * n + 1;
     const int e = int(threadIdx.x);
     double* o = out + size_t(C) * size_t(M) * M * M + size_t(M) * (J + size_t(M) * K);
@@ -261,45 +229,11 @@ __device__ __forceinline__ void bt_line(int n, double s, const double* __restric
         for (int i = e; i < M; i += int(blockDim.x)) o[i] = 0.0;
         return;
     }
-    if (e < 9) {   // the 9 (b, k) weights of the line
-        double wy[3], wz[3];
-        bt_row<C, 1>(J, wy);
-        bt_row<C, 2>(K, wz);
-        w[e] = q2::split_double(wy[e % 3] * wz[e / 3]);
-    }
+    if (e < 9) w[e] = bt_weight<C>(J, K, e);
     __syncthreads();
-    const int by = J / 2 - 1, bz = K / 2 - 1;
-    if (e < P) {
-        df64 acc;
-#pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            const int b = by + q % 3, k = bz + q / 3;
-            if (b < 0 || b >= P || k < 0 || k >= P) continue;   // zero weights only
-            q2::mac(acc, w[q], q2::split_double(p[size_t(e) + size_t(P) * (b + size_t(P) * k)]));
-        }
-        q2::renorm(acc);
-        t[e] = acc;
-    }
+    if (e < P) t[e] = bt_t<C>(n, p, J, K, e, w);
     __syncthreads();
-    if (e >= P) return;
-    const int i0 = 2 * e;
-    if (i0 == 0 || i0 == M - 1) {
-        o[i0] = 0.0;
-    } else {
-        df64 v;
-        q2::mac(v, df64(bt_x_row<C>(i0, e - 1, e)), t[e - 1]);
-        q2::mac(v, df64(bt_x_row<C>(i0, e, e)), t[e]);
-        q2::mac(v, df64(bt_x_row<C>(i0, e + 1, e)), t[e + 1]);
-        q2::renorm(v);
-        o[i0] = s * v.to_double();
-    }
-    if (e < n) {
-        df64 v;
-        q2::mac(v, df64(bt_x_row<C>(i0 + 1, e, e)), t[e]);
-        q2::mac(v, df64(bt_x_row<C>(i0 + 1, e + 1, e)), t[e + 1]);
-        q2::renorm(v);
-        o[i0 + 1] = s * v.to_double();
-    }
+    if (e < P) bt_out<C>(n, s, o, e, t);
 }
 
 __global__ void k_bt_gather(int n, double h, const double* __restrict__ p, double* __restrict__ out) {
@@ -321,59 +255,16 @@ __global__ void k_mass_scale(size_t cells, double h, const double* __restrict__ 
     if (cell < cells) scale[cell] = h * h * h / mu[cell];
 }
 
-// One Jacobi-Chebyshev step of S_hat^-1 with the M_p product gathered per pressure vertex:
-//   d' = c1 d + c2 D^-1 (r - M_p z),  z' = z + d'   (into the other buffers of the pairs).
-// (M_p z)_v sums the element products of the up to 8 cells around v, s_K sum_w m(v, w) z_w with
-// m = M1 x M1 x M1 (M1 the 1D Q1 mass matrix on [0,1]); no atomics, one thread per vertex. The
-// products run in double-float on the FP32 pipes (the 27 neighbouring values split once): in FP64
-// the 64 multiply-adds per vertex would bind the kernel to the FP64 pipe (1/72 of the FP32 rate).
+// One Jacobi-Chebyshev step of S_hat^-1 with the M_p product gathered per pressure vertex
+// (pressure.cuh schur_vertex): one thread per vertex, no atomics.
 __global__ void __launch_bounds__(128) k_schur_cheb(int n, const double* __restrict__ scale, const double* __restrict__ r,
                                                     const double* __restrict__ dinv, const double* __restrict__ z,
                                                     const double* __restrict__ d, double* __restrict__ z_new,
                                                     double* __restrict__ d_new, double c1, double c2) {
-    using q2::df64;
     const int P = n + 1;
     const size_t vtx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (vtx >= size_t(P) * P * P) return;
-    const int vi = int(vtx % P), vj = int((vtx / P) % P), vk = int(vtx / (size_t(P) * P));
-    df64 zz[3][3][3];   // [k][j][i], the vertex (vi + i - 1, vj + j - 1, vk + k - 1)
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const int wi = vi + i - 1, wj = vj + j - 1, wk = vk + k - 1;
-                const bool in = wi >= 0 && wj >= 0 && wk >= 0 && wi < P && wj < P && wk < P;
-                zz[k][j][i] = in ? q2::split_double(z[size_t(wi) + size_t(P) * (wj + size_t(P) * wk)]) : df64();
-            }
-    df64 acc;
-#pragma unroll
-    for (int ck = 0; ck < 2; ++ck)
-#pragma unroll
-        for (int cj = 0; cj < 2; ++cj)
-#pragma unroll
-            for (int ci = 0; ci < 2; ++ci) {
-                // cell (vi - 1 + ci, ...): v is its local corner (1 - ci, 1 - cj, 1 - ck)
-                const int gi = vi - 1 + ci, gj = vj - 1 + cj, gk = vk - 1 + ck;
-                if (gi < 0 || gj < 0 || gk < 0 || gi >= n || gj >= n || gk >= n) continue;
-                df64 inner;
-#pragma unroll
-                for (int wk = 0; wk < 2; ++wk)
-#pragma unroll
-                    for (int wj = 0; wj < 2; ++wj)
-#pragma unroll
-                        for (int wi = 0; wi < 2; ++wi) {
-                            const double m = q2::M1(1 - ci, wi) * q2::M1(1 - cj, wj) * q2::M1(1 - ck, wk);
-                            q2::mac(inner, df64(m), zz[ck + wk][cj + wj][ci + wi]);
-                        }
-                q2::renorm(inner);
-                acc = acc + q2::split_double(scale[size_t(gi) + size_t(n) * (gj + size_t(n) * gk)]) * inner;
-            }
-    const double mz = acc.to_double();
-    const double dn = (c1 != 0.0 ? c1 * d[vtx] : 0.0) + c2 * (dinv[vtx] * (r[vtx] - mz));
-    d_new[vtx] = dn;
-    z_new[vtx] = z[vtx] + dn;
+    schur_vertex(n, scale, r, dinv, z, d, z_new, d_new, c1, c2, vtx);
 }
 
 __global__ void k_mass_p_diag(int n, double h, const double* __restrict__ mu, double* __restrict__ diag,
