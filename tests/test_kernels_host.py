@@ -167,3 +167,42 @@ def test_schur_step_matches_oracle(pressure_lib, name, c1):
                                         d.ctypes.data, z_new.ctypes.data, d_new.ctypes.data, c1, c2) == 0
     assert rel(d_new, d_ref) <= 1e-13
     assert rel(z_new, z_ref) <= 1e-13
+
+
+def log_uniform(rng, size, lo, hi):
+    return 10.0 ** rng.uniform(np.log10(lo), np.log10(hi), size)
+
+
+def test_bt_gather_wide_magnitudes(pressure_lib):
+    """Double-float B^T (float exponent range, ~47-bit significands) with pressures of magnitude
+    1e-6..1e6 and random signs, h = 1/8: still within 1e-12 of the oracle's FP64 B^T."""
+    n = 8
+    m = mesh.Mesh(n)
+    ops = operators.Operators(m, np.ones(m.n_cells))
+    rng = np.random.default_rng(100)
+    p = rng.choice([-1.0, 1.0], m.n_p) * log_uniform(rng, m.n_p, 1e-6, 1e6)
+    ref = ops.apply_BT(p)
+    out = np.empty(m.n_u)
+    assert pressure_lib.bt_apply_host(n, m.h, p.ctypes.data, out.ctypes.data) == 0
+    assert rel(out, ref) <= 1e-12
+
+
+def test_schur_step_wide_viscosity(pressure_lib):
+    """The S_hat^-1 step with the cell viscosity log-uniform over 1e-12..1e12 (s_K = h^3 / mu_K over
+    24 decades) and z, d, r of magnitude 1e-6..1e6: within 1e-12 of the FP64 step."""
+    n = 8
+    m = mesh.Mesh(n)
+    rng = np.random.default_rng(101)
+    mu = log_uniform(rng, m.n_cells, 1e-12, 1e12)
+    ops = operators.Operators(m, mu)
+    r, z, d = (rng.choice([-1.0, 1.0], m.n_p) * log_uniform(rng, m.n_p, 1e-6, 1e6) for _ in range(3))
+    dinv = 1.0 / ops.diag_Mp()
+    c1, c2 = 0.37, 1.9
+    d_ref = c1 * d + c2 * dinv * (r - ops.apply_Mp(z))
+    scale = np.ascontiguousarray(m.h ** 3 / mu)
+    z_new = np.empty(m.n_p)
+    d_new = np.empty(m.n_p)
+    assert pressure_lib.schur_step_host(n, scale.ctypes.data, r.ctypes.data, dinv.ctypes.data, z.ctypes.data,
+                                        d.ctypes.data, z_new.ctypes.data, d_new.ctypes.data, c1, c2) == 0
+    assert rel(d_new, d_ref) <= 1e-12
+    assert rel(z_new, z + d_ref) <= 1e-12
