@@ -116,6 +116,81 @@ def test_element_B_and_Mp_closed_forms():
     assert abs(px @ fe.element_Mp(h, 1.0) @ px - h ** 5 / 3.0) < 1e-15
 
 
+
+def _exact_1d_q2():
+    """Exact 1D matrices of the Q2 Lagrange basis on [0, 1] (nodes 0, 1/2, 1), by integrating the
+    polynomial products with rational arithmetic: K_pq = int l_p' l_q', M_pq = int l_p l_q,
+    C_pq = int l_p' l_q."""
+    from fractions import Fraction as Fr
+    basis = [[Fr(1), Fr(-3), Fr(2)], [Fr(0), Fr(4), Fr(-4)], [Fr(0), Fr(-1), Fr(2)]]   # coefficients of 1, x, x^2
+
+    def deriv(a):
+        return [a[1], 2 * a[2], Fr(0)]
+
+    def integral(a, b):   # int_0^1 a(x) b(x) dx
+        return sum(a[i] * b[j] / (i + j + 1) for i in range(3) for j in range(3))
+
+    d = [deriv(a) for a in basis]
+    K = [[integral(d[p], d[q]) for q in range(3)] for p in range(3)]
+    M = [[integral(basis[p], basis[q]) for q in range(3)] for p in range(3)]
+    C = [[integral(d[p], basis[q]) for q in range(3)] for p in range(3)]
+    return K, M, C
+
+
+def test_element_A_is_the_exact_tensor_product_form():
+    """The 81 x 81 element matrix of 2 mu eps:eps, entry by entry, against its closed form from
+    exactly integrated 1D matrices. For test function phi_I e_a and trial function phi_J e_b,
+    2 eps(phi_J e_b):eps(phi_I e_a) = delta_ab grad phi_I . grad phi_J + d_a phi_J d_b phi_I, and
+    each integral over the cube [0, h]^3 is a product of 1D factors (K / h along an axis that
+    carries both derivatives, the mixed C along an axis that carries one, h M elsewhere).
+    So 5400 A_hat / (mu h) is an integer matrix (lcm of 3 * 30 * 30 and 6 * 6 * 30), with entries
+    up to 2^15 on the diagonal."""
+    from fractions import Fraction as Fr
+    K, M, C = _exact_1d_q2()
+    # the textbook forms: K = [7 -8 1; -8 16 -8; 1 -8 7] / 3, M = [4 2 -1; 2 16 2; -1 2 4] / 30
+    assert K == [[Fr(7, 3), Fr(-8, 3), Fr(1, 3)], [Fr(-8, 3), Fr(16, 3), Fr(-8, 3)], [Fr(1, 3), Fr(-8, 3), Fr(7, 3)]]
+    assert M == [[Fr(4, 30), Fr(2, 30), Fr(-1, 30)], [Fr(2, 30), Fr(16, 30), Fr(2, 30)], [Fr(-1, 30), Fr(2, 30), Fr(4, 30)]]
+    h, mu = 0.37, 1.7
+    idx = [(i, j, k) for k in range(3) for j in range(3) for i in range(3)]   # local node i + 3 j + 9 k
+    want = np.zeros((81, 81))
+    for a in range(3):
+        for b in range(3):
+            for I, ni in enumerate(idx):
+                for J, nj in enumerate(idx):
+                    grad = Fr(0)
+                    if a == b:
+                        for d in range(3):   # axis d carries both derivatives
+                            t = K[ni[d]][nj[d]]
+                            for e in range(3):
+                                if e != d:
+                                    t *= M[ni[e]][nj[e]]
+                            grad += t
+                    cpl = Fr(1)
+                    for d in range(3):   # d_a phi_J d_b phi_I
+                        if d == a and d == b:
+                            cpl *= K[nj[d]][ni[d]]
+                        elif d == a:
+                            cpl *= C[nj[d]][ni[d]]
+                        elif d == b:
+                            cpl *= C[ni[d]][nj[d]]
+                        else:
+                            cpl *= M[nj[d]][ni[d]]
+                    want[a * 27 + I, b * 27 + J] = float(grad + cpl)
+    assert np.allclose(want * 5400, np.round(want * 5400), rtol=0, atol=1e-9)
+    assert np.abs(np.round(want * 5400)).max() == 2 ** 15
+    got = fe.element_A(h, mu)
+    assert np.abs(got - mu * h * want).max() <= 1e-13 * np.abs(got).max()
+
+
+def test_element_Mp_is_the_q1_mass_tensor_product():
+    """M_p's element matrix with the cell value of 1/mu is (h^3 / mu) m1 x m1 x m1, m1 = [2 1; 1 2] / 6
+    the exact 1D Q1 mass matrix on [0, 1], for every entry."""
+    h, inv_mu = 0.4, 0.3
+    m1 = np.array([[2.0, 1.0], [1.0, 2.0]]) / 6.0
+    want = inv_mu * h ** 3 * np.kron(m1, np.kron(m1, m1))
+    assert np.abs(fe.element_Mp(h, inv_mu) - want).max() <= 1e-15 * want.max()
+
+
 # ---------------------------------------------------------------- global operators
 def _int_phi_1d(M):
     """int of the global 1D Q2 basis function of each node on [0,1] with spacing h/2:
