@@ -1,0 +1,204 @@
+// sliced.cuh -- the outer Stokes operator [A B^T; B 0] of one cube cell (Section 2.1) as exact
+// products of small integer tables with fixed-point digit slices of the FP64 inputs: the
+// arithmetic of a tensor-core form of the outer operator, as plain functions that a host program
+// can run cell by cell.
+//
+// On a cube cell of side h with cell viscosity mu_c the element blocks are A = mu_c h A_ref,
+// B = -h^2 R and B^T = -h^2 R^T (A_ref the mu = h = 1 velocity operator, R the moments
+// int d_c(phi_m) psi_v on the reference cell). 5400 A_ref and 216 R are integer matrices (exact
+// integration of the Q2 and Q1 polynomials; at most 6 significant bits and magnitude <= 2^15), so
+//   y_u = (mu_c h / 5400) K_X x,   x = [u; (25 h / mu_c) p],   K_X = [5400 A_ref | -216 R^T],
+//   y_p = (h^2 / 216) K_U u,                                  K_U = -216 R.
+// Each input vector of a cell (x, and u alone for y_p) is written in fixed point against its own
+// largest magnitude 2^E (|v| < 2^E): X = round(v 2^(54 - E)), |X| <= 2^54, then as 7 balanced
+// base-256 digits, X = sum_j d_j 256^j with d_j in [-128, 127]. One digit slice times a table row is
+// an integer below 78,464 * 2^7 < 2^24 in magnitude at every partial sum (78,464 is the largest row
+// absolute sum of K_X), so a product of f16 digits with the f16-exact table accumulated in FP32 is
+// exact in any order: D_j = K d_j exactly. The slices are recombined, V = sum_j 256^j D_j (up to
+// 2^72), in double-float, multiplied by the cell's scale, and written as the FP64 value
+// V s 2^(E - 54) with integer instructions only (GB300 runs FP64 instructions at 1/72 of the FP32
+// rate). Error against exact arithmetic: 2^-55 of the largest input per input, ~2^-46 of the
+// recombined value per output.
+#pragma once
+
+#include "df64.cuh"
+#include "q2_basis.cuh"
+
+namespace stk {
+namespace sliced {
+
+constexpr int kNu = 81;            // velocity DoFs of a cell (27 c + a)
+constexpr int kNp = 8;             // pressure DoFs of a cell
+constexpr int kNx = kNu + kNp;     // inputs of the y_u product
+constexpr int kDigits = 7;         // balanced base-256 digits of a 54-bit fixed-point value
+constexpr int kFrac = 54;          // X = round(v 2^(kFrac - E))
+constexpr double kScaleA = 5400.0; // 5400 A_ref is an integer matrix
+constexpr double kScaleB = 216.0;  // 216 R is an integer matrix
+
+// ---- the integer tables, built from the library's own reference-cell operators
+// Column k of K_X (k < 81: velocity DoF k; k >= 81: pressure vertex k - 81) into col[0..80];
+// column k of K_U (k < 81) into colp[0..7]. Values are the integers in double; entries that are
+// not integers to 1e-6 are reported through the return value (false).
+__host__ __device__ inline bool table_column(int k, double (&col)[kNu], double (&colp)[kNp]) {
+    for (int n = 0; n < kNu; ++n) col[n] = 0.0;
+    for (int v = 0; v < kNp; ++v) colp[v] = 0.0;
+    if (k < kNu) {
+        double u[3][27], w[3][27];
+        for (int c = 0; c < 3; ++c)
+            for (int a = 0; a < 27; ++a) u[c][a] = (27 * c + a == k) ? 1.0 : 0.0;
+        double ulin[81];
+        for (int c = 0; c < 3; ++c)
+            for (int a = 0; a < 27; ++a) ulin[27 * c + a] = u[c][a];
+        q2::cell_A(u, w);   // overwrites u
+        for (int n = 0; n < kNu; ++n) col[n] = kScaleA * w[n / 27][n % 27];
+        double r[kNp] = {0, 0, 0, 0, 0, 0, 0, 0};
+        q2::b_component<0>(ulin, r);
+        q2::b_component<1>(ulin + 27, r);
+        q2::b_component<2>(ulin + 54, r);
+        for (int v = 0; v < kNp; ++v) colp[v] = -kScaleB * r[v];
+    } else {
+        double p[kNp] = {0, 0, 0, 0, 0, 0, 0, 0};
+        p[k - kNu] = 1.0;
+        double out[kNu];
+        for (int n = 0; n < kNu; ++n) out[n] = 0.0;
+        q2::bt_component<0>(p, out);
+        q2::bt_component<1>(p, out + 27);
+        q2::bt_component<2>(p, out + 54);
+        for (int n = 0; n < kNu; ++n) col[n] = -kScaleB * out[n];
+    }
+    bool ok = true;
+    auto snap = [&ok](double& v) {
+        const double r = double((long long)(v < 0 ? v - 0.5 : v + 0.5));
+        if (v - r > 1e-6 || r - v > 1e-6) ok = false;
+        v = r;
+    };
+    for (int n = 0; n < kNu; ++n) snap(col[n]);
+    for (int v = 0; v < kNp; ++v) snap(colp[v]);
+    return ok;
+}
+
+// ---- fixed point and digits
+// Exponent of the binade of v (v = m 2^E with 1/2 <= |m| < 1, so |v| < 2^E); zero and FP64
+// subnormals give kNoExp (they read as 0 in fixed point).
+constexpr int kNoExp = -4096;
+__host__ __device__ __forceinline__ int binade(double v) {
+    const unsigned long long b = q2::dbl_bits(v);
+    const int e = int((b >> 52) & 0x7FFu);
+    return e == 0 ? kNoExp : e - 1022;
+}
+
+// X = round(v 2^(kFrac - E)) (ties away from zero) for |v| < 2^E, by integer instructions on the
+// bits of v: |X| <= 2^54.
+__host__ __device__ __forceinline__ long long to_fixed(double v, int E) {
+    const unsigned long long b = q2::dbl_bits(v);
+    const int e = int((b >> 52) & 0x7FFu);
+    if (e == 0) return 0;
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);   // |v| = m 2^(e - 1075)
+    const int r = 1075 - kFrac + E - e;   // right shift of m; >= -1 when |v| < 2^E
+    unsigned long long X;
+    if (r <= 0) X = m << (-r);
+    else if (r >= 64) X = 0;
+    else X = (m + (1ull << (r - 1))) >> r;
+    return (b >> 63) ? -(long long)X : (long long)X;
+}
+
+// X = sum_j d[j] 256^j, d[j] in [-128, 127] (balanced digits, lowest first) for |X| <= 2^55.
+__host__ __device__ __forceinline__ void digits(long long X, int (&d)[kDigits]) {
+#pragma unroll
+    for (int j = 0; j < kDigits; ++j) {
+        const int dj = int((signed char)(X & 0xFF));
+        d[j] = dj;
+        X = (X - dj) / 256;   // exact: X - dj is a multiple of 256
+    }
+}
+
+// ---- recombination of the slice products and the FP64 result
+// V = sum_j 256^j D[j] for integer-valued floats |D[j]| < 2^24, in double-float: Horner from the
+// top slice, each step an exact scaling by 256 and a two_sum into the high part.
+__host__ __device__ __forceinline__ q2::df64 combine(const float (&D)[kDigits]) {
+    float hi = D[kDigits - 1], lo = 0.0f;
+#pragma unroll
+    for (int j = kDigits - 2; j >= 0; --j) {
+        hi = q2::mul_f(hi, 256.0f);
+        lo = q2::mul_f(lo, 256.0f);
+        const float s = q2::add_f(hi, D[j]);
+        const float bb = q2::sub_f(s, hi);
+        const float e = q2::add_f(q2::sub_f(hi, q2::sub_f(s, bb)), q2::sub_f(D[j], bb));
+        const q2::df64 r = q2::fast_two_sum(s, q2::add_f(lo, e));
+        hi = r.hi;
+        lo = r.lo;
+    }
+    return q2::df64(hi, lo);
+}
+
+__host__ __device__ __forceinline__ int clz64(unsigned long long x) {
+#ifdef __CUDA_ARCH__
+    return __clzll((long long)x);
+#else
+    return __builtin_clzll(x);
+#endif
+}
+__host__ __device__ __forceinline__ unsigned flt_bits(float f) {
+#ifdef __CUDA_ARCH__
+    return __float_as_uint(f);
+#else
+    unsigned u;
+    __builtin_memcpy(&u, &f, sizeof u);
+    return u;
+#endif
+}
+__host__ __device__ __forceinline__ double dbl_from_bits(unsigned long long b) {
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)b);
+#else
+    double d;
+    __builtin_memcpy(&d, &b, sizeof d);
+    return d;
+#endif
+}
+
+// The FP64 value (double(v.hi) + double(v.lo)) 2^shift rounded to nearest even, as FP64 arithmetic
+// would give it, with integer instructions: v.hi's 24-bit significand and v.lo aligned below it in
+// a 64-bit integer with 8 guard bits and a sticky bit, one add, one rounding. Needs a normalised
+// pair (|v.lo| <= ulp(v.hi) / 2, as fast_two_sum leaves it); zero, subnormal floats and results
+// outside the normal FP64 range take the FP64 instructions instead.
+__host__ __device__ __forceinline__ double compose(q2::df64 v, int shift) {
+    const unsigned bh = flt_bits(v.hi), bl = flt_bits(v.lo);
+    const int eh = int((bh >> 23) & 0xFFu), el = int((bl >> 23) & 0xFFu);
+    constexpr int G = 8;
+    if (eh != 0 && eh != 255 && el != 255 && (el != 0 || (bl & 0x7FFFFFFFu) == 0)) {
+        const unsigned long long H = (unsigned long long)((bh & 0x7FFFFFu) | 0x800000u) << (29 + G);
+        unsigned long long L = 0;
+        if (el != 0) {
+            const unsigned long long ml = (bl & 0x7FFFFFu) | 0x800000u;
+            const int s = el - eh + 29 + G;   // lo's significand position in H's units
+            if (s >= 0) L = ml << s;   // s <= G + 5: |lo| <= ulp(hi) / 2
+            else if (s > -64) L = (ml >> (-s)) | ((ml & ((1ull << (-s)) - 1)) != 0 ? 1ull : 0ull);
+            else L = 1;   // sticky only
+        }
+        const bool same = ((bh ^ bl) >> 31) == 0 || L == 0;
+        const unsigned long long S = same ? H + L : H - L;   // > 0: |lo| < |hi|
+        const int nb = 64 - clz64(S);                         // 60..62 bits
+        const int r = nb - 53;                                // >= 7
+        unsigned long long q = S >> r;
+        const unsigned long long rem = S & ((1ull << r) - 1), half = 1ull << (r - 1);
+        if (rem > half || (rem == half && (q & 1))) ++q;
+        int ebias = eh - 127 - 52 - G + r + 52 + 1023 + shift;   // biased exponent of q's leading bit
+        if (q == (1ull << 53)) {
+            q >>= 1;
+            ++ebias;
+        }
+        if (ebias >= 1 && ebias <= 2046)
+            return dbl_from_bits((unsigned long long)(bh >> 31) << 63 | (unsigned long long)ebias << 52 |
+                                 (q & 0xFFFFFFFFFFFFFull));
+    }
+    // rare: zero, subnormal or non-finite parts, or a result outside the normal range
+    double r = double(v.hi) + double(v.lo);
+    if (r == 0.0) return r;
+    while (shift > 0) { const int s = shift > 1000 ? 1000 : shift; r *= dbl_from_bits((unsigned long long)(1023 + s) << 52); shift -= s; }
+    while (shift < 0) { const int s = -shift > 1000 ? 1000 : -shift; r *= dbl_from_bits((unsigned long long)(1023 - s) << 52); shift += s; }
+    return r;
+}
+
+}  // namespace sliced
+}  // namespace stk
