@@ -9,16 +9,17 @@
 // integration of the Q2 and Q1 polynomials; at most 6 significant bits and magnitude <= 2^15), so
 //   y_u = (mu_c h / 5400) K_X x,   x = [u; (25 h / mu_c) p],   K_X = [5400 A_ref | -216 R^T],
 //   y_p = (h^2 / 216) K_U u,                                  K_U = -216 R.
-// Each input vector of a cell (x, and u alone for y_p) is written in fixed point against its own
-// largest magnitude 2^E (|v| < 2^E): X = round(v 2^(54 - E)), |X| <= 2^54, then as 7 balanced
-// base-256 digits, X = sum_j d_j 256^j with d_j in [-128, 127]. One digit slice times a table row is
-// an integer below 78,464 * 2^7 < 2^24 in magnitude at every partial sum (78,464 is the largest row
-// absolute sum of K_X), so a product of f16 digits with the f16-exact table accumulated in FP32 is
-// exact in any order: D_j = K d_j exactly. The slices are recombined, V = sum_j 256^j D_j (up to
-// 2^72), in double-float, multiplied by the cell's scale, and written as the FP64 value
-// V s 2^(E - 54) with integer instructions only (GB300 runs FP64 instructions at 1/72 of the FP32
-// rate). Error against exact arithmetic: 2^-55 of the largest input per input, ~2^-46 of the
-// recombined value per output.
+// The 89 inputs x of a cell are written in fixed point against their largest magnitude 2^E
+// (|v| < 2^E): X = round(v 2^(54 - E)), |X| <= 2^54, then as 7 balanced base-256 digits,
+// X = sum_j d_j 256^j with d_j in [-128, 127]. One digit slice times a row of K = [K_X; K_U 0] is an
+// integer below 78,464 * 2^7 < 2^24 in magnitude at every partial sum (78,464 is the largest row
+// absolute sum), so a product of f16 digits with the f16-exact table accumulated in FP32 is exact
+// in any order: D_j = K d_j exactly. The slices are recombined, V = sum_j 256^j D_j (up to 2^72),
+// in double-float, multiplied by the cell's scale, and written as the FP64 value V s 2^(E - 54)
+// with integer instructions only (GB300 runs FP64 instructions at 1/72 of the FP32 rate). The
+// pressure rows see u against x's exponent; a cell where (25 h / mu_c) p exceeds u by more than
+// 2^8 forms its B u with double-float moments instead. Error against exact arithmetic: 2^-55 of
+// the largest input per input, ~2^-46 of the recombined value per output.
 #pragma once
 
 #include "df64.cuh"
@@ -113,22 +114,37 @@ __host__ __device__ __forceinline__ void digits(long long X, int (&d)[kDigits]) 
 }
 
 // ---- recombination of the slice products and the FP64 result
-// V = sum_j 256^j D[j] for integer-valued floats |D[j]| < 2^24, in double-float: Horner from the
-// top slice, each step an exact scaling by 256 and a two_sum into the high part.
-__host__ __device__ __forceinline__ q2::df64 combine(const float (&D)[kDigits]) {
-    float hi = D[kDigits - 1], lo = 0.0f;
-#pragma unroll
-    for (int j = kDigits - 2; j >= 0; --j) {
-        hi = q2::mul_f(hi, 256.0f);
-        lo = q2::mul_f(lo, 256.0f);
-        const float s = q2::add_f(hi, D[j]);
-        const float bb = q2::sub_f(s, hi);
-        const float e = q2::add_f(q2::sub_f(hi, q2::sub_f(s, bb)), q2::sub_f(D[j], bb));
-        const q2::df64 r = q2::fast_two_sum(s, q2::add_f(lo, e));
-        hi = r.hi;
-        lo = r.lo;
+// The slice products arrive lowest digit first. acc <- acc 2^-8 + D (exact scaling, then a two_sum
+// of D into the high part), starting from acc = D[0]; after the 7 slices acc = V 2^-48 with
+// V = sum_j 256^j D[j]. D integer-valued, |D| < 2^24.
+__host__ __device__ __forceinline__ void slice_step(q2::df64& acc, float D, bool first) {
+    if (first) {
+        acc = q2::df64(D, 0.0f);
+        return;
     }
-    return q2::df64(hi, lo);
+    const float hi = q2::mul_f(acc.hi, 0.00390625f), lo = q2::mul_f(acc.lo, 0.00390625f);
+    const float s = q2::add_f(hi, D);
+    const float bb = q2::sub_f(s, hi);
+    const float e = q2::add_f(q2::sub_f(hi, q2::sub_f(s, bb)), q2::sub_f(D, bb));
+    acc = q2::fast_two_sum(s, q2::add_f(lo, e));
+}
+constexpr int kCombineShift = 48;   // combine() returns V 2^-48
+__host__ __device__ __forceinline__ q2::df64 combine(const float (&D)[kDigits]) {
+    q2::df64 acc;
+#pragma unroll
+    for (int j = 0; j < kDigits; ++j) slice_step(acc, D[j], j == 0);
+    return acc;
+}
+
+// The pressure rows take u's digits against the exponent of the whole input x; when x's largest
+// magnitude exceeds u's by more than 2^kMaxGap, the cell's B u is formed from u directly with the
+// sum-factorised double-float moments (R u, without the factor -h^2).
+constexpr int kMaxGap = 8;
+__host__ __device__ __forceinline__ void bu_moments(const q2::df64 (&u)[kNu], q2::df64 (&out)[kNp]) {
+    for (int v = 0; v < kNp; ++v) out[v] = q2::df64();
+    q2::b_component<0>(u, out);
+    q2::b_component<1>(u + 27, out);
+    q2::b_component<2>(u + 54, out);
 }
 
 __host__ __device__ __forceinline__ int clz64(unsigned long long x) {

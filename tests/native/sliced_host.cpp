@@ -42,8 +42,8 @@ extern "C" void compose_host(int count, const float* hi, const float* lo, const 
 }
 
 // D[j][n] = sum_k K[n][k] d[j][k] as exact integers (|partial sums| < 2^24 by the table bound).
-template <int N, int K>
-static void slice_products(const double* T, const int (&d)[K][kDigits], float (&D)[N][kDigits]) {
+template <int N, int K, int KD>
+static void slice_products(const double* T, const int (&d)[KD][kDigits], float (&D)[N][kDigits]) {
     for (int n = 0; n < N; ++n)
         for (int j = 0; j < kDigits; ++j) {
             long long s = 0;
@@ -79,24 +79,31 @@ extern "C" int sliced_apply_host(int n, const double* mu, const double* src_u, c
                     vtx[v] = size_t(ci + (v & 1)) + size_t(P) * (cj + ((v >> 1) & 1) + size_t(P) * (ck + (v >> 2)));
                     x[kNu + v] = ps * src_p[vtx[v]];
                 }
-                // the two digit sets: x against its largest magnitude (y_u), u against its own (y_p)
+                // one digit set against x's largest magnitude; the pressure rows of the same
+                // products, or the double-float moments where x exceeds u by more than 2^kMaxGap
                 int Ex = kNoExp, Eu = kNoExp;
                 for (int k = 0; k < kNx; ++k) {
                     const int b = binade(x[k]);
                     Ex = b > Ex ? b : Ex;
                     if (k < kNu) Eu = b > Eu ? b : Eu;
                 }
-                static int dx[kNx][kDigits], du[kNu][kDigits];
-                for (int k = 0; k < kNx; ++k) digits(Ex == kNoExp ? 0 : to_fixed(x[k], Ex), dx[k]);
-                for (int k = 0; k < kNu; ++k) digits(Eu == kNoExp ? 0 : to_fixed(x[k], Eu), du[k]);
+                if (Ex == kNoExp) continue;
+                static int dx[kNx][kDigits];
+                for (int k = 0; k < kNx; ++k) digits(to_fixed(x[k], Ex), dx[k]);
                 static float DX[kNu][kDigits], DU[kNp][kDigits];
                 slice_products<kNu, kNx>(KX, dx, DX);
-                slice_products<kNp, kNu>(KU, du, DU);
+                slice_products<kNp, kNu>(KU, dx, DU);   // the first 81 digit rows: u's
                 const q2::df64 sA = q2::split_double(m * h / kScaleA), sB = q2::split_double(h * h / kScaleB);
-                if (Ex != kNoExp)
-                    for (int r = 0; r < kNu; ++r) dst_u[dof[r]] += compose(combine(DX[r]) * sA, Ex - kFrac);
-                if (Eu != kNoExp)
-                    for (int v = 0; v < kNp; ++v) dst_p[vtx[v]] += compose(combine(DU[v]) * sB, Eu - kFrac);
+                const int shift = Ex - kFrac + kCombineShift;
+                for (int r = 0; r < kNu; ++r) dst_u[dof[r]] += compose(combine(DX[r]) * sA, shift);
+                if (Eu != kNoExp && Ex - Eu > kMaxGap) {
+                    q2::df64 ud[kNu], bu[kNp];
+                    for (int k = 0; k < kNu; ++k) ud[k] = q2::split_double(x[k]);
+                    bu_moments(ud, bu);
+                    for (int v = 0; v < kNp; ++v) dst_p[vtx[v]] += -h * h * bu[v].to_double();
+                } else {
+                    for (int v = 0; v < kNp; ++v) dst_p[vtx[v]] += compose(combine(DU[v]) * sB, shift);
+                }
             }
     for (int k = 0; k < M; ++k)
         for (int j = 0; j < M; ++j)
