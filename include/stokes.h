@@ -109,7 +109,15 @@ typedef struct {
                                    1 = double-float (pairs of floats, ~48-bit significand) on the FP32
                                    units for every block (default; GB300's FP64 rate is 1/72 of FP32: the
                                    Stokes block takes 0.83 vs 1.95 ms, B^T alone 0.15 vs 0.22 ms at
-                                   64^3). Both match the FP64 oracle to 1e-12. */
+                                   64^3). Both match the FP64 oracle to 1e-12.
+                                   2 = the whole operator [A B^T; B 0] of uniform meshes on the tensor
+                                   cores, exactly: each cell's FP64 inputs in fixed point against their
+                                   largest magnitude, split into 7 digit slices of 8 bits, times the
+                                   integer element table [[5400 A_ref, -216 R^T], [-216 R, 0]] (f16,
+                                   tcgen05.mma with FP32 accumulation, exact because every partial sum
+                                   is an integer below 2^24), recombined in double-float and written
+                                   as FP64 with integer instructions; every other block and the
+                                   Krylov basis as in 1. Not yet the default: its speed is unmeasured. */
     int vmult_kernel;           /* level operator of the V-cycle: 0 = one thread per cell with atomic adds
                                    and a separate epilogue pass (default); 1 = brick-tiled, atomic-free
                                    and deterministic, epilogue fused; 2 = FP32 levels: the brick-tiled

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libstokes_gb300.so")
 DEBUG_LIB = os.path.join(HERE, "libstokes_gb300_debug.so")
-SOURCES = ["ops.cu", "vec.cu", "krylov.cu", "brick.cu", "brick_tc.cu", "batch.cu", "outer.cu", "octree.cu",
+SOURCES = ["ops.cu", "vec.cu", "krylov.cu", "brick.cu", "brick_tc.cu", "batch.cu", "outer.cu", "outer_tc.cu", "octree.cu",
            "octree_host.cpp", "api.cu", "noalloc.cu", "probe.cu"]
 DEBUG_SOURCES = ["octree.cu", "api.cu"]   # the only sources that test STOKES_DEBUG
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -224,6 +224,7 @@ struct stokes_ctx {
     // tensor-core level operator: f16 table of 5400 A_hat; device status word (bit 0: a bounded
     // wait inside a kernel gave up), checked by stokes_device_status and at the end of a solve
     void* tc_table = nullptr;
+    void* outer_tc_table = nullptr;   // outer_arith 2: the f16 integer element table
     unsigned* dev_status = nullptr;
     TcArgs tc{};
 };
@@ -658,9 +659,16 @@ stokes_status apply_stokes(stokes_ctx* c, const double* src, double* dst, cudaSt
         return STOKES_OK;
     }
     Level& F = c->lev[c->L - 1];
+    if (!native && c->opt.outer_arith == 2 && c->outer_tc_table) {   // exact digit slices on the tensor cores
+        CK(cudaMemsetAsync(dst, 0, (F.g.n_u + F.g.n_p) * sizeof(double), s));
+        CK(launch_outer_tc(F.g, F.v64.mu, src, src + F.g.n_u, dst, dst + F.g.n_u, c->outer_tc_table, c->tc.status,
+                           c->tc.wait_ns, s));
+        CK(launch_copy_boundary<double>(F.g, src, dst, s));   // identity rows
+        return STOKES_OK;
+    }
     if (native) prof_override(PROF_RESID_F64);
     const cudaError_t e = launch_stokes_blocks(F.g, F.v64.mu, src, src + F.g.n_u, dst, dst + F.g.n_u, true, true,
-                                               true, c->opt.outer_arith == 1 && !native, s);
+                                               true, c->opt.outer_arith >= 1 && !native, s);
     prof_override(-1);
     CK(e);
     return STOKES_OK;
@@ -691,7 +699,7 @@ stokes_status precondition(stokes_ctx* c, int prec, const double* r, double* z, 
     if (c->opt.precond_kind != 1) {
         CK(launch_axpby(np, -1.0, zp, 0.0, zp, s));                           // z_p = -S^-1 r_p
         CK(launch_stokes_blocks(F.g, F.v64.mu, nullptr, zp, c->tu, nullptr, false, true, false,
-                                c->opt.outer_arith == 1, s));
+                                c->opt.outer_arith >= 1, s));
         CK(launch_axpby(nu, 1.0, r, -1.0, c->tu, s));                        // t = r_u - B^T z_p
     }   // else P_D: z_p = S_hat^-1 r_p, z_u = A_hat^-1 r_u
     if (prec == STOKES_FP64) return vcycle<double>(c, rin, z, s);
@@ -831,7 +839,7 @@ stokes_status fgmres_enqueue(FgmresRun& r) {
                 CK(cudaMemcpyAsync(c->dots_host, c->hdev, size_t(3 * (m + 4)) * sizeof(double), cudaMemcpyDeviceToHost, s));
                 return STOKES_OK;
             }
-            const bool df = c->opt.outer_arith == 1 && m <= gs_max_k();   // V as double-float pairs (krylov.cu)
+            const bool df = c->opt.outer_arith >= 1 && m <= gs_max_k();   // V as double-float pairs (krylov.cu)
             if (r.batch_stage == 1) {
                 CKS(fgmres_resume_after_levels(r));
             } else if (df) {
@@ -886,7 +894,7 @@ stokes_status fgmres_update_x(FgmresRun& r, int k) {
         CK(cudaMemcpyAsync(c->hdev, r.y.data(), size_t(k) * sizeof(double), cudaMemcpyHostToDevice, r.s));
         CK(launch_multiaxpy(N, k, c->Z, N, c->hdev, r.x, 1.0, r.s));
     } else {
-        const bool df = c->opt.outer_arith == 1 && r.m <= gs_max_k();
+        const bool df = c->opt.outer_arith >= 1 && r.m <= gs_max_k();
         CK(cudaMemsetAsync(c->w, 0, N * sizeof(double), r.s));
         if (df) {
             for (int i = 0; i < k; ++i) r.y[i] = -r.y[i];
@@ -1023,7 +1031,7 @@ stokes_status fgmres_init(FgmresRun& r, stokes_ctx* c, int prec, const double* b
     r.info = info;
     r.m = c->opt.restart;
     r.flexible = c->opt.outer_solver != 2;
-    r.lag = r.flexible && c->opt.gram_schmidt == 1 && c->opt.outer_arith == 1 && r.m <= gs_max_k();
+    r.lag = r.flexible && c->opt.gram_schmidt == 1 && c->opt.outer_arith >= 1 && r.m <= gs_max_k();
     r.H.assign(size_t(r.m + 1) * r.m, 0.0);
     r.cs.assign(r.m, 0.0);
     r.sn.assign(r.m, 0.0);
@@ -1553,13 +1561,26 @@ stokes_status validate_mu(const stokes_mu* mu, size_t cells) {
     return fail(STOKES_EINVAL, "unknown viscosity kind");
 }
 
-// The context's device status word, and for vmult_kernel 2 the tensor-core operator's f16 table
-// (5400 A_hat from the library's own sum-factorised cell operator, checked to be exact in f16).
+// The context's device status word, for outer_arith 2 the outer operator's f16 integer element
+// table, and for vmult_kernel 2 the tensor-core level operator's f16 table (5400 A_hat from the
+// library's own sum-factorised cell operator); both checked to be exact in f16.
 stokes_status setup_device_status(stokes_ctx* c, cudaStream_t s) {
     CKS(dalloc(c, &c->dev_status, kStatusWords));
     CK(cudaMemsetAsync(c->dev_status, 0, kStatusWords * sizeof(unsigned), s));
     c->tc.status = c->dev_status;
     c->tc.wait_ns = (unsigned long long)(c->opt.wait_limit_s * 1e9);
+    if (c->opt.outer_arith == 2) {
+        unsigned char* table = nullptr;
+        int* flag = nullptr;
+        CKS(dalloc(c, &table, outer_tc_table_bytes()));
+        CKS(dalloc(c, &flag, 1));
+        CK(outer_tc_setup(table, flag, s));
+        int hflag = 0;
+        CK(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (hflag != 0) return fail(STOKES_ECUDA, "the integer element table is not exact in f16 (outer_arith 2)");
+        c->outer_tc_table = table;
+    }
     if (c->opt.vmult_kernel != 2) return STOKES_OK;
     CK(tc_configure());
     unsigned char* table = nullptr;
@@ -1609,7 +1630,7 @@ stokes_status debug_status(stokes_ctx* c, cudaStream_t s, stokes_status st) {
 
 stokes_status validate_options(const stokes_options& o) {
     if (o.cheb_degree < 1 || o.smoothing_range <= 1.0 || o.eig_safety <= 0.0 || o.lanczos_steps < 1 ||
-        o.schur_degree < 0 || o.restart < 1 || o.restart > 500 || (o.outer_arith != 0 && o.outer_arith != 1) ||
+        o.schur_degree < 0 || o.restart < 1 || o.restart > 500 || (o.outer_arith < 0 || o.outer_arith > 2) ||
         o.vmult_kernel < 0 || o.vmult_kernel > 3 || (o.graphs != 0 && o.graphs != 1) || !(o.wait_limit_s >= 0.0) ||
         (o.batch_vcycle != 0 && o.batch_vcycle != 1) || (o.fused_smoother != 0 && o.fused_smoother != 1) ||
         o.wait_limit_s > 1e6 ||
@@ -2423,10 +2444,10 @@ stokes_status stokes_vmult(stokes_ctx* c, int level, int block, int prec, const 
     double* dd = static_cast<double*>(dst);
     switch (block) {
         case STOKES_BLOCK_B:
-            CK(launch_stokes_blocks(Lv.g, Lv.v64.mu, sd, nullptr, nullptr, dd, false, false, true, c->opt.outer_arith == 1, s));
+            CK(launch_stokes_blocks(Lv.g, Lv.v64.mu, sd, nullptr, nullptr, dd, false, false, true, c->opt.outer_arith >= 1, s));
             return STOKES_OK;
         case STOKES_BLOCK_BT:
-            CK(launch_stokes_blocks(Lv.g, Lv.v64.mu, nullptr, sd, dd, nullptr, false, true, false, c->opt.outer_arith == 1, s));
+            CK(launch_stokes_blocks(Lv.g, Lv.v64.mu, nullptr, sd, dd, nullptr, false, true, false, c->opt.outer_arith >= 1, s));
             return STOKES_OK;
         case STOKES_BLOCK_MP:
             CK(launch_mass_p(Lv.g, Lv.v64.mu, sd, dd, s));

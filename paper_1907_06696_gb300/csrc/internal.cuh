@@ -42,6 +42,15 @@ cudaError_t launch_stokes_blocks(const LevelGeom& g, const double* mu, const dou
 // The same blocks in double-float arithmetic, one velocity component per thread (outer.cu).
 cudaError_t launch_outer_df64(const LevelGeom& g, const double* mu, const double* src_u, const double* src_p,
                               double* dst_u, double* dst_p, bool do_a, bool do_bt, bool do_b, cudaStream_t s);
+// The whole outer operator [A B^T; B 0] to FP64 accuracy on the tensor cores, by exact integer
+// products with fixed-point digit slices (outer_tc.cu; the caller clears dst_u and dst_p and copies
+// the constrained rows afterwards). outer_tc_setup builds the f16 table (outer_tc_table_bytes()
+// bytes) and sets the kernel's shared-memory size; flag != 0 afterwards if an entry is not exact.
+size_t outer_tc_table_bytes();
+cudaError_t outer_tc_setup(void* table, int* flag, cudaStream_t s);
+cudaError_t launch_outer_tc(const LevelGeom& g, const double* mu, const double* src_u, const double* src_p,
+                            double* dst_u, double* dst_p, const void* table, unsigned* status,
+                            unsigned long long wait_ns, cudaStream_t s);
 // dst = M_p src (weighted pressure mass, FP64).
 cudaError_t launch_mass_p(const LevelGeom& g, const double* mu, const double* src, double* dst, cudaStream_t s);
 // out = B^T p on the uniform mesh (velocity boundary nodes 0), gathered per node pair; no atomics
