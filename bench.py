@@ -81,6 +81,8 @@ def parse():
                     help="with --kernels: also 40 FGMRES iterations (Gram-Schmidt passes up to a 40-vector basis)")
     ap.add_argument("--vmult-kernel", type=int, default=None,
                     help="with --kernels: level operator (0 cell kernel, 1 brick, 2 tensor cores)")
+    ap.add_argument("--outer-arith", type=int, default=None,
+                    help="with --kernels: outer operator (0 native FP64, 1 double-float, 2 tensor-core digit slices)")
     return ap.parse_args()
 
 
@@ -694,6 +696,8 @@ def run_kernels(args):
     opt = capi.stokes_default_options()
     if args.vmult_kernel is not None:
         opt.vmult_kernel = args.vmult_kernel
+    if args.outer_arith is not None:
+        opt.outer_arith = args.outer_arith
     ctx = capi.stokes_setup_problem(prob, options=opt)
     n_u, n_p = ctx.n_u, ctx.n_p
     x = torch.rand(n_u, device="cuda", dtype=torch.float32)
