@@ -65,7 +65,8 @@ def test_null_arguments(lib):
 
 
 @pytest.mark.parametrize("field,value", [("outer_solver", 4), ("outer_solver", -1), ("idr_s", 9),
-                                         ("precond_kind", 2), ("outer_solver", 3)])
+                                         ("precond_kind", 2), ("outer_solver", 3), ("outer_arith", 3),
+                                         ("outer_arith", -1), ("vmult_kernel", 4), ("fused_smoother", 2)])
 def test_option_validation(lib, field, value):
     """Options are checked before any device work: out-of-range solvers, and MINRES (outer_solver 3)
     without the symmetric positive definite P_D (precond_kind 1), are EINVAL."""
