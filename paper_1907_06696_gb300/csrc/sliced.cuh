@@ -113,6 +113,20 @@ __host__ __device__ __forceinline__ void digits(long long X, int (&d)[kDigits]) 
     }
 }
 
+// The digits of X all at once: Y = X + 0x80808080808080 (>= 0, < 2^56 for |X| <= 2^54) has the
+// biased digits d_j + 128 as its bytes. For two values, the f16 bits of 1536 + d_j, packed (first
+// value in the low half): 1408 + byte lies in [1024, 2048), where f16 has unit spacing, so its bits
+// are 0x6400 + (1408 + byte - 1024) = 0x6580 + byte. One f16 subtraction of 1536 per pair gives the
+// digits exactly.
+constexpr long long kDigitBias = 0x80808080808080LL;
+__host__ __device__ __forceinline__ unsigned long long biased_digits(long long X) {
+    return (unsigned long long)(X + kDigitBias);
+}
+__host__ __device__ __forceinline__ unsigned digit_pair_f16(unsigned long long Y0, unsigned long long Y1, int j) {
+    const unsigned b0 = unsigned(Y0 >> (8 * j)) & 0xFFu, b1 = unsigned(Y1 >> (8 * j)) & 0xFFu;
+    return (b0 | (b1 << 16)) + 0x65806580u;
+}
+
 // ---- recombination of the slice products and the FP64 result
 // The slice products arrive lowest digit first. acc <- acc 2^-8 + D (exact scaling, then a two_sum
 // of D into the high part), starting from acc = D[0]; after the 7 slices acc = V 2^-48 with

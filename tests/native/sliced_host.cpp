@@ -30,6 +30,10 @@ extern "C" void digits_host(long long X, int* d) {
     digits(X, t);
     for (int j = 0; j < kDigits; ++j) d[j] = t[j];
 }
+extern "C" void digit_pairs_host(long long X0, long long X1, unsigned* bits) {   // bits[kDigits]
+    const unsigned long long Y0 = biased_digits(X0), Y1 = biased_digits(X1);
+    for (int j = 0; j < kDigits; ++j) bits[j] = digit_pair_f16(Y0, Y1, j);
+}
 extern "C" void combine_host(const float* D, float* hilo) {
     float t[kDigits];
     for (int j = 0; j < kDigits; ++j) t[j] = D[j];

@@ -44,6 +44,8 @@ def lib(tmp_path_factory):
     L.binade_host.argtypes = [C.c_double]
     L.digits_host.restype = None
     L.digits_host.argtypes = [C.c_longlong, C.c_void_p]
+    L.digit_pairs_host.restype = None
+    L.digit_pairs_host.argtypes = [C.c_longlong, C.c_longlong, C.c_void_p]
     L.combine_host.restype = None
     L.combine_host.argtypes = [C.c_void_p, C.c_void_p]
     L.compose_host.restype = None
@@ -120,6 +122,22 @@ def test_balanced_digits_reconstruct(lib):
         lib.digits_host(X, d.ctypes.data)
         assert all(-128 <= int(v) <= 127 for v in d)
         assert sum(int(d[j]) * 256 ** j for j in range(7)) == X
+
+
+def test_digit_pairs_as_f16_bits(lib):
+    """The packed f16 bits of 1536 + d_j for two values, minus 1536 in f16, are the balanced digits
+    of each (the same digits as the digit-by-digit extraction)."""
+    rng = np.random.default_rng(206)
+    xs = [int(x) for x in rng.integers(-(2 ** 54), 2 ** 54, 4000, dtype=np.int64)]
+    xs += [2 ** 54, -(2 ** 54), 0, -1, 1, 127, 128, -128, -129]
+    bits = np.empty(7, dtype=np.uint32)
+    d = np.empty(7, dtype=np.int32)
+    for X0, X1 in zip(xs[0::2], xs[1::2]):
+        lib.digit_pairs_host(X0, X1, bits.ctypes.data)
+        halves = bits.view(np.uint16).reshape(7, 2).view(np.float16).astype(np.float64) - 1536.0
+        for col, X in ((0, X0), (1, X1)):
+            lib.digits_host(X, d.ctypes.data)
+            assert np.array_equal(halves[:, col], d.astype(np.float64))
 
 
 def test_combine_is_accurate(lib):
