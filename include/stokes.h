@@ -152,7 +152,7 @@ typedef struct {
                                    carried by the recurrence and checked against b - K x (a drift
                                    restarts MINRES from x, at most 10 times). Not for batches. */
     int idr_s;                  /* shadow-space dimension of IDR(s), 1..8 (2) */
-    int gram_schmidt;           /* FGMRES orthogonalisation with the double-float basis (outer_arith 1,
+    int gram_schmidt;           /* FGMRES orthogonalisation with the double-float basis (outer_arith 1 or 2,
                                    restart <= 64): 1 = classical Gram-Schmidt twice with the second
                                    projection of each basis vector delayed into the next step, two
                                    passes over the basis per iteration (default: the FGMRES vector
