@@ -20,6 +20,12 @@
 // pressure rows see u against x's exponent; a cell where (25 h / mu_c) p exceeds u by more than
 // 2^8 forms its B u with double-float moments instead. Error against exact arithmetic: 2^-55 of
 // the largest input per input, ~2^-46 of the recombined value per output.
+// Splitting the inputs into fixed-point slices whose products a low-precision matrix unit forms
+// exactly is the error-free transformation of K. Ozaki, T. Ogita, S. Oishi and S. M. Rump, "Error-free
+// transformations of matrix multiplication by using fast routines of matrix multiplication and its
+// applications", Numer. Algorithms 59 (2012); here the element table is itself an integer matrix, so
+// only the inputs are split, and the slices are balanced base-256 digits of one 54-bit integer per
+// input.
 #pragma once
 
 #include "df64.cuh"
